@@ -1,0 +1,308 @@
+"""Benchmark of the correlator X-engine on one GB300 (or N replicas).
+
+One step = one whole integration through the public C ABI: xeng_push of the
+block [T][F][N] (decode + tensor-core correlation + packed triangle) and
+xeng_dump of the int32 triangle to a caller buffer.  Inputs are synthetic,
+generated on the device from a seed (shape and statistics of the workload
+named by --workload) and larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Metric: useful correlation TOPS, 8 real
+operations per complex multiply-accumulate, N(N+1)/2 baselines per channel.
+`--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (recipe attribute in synth, description)
+    "chime_full": ("CHIME_FULL", "full-CHIME-shaped: N=2048 inputs, 1024 channels, T=8192, sky+noise (rho 0.1, sigma 2.5)"),
+    "pathfinder_full": ("PATHFINDER_FULL", "full Pathfinder rate: N=256, 1024 channels, T=32768, sky+noise (rho 0.1, sigma 2.5)"),
+    "pathfinder_small": ("PATHFINDER_SMALL", "Pathfinder-shaped small: N=256, 8 channels, T=4096, uniform nibbles"),
+}
+METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)"
+
+
+def useful_ops(T, F, N):
+    return 8.0 * T * F * N * (N + 1) / 2
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                             parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max(r[2] for r in rows)}
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and all(v.strip().isdigit() for v in ids) and local_rank < len(ids):
+        return int(ids[local_rank])
+    return local_rank
+
+
+def cpu_oracle_sample(rec, T, F, N, out_dev=None):
+    """Time the oracle (as it stands) on a bounded sample; check the GPU output on it."""
+    import numpy as np
+    import oracle
+    nf = {2048: 1, 256: 8}.get(N, 1)
+    nf = min(nf, F)
+    host = rec.host(f0=0, nf=nf)
+    t0 = time.perf_counter()
+    want = oracle.correlate(host)
+    dt = time.perf_counter() - t0
+    ops = useful_ops(T, nf, N)
+    exact = None
+    if out_dev is not None:
+        got = out_dev[:nf].cpu().numpy().astype(np.int64)
+        exact = bool(np.array_equal(got, want))
+    return {"value": ops / dt / 1e12, "unit": "TOPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "channels 0..%d of the workload (all %d inputs, all %d samples), int64 oracle, %.1f s"
+                      % (nf - 1, N, T, dt)}, exact
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step correlates a bounded sample."""
+    import synth
+    import oracle
+    rec = getattr(synth, WORKLOADS[args.workload][0])
+    T, F, N = rec.T, rec.F, rec.N
+    if rank != 0:
+        return
+    # sample: channel 0, all inputs, the first Ts samples (about a second or two per step)
+    Ts = {2048: 512, 256: 8192}.get(N, T)
+    Ts = min(Ts, T)
+    host = rec.host(f0=0, nf=1, t0=0, nt=Ts)
+    for _ in range(args.warmup):
+        oracle.correlate(host)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.correlate(host)
+    dt = (time.perf_counter() - t0) / args.steps
+    ops = useful_ops(Ts, 1, N)
+    value = ops / dt / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded generator)",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
+                       "n_inputs": N, "n_freq": F, "t_integ": T, "step_sample": "channel 0, %d samples" % Ts},
+            "cpu_baseline": {"value": value, "unit": "TOPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "channel 0, all %d inputs, %d samples per step" % (N, Ts)},
+            "e2e": {"value": value, "unit": "TOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="xeng", choices=["xeng", "reference"])
+    ap.add_argument("--workload", default="chime_full", choices=sorted(WORKLOADS))
+    ap.add_argument("--engine", default="tensor", choices=["tensor", "dp4a"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import synth
+    import paper_1503_06202_gb300 as xe
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    rec = getattr(synth, WORKLOADS[args.workload][0])
+    T, F, N = rec.T, rec.F, rec.N
+    B = N * (N + 1) // 2
+    engine = xe.XENG_ENGINE_TENSOR if args.engine == "tensor" else xe.XENG_ENGINE_DP4A
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        block = rec.device(stream)
+        out = torch.empty((F, B, 2), dtype=torch.int32, device="cuda")
+    stream.synchronize()
+    eng = xe.XEngine(N, F, T, engine)
+
+    def step():
+        eng.push(block, T, stream)
+        eng.dump(out, stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    eng.set_profiling(True)
+    eng.stats(reset=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index_for(local_rank)) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    st = eng.stats(reset=True)
+    eng.set_profiling(False)
+    clocks = clk.summary()
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ops = useful_ops(T, F, N)
+    value = ops * world / (ms * 1e-3) / 1e12
+
+    # dominant kernel: the correlation launches, timed live over the timed region
+    peaks, peak_src = load_peaks()
+    corr_ms = st["correlate_ms"] / max(1, st["timed_correlate"])
+    launches_per_step = st["correlate_launches"] / args.steps
+    flops_per_launch = ops / launches_per_step
+    if args.engine == "tensor":
+        peak = 2.0 * peaks["bf16_tflops_sustained"]
+        peak_note = ("fp8 dense = 2 x %s sustained bf16 %.1f TFLOP/s (nominal fp8:bf16 = 4.5:2.25); "
+                     "sm_103a has no tcgen05 kind::i8" % (peak_src, peaks["bf16_tflops_sustained"]))
+        roof = {"bound": "tensor", "kernel": "correlate_tc_kernel", "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "traffic": None, "peak_note": peak_note}
+        roof["frac"] = roof["achieved"] / peak
+    else:
+        roof = {"bound": "alu", "kernel": "correlate_dp4a_kernel",
+                "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12, "peak": None, "unit": "TFLOP/s",
+                "traffic": None, "frac": None}
+    roof["avg_launch_ms"] = corr_ms
+    roof["decode_ms_per_step"] = st["decode_ms"] / args.steps
+
+    # end to end through the ABI with host buffers: H2D of the block, D2H of the triangle
+    e2e = None
+    if not args.no_e2e:
+        hblock = torch.empty((T, F, N), dtype=torch.uint8, pin_memory=True)
+        hblock.copy_(block)
+        hout = torch.empty((F, B, 2), dtype=torch.int32, pin_memory=True)
+        eng.push(hblock, T, stream)
+        eng.dump(hout, stream)  # warm: staging allocation
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            eng.push(hblock, T, stream)
+            eng.dump(hout, stream)  # returns once the triangle is in host memory
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ops * world / dt / 1e12, "unit": "TOPS", "h2d_bytes_per_step": T * F * N,
+               "d2h_bytes_per_step": F * B * 8, "ms_per_step": dt * 1e3}
+        del hblock, hout
+
+    cpu = None
+    exact = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, exact = cpu_oracle_sample(rec, T, F, N, out)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TOPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)" if args.engine == "tensor" else "int8->int32",
+                "data": "synthetic (seeded on-device generator)",
+                "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
+                           "n_inputs": N, "n_freq": F, "t_integ": T, "engine": args.engine,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
+                "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8,
+                "gpu_launches": int(st["launches"]), "roofline": roof, "clocks": clocks, "e2e": e2e,
+                "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,156 @@
+/*
+ * xeng.h -- C ABI of the GB300 correlator X-engine (libxeng.so).
+ *
+ * The operation (paper Sec. IV-C-1 "Full Correlation", cost in Eq. 1): for
+ * every frequency channel f and every input pair i <= j, integrate the
+ * visibility
+ *
+ *     V_ij(f) = sum_t x_i(t, f) * conj(x_j(t, f))
+ *
+ * over all N(N+1)/2 pairs (autocorrelations included) and over every sample
+ * pushed since the last dump.  Samples are 4+4-bit offset-encoded complex
+ * numbers (Sec. II-A and its footnote: each nibble stores value + 8, values
+ * in [-8, 7]); the high nibble is the real part, the low nibble the
+ * imaginary part.  The arithmetic is exact: results are bit-identical to an
+ * integer reference for every input.
+ *
+ * Layouts
+ *   block  uint8  [n_samples][n_freq][n_inputs]   (input index fastest)
+ *   out    int32  [n_freq][N(N+1)/2][2]           (Re, Im) pairs, per channel
+ *          the upper triangle row-major: pair (i, j), i <= j, sits at
+ *          i*N - i*(i-1)/2 + (j - i).
+ *
+ * Conventions
+ *   - Every entry point returns XENG_OK (0) or a negative XENG_ERR_* code
+ *     (xeng_dump returns the number of integrated samples on success); none
+ *     aborts or prints.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it asynchronously unless stated.
+ *   - Asynchronous CUDA faults and device-side wait time-outs are reported
+ *     as XENG_ERR_CUDA / XENG_ERR_TIMEOUT by the next call on the handle and
+ *     stay sticky for that handle.
+ *   - A handle is not thread-safe: one thread drives it at a time.
+ *   - The library owns all device state of a handle; the caller owns every
+ *     buffer passed in.
+ *   - The library needs an sm_103 (GB300-class) device; on anything else
+ *     xeng_create returns XENG_ERR_UNSUPPORTED.  There is no CPU fallback.
+ */
+#ifndef XENG_H
+#define XENG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XENG_API __attribute__((visibility("default")))
+
+/* Status codes. */
+#define XENG_OK               0
+#define XENG_ERR_ARG         -1  /* NULL handle/pointer or invalid value      */
+#define XENG_ERR_RANGE       -2  /* size outside the supported range          */
+#define XENG_ERR_OVERFLOW    -3  /* push would integrate more than t_integ    */
+#define XENG_ERR_NOMEM       -4  /* device allocation failed                  */
+#define XENG_ERR_CUDA        -5  /* a CUDA call or kernel failed              */
+#define XENG_ERR_TIMEOUT     -6  /* a device-side wait gave up (kernel status) */
+#define XENG_ERR_UNSUPPORTED -7  /* no usable sm_103 device                    */
+
+/* Limits.  t_integ <= 2^24 - 1 keeps every |Re|, |Im| <= 128 * t_integ below
+ * 2^31, so the int32 result of an integration cannot overflow (per sample
+ * Re lies in [-112, 128] and |Im| <= 120). */
+#define XENG_MAX_INPUTS   4096
+#define XENG_MAX_T_INTEG  16777215LL
+
+/* Correlation engines (both give identical bits). */
+#define XENG_ENGINE_TENSOR 0  /* decode to FP8 planes + tcgen05 tensor-core GEMM (default) */
+#define XENG_ENGINE_DP4A   1  /* plain CUDA-core kernel: int8 dp4a straight from the bytes  */
+
+typedef struct xeng_s *xeng_t;
+
+/*
+ * xeng_create -- make an X-engine for n_inputs inputs (N), n_freq channels
+ * (F) and integrations of at most t_integ samples.
+ *   Ranges: 1 <= N <= XENG_MAX_INPUTS, F >= 1, 1 <= t_integ <= XENG_MAX_T_INTEG
+ *   (else XENG_ERR_RANGE).  Allocates the device accumulators
+ *   (F * N(N+1)/2 * 8 bytes) and the tensor engine's decode buffer on the
+ *   current CUDA device (XENG_ERR_NOMEM on failure).  *out_handle is set only
+ *   on success.  Synchronous.
+ */
+XENG_API int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_handle);
+
+/*
+ * xeng_push -- integrate n_samples more samples (Sec. IV-C-1: integration).
+ *   block: [n_samples][F][N] bytes, device memory or host memory (host memory
+ *   is copied to the device on `stream` first; pinned host memory keeps the
+ *   copy asynchronous).  The caller keeps `block` unchanged until `stream`
+ *   has passed this call.  If samples already integrated + n_samples would
+ *   exceed t_integ the call returns XENG_ERR_OVERFLOW and changes nothing.
+ *   n_samples == 0 is a no-op.
+ */
+XENG_API int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream);
+
+/*
+ * xeng_dump -- write the integrated triangle and start a new integration.
+ *   out: [F][N(N+1)/2][2] int32, device or host memory.  With host memory
+ *   the call returns after the data is in `out`; with device memory it is
+ *   asynchronous on `stream`.  A dump with no samples integrated writes zeros.
+ *   Returns the number of samples integrated (>= 0) or an XENG_ERR_* code.
+ */
+XENG_API int64_t xeng_dump(xeng_t h, int32_t *out, void *stream);
+
+/* xeng_destroy -- free the handle and its device memory; NULL is a no-op.
+ * Synchronizes the device first. */
+XENG_API void xeng_destroy(xeng_t h);
+
+/* xeng_strerror -- static text for a status code. */
+XENG_API const char *xeng_strerror(int code);
+
+/*
+ * xeng_set_engine -- choose XENG_ENGINE_TENSOR or XENG_ENGINE_DP4A for the
+ *   following pushes (XENG_ERR_ARG for other values).  Both engines add into
+ *   the same int32 accumulators, so an integration may mix them.
+ */
+XENG_API int xeng_set_engine(xeng_t h, int32_t engine);
+
+/*
+ * xeng_decode -- the standalone nibble-unpack / offset-decode stage (Sec.
+ *   II-A footnote) as the tensor engine runs it: channels [f0, f0 + nf) and
+ *   samples [0, n_samples) of block [n_samples][F][N] (device memory) become
+ *   FP8 E4M3 codes of the integer values in
+ *     planes [nf][2][n_pad][t_pad]   (plane 0 = real parts, 1 = imaginary)
+ *   with n_pad = N rounded up to 128 and t_pad = n_samples rounded up to 128;
+ *   padding is written as code 0x00 (+0.0).  planes is device memory of
+ *   nf * 2 * n_pad * t_pad bytes.  Asynchronous on `stream`.
+ */
+XENG_API int xeng_decode(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t n_inputs,
+                         int32_t f0, int32_t nf, uint8_t *planes, void *stream);
+
+/* Launch and device-time counters of one handle (see xeng_set_profiling). */
+typedef struct {
+    int64_t launches;          /* kernels launched by this handle so far      */
+    int64_t decode_launches;   /* ... of which decode kernels                 */
+    int64_t correlate_launches;/* ... of which correlation kernels            */
+    double  decode_ms;         /* summed device time of timed decode launches */
+    double  correlate_ms;      /* summed device time of timed correlations    */
+    int64_t timed_decode;      /* decode launches included in decode_ms       */
+    int64_t timed_correlate;   /* correlation launches in correlate_ms        */
+} xeng_stats_t;
+
+/*
+ * xeng_set_profiling -- on != 0: bracket every kernel this handle launches
+ *   with CUDA events on its stream, so xeng_get_stats can report device
+ *   times per kernel kind.  Off by default.
+ */
+XENG_API int xeng_set_profiling(xeng_t h, int32_t on);
+
+/*
+ * xeng_get_stats -- copy the counters into *stats.  If reset != 0, zero them
+ *   afterwards.  Waits for the timed launches to finish.
+ */
+XENG_API int xeng_get_stats(xeng_t h, xeng_stats_t *stats, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XENG_H */

@@ -1,0 +1,420 @@
+// correlate_tc.cu -- Hermitian correlation on the 5th-generation tensor cores.
+//
+// Computes, for every channel of a group and every upper-triangle tile pair
+// (I <= J) of 128 x 128 inputs, the visibility block (paper Sec. IV-C-1, Eq. 1)
+//     V_ij = sum_t x_i(t) conj(x_j(t)),   i in tile I, j in tile J,
+// as a real GEMM on decoded planes a = Re x, b = Im x (K = samples):
+//     D[:, 0:128]   = A_a B_a^T + A_b B_b^T          = Re V
+//     D[:, 128:256] = A_a B_b^T - A_b B_a^T          = -Im V
+// issued per 32-sample K step as three tcgen05.mma (kind::f8f6f4, E4M3 x E4M3
+// -> f32 in TMEM):
+//     D[:, 0:256]  += A_a x [B_a ; B_b]^T      (N = 256, B_b follows B_a in smem)
+//     D[:, 0:128]  += A_b x B_b^T              (N = 128)
+//     D[:, 128:256]+= (-A_b) x B_a^T           (N = 128, A negated by the
+//                                               instruction descriptor)
+// Every product is an integer of magnitude <= 64 and every partial sum an
+// integer of magnitude <= 128 * 65536 = 2^23, so the f32 accumulation is exact
+// provided the tensor core adds without dropping bits below 2^24; the tests
+// check this against the integer oracle on adversarial inputs.
+//
+// Structure: persistent CTAs (one per SM), static round-robin over tiles,
+// channel-major so one channel's operands stay in L2 while its tiles run.
+//   warp 0      TMA producer: 128x128-byte SWIZZLE_128B boxes of the planes
+//   warp 1      TMEM allocator and single-thread MMA issuer
+//   warps 2..5  epilogue: tcgen05.ld -> int32 -> packed triangle in HBM
+// Smem ring of 3 stages x 64 KB (A_a, A_b, B_a, B_b of a 128-sample chunk;
+// diagonal tiles load only A and reuse it as B).  Two 256-column TMEM
+// accumulators let the epilogue of one tile overlap the MMAs of the next.
+// Every wait is bounded: on time-out the thread records a status in the
+// error word, the others see it and leave their loops, the MMA thread drains
+// its tensor-core work and TMEM is freed before the CTA exits.
+#include "xeng_internal.h"
+
+namespace xeng {
+namespace {
+
+constexpr int kStages = 3;
+constexpr int kPlaneTile = kTile * kTile;     // 16 KB: 128 rows x 128 bytes
+constexpr int kStageBytes = 4 * kPlaneTile;   // A_a, A_b, B_a, B_b
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kNumBars = 2 * kStages + 5;     // full, empty, acc_full x2, acc_empty x2, drain
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + kNumBars * 8 + 16;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B E4M3
+// (formats 0), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28,
+// bit 13 negates A.
+__host__ __device__ constexpr uint32_t make_idesc(int n, bool neg_a)
+{
+    return (1u << 4) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+constexpr uint32_t kIdescN256 = make_idesc(256, false);
+constexpr uint32_t kIdescN128 = make_idesc(128, false);
+constexpr uint32_t kIdescN128Neg = make_idesc(128, true);
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
+// bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.  Returns
+// false if the error word is set by someone else or if the limit passes
+// (then this thread sets it to `code`).
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*(volatile int *)err != 0) return false;
+            if (globaltimer() - t0 > kWaitLimitNs) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Upper-triangle tile pair number r (row-major over I <= J) of an nt x nt grid.
+__device__ __forceinline__ void tile_pair(int r, int nt, int &I, int &J)
+{
+    int i = 0;
+    while (r >= nt - i) {
+        r -= nt - i;
+        ++i;
+    }
+    I = i;
+    J = i + r;
+}
+
+struct Sched {
+    int nt, tiles_per_ch, n_tiles;
+    __device__ __forceinline__ void decode(int tile, int &fl, int &I, int &J) const
+    {
+        fl = tile / tiles_per_ch;
+        tile_pair(tile - fl * tiles_per_ch, nt, I, J);
+    }
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, const Sched sc, const int n_k)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    const uint32_t bars = sbase + kStages * kStageBytes;
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (kStages + s); };
+    auto accf_bar = [&](int b) { return bars + 8u * (2 * kStages + b); };
+    auto acce_bar = [&](int b) { return bars + 8u * (2 * kStages + 2 + b); };
+    const uint32_t drain_bar = bars + 8u * (2 * kStages + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * kNumBars - raw));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *err = a.err;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 128);
+        }
+        mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < sc.n_tiles; tile += gridDim.x) {
+                int fl, I, J;
+                sc.decode(tile, fl, I, J);
+                const bool diag = (I == J);
+                const int rowA = fl * 2 * a.n_pad + I * kTile;
+                const int rowB = fl * 2 * a.n_pad + J * kTile;
+                for (int kc = 0; kc < n_k; kc++) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + stage * kStageBytes;
+                    mbar_expect_tx(full_bar(stage), diag ? 2 * kPlaneTile : 4 * kPlaneTile);
+                    tma_load_2d(st, &tmap, kc * kTile, rowA, full_bar(stage));
+                    tma_load_2d(st + kPlaneTile, &tmap, kc * kTile, rowA + a.n_pad, full_bar(stage));
+                    if (!diag) {
+                        tma_load_2d(st + 2 * kPlaneTile, &tmap, kc * kTile, rowB, full_bar(stage));
+                        tma_load_2d(st + 3 * kPlaneTile, &tmap, kc * kTile, rowB + a.n_pad, full_bar(stage));
+                    }
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the copies already issued land before the CTA can exit.
+                for (int k = 1; k <= kStages && k <= issued; k++) {
+                    int s = stage - k, p = (int)phase;
+                    if (s < 0) { s += kStages; p ^= 1; }
+                    (void)mbar_wait(full_bar(s), (uint32_t)p, err, kDevTimeoutProducer);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t uses[2] = {0, 0};
+            bool ok = true;
+            int local = 0;
+            for (int tile = blockIdx.x; ok && tile < sc.n_tiles; tile += gridDim.x, ++local) {
+                int fl, I, J;
+                sc.decode(tile, fl, I, J);
+                const bool diag = (I == J);
+                const int ab = local & 1;
+                if (!mbar_wait(acce_bar(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma)) break;
+                ++uses[ab];
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)ab * 256u;
+                for (int kc = 0; kc < n_k; kc++) {
+                    if (!mbar_wait(full_bar(stage), phase, err, kDevTimeoutMma)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t st = sbase + stage * kStageBytes;
+                    const uint32_t a_re = st, a_im = st + kPlaneTile;
+                    const uint32_t b_re = diag ? a_re : st + 2 * kPlaneTile;
+                    const uint32_t b_im = b_re + kPlaneTile;
+                    #pragma unroll
+                    for (int kk = 0; kk < 4; kk++) {
+                        const uint32_t off = kk * 32;
+                        mma_f8(d, sw128_desc(a_re + off), sw128_desc(b_re + off), kIdescN256, (kc | kk) != 0);
+                        mma_f8(d, sw128_desc(a_im + off), sw128_desc(b_im + off), kIdescN128, 1u);
+                        mma_f8(d + 128u, sw128_desc(a_im + off), sw128_desc(b_re + off), kIdescN128Neg, 1u);
+                    }
+                    mma_commit(empty_bar(stage));
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(accf_bar(ab));
+            }
+            // Drain: every MMA issued above has finished once this completes.
+            mma_commit(drain_bar);
+            (void)mbar_wait(drain_bar, 0u, err, kDevTimeoutMma);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row = q * 32 + lane;
+        uint32_t uses[2] = {0, 0};
+        int local = 0;
+        const int64_t N = a.N;
+        const int64_t nb2 = N * (N + 1);  // int32 words per channel (2 per baseline)
+        for (int tile = blockIdx.x; tile < sc.n_tiles; tile += gridDim.x, ++local) {
+            int fl, I, J;
+            sc.decode(tile, fl, I, J);
+            const int ab = local & 1;
+            const bool ok = mbar_wait(accf_bar(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue);
+            if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
+            ++uses[ab];
+            fence_after();
+            const int64_t i = (int64_t)I * kTile + row;
+            const bool row_ok = i < N;
+            // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle
+            const int64_t row_base = i * N - i * (i - 1) / 2 - i;
+            int2 *out = reinterpret_cast<int2 *>(a.acc + (int64_t)fl * nb2);
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u;
+            const int64_t jbase = (int64_t)J * kTile;
+            for (int c = 0; c < kTile; c += 16) {
+                uint32_t re[16], nim[16];
+                tmem_ld16(taddr + c, re);
+                tmem_ld16(taddr + 128 + c, nim);
+                tmem_ld_wait();
+                if (row_ok) {
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const int64_t j = jbase + c + e;
+                        if (j >= i && j < N) {
+                            const int vr = __float2int_rn(__uint_as_float(re[e]));
+                            const int vi = -__float2int_rn(__uint_as_float(nim[e]));
+                            int2 *p = out + row_base + j;
+                            if (a.accumulate) {
+                                int2 o = *p;
+                                *p = make_int2(o.x + vr, o.y + vi);
+                            } else {
+                                *p = make_int2(vr, vi);
+                            }
+                        }
+                    }
+                }
+            }
+            fence_before();
+            mbar_arrive(acce_bar(ab));
+        }
+    }
+
+    __syncwarp();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up through the runtime so the
+// library does not link libcuda directly (it then loads on hosts without a
+// driver, where only its exports are inspected).
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
+{
+    if (a.nf <= 0) return cudaSuccess;
+    if (a.t_pad % kTile != 0 || a.n_pad % kTile != 0 || a.t_pad > kMaxChunkSamples) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)a.t_pad, (cuuint64_t)a.nf * 2 * a.n_pad};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.t_pad};
+    const cuuint32_t box[2] = {kTile, kTile};
+    const cuuint32_t estr[2] = {1, 1};
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)a.planes, dims, strides,
+                                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(correlate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    Sched sc;
+    sc.nt = a.n_pad / kTile;
+    sc.tiles_per_ch = sc.nt * (sc.nt + 1) / 2;
+    sc.n_tiles = a.nf * sc.tiles_per_ch;
+    const int grid = sc.n_tiles < num_sms ? sc.n_tiles : num_sms;
+    correlate_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kTile));
+    return cudaGetLastError();
+}
+
+}  // namespace xeng

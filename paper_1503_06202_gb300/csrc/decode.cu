@@ -1,0 +1,139 @@
+// decode.cu -- nibble unpack and offset decode (paper Sec. II-A and its
+// footnote: each 4-bit nibble stores value + 8, values in [-8, 7]; high
+// nibble = real part, low nibble = imaginary part), producing the tensor
+// engine's operands.
+//
+// In:  block  [T][F][N] bytes (input index fastest).
+// Out: planes [nf][2][n_pad][t_pad] bytes: for channel f0 + fl, plane 0 holds
+//      the real parts and plane 1 the imaginary parts, one row per input,
+//      samples contiguous ("K-major" for the correlation GEMM), each value
+//      as its FP8 E4M3 code.  Integers -8..7 are exact in E4M3.  Rows i >= N
+//      and samples t >= T are written as +0.0.
+//
+// One CTA transposes and decodes a 128-sample x 128-input tile of one
+// channel: coalesced 16-byte loads into shared memory, then each thread
+// takes 4 inputs x 16 samples, transposes 4x4 byte blocks with byte permutes,
+// decodes through half precision (the nibble is placed in the mantissa of
+// 1024.0, so the half value is 1024 + u, minus 1032 gives u - 8 exactly) and
+// packs pairs to E4M3 with the hardware converter.  HBM-bound: 1 byte read,
+// 2 bytes written per (input, sample).
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include "xeng_internal.h"
+
+namespace xeng {
+namespace {
+
+constexpr int kDecThreads = 256;
+constexpr int kRowWords = 33;  // 128 bytes + 4 bytes of padding per sample row
+// Row t of the shared tile starts at word t * 33 + (t / 16) * 4: the extra
+// skew per 16-row group keeps the column reads of phase 2 conflict-free.
+__device__ __forceinline__ int row_word(int t) { return t * kRowWords + (t >> 4) * 4; }
+constexpr int kTileWords = 128 * kRowWords + 8 * 4;
+
+// Two offset nibbles (in bits 0-3 and 16-19 of x) to two E4M3 codes.
+__device__ __forceinline__ uint32_t nib2_to_e4m3(uint32_t x)
+{
+    __half2_raw h;
+    uint32_t v = (x & 0x000F000Fu) | 0x64006400u;  // half2(1024 + u_lo, 1024 + u_hi)
+    __half2 hv = *reinterpret_cast<__half2 *>(&v);
+    hv = __hsub2(hv, __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408)));  // - 1032
+    h = *reinterpret_cast<__half2_raw *>(&hv);
+    return (uint32_t)__nv_cvt_halfraw2_to_fp8x2(h, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Word of 4 samples (bytes = times t..t+3 of one input) -> (real codes, imag codes).
+__device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &im)
+{
+    uint32_t r02 = nib2_to_e4m3(c >> 4);   // high nibbles of bytes 0 and 2
+    uint32_t r13 = nib2_to_e4m3(c >> 12);  // high nibbles of bytes 1 and 3
+    uint32_t i02 = nib2_to_e4m3(c);        // low nibbles of bytes 0 and 2
+    uint32_t i13 = nib2_to_e4m3(c >> 8);   // low nibbles of bytes 1 and 3
+    re = __byte_perm(r02, r13, 0x5140);
+    im = __byte_perm(i02, i13, 0x5140);
+}
+
+__global__ void __launch_bounds__(kDecThreads)
+decode_kernel(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N, int32_t f0,
+              uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int vec_ok)
+{
+    __shared__ uint32_t tile[kTileWords];
+    const int tb = blockIdx.x, ib = blockIdx.y, fl = blockIdx.z;
+    const int64_t t0 = (int64_t)tb * 128;
+    const int i0 = ib * 128;
+    const int64_t f = f0 + fl;
+    const int tid = threadIdx.x;
+
+    // Phase 1: 128 rows x 8 chunks of 16 bytes; value 0x88 (0 + 0i) outside.
+    for (int ch = tid; ch < 128 * 8; ch += kDecThreads) {
+        const int t = ch >> 3, c = ch & 7;
+        const int64_t tt = t0 + t;
+        const int ic = i0 + c * 16;
+        uint32_t w[4];
+        if (tt < T && vec_ok && ic + 16 <= N) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(block + (tt * F + f) * N + ic);
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        } else {
+            for (int k = 0; k < 4; k++) {
+                uint32_t word = 0;
+                for (int b = 0; b < 4; b++) {
+                    const int i = ic + k * 4 + b;
+                    uint32_t byte = 0x88;
+                    if (tt < T && i < N) byte = block[(tt * F + f) * N + i];
+                    word |= byte << (8 * b);
+                }
+                w[k] = word;
+            }
+        }
+        uint32_t *dst = tile + row_word(t) + c * 4;
+        dst[0] = w[0]; dst[1] = w[1]; dst[2] = w[2]; dst[3] = w[3];
+    }
+    __syncthreads();
+
+    // Phase 2: thread = (input quad q, 16-sample block b).
+    const int b = tid & 7;    // lanes 0..7 of a row group write one 128-byte row segment
+    const int q = tid >> 3;   // 0..31
+    uint32_t re[4][4], im[4][4];  // [input k][word g] (word g = samples 4g..4g+3)
+    #pragma unroll
+    for (int g = 0; g < 4; g++) {
+        uint32_t r[4];
+        #pragma unroll
+        for (int k = 0; k < 4; k++) r[k] = tile[row_word(b * 16 + g * 4 + k) + q];
+        // 4x4 byte transpose: r[k] byte m = (time k, input m) -> c[m] byte k
+        const uint32_t lo01 = __byte_perm(r[0], r[1], 0x5140);
+        const uint32_t hi01 = __byte_perm(r[0], r[1], 0x7362);
+        const uint32_t lo23 = __byte_perm(r[2], r[3], 0x5140);
+        const uint32_t hi23 = __byte_perm(r[2], r[3], 0x7362);
+        const uint32_t c0 = __byte_perm(lo01, lo23, 0x5410);
+        const uint32_t c1 = __byte_perm(lo01, lo23, 0x7632);
+        const uint32_t c2 = __byte_perm(hi01, hi23, 0x5410);
+        const uint32_t c3 = __byte_perm(hi01, hi23, 0x7632);
+        decode_word(c0, re[0][g], im[0][g]);
+        decode_word(c1, re[1][g], im[1][g]);
+        decode_word(c2, re[2][g], im[2][g]);
+        decode_word(c3, re[3][g], im[3][g]);
+    }
+    const int64_t tcol = t0 + b * 16;
+    #pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int64_t i = i0 + q * 4 + k;
+        uint8_t *rowre = planes + ((int64_t)fl * 2 * n_pad + i) * t_pad + tcol;
+        uint8_t *rowim = planes + ((int64_t)fl * 2 * n_pad + n_pad + i) * t_pad + tcol;
+        *reinterpret_cast<uint4 *>(rowre) = make_uint4(re[k][0], re[k][1], re[k][2], re[k][3]);
+        *reinterpret_cast<uint4 *>(rowim) = make_uint4(im[k][0], im[k][1], im[k][2], im[k][3]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0,
+                          int32_t nf, uint8_t *planes, int64_t t_pad, int64_t n_pad, cudaStream_t s)
+{
+    if (nf <= 0 || t_pad <= 0) return cudaSuccess;
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(block) & 15) == 0) && (N % 16 == 0);
+    dim3 grid((unsigned)(t_pad / 128), (unsigned)(n_pad / 128), (unsigned)nf);
+    decode_kernel<<<grid, kDecThreads, 0, s>>>(block, T, F, N, f0, planes, t_pad, n_pad, vec_ok);
+    return cudaGetLastError();
+}
+
+}  // namespace xeng

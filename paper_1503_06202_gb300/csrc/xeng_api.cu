@@ -1,0 +1,363 @@
+// xeng_api.cu -- the C ABI (include/xeng.h): handle state, argument checks,
+// chunking of a push into decode + correlation launches, dumps and counters.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/xeng.h"
+#include "xeng_internal.h"
+
+using namespace xeng;
+
+struct TimedLaunch {
+    int kind;  // 0 = decode, 1 = correlate
+    cudaEvent_t start, stop;
+};
+
+struct xeng_s {
+    int32_t N = 0, F = 0;
+    int64_t t_integ = 0;
+    int32_t engine = XENG_ENGINE_TENSOR;
+    int device = 0;
+    int num_sms = 0;
+    int64_t samples = 0;   // integrated since the last dump
+    bool fresh = true;     // accumulators hold nothing yet: the next launch stores
+    int32_t *acc = nullptr;        // [F][N(N+1)/2][2]
+    uint8_t *planes = nullptr;     // decode buffer of the tensor engine
+    int64_t planes_bytes = 0;
+    int32_t group_f = 0;           // channels per decode + correlate round
+    int64_t chunk_t = 0;           // samples per round
+    uint8_t *staging = nullptr;    // device copy of host blocks
+    int64_t staging_bytes = 0;
+    int *d_err = nullptr;          // device status word of the kernels
+    int *h_err = nullptr;          // pinned mirror, refreshed after each push
+    int sticky = XENG_OK;
+    bool profiling = false;
+    xeng_stats_t stats{};
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+int64_t acc_bytes(const xeng_s *h) { return (int64_t)h->F * n_baselines(h->N) * 8; }
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return XENG_OK;
+    if (e == cudaErrorMemoryAllocation) return XENG_ERR_NOMEM;
+    return XENG_ERR_CUDA;
+}
+
+// Surface earlier asynchronous failures: sticky CUDA errors and the kernels'
+// device status word (its pinned mirror is written by completed work only).
+int check_sticky(xeng_s *h)
+{
+    if (h->sticky != XENG_OK) return h->sticky;
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->sticky = XENG_ERR_CUDA;
+        return h->sticky;
+    }
+    if (h->h_err && *(volatile int *)h->h_err != 0) {
+        h->sticky = XENG_ERR_TIMEOUT;
+        return h->sticky;
+    }
+    return XENG_OK;
+}
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t take_event(xeng_s *h)
+{
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Run one kernel launch, bracketed by events when profiling.
+template <class F>
+cudaError_t timed_launch(xeng_s *h, int kind, cudaStream_t s, F &&fn)
+{
+    TimedLaunch tl{kind, nullptr, nullptr};
+    if (h->profiling) {
+        tl.start = take_event(h);
+        tl.stop = take_event(h);
+        if (tl.start && tl.stop) cudaEventRecord(tl.start, s);
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess) return e;
+    h->stats.launches++;
+    if (kind == 0) h->stats.decode_launches++;
+    else h->stats.correlate_launches++;
+    if (h->profiling && tl.start && tl.stop) {
+        cudaEventRecord(tl.stop, s);
+        h->timed.push_back(tl);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *xeng_strerror(int code)
+{
+    switch (code) {
+    case XENG_OK: return "ok";
+    case XENG_ERR_ARG: return "invalid argument";
+    case XENG_ERR_RANGE: return "size outside the supported range";
+    case XENG_ERR_OVERFLOW: return "push would exceed the integration length";
+    case XENG_ERR_NOMEM: return "device allocation failed";
+    case XENG_ERR_CUDA: return "CUDA call or kernel failed";
+    case XENG_ERR_TIMEOUT: return "device-side wait timed out";
+    case XENG_ERR_UNSUPPORTED: return "no usable sm_103 device";
+    default: return "unknown status";
+    }
+}
+
+int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_handle)
+{
+    if (!out_handle) return XENG_ERR_ARG;
+    if (n_inputs < 1 || n_inputs > XENG_MAX_INPUTS || n_freq < 1 || t_integ < 1 || t_integ > XENG_MAX_T_INTEG)
+        return XENG_ERR_RANGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return XENG_ERR_UNSUPPORTED;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return XENG_ERR_UNSUPPORTED;
+    }
+    if (prop.major != 10 || prop.minor != 3) return XENG_ERR_UNSUPPORTED;
+
+    xeng_s *h = new (std::nothrow) xeng_s;
+    if (!h) return XENG_ERR_NOMEM;
+    h->N = n_inputs;
+    h->F = n_freq;
+    h->t_integ = t_integ;
+    h->device = dev;
+    h->num_sms = prop.multiProcessorCount;
+
+    // Decode buffer: rounds of (group_f channels x chunk_t samples); the
+    // budget bounds it at 16 GiB or a quarter of the free memory.
+    const int64_t n_pad = round_up(n_inputs, kTile);
+    h->chunk_t = round_up(t_integ < kMaxChunkSamples ? t_integ : kMaxChunkSamples, kTile);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    int64_t budget = (int64_t)16 << 30;
+    if ((int64_t)free_b / 4 < budget) budget = (int64_t)free_b / 4;
+    const int64_t per_ch = 2 * n_pad * h->chunk_t;
+    int64_t g = budget / per_ch;
+    if (g < 1) g = 1;
+    if (g > n_freq) g = n_freq;
+    if (g > 65535) g = 65535;
+    h->group_f = (int32_t)g;
+    h->planes_bytes = g * per_ch;
+
+    cudaError_t e = cudaMalloc(&h->acc, (size_t)acc_bytes(h));
+    if (e == cudaSuccess) e = cudaMalloc(&h->planes, (size_t)h->planes_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        xeng_destroy(h);
+        return e == cudaErrorMemoryAllocation ? XENG_ERR_NOMEM : XENG_ERR_CUDA;
+    }
+    *h->h_err = 0;
+    *out_handle = h;
+    return XENG_OK;
+}
+
+void xeng_destroy(xeng_t h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->acc);
+    cudaFree(h->planes);
+    cudaFree(h->staging);
+    cudaFree(h->d_err);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    for (auto &t : h->timed) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete h;
+}
+
+int xeng_set_engine(xeng_t h, int32_t engine)
+{
+    if (!h) return XENG_ERR_ARG;
+    if (engine != XENG_ENGINE_TENSOR && engine != XENG_ENGINE_DP4A) return XENG_ERR_ARG;
+    h->engine = engine;
+    return XENG_OK;
+}
+
+int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
+{
+    if (!h) return XENG_ERR_ARG;
+    if (n_samples < 0) return XENG_ERR_ARG;
+    if (n_samples > 0 && !block) return XENG_ERR_ARG;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
+    if (n_samples == 0) return XENG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->N, F = h->F;
+    const int64_t bytes = n_samples * F * N;
+
+    const uint8_t *dblock = block;
+    if (!is_device_pointer(block)) {
+        if (h->staging_bytes < bytes) {
+            cudaFree(h->staging);
+            h->staging = nullptr;
+            h->staging_bytes = 0;
+            if (cudaMalloc(&h->staging, (size_t)bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return XENG_ERR_NOMEM;
+            }
+            h->staging_bytes = bytes;
+        }
+        cudaError_t e = cudaMemcpyAsync(h->staging, block, (size_t)bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+        dblock = h->staging;
+    }
+
+    const int64_t n_pad = round_up(N, kTile);
+    const int64_t nb2 = N * (N + 1);
+    cudaError_t e = cudaSuccess;
+    if (h->engine == XENG_ENGINE_DP4A) {
+        e = timed_launch(h, 1, s, [&] {
+            return launch_correlate_dp4a(dblock, n_samples, (int32_t)F, (int32_t)N, h->acc, h->fresh ? 0 : 1, s);
+        });
+    } else {
+        for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
+            const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
+            const int64_t t_pad = round_up(nt, kTile);
+            const int accumulate = (h->fresh && t0 == 0) ? 0 : 1;
+            for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += h->group_f) {
+                const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
+                const uint8_t *src = dblock + t0 * F * N;
+                e = timed_launch(h, 0, s, [&] {
+                    return launch_decode(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes, t_pad, n_pad, s);
+                });
+                if (e != cudaSuccess) break;
+                TcArgs a;
+                a.planes = h->planes;
+                a.t_pad = t_pad;
+                a.n_pad = (int32_t)n_pad;
+                a.N = (int32_t)N;
+                a.nf = nf;
+                a.acc = h->acc + f0 * nb2;
+                a.accumulate = accumulate;
+                a.err = h->d_err;
+                e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+            }
+        }
+    }
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    h->samples += n_samples;
+    h->fresh = false;
+    return XENG_OK;
+}
+
+int64_t xeng_dump(xeng_t h, int32_t *out, void *stream)
+{
+    if (!h || !out) return XENG_ERR_ARG;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev_out = is_device_pointer(out);
+    const int64_t bytes = acc_bytes(h);
+    cudaError_t e;
+    if (h->fresh) {
+        if (dev_out) {
+            e = cudaMemsetAsync(out, 0, (size_t)bytes, s);
+        } else {
+            e = cudaStreamSynchronize(s);
+            memset(out, 0, (size_t)bytes);
+        }
+    } else {
+        e = cudaMemcpyAsync(out, h->acc, (size_t)bytes, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && !dev_out) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    if (!dev_out) {
+        st = check_sticky(h);
+        if (st != XENG_OK) return st;
+    }
+    const int64_t n = h->samples;
+    h->samples = 0;
+    h->fresh = true;
+    return n;
+}
+
+int xeng_decode(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t n_inputs, int32_t f0, int32_t nf,
+                uint8_t *planes, void *stream)
+{
+    if (!block || !planes) return XENG_ERR_ARG;
+    if (n_samples < 1 || n_inputs < 1 || n_inputs > XENG_MAX_INPUTS || n_freq < 1 || f0 < 0 || nf < 1 ||
+        f0 + nf > n_freq || nf > 65535 || n_samples > XENG_MAX_T_INTEG)
+        return XENG_ERR_RANGE;
+    if (!is_device_pointer(block) || !is_device_pointer(planes)) return XENG_ERR_ARG;
+    const int64_t t_pad = round_up(n_samples, kTile);
+    const int64_t n_pad = round_up(n_inputs, kTile);
+    if (t_pad / kTile > 2147483647LL) return XENG_ERR_RANGE;
+    cudaError_t e = launch_decode(block, n_samples, n_freq, n_inputs, f0, nf, planes, t_pad, n_pad,
+                                  (cudaStream_t)stream);
+    return cuda_status(e);
+}
+
+int xeng_set_profiling(xeng_t h, int32_t on)
+{
+    if (!h) return XENG_ERR_ARG;
+    h->profiling = on != 0;
+    return XENG_OK;
+}
+
+int xeng_get_stats(xeng_t h, xeng_stats_t *stats, int32_t reset)
+{
+    if (!h || !stats) return XENG_ERR_ARG;
+    for (auto &t : h->timed) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.stop) == cudaSuccess && cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+            if (t.kind == 0) {
+                h->stats.decode_ms += ms;
+                h->stats.timed_decode++;
+            } else {
+                h->stats.correlate_ms += ms;
+                h->stats.timed_correlate++;
+            }
+        }
+        h->event_pool.push_back(t.start);
+        h->event_pool.push_back(t.stop);
+    }
+    h->timed.clear();
+    *stats = h->stats;
+    if (reset) h->stats = xeng_stats_t{};
+    return check_sticky(h);
+}
+
+}  // extern "C"

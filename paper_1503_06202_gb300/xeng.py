@@ -1,0 +1,193 @@
+"""Python binding of libxeng.so (include/xeng.h): argument marshalling only.
+
+Every step of the correlation runs in the library's CUDA kernels; this module
+converts Python values, torch tensors (device memory, via data_ptr()) and
+numpy arrays (host memory) into the C ABI's pointers and sizes.  It raises if
+the compiled library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxeng.so")
+
+XENG_OK = 0
+XENG_ERR_ARG = -1
+XENG_ERR_RANGE = -2
+XENG_ERR_OVERFLOW = -3
+XENG_ERR_NOMEM = -4
+XENG_ERR_CUDA = -5
+XENG_ERR_TIMEOUT = -6
+XENG_ERR_UNSUPPORTED = -7
+XENG_MAX_INPUTS = 4096
+XENG_MAX_T_INTEG = 16777215
+XENG_ENGINE_TENSOR = 0
+XENG_ENGINE_DP4A = 1
+
+
+class XengStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("decode_launches", ctypes.c_int64),
+                ("correlate_launches", ctypes.c_int64), ("decode_ms", ctypes.c_double),
+                ("correlate_ms", ctypes.c_double), ("timed_decode", ctypes.c_int64),
+                ("timed_correlate", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class XengError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, xeng_strerror(code), code))
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libxeng.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libxeng.so is not built (run __graft_entry__.build()); no fallback exists")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.xeng_create.argtypes = [i32, i32, i64, ctypes.POINTER(vp)]
+        L.xeng_create.restype = ctypes.c_int
+        L.xeng_push.argtypes = [vp, vp, i64, vp]
+        L.xeng_push.restype = ctypes.c_int
+        L.xeng_dump.argtypes = [vp, vp, vp]
+        L.xeng_dump.restype = i64
+        L.xeng_destroy.argtypes = [vp]
+        L.xeng_destroy.restype = None
+        L.xeng_strerror.argtypes = [ctypes.c_int]
+        L.xeng_strerror.restype = ctypes.c_char_p
+        L.xeng_set_engine.argtypes = [vp, i32]
+        L.xeng_set_engine.restype = ctypes.c_int
+        L.xeng_decode.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp]
+        L.xeng_decode.restype = ctypes.c_int
+        L.xeng_set_profiling.argtypes = [vp, i32]
+        L.xeng_set_profiling.restype = ctypes.c_int
+        L.xeng_get_stats.argtypes = [vp, ctypes.POINTER(XengStats), i32]
+        L.xeng_get_stats.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor, numpy array or address, got %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def xeng_strerror(code: int) -> str:
+    return lib().xeng_strerror(code).decode()
+
+
+def xeng_create(n_inputs: int, n_freq: int, t_integ: int):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().xeng_create(n_inputs, n_freq, t_integ, ctypes.byref(h))
+    return rc, (h.value if rc == XENG_OK else None)
+
+
+def xeng_push(h, block, n_samples: int, stream=None) -> int:
+    return lib().xeng_push(h, _ptr(block), n_samples, _stream(stream))
+
+
+def xeng_dump(h, out, stream=None) -> int:
+    return lib().xeng_dump(h, _ptr(out), _stream(stream))
+
+
+def xeng_destroy(h) -> None:
+    lib().xeng_destroy(h)
+
+
+def xeng_set_engine(h, engine: int) -> int:
+    return lib().xeng_set_engine(h, engine)
+
+
+def xeng_decode(block, n_samples, n_freq, n_inputs, f0, nf, planes, stream=None) -> int:
+    return lib().xeng_decode(_ptr(block), n_samples, n_freq, n_inputs, f0, nf, _ptr(planes), _stream(stream))
+
+
+def xeng_set_profiling(h, on: bool) -> int:
+    return lib().xeng_set_profiling(h, 1 if on else 0)
+
+
+def xeng_get_stats(h, reset: bool = False):
+    """Returns (status, stats dict)."""
+    st = XengStats()
+    rc = lib().xeng_get_stats(h, ctypes.byref(st), 1 if reset else 0)
+    return rc, st.as_dict()
+
+
+class XEngine:
+    """Owning wrapper: create on construction, destroy on close()/__del__."""
+
+    def __init__(self, n_inputs: int, n_freq: int, t_integ: int, engine: int = XENG_ENGINE_TENSOR):
+        rc, h = xeng_create(n_inputs, n_freq, t_integ)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_create")
+        self.h = h
+        self.n_inputs, self.n_freq, self.t_integ = n_inputs, n_freq, t_integ
+        self.set_engine(engine)
+
+    @property
+    def n_baselines(self) -> int:
+        return self.n_inputs * (self.n_inputs + 1) // 2
+
+    def set_engine(self, engine: int) -> None:
+        rc = xeng_set_engine(self.h, engine)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_set_engine")
+
+    def push(self, block, n_samples: int | None = None, stream=None) -> None:
+        if n_samples is None:
+            n_samples = block.shape[0]
+        rc = xeng_push(self.h, block, n_samples, stream)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_push")
+
+    def dump(self, out, stream=None) -> int:
+        n = xeng_dump(self.h, out, stream)
+        if n < 0:
+            raise XengError(n, "xeng_dump")
+        return n
+
+    def set_profiling(self, on: bool) -> None:
+        xeng_set_profiling(self.h, on)
+
+    def stats(self, reset: bool = False) -> dict:
+        rc, s = xeng_get_stats(self.h, reset)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_get_stats")
+        return s
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            xeng_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, bit for bit.
+
+Integer results, so the bar is exact equality.  Small and ragged shapes are
+compared in full; the full-size workloads (in the launch configuration the
+benchmark times) on sampled outputs plus the beam-power identity on every
+channel (an exact fp64 computation on the GPU from the input bytes, which
+never forms pair products).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1503_06202_gb300 as xe  # noqa: E402
+
+ENGINES = {"tensor": xe.XENG_ENGINE_TENSOR, "dp4a": xe.XENG_ENGINE_DP4A}
+
+
+def to_dev(block: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(block)).cuda()
+
+
+def run(block_dev, engine, pieces=None, t_integ=None):
+    T, F, N = block_dev.shape
+    eng = xe.XEngine(N, F, t_integ or max(T, 1), engine)
+    out = torch.full((F, N * (N + 1) // 2, 2), -7, dtype=torch.int32, device="cuda")
+    bounds = [0] + list(pieces or []) + [T]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        eng.push(block_dev[a:b], b - a)
+    n = eng.dump(out)
+    torch.cuda.synchronize()
+    eng.close()
+    assert n == T
+    return out.cpu().numpy().astype(np.int64)
+
+
+def assert_same(got, want, what=""):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        raise AssertionError("%s: %d entries differ, first %s: got %s want %s" % (
+            what, len(bad), bad[0].tolist(), got[tuple(bad[0])], want[tuple(bad[0])]))
+
+
+# --------------------------------------------------------------- decode ----
+
+def test_decode_stage_codes():
+    rng = np.random.default_rng(20)
+    T, F, N, f0, nf = 300, 3, 200, 1, 2
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    t_pad, n_pad = 384, 256
+    planes = torch.full((nf, 2, n_pad, t_pad), 0x55, dtype=torch.uint8, device="cuda")
+    assert xe.xeng_decode(to_dev(blk), T, F, N, f0, nf, planes) == xe.XENG_OK
+    torch.cuda.synchronize()
+    vals = planes.view(torch.float8_e4m3fn).float().cpu().numpy()
+    assert np.array_equal(vals, np.rint(vals))
+    b = blk[:, f0:f0 + nf, :].astype(np.int64)  # [T][nf][N]
+    want = np.zeros((nf, 2, n_pad, t_pad))
+    want[:, 0, :N, :T] = np.transpose((b >> 4) - 8, (1, 2, 0))   # Sec. II-A: value = nibble - 8
+    want[:, 1, :N, :T] = np.transpose((b & 15) - 8, (1, 2, 0))
+    assert np.array_equal(vals, want)
+    # padding is +0.0, not -0.0
+    pad = planes[:, :, N:, :].cpu().numpy()
+    assert (pad == 0).all()
+
+
+# ------------------------------------------------------------ small/ragged --
+
+SHAPES = [(1, 1, 1), (5, 3, 2), (129, 2, 7), (300, 2, 127), (128, 1, 128), (257, 2, 129), (1000, 3, 200),
+          (700, 2, 300), (1024, 1, 513), (64, 2, 1024)]
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+@pytest.mark.parametrize("T,F,N", SHAPES)
+def test_parity_small_and_ragged(T, F, N, engine):
+    rng = np.random.default_rng(T * 7919 + F * 31 + N)
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    assert_same(run(to_dev(blk), ENGINES[engine]), oracle.correlate(blk), "%s T=%d F=%d N=%d" % (engine, T, F, N))
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_pathfinder_small_exact(engine):
+    rec = synth.PATHFINDER_SMALL  # N=256, F=8, T=4096, uniform nibbles
+    assert_same(run(rec.device(), ENGINES[engine]), oracle.correlate(rec.host()), engine)
+
+
+# ------------------------------------------------- exactness (f32 in TMEM) --
+
+def test_exact_at_largest_chunk_sums():
+    # every sample -8-8i: Re = 128 T = 2^23 for every pair, Im = 0
+    T, F, N = 65536, 1, 256
+    out = run(torch.zeros((T, F, N), dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
+
+
+def test_exact_small_terms_after_large_sums():
+    # a large partial sum first, then +-1 / +-i terms that an accumulator
+    # keeping fewer than 24 bits would drop
+    rng = np.random.default_rng(21)
+    T, F, N = 65536, 1, 192
+    blk = np.zeros((T, F, N), np.uint8)
+    tail = rng.choice(np.array([0x98, 0x78, 0x89, 0x87, 0x88], np.uint8), size=(T // 2, F, N))
+    blk[T // 2:] = tail
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "large-then-small")
+
+
+def test_exact_extremes_mix():
+    rng = np.random.default_rng(22)
+    T, F, N = 20000, 2, 160
+    blk = rng.choice(np.array([0x00, 0xFF, 0x0F, 0xF0, 0x88, 0x98, 0x78, 0x08, 0x80], np.uint8), size=(T, F, N))
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "extremes")
+
+
+def test_int32_accumulation_across_chunks():
+    # 140000 samples of -8-8i: Re = 17,920,000 > 2^24, split over three chunks
+    T, F, N = 140000, 1, 130
+    for engine in ENGINES.values():
+        out = run(torch.zeros((T, F, N), dtype=torch.uint8, device="cuda"), engine)
+        assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
+
+
+# ------------------------------------------------------------ API semantics --
+
+def test_push_in_pieces_equals_one_push():
+    rng = np.random.default_rng(23)
+    T, F, N = 1000, 3, 200
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    for engine in ENGINES.values():
+        assert_same(run(to_dev(blk), engine, pieces=[1, 300, 301]), want, "pieces")
+
+
+def test_engines_can_mix_within_an_integration():
+    rng = np.random.default_rng(24)
+    T, F, N = 600, 2, 140
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    d = to_dev(blk)
+    eng = xe.XEngine(N, F, T)
+    eng.set_engine(xe.XENG_ENGINE_DP4A)
+    eng.push(d[:250])
+    eng.set_engine(xe.XENG_ENGINE_TENSOR)
+    eng.push(d[250:])
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    assert eng.dump(out) == T
+    assert_same(out.cpu().numpy().astype(np.int64), oracle.correlate(blk), "mixed engines")
+    eng.close()
+
+
+def test_dump_and_overflow_semantics():
+    rng = np.random.default_rng(25)
+    T, F, N = 500, 2, 70
+    blk = rng.integers(0, 256, size=(T + 50, F, N), dtype=np.uint8)
+    d = to_dev(blk)
+    eng = xe.XEngine(N, F, T)
+    out = torch.full((F, N * (N + 1) // 2, 2), 9, dtype=torch.int32, device="cuda")
+    assert eng.dump(out) == 0  # nothing integrated: zeros
+    assert not out.any().item()
+    eng.push(d[:300])
+    assert xe.xeng_push(eng.h, d[300:], 201) == xe.XENG_ERR_OVERFLOW  # 300 + 201 > 500
+    assert xe.xeng_push(eng.h, d, -1) == xe.XENG_ERR_ARG
+    assert xe.xeng_push(eng.h, d, 0) == xe.XENG_OK
+    eng.push(d[300:500])
+    assert eng.dump(out) == 500
+    assert_same(out.cpu().numpy().astype(np.int64), oracle.correlate(blk[:500]), "after overflow")
+    eng.push(d[500:550])  # a new integration starts from zero
+    assert eng.dump(out) == 50
+    assert_same(out.cpu().numpy().astype(np.int64), oracle.correlate(blk[500:550]), "second integration")
+    eng.close()
+
+
+def test_host_buffers_in_and_out():
+    rng = np.random.default_rng(26)
+    T, F, N = 333, 2, 100
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    for engine in ENGINES.values():
+        eng = xe.XEngine(N, F, T, engine)
+        pinned = torch.from_numpy(blk).pin_memory()
+        eng.push(pinned)             # pinned host memory
+        host_out = np.zeros((F, N * (N + 1) // 2, 2), np.int32)
+        assert eng.dump(host_out) == T
+        assert_same(host_out.astype(np.int64), oracle.correlate(blk), "host buffers")
+        eng.push(blk)                # pageable host memory
+        assert eng.dump(host_out) == T
+        assert_same(host_out.astype(np.int64), oracle.correlate(blk), "pageable")
+        eng.close()
+
+
+def test_create_rejects_bad_sizes_on_gpu():
+    for args in [(0, 1, 1), (4097, 1, 1), (1, 0, 1), (1, 1, 0), (1, 1, 2 ** 24)]:
+        rc, h = xe.xeng_create(*args)
+        assert rc == xe.XENG_ERR_RANGE and h is None
+
+
+# ------------------------------------------------------- full-size checks --
+
+def beam_power_gpu(block_dev, w):
+    """LHS of the beam-power identity per channel, exact in fp64 on the GPU."""
+    T, F, N = block_dev.shape
+    acc = torch.zeros(F, dtype=torch.float64, device="cuda")
+    tc = max(1, (1 << 26) // (F * N))
+    for t0 in range(0, T, tc):
+        b = block_dev[t0:t0 + tc].to(torch.int32)
+        x = torch.complex(((b >> 4) - 8).double(), ((b & 15) - 8).double())  # [t][F][N]
+        s = (x * w).sum(dim=-1)  # [t][F]
+        acc += (s.real ** 2 + s.imag ** 2).sum(dim=0)
+    return acc
+
+
+def weighted_sum_gpu(vis_dev, w):
+    """RHS: sum_i |w_i|^2 V_ii + 2 Re sum_{i<j} w_i conj(w_j) V_ij, exact in fp64."""
+    F, B, _ = vis_dev.shape
+    N = w.shape[0]
+    ii, jj = torch.triu_indices(N, N, device="cuda")
+    p = w[ii] * torch.conj(w[jj])
+    mult = torch.where(ii == jj, 1.0, 2.0).double()
+    res = torch.zeros(F, dtype=torch.float64, device="cuda")
+    for f0 in range(0, F, 8):
+        v = vis_dev[f0:f0 + 8].double()
+        res[f0:f0 + 8] = ((p.real * v[..., 0] - p.imag * v[..., 1]) * mult).sum(dim=-1)
+    return res
+
+
+def sampled_pairs(rng, N, n):
+    edges = np.array(sorted({0, 1, 126, 127, 128, 129, 255, 256, N // 2, N - 2, N - 1} & set(range(N))))
+    i = np.concatenate([rng.integers(0, N, n), np.repeat(edges, len(edges))])
+    j = np.concatenate([rng.integers(0, N, n), np.tile(edges, len(edges))])
+    return np.minimum(i, j), np.maximum(i, j)
+
+
+@pytest.mark.parametrize("name", ["pathfinder_full", "chime_full"])
+def test_full_size_workload(name):
+    rec = {"pathfinder_full": synth.PATHFINDER_FULL, "chime_full": synth.CHIME_FULL}[name]
+    T, F, N = rec.T, rec.F, rec.N
+    B = N * (N + 1) // 2
+    block = rec.device()
+    eng = xe.XEngine(N, F, T)
+    out = torch.empty((F, B, 2), dtype=torch.int32, device="cuda")
+    eng.push(block)
+    assert eng.dump(out) == T
+    torch.cuda.synchronize()
+    eng.close()
+    rng = np.random.default_rng(27)
+    # 1. sampled outputs against the oracle, on channels spread over the band
+    for f in (0, 1, F // 2, F - 1):
+        host = rec.host(f0=f, nf=1)
+        i, j = sampled_pairs(rng, N, 4000)
+        want = oracle.correlate_pairs(host, np.zeros_like(i), i, j)
+        got = out[f][torch.from_numpy(oracle.triangle_index(i, j, N)).cuda()].cpu().numpy().astype(np.int64)
+        assert_same(got, want, "%s channel %d" % (name, f))
+    # 2. every channel: autocorrelations real and non-negative, beam-power identity
+    diag = torch.from_numpy(oracle.triangle_index(np.arange(N), np.arange(N), N)).cuda()
+    assert (out[:, diag, 1] == 0).all().item() and (out[:, diag, 0] >= 0).all().item()
+    for seed in (1, 2):
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        w = torch.complex(torch.randint(-4, 5, (N,), generator=g).double(),
+                          torch.randint(-4, 5, (N,), generator=g).double()).cuda()
+        lhs = beam_power_gpu(block, w)
+        rhs = weighted_sum_gpu(out, w)
+        assert torch.equal(lhs, rhs), "beam-power identity fails on %d channels" % int((lhs != rhs).sum())
