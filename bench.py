@@ -30,8 +30,15 @@ WORKLOADS = {
     "chime_full": ("CHIME_FULL", "full-CHIME-shaped: N=2048 inputs, 1024 channels, T=8192, sky+noise (rho 0.1, sigma 2.5)"),
     "pathfinder_full": ("PATHFINDER_FULL", "full Pathfinder rate: N=256, 1024 channels, T=32768, sky+noise (rho 0.1, sigma 2.5)"),
     "pathfinder_small": ("PATHFINDER_SMALL", "Pathfinder-shaped small: N=256, 8 channels, T=4096, uniform nibbles"),
+    "chime_slice": ("CHIME_SLICE", "16 channels of the full-CHIME shape (N=2048, T=8192): profiling case"),
 }
 METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)"
+
+# DRAM bytes (read + write) per channel of one correlate_tc_kernel launch, from
+# one ncu capture of the 16-channel slice of the same (N, T) shape; traffic
+# grows in proportion to channels.  Keyed by (N, T); must be re-taken (or
+# removed) whenever the kernel changes.
+CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (643.938560e6 + 242.520064e6) / 16}
 
 
 def useful_ops(T, F, N):
@@ -172,6 +179,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the dense-throughput probes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -196,6 +204,13 @@ def main():
     rec = getattr(synth, WORKLOADS[args.workload][0])
     T, F, N = rec.T, rec.F, rec.N
     B = N * (N + 1) // 2
+    probes = None
+    if not args.no_peaks:
+        probes = {}
+        for name, kind, iters in (("tc_f8f6f4", xe.XENG_PEAK_TC_F8F6F4, 1 << 21), ("tc_f16", xe.XENG_PEAK_TC_F16, 1 << 20),
+                                  ("mma_sync_s8", xe.XENG_PEAK_MMA_SYNC_S8, 200000), ("dp4a", xe.XENG_PEAK_DP4A, 500000)):
+            rc, tf, pms = xe.xeng_peak_probe(kind, iters)
+            probes[name] = round(tf, 1) if rc == 0 else None
     engine = xe.XENG_ENGINE_TENSOR if args.engine == "tensor" else xe.XENG_ENGINE_DP4A
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -247,9 +262,21 @@ def main():
         peak = 2.0 * peaks["bf16_tflops_sustained"]
         peak_note = ("fp8 dense = 2 x %s sustained bf16 %.1f TFLOP/s (nominal fp8:bf16 = 4.5:2.25); "
                      "sm_103a has no tcgen05 kind::i8" % (peak_src, peaks["bf16_tflops_sustained"]))
+        per_ch = CORRELATE_TC_DRAM_BYTES_PER_CHANNEL.get((N, T))
+        traffic = per_ch * F / launches_per_step if per_ch else None
         roof = {"bound": "tensor", "kernel": "correlate_tc_kernel", "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "traffic": None, "peak_note": peak_note}
+                "peak": peak, "unit": "TFLOP/s", "traffic": traffic, "peak_note": peak_note}
         roof["frac"] = roof["achieved"] / peak
+        if probes and probes.get("tc_f8f6f4"):
+            roof["peak_probe_fp8"] = probes["tc_f8f6f4"]
+            roof["frac_of_probe_fp8"] = roof["achieved"] / probes["tc_f8f6f4"]
+            # useful ops exclude the lower halves of diagonal tiles the MMAs also compute
+            nt = -(-N // 128)
+            executed = nt * (nt + 1) // 2 * 128 * 128 / (N * (N + 1) / 2)
+            roof["executed_over_useful"] = executed
+            roof["frac_executed_of_probe_fp8"] = roof["achieved"] * executed / probes["tc_f8f6f4"]
+        if probes and probes.get("mma_sync_s8"):
+            roof["frac_of_probe_int8_mma_sync"] = roof["achieved"] / probes["mma_sync_s8"]
     else:
         roof = {"bound": "alu", "kernel": "correlate_dp4a_kernel",
                 "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12, "peak": None, "unit": "TFLOP/s",
@@ -296,7 +323,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8,
-                "gpu_launches": int(st["launches"]), "roofline": roof, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": int(st["launches"]), "roofline": roof, "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}
         print(json.dumps(line), flush=True)
     eng.close()

@@ -191,3 +191,19 @@ class XEngine:
             self.close()
         except Exception:
             pass
+
+
+XENG_PEAK_TC_F8F6F4, XENG_PEAK_TC_F16, XENG_PEAK_MMA_SYNC_S8, XENG_PEAK_DP4A = 0, 1, 2, 3
+
+
+def xeng_peak_probe(kind: int, iters: int):
+    """Returns (status, TFLOP/s, ms) of one dense-throughput probe (include/xeng_peaks.h)."""
+    L = lib()
+    if not getattr(L.xeng_peak_probe, "_typed", False):
+        L.xeng_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.xeng_peak_probe.restype = ctypes.c_int
+        L.xeng_peak_probe._typed = True
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = L.xeng_peak_probe(kind, iters, ctypes.byref(tf), ctypes.byref(ms))
+    return rc, tf.value, ms.value

@@ -178,3 +178,6 @@ class Recipe:
 PATHFINDER_SMALL = Recipe("uniform", T=4096, F=8, N=256, seed=0)
 PATHFINDER_FULL = Recipe("sky", T=32768, F=1024, N=256, seed=1)
 CHIME_FULL = Recipe("sky", T=8192, F=1024, N=2048, seed=2)
+# 16 channels of the full-CHIME shape: inputs (256 MiB) still exceed L2 while
+# the whole working set stays near 1.3 GB -- the profiling case.
+CHIME_SLICE = Recipe("sky", T=8192, F=16, N=2048, seed=2)
