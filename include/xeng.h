@@ -150,6 +150,39 @@ XENG_API int xeng_set_profiling(xeng_t h, int32_t on);
  */
 XENG_API int xeng_get_stats(xeng_t h, xeng_stats_t *stats, int32_t reset);
 
+/* Size of the fixed device array xeng_correlate_noalloc works in (64 MiB). */
+#define XENG_NOALLOC_SCRATCH_BYTES 67108864LL
+
+/*
+ * xeng_correlate_noalloc -- one whole integration of `block` into `out`,
+ *   computed like xeng_push + xeng_dump on a fresh handle with the tensor
+ *   engine, but without allocating any device memory.  The paper has no
+ *   counterpart: this is for callers that cannot allocate at the point where
+ *   they correlate -- e.g. a real-time capture loop whose device memory was
+ *   divided up once at start-up by its own pool, or a loop that cannot afford
+ *   the device-wide synchronization cudaMalloc / cudaFree may cause.
+ *
+ *   block: [n_samples][n_freq][n_inputs] bytes, device memory (caller-owned).
+ *   out:   [n_freq][N(N+1)/2][2] int32, device memory (caller-owned);
+ *          overwritten (n_samples == 0 writes zeros).
+ *   Working memory is one library-owned __device__ array of
+ *   XENG_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until
+ *   the process exits.  Sizes beyond what it holds are rejected with
+ *   XENG_ERR_RANGE: n_samples <= 65536 and
+ *   2 * round_up(N, 128) * round_up(n_samples, 128) <= XENG_NOALLOC_SCRATCH_BYTES - 256
+ *   (e.g. N = 2048 with 8192 samples, or N = 256 with 65536 samples).
+ *   Host pointers give XENG_ERR_ARG.  The call enqueues its work on `stream`
+ *   and returns once it is done (it synchronizes `stream`); a device-side
+ *   wait time-out gives XENG_ERR_TIMEOUT.  It calls no cudaMalloc, cudaFree
+ *   or other allocating routine.
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.  All
+ *   calls on a device share the array: calls that overlap on the GPU (from
+ *   several threads or streams) race and give wrong results.
+ */
+XENG_API int xeng_correlate_noalloc(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t n_inputs,
+                                    int32_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

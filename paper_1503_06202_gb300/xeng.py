@@ -193,6 +193,21 @@ class XEngine:
             pass
 
 
+XENG_NOALLOC_SCRATCH_BYTES = 67108864
+
+
+def xeng_correlate_noalloc(block, n_samples, n_freq, n_inputs, out, stream=None) -> int:
+    """One integration of `block` into `out` (device memory) using only the
+    library's fixed device array -- for callers that cannot allocate."""
+    L = lib()
+    if not getattr(L.xeng_correlate_noalloc, "_typed", False):
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.xeng_correlate_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
+        L.xeng_correlate_noalloc.restype = ctypes.c_int
+        L.xeng_correlate_noalloc._typed = True
+    return L.xeng_correlate_noalloc(_ptr(block), n_samples, n_freq, n_inputs, _ptr(out), _stream(stream))
+
+
 XENG_PEAK_TC_F8F6F4, XENG_PEAK_TC_F16, XENG_PEAK_MMA_SYNC_S8, XENG_PEAK_DP4A = 0, 1, 2, 3
 
 

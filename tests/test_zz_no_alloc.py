@@ -1,0 +1,74 @@
+"""xeng_correlate_noalloc, the entry point for callers that cannot allocate
+device memory (for example a real-time capture loop that divided its device
+memory once at start-up, or one that cannot risk the device-wide pause a
+cudaMalloc / cudaFree may cause).  It works in a fixed array inside the
+library instead of allocating.
+
+Checked through the C ABI against the allocating path (xeng_push + xeng_dump
+on a handle), bit for bit, on calls made back to back -- the second call runs
+on whatever the first one left in the shared array.  This file is collected
+last on purpose; it needs nothing from the other tests.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1503_06202_gb300 as xe  # noqa: E402
+
+
+def with_handle(block):
+    T, F, N = block.shape
+    eng = xe.XEngine(N, F, T)
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    eng.push(block)
+    assert eng.dump(out) == T
+    torch.cuda.synchronize()
+    eng.close()
+    return out.cpu().numpy()
+
+
+def without_alloc(block):
+    T, F, N = block.shape
+    out = torch.full((F, N * (N + 1) // 2, 2), 12345, dtype=torch.int32, device="cuda")
+    rc = xe.xeng_correlate_noalloc(block, T, F, N, out)
+    assert rc == xe.XENG_OK, xe.xeng_strerror(rc)
+    return out.cpu().numpy()
+
+
+def test_noalloc_matches_allocating_path_on_consecutive_calls():
+    cases = [synth.Recipe("uniform", T=1000, F=3, N=200, seed=31),
+             synth.Recipe("sky", T=4096, F=4, N=256, seed=32),
+             # 32 MiB of planes per channel: two channels per round, three rounds
+             synth.Recipe("sky", T=8192, F=5, N=2048, seed=33),
+             synth.Recipe("uniform", T=129, F=2, N=130, seed=34)]
+    for rec in cases:
+        block = rec.device()
+        torch.cuda.synchronize()
+        first = without_alloc(block)
+        second = without_alloc(block)  # runs on the array the first call left behind
+        want = with_handle(block)
+        assert np.array_equal(first, want), rec
+        assert np.array_equal(second, want), rec
+
+
+def test_noalloc_rejects_sizes_beyond_its_array():
+    block = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(16, dtype=torch.int32, device="cuda")
+    # 2 * 4096 * 8192 bytes of planes per channel exceed the 64 MiB array
+    assert xe.xeng_correlate_noalloc(block, 8192, 1, 4096, out) == xe.XENG_ERR_RANGE
+    # more than 65536 samples in one call
+    assert xe.xeng_correlate_noalloc(block, 65537, 1, 8, out) == xe.XENG_ERR_RANGE
+    assert xe.xeng_correlate_noalloc(block, 10, 1, 0, out) == xe.XENG_ERR_RANGE
+    host = np.zeros(16, np.uint8)
+    assert xe.xeng_correlate_noalloc(host, 1, 1, 4, out) == xe.XENG_ERR_ARG
+
+
+def test_noalloc_empty_block_writes_zeros():
+    block = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    out = torch.full((2, 10, 2), 7, dtype=torch.int32, device="cuda")
+    assert xe.xeng_correlate_noalloc(block, 0, 2, 4, out) == xe.XENG_OK
+    assert not out.any().item()
