@@ -99,6 +99,19 @@ XENG_API int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *
  */
 XENG_API int64_t xeng_dump(xeng_t h, int32_t *out, void *stream);
 
+/*
+ * xeng_correlate -- one whole integration in one call (Sec. IV-C-1): the
+ *   visibilities of exactly these n_samples samples, written to `out`
+ *   ([F][N(N+1)/2][2] int32), as xeng_push + xeng_dump on a fresh handle
+ *   would give, but straight into `out` when it is device memory (no copy of
+ *   the triangle).  block as for xeng_push; n_samples <= t_integ (else
+ *   XENG_ERR_OVERFLOW).  With device `out` the call is asynchronous on
+ *   `stream` and leaves any integration in progress on the handle untouched;
+ *   with host `out` it returns once the data is there, and needs the handle
+ *   to have no integration in progress (else XENG_ERR_ARG).
+ */
+XENG_API int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *out, void *stream);
+
 /* xeng_destroy -- free the handle and its device memory; NULL is a no-op.
  * Synchronizes the device first. */
 XENG_API void xeng_destroy(xeng_t h);

@@ -214,6 +214,80 @@ int xeng_set_engine(xeng_t h, int32_t engine)
     return XENG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device copy of a caller block: the block itself, or the staging buffer after
+// an asynchronous host-to-device copy on `s`.  Returns nullptr on failure.
+const uint8_t *device_block(xeng_s *h, const uint8_t *block, int64_t bytes, cudaStream_t s, int *status)
+{
+    *status = XENG_OK;
+    if (is_device_pointer(block)) return block;
+    if (h->staging_bytes < bytes) {
+        cudaFree(h->staging);
+        h->staging = nullptr;
+        h->staging_bytes = 0;
+        if (cudaMalloc(&h->staging, (size_t)bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *status = XENG_ERR_NOMEM;
+            return nullptr;
+        }
+        h->staging_bytes = bytes;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->staging, block, (size_t)bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        *status = (h->sticky = cuda_status(e));
+        return nullptr;
+    }
+    return h->staging;
+}
+
+// Integrate n samples of the device block into `target` ([F][B][2] int32):
+// the first launch stores when `fresh`, every later one adds.  Work is
+// ordered after earlier work on `s` and before later work on `s`.
+cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32_t *target, bool fresh,
+                      cudaStream_t s)
+{
+    const int64_t N = h->N, F = h->F;
+    const int64_t n_pad = round_up(N, kTile);
+    const int64_t nb2 = N * (N + 1);
+    if (h->engine == XENG_ENGINE_DP4A) {
+        return timed_launch(h, 1, s, [&] {
+            return launch_correlate_dp4a(dblock, n_samples, (int32_t)F, (int32_t)N, target, fresh ? 0 : 1, s);
+        });
+    }
+    cudaError_t e = cudaSuccess;
+    for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
+        const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
+        const int64_t t_pad = round_up(nt, kTile);
+        const int accumulate = (fresh && t0 == 0) ? 0 : 1;
+        for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += h->group_f) {
+            const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
+            const uint8_t *src = dblock + t0 * F * N;
+            e = timed_launch(h, 0, s, [&] {
+                return launch_decode(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes, t_pad, n_pad, s);
+            });
+            if (e != cudaSuccess) break;
+            TcArgs a;
+            a.planes = h->planes;
+            a.t_pad = t_pad;
+            a.n_pad = (int32_t)n_pad;
+            a.N = (int32_t)N;
+            a.nf = nf;
+            a.acc = target + f0 * nb2;
+            a.accumulate = accumulate;
+            a.err = h->d_err;
+            e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+        }
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
 {
     if (!h) return XENG_ERR_ARG;
@@ -224,63 +298,45 @@ int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
     if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples == 0) return XENG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = h->N, F = h->F;
-    const int64_t bytes = n_samples * F * N;
-
-    const uint8_t *dblock = block;
-    if (!is_device_pointer(block)) {
-        if (h->staging_bytes < bytes) {
-            cudaFree(h->staging);
-            h->staging = nullptr;
-            h->staging_bytes = 0;
-            if (cudaMalloc(&h->staging, (size_t)bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return XENG_ERR_NOMEM;
-            }
-            h->staging_bytes = bytes;
-        }
-        cudaError_t e = cudaMemcpyAsync(h->staging, block, (size_t)bytes, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return (h->sticky = cuda_status(e));
-        dblock = h->staging;
-    }
-
-    const int64_t n_pad = round_up(N, kTile);
-    const int64_t nb2 = N * (N + 1);
-    cudaError_t e = cudaSuccess;
-    if (h->engine == XENG_ENGINE_DP4A) {
-        e = timed_launch(h, 1, s, [&] {
-            return launch_correlate_dp4a(dblock, n_samples, (int32_t)F, (int32_t)N, h->acc, h->fresh ? 0 : 1, s);
-        });
-    } else {
-        for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
-            const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
-            const int64_t t_pad = round_up(nt, kTile);
-            const int accumulate = (h->fresh && t0 == 0) ? 0 : 1;
-            for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += h->group_f) {
-                const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
-                const uint8_t *src = dblock + t0 * F * N;
-                e = timed_launch(h, 0, s, [&] {
-                    return launch_decode(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes, t_pad, n_pad, s);
-                });
-                if (e != cudaSuccess) break;
-                TcArgs a;
-                a.planes = h->planes;
-                a.t_pad = t_pad;
-                a.n_pad = (int32_t)n_pad;
-                a.N = (int32_t)N;
-                a.nf = nf;
-                a.acc = h->acc + f0 * nb2;
-                a.accumulate = accumulate;
-                a.err = h->d_err;
-                e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
-            }
-        }
-    }
+    const uint8_t *dblock = device_block(h, block, n_samples * h->F * h->N, s, &st);
+    if (!dblock) return st;
+    cudaError_t e = integrate(h, dblock, n_samples, h->acc, h->fresh, s);
     if (e != cudaSuccess) return (h->sticky = cuda_status(e));
     cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     h->samples += n_samples;
     h->fresh = false;
     return XENG_OK;
+}
+
+int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *out, void *stream)
+{
+    if (!h || !out) return XENG_ERR_ARG;
+    if (n_samples < 0 || (n_samples > 0 && !block)) return XENG_ERR_ARG;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    if (n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev_out = is_device_pointer(out);
+    if (!dev_out && (h->samples > 0 || !h->fresh)) return XENG_ERR_ARG;  // would clobber an open integration
+    const int64_t bytes = acc_bytes(h);
+    cudaError_t e = cudaSuccess;
+    if (n_samples == 0) {
+        if (dev_out) return cuda_status(cudaMemsetAsync(out, 0, (size_t)bytes, s));
+        e = cudaStreamSynchronize(s);
+        memset(out, 0, (size_t)bytes);
+        return cuda_status(e);
+    }
+    const uint8_t *dblock = device_block(h, block, n_samples * h->F * h->N, s, &st);
+    if (!dblock) return st;
+    // device output: written in place; host output: through the accumulators
+    e = integrate(h, dblock, n_samples, dev_out ? out : h->acc, true, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !dev_out) {
+        e = cudaMemcpyAsync(out, h->acc, (size_t)bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    return dev_out ? XENG_OK : check_sticky(h);
 }
 
 int64_t xeng_dump(xeng_t h, int32_t *out, void *stream)

@@ -60,6 +60,8 @@ def lib():
         L.xeng_push.restype = ctypes.c_int
         L.xeng_dump.argtypes = [vp, vp, vp]
         L.xeng_dump.restype = i64
+        L.xeng_correlate.argtypes = [vp, vp, i64, vp, vp]
+        L.xeng_correlate.restype = ctypes.c_int
         L.xeng_destroy.argtypes = [vp]
         L.xeng_destroy.restype = None
         L.xeng_strerror.argtypes = [ctypes.c_int]
@@ -114,6 +116,10 @@ def xeng_push(h, block, n_samples: int, stream=None) -> int:
 
 def xeng_dump(h, out, stream=None) -> int:
     return lib().xeng_dump(h, _ptr(out), _stream(stream))
+
+
+def xeng_correlate(h, block, n_samples: int, out, stream=None) -> int:
+    return lib().xeng_correlate(h, _ptr(block), n_samples, _ptr(out), _stream(stream))
 
 
 def xeng_destroy(h) -> None:
@@ -171,6 +177,13 @@ class XEngine:
         if n < 0:
             raise XengError(n, "xeng_dump")
         return n
+
+    def correlate(self, block, out, n_samples: int | None = None, stream=None) -> None:
+        if n_samples is None:
+            n_samples = block.shape[0]
+        rc = xeng_correlate(self.h, block, n_samples, out, stream)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_correlate")
 
     def set_profiling(self, on: bool) -> None:
         xeng_set_profiling(self.h, on)

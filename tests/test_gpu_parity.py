@@ -114,6 +114,16 @@ def test_exact_extremes_mix():
     assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "extremes")
 
 
+def test_multi_round_push_random():
+    # three sample chunks: three decode + correlation rounds adding into int32
+    rng = np.random.default_rng(28)
+    T, F, N = 140000, 2, 130
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), want, "multi-round")
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR, pieces=[70000]), want, "multi-round pieces")
+
+
 def test_int32_accumulation_across_chunks():
     # 140000 samples of -8-8i: Re = 17,920,000 > 2^24, split over three chunks
     T, F, N = 140000, 1, 130
@@ -188,6 +198,31 @@ def test_host_buffers_in_and_out():
         eng.close()
 
 
+def test_one_shot_correlate():
+    rng = np.random.default_rng(29)
+    T, F, N = 900, 3, 150
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    d = to_dev(blk)
+    for engine in ENGINES.values():
+        eng = xe.XEngine(N, F, T, engine)
+        out = torch.full((F, N * (N + 1) // 2, 2), 5, dtype=torch.int32, device="cuda")
+        eng.push(d[:100])                       # an open integration is left untouched
+        eng.correlate(d, out)
+        torch.cuda.synchronize()
+        assert_same(out.cpu().numpy().astype(np.int64), want, "one-shot device out")
+        host = np.zeros((F, N * (N + 1) // 2, 2), np.int32)
+        assert xe.xeng_correlate(eng.h, d, T, host) == xe.XENG_ERR_ARG  # host out needs no open integration
+        assert eng.dump(out) == 100
+        assert_same(out.cpu().numpy().astype(np.int64), oracle.correlate(blk[:100]), "open integration kept")
+        eng.correlate(blk, host)                # host in, host out
+        assert_same(host.astype(np.int64), want, "one-shot host out")
+        assert xe.xeng_correlate(eng.h, d, T + 1, out) == xe.XENG_ERR_OVERFLOW
+        eng.correlate(d[:0], out, 0)
+        assert not out.any().item()
+        eng.close()
+
+
 def test_create_rejects_bad_sizes_on_gpu():
     for args in [(0, 1, 1), (4097, 1, 1), (1, 0, 1), (1, 1, 0), (1, 1, 2 ** 24)]:
         rc, h = xe.xeng_create(*args)
@@ -238,10 +273,14 @@ def test_full_size_workload(name):
     block = rec.device()
     eng = xe.XEngine(N, F, T)
     out = torch.empty((F, B, 2), dtype=torch.int32, device="cuda")
+    eng.correlate(block, out)  # the benchmark's call
+    out2 = torch.empty_like(out)
     eng.push(block)
-    assert eng.dump(out) == T
+    assert eng.dump(out2) == T
     torch.cuda.synchronize()
     eng.close()
+    assert torch.equal(out, out2), "push + dump differs from the one-shot call"
+    del out2
     rng = np.random.default_rng(27)
     # 1. sampled outputs against the oracle, on channels spread over the band
     for f in (0, 1, F // 2, F - 1):
