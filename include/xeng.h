@@ -163,6 +163,77 @@ XENG_API int xeng_set_profiling(xeng_t h, int32_t on);
  */
 XENG_API int xeng_get_stats(xeng_t h, xeng_stats_t *stats, int32_t reset);
 
+/*
+ * Batches: many independent whole integrations (Sec. IV-C-1) of uneven
+ * sizes -- different N, F and T per job -- planned once and then run as one
+ * decode launch plus one persistent tensor-core launch, captured in a CUDA
+ * graph.  Every job's result is bit-identical to correlating it alone.
+ */
+typedef struct {
+    int32_t n_inputs;       /* N of this job, 1..XENG_MAX_INPUTS                  */
+    int32_t n_freq;         /* F of this job, >= 1                                */
+    int64_t n_samples;      /* T of this job, 1..XENG_MAX_T_INTEG                 */
+    const uint8_t *block;   /* device memory [T][F][N], caller-owned              */
+    int32_t *out;           /* device memory [F][N(N+1)/2][2] int32, caller-owned */
+} xeng_job_t;
+
+#define XENG_SCHED_LPT         0  /* longest items first onto the least-loaded CTA */
+#define XENG_SCHED_ROUND_ROBIN 1  /* items dealt round-robin in job order          */
+
+typedef struct {
+    int32_t max_chunks_per_item; /* split a tile's integration into items of at most this many
+                                    128-sample chunks (1..512; <= 0 means 512)            */
+    int32_t policy;              /* XENG_SCHED_LPT or XENG_SCHED_ROUND_ROBIN              */
+    int32_t use_graph;           /* != 0: capture the run in a CUDA graph once, replay it */
+} xeng_batch_opts_t;
+
+typedef struct {
+    int32_t n_jobs;
+    int64_t n_items;             /* work items of the persistent launch                  */
+    int32_t grid;                /* persistent CTAs (one per SM)                         */
+    int64_t decode_ctas;         /* CTAs of the decode launch                            */
+    int64_t planes_bytes;        /* decode scratch owned by the batch                    */
+    int32_t max_chunks_per_item;
+    int32_t policy;
+    double  load_imbalance;      /* planned max / mean CTA load                          */
+} xeng_batch_info_t;
+
+typedef struct xeng_batch_s *xeng_batch_t;
+
+/*
+ * xeng_batch_create -- plan a batch over jobs[0..n_jobs) on the current
+ *   device: allocates the decode scratch (about twice the jobs' input bytes),
+ *   per-job TMA descriptors and the work list, and (use_graph) captures the
+ *   run in a CUDA graph.  The block and out pointers are bound now and used by
+ *   every run.  opts may be NULL (LPT, 512 chunks, graph).  Synchronous.
+ *   XENG_ERR_ARG for NULL or host pointers, XENG_ERR_RANGE for bad sizes.
+ */
+XENG_API int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_opts_t *opts,
+                               xeng_batch_t *out_batch);
+
+/* xeng_batch_run -- enqueue one run on `stream`: every job's visibilities of
+ *   its whole block are written to its out (overwritten).  Asynchronous; a
+ *   device-side time-out of an earlier run is reported as XENG_ERR_TIMEOUT. */
+XENG_API int xeng_batch_run(xeng_batch_t b, void *stream);
+
+/* xeng_batch_info -- the plan's sizes and its predicted load balance. */
+XENG_API int xeng_batch_info(xeng_batch_t b, xeng_batch_info_t *info);
+
+/* xeng_batch_destroy -- free the batch (synchronizes the device); NULL is a no-op. */
+XENG_API void xeng_batch_destroy(xeng_batch_t b);
+
+/*
+ * xeng_batch_autotune -- pick xeng_batch_opts_t for these jobs by timing every
+ *   (max_chunks_per_item in {16, 32, 64, 128, 256, 512}) x (policy) candidate
+ *   for `reps` runs each (overwriting the jobs' outputs).  With a cache_path,
+ *   a text file of "signature max_chunks policy ms" lines keyed by the jobs'
+ *   (N, F, T) list and the SM count is read first (hit: returns 1 without
+ *   timing) and the winner appended after tuning (returns 0).  *best_ms (may
+ *   be NULL) receives the winner's time per run.  Negative XENG_ERR_* on error.
+ */
+XENG_API int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cache_path, int32_t reps,
+                                 xeng_batch_opts_t *best, double *best_ms);
+
 /* Size of the fixed device array xeng_correlate_noalloc works in (64 MiB). */
 #define XENG_NOALLOC_SCRATCH_BYTES 67108864LL
 

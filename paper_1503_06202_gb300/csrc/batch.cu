@@ -1,0 +1,431 @@
+// batch.cu -- many independent correlations (uneven N, F, T) in one pass:
+// one decode launch over every job's tiles, then one persistent tensor-core
+// launch over a host-planned work list, both captured once in a CUDA graph
+// and replayed per run.  Each job is a whole integration (paper Sec. IV-C-1)
+// written to its own output; results are bit-identical to correlating each
+// job alone.
+//
+// Planning: every job gets its own region of one decode buffer and its own
+// TMA descriptor.  Its upper-triangle 128x128 tile pairs (per channel) become
+// work items; a tile whose integration is longer than `max_chunks` 128-sample
+// chunks is split along time into several items whose int32 results are added
+// with atomics (exact: integer addition is order-independent).  Items are
+// assigned to one persistent CTA per SM either longest-first onto the
+// least-loaded CTA (LPT) or round-robin in job order; each CTA then runs its
+// items in job/channel order so CTAs sweep the jobs together and operands stay
+// in L2.
+#include <algorithm>
+#include <cinttypes>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "../../include/xeng.h"
+#include "xeng_internal.h"
+
+using namespace xeng;
+
+struct xeng_batch_s {
+    std::vector<xeng_job_t> jobs;
+    xeng_batch_opts_t opts{};
+    int device = 0, num_sms = 0;
+    uint8_t *planes = nullptr;
+    int64_t planes_bytes = 0;
+    CUtensorMap *d_maps = nullptr;
+    JobDesc *d_jobs = nullptr;
+    WorkItem *d_items = nullptr;
+    int32_t *d_cta_begin = nullptr;
+    DecodeJob *d_dec = nullptr;
+    int64_t dec_ctas = 0;
+    int grid = 0;
+    int64_t n_items = 0;
+    double max_load = 0, mean_load = 0;
+    std::vector<std::pair<int32_t *, size_t>> zero_outs;  // outputs of split jobs, cleared each run
+    int *d_err = nullptr, *h_err = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int sticky = XENG_OK;
+};
+
+namespace {
+
+int status_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return XENG_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? XENG_ERR_NOMEM : XENG_ERR_CUDA;
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &v)
+{
+    const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_batch(xeng_batch_s *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->planes);
+    cudaFree(b->d_maps);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_cta_begin);
+    cudaFree(b->d_dec);
+    cudaFree(b->d_err);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    cudaGetLastError();
+    delete b;
+}
+
+// Enqueue one run: clear split outputs, decode all jobs, correlate all items.
+cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
+    for (auto &z : b->zero_outs)
+        if (e == cudaSuccess) e = cudaMemsetAsync(z.first, 0, z.second, s);
+    if (e == cudaSuccess) e = launch_decode_batch(b->d_dec, (int)b->jobs.size(), b->dec_ctas, s);
+    if (e == cudaSuccess) {
+        ListArgs L;
+        L.maps = b->d_maps;
+        L.jobs = b->d_jobs;
+        L.items = b->d_items;
+        L.cta_begin = b->d_cta_begin;
+        L.err = b->d_err;
+        e = launch_correlate_tc_listed(L, b->grid, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+int plan(xeng_batch_s *b)
+{
+    const int n = (int)b->jobs.size();
+    std::vector<int64_t> off(n), n_pad(n), t_pad(n);
+    int64_t total = 0;
+    for (int j = 0; j < n; j++) {
+        const xeng_job_t &jb = b->jobs[j];
+        n_pad[j] = round_up(jb.n_inputs, kTile);
+        t_pad[j] = round_up(jb.n_samples, kTile);
+        off[j] = total;
+        total += round_up((int64_t)jb.n_freq * 2 * n_pad[j] * t_pad[j], 1024);
+    }
+    b->planes_bytes = total;
+    cudaError_t e = cudaMalloc(&b->planes, (size_t)std::max<int64_t>(total, 1));
+    if (e != cudaSuccess) return status_of(e);
+
+    std::vector<CUtensorMap> maps(n);
+    std::vector<JobDesc> jd(n);
+    std::vector<DecodeJob> dj(n);
+    const int maxc = b->opts.max_chunks_per_item;
+    struct Cand { WorkItem w; double cost; int64_t order; };
+    std::vector<Cand> cand;
+    int64_t cta0 = 0;
+    for (int j = 0; j < n; j++) {
+        const xeng_job_t &jb = b->jobs[j];
+        uint8_t *pl = b->planes + off[j];
+        e = encode_planes_map(&maps[j], pl, t_pad[j], (int64_t)jb.n_freq * 2 * n_pad[j]);
+        if (e != cudaSuccess) return status_of(e);
+        const int n_k = (int)(t_pad[j] / kTile);
+        const int ns = (n_k + maxc - 1) / maxc;
+        jd[j].out = jb.out;
+        jd[j].n_pad = (int32_t)n_pad[j];
+        jd[j].N = jb.n_inputs;
+        jd[j].split = ns > 1 ? 1 : 0;
+        jd[j].pad_ = 0;
+        dj[j].block = jb.block;
+        dj[j].planes = pl;
+        dj[j].T = jb.n_samples;
+        dj[j].t_pad = t_pad[j];
+        dj[j].n_pad = n_pad[j];
+        dj[j].cta0 = cta0;
+        dj[j].F = jb.n_freq;
+        dj[j].N = jb.n_inputs;
+        dj[j].vec_ok = decode_vec_ok(jb.block, jb.n_inputs);
+        dj[j].pad_ = 0;
+        cta0 += decode_ctas(t_pad[j], n_pad[j], jb.n_freq);
+        if (ns > 1) b->zero_outs.push_back({jb.out, (size_t)jb.n_freq * n_baselines(jb.n_inputs) * 8});
+        const int nt = (int)(n_pad[j] / kTile);
+        for (int f = 0; f < jb.n_freq; f++)
+            for (int I = 0; I < nt; I++)
+                for (int J = I; J < nt; J++)
+                    for (int sp = 0; sp < ns; sp++) {
+                        Cand c;
+                        c.w.job = j;
+                        c.w.fl = f;
+                        c.w.I = (int16_t)I;
+                        c.w.J = (int16_t)J;
+                        c.w.kc0 = sp * maxc;
+                        c.w.kc1 = std::min(n_k, (sp + 1) * maxc);
+                        // MMA time per chunk, plus a fixed cost for the epilogue and pipeline fill
+                        c.cost = (double)(c.w.kc1 - c.w.kc0) + 2.0;
+                        c.order = (int64_t)cand.size();
+                        cand.push_back(c);
+                    }
+    }
+    b->dec_ctas = cta0;
+    b->n_items = (int64_t)cand.size();
+    if (cand.size() > 2147483647ull) return XENG_ERR_RANGE;
+
+    // assignment to persistent CTAs
+    const int P = (int)std::max<int64_t>(1, std::min<int64_t>(b->num_sms, (int64_t)cand.size()));
+    std::vector<std::vector<int64_t>> per(P);
+    std::vector<double> load(P, 0.0);
+    if (b->opts.policy == XENG_SCHED_ROUND_ROBIN) {
+        for (size_t k = 0; k < cand.size(); k++) {
+            per[k % P].push_back((int64_t)k);
+            load[k % P] += cand[k].cost;
+        }
+    } else {
+        std::vector<int64_t> idx(cand.size());
+        for (size_t k = 0; k < idx.size(); k++) idx[k] = (int64_t)k;
+        std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return cand[x].cost > cand[y].cost; });
+        typedef std::pair<double, int> LoadCta;
+        std::priority_queue<LoadCta, std::vector<LoadCta>, std::greater<LoadCta>> heap;
+        for (int c = 0; c < P; c++) heap.push({0.0, c});
+        for (int64_t k : idx) {
+            LoadCta t = heap.top();
+            heap.pop();
+            per[t.second].push_back(k);
+            t.first += cand[k].cost;
+            load[t.second] = t.first;
+            heap.push(t);
+        }
+        for (auto &v : per) std::sort(v.begin(), v.end());  // job / channel / tile order within a CTA
+    }
+    std::vector<WorkItem> items;
+    items.reserve(cand.size());
+    std::vector<int32_t> begin(P + 1, 0);
+    double sum = 0, mx = 0;
+    for (int c = 0; c < P; c++) {
+        begin[c] = (int32_t)items.size();
+        for (int64_t k : per[c]) items.push_back(cand[k].w);
+        sum += load[c];
+        mx = std::max(mx, load[c]);
+    }
+    begin[P] = (int32_t)items.size();
+    b->grid = cand.empty() ? 0 : P;
+    b->max_load = mx;
+    b->mean_load = P ? sum / P : 0;
+
+    e = upload(&b->d_maps, maps);
+    if (e == cudaSuccess) e = upload(&b->d_jobs, jd);
+    if (e == cudaSuccess) e = upload(&b->d_items, items);
+    if (e == cudaSuccess) e = upload(&b->d_cta_begin, begin);
+    if (e == cudaSuccess) e = upload(&b->d_dec, dj);
+    return status_of(e);
+}
+
+uint64_t batch_signature(const xeng_job_t *jobs, int n, int num_sms)
+{
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the jobs' shapes
+    auto mix = [&](uint64_t v) {
+        for (int k = 0; k < 8; k++) {
+            h ^= (v >> (8 * k)) & 0xFF;
+            h *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)num_sms);
+    for (int j = 0; j < n; j++) {
+        mix((uint64_t)jobs[j].n_inputs);
+        mix((uint64_t)jobs[j].n_freq);
+        mix((uint64_t)jobs[j].n_samples);
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_opts_t *opts, xeng_batch_t *out)
+{
+    if (!out || !jobs || n_jobs < 1) return XENG_ERR_ARG;
+    int dev = 0, major = 0, minor = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return XENG_ERR_UNSUPPORTED;
+    }
+    if (major != 10 || minor != 3) return XENG_ERR_UNSUPPORTED;
+    xeng_batch_opts_t o;
+    o.max_chunks_per_item = kMaxChunkSamples / kTile;
+    o.policy = XENG_SCHED_LPT;
+    o.use_graph = 1;
+    if (opts) {
+        o = *opts;
+        if (o.max_chunks_per_item <= 0 || o.max_chunks_per_item > kMaxChunkSamples / kTile)
+            o.max_chunks_per_item = kMaxChunkSamples / kTile;
+        if (o.policy != XENG_SCHED_LPT && o.policy != XENG_SCHED_ROUND_ROBIN) return XENG_ERR_ARG;
+    }
+    for (int j = 0; j < n_jobs; j++) {
+        const xeng_job_t &jb = jobs[j];
+        if (!jb.block || !jb.out) return XENG_ERR_ARG;
+        if (jb.n_inputs < 1 || jb.n_inputs > XENG_MAX_INPUTS || jb.n_freq < 1 || jb.n_samples < 1 ||
+            jb.n_samples > XENG_MAX_T_INTEG)
+            return XENG_ERR_RANGE;
+        if (!on_device(jb.block) || !on_device(jb.out)) return XENG_ERR_ARG;
+    }
+    xeng_batch_s *b = new (std::nothrow) xeng_batch_s;
+    if (!b) return XENG_ERR_NOMEM;
+    b->jobs.assign(jobs, jobs + n_jobs);
+    b->opts = o;
+    b->device = dev;
+    b->num_sms = sms;
+    int st = plan(b);
+    cudaError_t e = cudaSuccess;
+    if (st == XENG_OK) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (st == XENG_OK && e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(int));
+    if (st == XENG_OK && e == cudaSuccess) e = prepare_correlate_tc_listed();
+    if (st == XENG_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (st == XENG_OK && e == cudaSuccess && o.use_graph) {
+        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t er = enqueue_run(b, b->cap);
+            e = cudaStreamEndCapture(b->cap, &b->graph);
+            if (e == cudaSuccess) e = er;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    }
+    if (st == XENG_OK && e != cudaSuccess) st = status_of(e);
+    if (st != XENG_OK) {
+        free_batch(b);
+        return st;
+    }
+    *b->h_err = 0;
+    *out = b;
+    return XENG_OK;
+}
+
+int xeng_batch_run(xeng_batch_t b, void *stream)
+{
+    if (!b) return XENG_ERR_ARG;
+    if (b->sticky != XENG_OK) return b->sticky;
+    if (*(volatile int *)b->h_err != 0) return (b->sticky = XENG_ERR_TIMEOUT);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, s) : enqueue_run(b, s);
+    if (e != cudaSuccess) return (b->sticky = status_of(e));
+    return XENG_OK;
+}
+
+int xeng_batch_info(xeng_batch_t b, xeng_batch_info_t *info)
+{
+    if (!b || !info) return XENG_ERR_ARG;
+    info->n_jobs = (int32_t)b->jobs.size();
+    info->n_items = b->n_items;
+    info->grid = b->grid;
+    info->decode_ctas = b->dec_ctas;
+    info->planes_bytes = b->planes_bytes;
+    info->max_chunks_per_item = b->opts.max_chunks_per_item;
+    info->policy = b->opts.policy;
+    info->load_imbalance = b->mean_load > 0 ? b->max_load / b->mean_load : 1.0;
+    return XENG_OK;
+}
+
+void xeng_batch_destroy(xeng_batch_t b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    free_batch(b);
+}
+
+int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cache_path, int32_t reps,
+                        xeng_batch_opts_t *best, double *best_ms)
+{
+    if (!jobs || n_jobs < 1 || !best) return XENG_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return XENG_ERR_UNSUPPORTED;
+    }
+    const uint64_t sig = batch_signature(jobs, n_jobs, sms);
+    if (cache_path) {
+        FILE *fp = fopen(cache_path, "r");
+        if (fp) {
+            char line[256];
+            while (fgets(line, sizeof(line), fp)) {
+                unsigned long long s = 0;
+                int mc = 0, pol = 0;
+                double ms = 0;
+                if (sscanf(line, "%llx %d %d %lf", &s, &mc, &pol, &ms) == 4 && (uint64_t)s == sig) {
+                    best->max_chunks_per_item = mc;
+                    best->policy = pol;
+                    best->use_graph = 1;
+                    if (best_ms) *best_ms = ms;
+                    fclose(fp);
+                    return 1;  // from the cache
+                }
+            }
+            fclose(fp);
+        }
+    }
+    if (reps < 1) reps = 3;
+    const int chunks[] = {16, 32, 64, 128, 256, 512};
+    const int policies[] = {XENG_SCHED_LPT, XENG_SCHED_ROUND_ROBIN};
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return XENG_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_t = -1;
+    int st_all = XENG_ERR_CUDA;
+    for (int pol : policies)
+        for (int mc : chunks) {
+            xeng_batch_opts_t o;
+            o.max_chunks_per_item = mc;
+            o.policy = pol;
+            o.use_graph = 1;
+            xeng_batch_t b = nullptr;
+            if (xeng_batch_create(jobs, n_jobs, &o, &b) != XENG_OK) continue;
+            int st = xeng_batch_run(b, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == XENG_OK; r++) st = xeng_batch_run(b, s);
+            cudaEventRecord(e1, s);
+            float ms = 0;
+            if (st == XENG_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                *(volatile int *)b->h_err == 0) {
+                const double t = ms / reps;
+                if (best_t < 0 || t < best_t) {
+                    best_t = t;
+                    *best = o;
+                }
+                st_all = XENG_OK;
+            }
+            xeng_batch_destroy(b);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (st_all != XENG_OK) return st_all;
+    if (best_ms) *best_ms = best_t;
+    if (cache_path) {
+        FILE *fp = fopen(cache_path, "a");
+        if (fp) {
+            fprintf(fp, "%016llx %d %d %.6f\n", (unsigned long long)sig, best->max_chunks_per_item, best->policy, best_t);
+            fclose(fp);
+        }
+    }
+    return XENG_OK;
+}
+
+}  // extern "C"

@@ -28,6 +28,8 @@
 // Every wait is bounded: on time-out the thread records a status in the
 // error word, the others see it and leave their loops, the MMA thread drains
 // its tensor-core work and TMEM is freed before the CTA exits.
+#include <cstring>
+
 #include "xeng_internal.h"
 
 namespace xeng {
@@ -178,8 +180,56 @@ struct Sched {
     }
 };
 
+enum EpiMode : int { kStore = 0, kAdd = 1, kAtomicAdd = 2 };
+
+// One unit of work as every role of the CTA sees it.
+struct Work {
+    const CUtensorMap *map;
+    int32_t *out;    // channel 0 of the job's [F][B][2] triangle
+    int n_pad, N;
+    int fl, I, J;
+    int kc0, kc1;    // 128-sample chunks [kc0, kc1)
+    int mode;
+};
+
+template <bool kListed>
+__device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, const TcArgs &a, const Sched &sc, int n_k,
+                                           const ListArgs &L)
+{
+    Work w;
+    if (kListed) {
+        const WorkItem wi = L.items[it];
+        const JobDesc &jd = L.jobs[wi.job];
+        w.map = &L.maps[wi.job];
+        w.out = jd.out;
+        w.n_pad = jd.n_pad;
+        w.N = jd.N;
+        w.fl = wi.fl;
+        w.I = wi.I;
+        w.J = wi.J;
+        w.kc0 = wi.kc0;
+        w.kc1 = wi.kc1;
+        w.mode = jd.split ? kAtomicAdd : kStore;
+    } else {
+        w.map = tmap;
+        w.out = a.acc;
+        w.n_pad = a.n_pad;
+        w.N = a.N;
+        sc.decode(it, w.fl, w.I, w.J);
+        w.kc0 = 0;
+        w.kc1 = n_k;
+        w.mode = a.accumulate ? kAdd : kStore;
+    }
+    return w;
+}
+
+// Persistent CTA (one per SM).  Single-instance launches walk the tiles of
+// `sc` round-robin; listed launches (batches) walk items
+// [cta_begin[b], cta_begin[b + 1]) of a host-planned work list.
+template <bool kListed>
 __global__ void __launch_bounds__(kThreads, 1)
-correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, const Sched sc, const int n_k)
+correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, const Sched sc, const int n_k,
+                    const ListArgs L)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -193,7 +243,10 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * kNumBars - raw));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *err = a.err;
+    int *err = kListed ? L.err : a.err;
+    const int it_begin = kListed ? L.cta_begin[blockIdx.x] : (int)blockIdx.x;
+    const int it_end = kListed ? L.cta_begin[blockIdx.x + 1] : sc.n_tiles;
+    const int it_step = kListed ? 1 : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -206,7 +259,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
         }
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap) : "memory");
+        if (!kListed) asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -225,24 +278,23 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             uint32_t phase = 0;
             int issued = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < sc.n_tiles; tile += gridDim.x) {
-                int fl, I, J;
-                sc.decode(tile, fl, I, J);
-                const bool diag = (I == J);
-                const int rowA = fl * 2 * a.n_pad + I * kTile;
-                const int rowB = fl * 2 * a.n_pad + J * kTile;
-                for (int kc = 0; kc < n_k; kc++) {
+            for (int it = it_begin; ok && it < it_end; it += it_step) {
+                const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
+                const bool diag = (w.I == w.J);
+                const int rowA = w.fl * 2 * w.n_pad + w.I * kTile;
+                const int rowB = w.fl * 2 * w.n_pad + w.J * kTile;
+                for (int kc = w.kc0; kc < w.kc1; kc++) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
                         ok = false;
                         break;
                     }
                     const uint32_t st = sbase + stage * kStageBytes;
                     mbar_expect_tx(full_bar(stage), diag ? 2 * kPlaneTile : 4 * kPlaneTile);
-                    tma_load_2d(st, &tmap, kc * kTile, rowA, full_bar(stage));
-                    tma_load_2d(st + kPlaneTile, &tmap, kc * kTile, rowA + a.n_pad, full_bar(stage));
+                    tma_load_2d(st, w.map, kc * kTile, rowA, full_bar(stage));
+                    tma_load_2d(st + kPlaneTile, w.map, kc * kTile, rowA + w.n_pad, full_bar(stage));
                     if (!diag) {
-                        tma_load_2d(st + 2 * kPlaneTile, &tmap, kc * kTile, rowB, full_bar(stage));
-                        tma_load_2d(st + 3 * kPlaneTile, &tmap, kc * kTile, rowB + a.n_pad, full_bar(stage));
+                        tma_load_2d(st + 2 * kPlaneTile, w.map, kc * kTile, rowB, full_bar(stage));
+                        tma_load_2d(st + 3 * kPlaneTile, w.map, kc * kTile, rowB + w.n_pad, full_bar(stage));
                     }
                     ++issued;
                     if (++stage == kStages) {
@@ -268,16 +320,15 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             uint32_t uses[2] = {0, 0};
             bool ok = true;
             int local = 0;
-            for (int tile = blockIdx.x; ok && tile < sc.n_tiles; tile += gridDim.x, ++local) {
-                int fl, I, J;
-                sc.decode(tile, fl, I, J);
-                const bool diag = (I == J);
+            for (int it = it_begin; ok && it < it_end; it += it_step, ++local) {
+                const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
+                const bool diag = (w.I == w.J);
                 const int ab = local & 1;
                 if (!mbar_wait(acce_bar(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma)) break;
                 ++uses[ab];
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)ab * 256u;
-                for (int kc = 0; kc < n_k; kc++) {
+                for (int kc = w.kc0; kc < w.kc1; kc++) {
                     if (!mbar_wait(full_bar(stage), phase, err, kDevTimeoutMma)) {
                         ok = false;
                         break;
@@ -290,7 +341,8 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     #pragma unroll
                     for (int kk = 0; kk < 4; kk++) {
                         const uint32_t off = kk * 32;
-                        mma_f8(d, sw128_desc(a_re + off), sw128_desc(b_re + off), kIdescN256, (kc | kk) != 0);
+                        mma_f8(d, sw128_desc(a_re + off), sw128_desc(b_re + off), kIdescN256,
+                               (kc != w.kc0 || kk != 0) ? 1u : 0u);
                         mma_f8(d, sw128_desc(a_im + off), sw128_desc(b_im + off), kIdescN128, 1u);
                         mma_f8(d + 128u, sw128_desc(a_im + off), sw128_desc(b_re + off), kIdescN128Neg, 1u);
                     }
@@ -313,23 +365,21 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
         const int row = q * 32 + lane;
         uint32_t uses[2] = {0, 0};
         int local = 0;
-        const int64_t N = a.N;
-        const int64_t nb2 = N * (N + 1);  // int32 words per channel (2 per baseline)
-        for (int tile = blockIdx.x; tile < sc.n_tiles; tile += gridDim.x, ++local) {
-            int fl, I, J;
-            sc.decode(tile, fl, I, J);
+        for (int it = it_begin; it < it_end; it += it_step, ++local) {
+            const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
             const int ab = local & 1;
             const bool ok = mbar_wait(accf_bar(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue);
             if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
             ++uses[ab];
             fence_after();
-            const int64_t i = (int64_t)I * kTile + row;
+            const int64_t N = w.N;
+            const int64_t i = (int64_t)w.I * kTile + row;
             const bool row_ok = i < N;
             // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle
             const int64_t row_base = i * N - i * (i - 1) / 2 - i;
-            int2 *out = reinterpret_cast<int2 *>(a.acc + (int64_t)fl * nb2);
+            int2 *out = reinterpret_cast<int2 *>(w.out + (int64_t)w.fl * N * (N + 1));
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u;
-            const int64_t jbase = (int64_t)J * kTile;
+            const int64_t jbase = (int64_t)w.J * kTile;
             for (int c = 0; c < kTile; c += 16) {
                 uint32_t re[16], nim[16];
                 tmem_ld16(taddr + c, re);
@@ -343,11 +393,14 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                             const int vr = __float2int_rn(__uint_as_float(re[e]));
                             const int vi = -__float2int_rn(__uint_as_float(nim[e]));
                             int2 *p = out + row_base + j;
-                            if (a.accumulate) {
+                            if (w.mode == kStore) {
+                                *p = make_int2(vr, vi);
+                            } else if (w.mode == kAdd) {
                                 int2 o = *p;
                                 *p = make_int2(o.x + vr, o.y + vi);
                             } else {
-                                *p = make_int2(vr, vi);
+                                atomicAdd(&p->x, vr);
+                                atomicAdd(&p->y, vi);
                             }
                         }
                     }
@@ -405,7 +458,7 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
                                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(correlate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(correlate_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     Sched sc;
@@ -413,7 +466,38 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
     sc.tiles_per_ch = sc.nt * (sc.nt + 1) / 2;
     sc.n_tiles = a.nf * sc.tiles_per_ch;
     const int grid = sc.n_tiles < num_sms ? sc.n_tiles : num_sms;
-    correlate_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kTile));
+    correlate_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kTile), ListArgs{});
+    return cudaGetLastError();
+}
+
+cudaError_t encode_planes_map(CUtensorMap *map, const uint8_t *planes, int64_t t_pad, int64_t rows)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)t_pad, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)t_pad};
+    const cuuint32_t box[2] = {kTile, kTile};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)planes, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_correlate_tc_listed()
+{
+    return cudaFuncSetAttribute(correlate_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes);
+}
+
+cudaError_t launch_correlate_tc_listed(const ListArgs &L, int grid, cudaStream_t s)
+{
+    if (grid <= 0) return cudaSuccess;
+    CUtensorMap unused;
+    memset(&unused, 0, sizeof(unused));
+    TcArgs a{};
+    Sched sc{};
+    correlate_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(unused, a, sc, 0, L);
     return cudaGetLastError();
 }
 

@@ -53,12 +53,11 @@ __device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &
     im = __byte_perm(i02, i13, 0x5140);
 }
 
-__global__ void __launch_bounds__(kDecThreads)
-decode_kernel(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N, int32_t f0,
-              uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int vec_ok)
+// Decode one 128-sample x 128-input tile (tb, ib) of channel f0 + fl.
+__device__ __forceinline__ void decode_tile(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N,
+                                            int32_t f0, uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad,
+                                            int vec_ok, int tb, int ib, int fl, uint32_t *tile)
 {
-    __shared__ uint32_t tile[kTileWords];
-    const int tb = blockIdx.x, ib = blockIdx.y, fl = blockIdx.z;
     const int64_t t0 = (int64_t)tb * 128;
     const int i0 = ib * 128;
     const int64_t f = f0 + fl;
@@ -124,15 +123,58 @@ decode_kernel(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N
     }
 }
 
+__global__ void __launch_bounds__(kDecThreads)
+decode_kernel(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N, int32_t f0,
+              uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int vec_ok)
+{
+    __shared__ uint32_t tile[kTileWords];
+    decode_tile(block, T, F, N, f0, planes, t_pad, n_pad, vec_ok, blockIdx.x, blockIdx.y, blockIdx.z, tile);
+}
+
+// All jobs of a batch in one launch: CTA b belongs to the job j with
+// cta0[j] <= b < cta0[j + 1] and takes that job's tile b - cta0[j].
+__global__ void __launch_bounds__(kDecThreads)
+decode_batch_kernel(const DecodeJob *__restrict__ jobs, int n_jobs)
+{
+    __shared__ uint32_t tile[kTileWords];
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {  // last job whose first CTA is <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].cta0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const DecodeJob &j = jobs[lo];
+    const int64_t local = b - j.cta0;
+    const int64_t ntb = j.t_pad / 128, nib = j.n_pad / 128;
+    const int tb = (int)(local % ntb);
+    const int ib = (int)((local / ntb) % nib);
+    const int fl = (int)(local / (ntb * nib));
+    decode_tile(j.block, j.T, j.F, j.N, 0, j.planes, j.t_pad, j.n_pad, j.vec_ok, tb, ib, fl, tile);
+}
+
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0,
                           int32_t nf, uint8_t *planes, int64_t t_pad, int64_t n_pad, cudaStream_t s)
 {
     if (nf <= 0 || t_pad <= 0) return cudaSuccess;
-    const int vec_ok = ((reinterpret_cast<uintptr_t>(block) & 15) == 0) && (N % 16 == 0);
+    const int vec_ok = decode_vec_ok(block, N);
     dim3 grid((unsigned)(t_pad / 128), (unsigned)(n_pad / 128), (unsigned)nf);
     decode_kernel<<<grid, kDecThreads, 0, s>>>(block, T, F, N, f0, planes, t_pad, n_pad, vec_ok);
+    return cudaGetLastError();
+}
+
+int decode_vec_ok(const uint8_t *block, int32_t N)
+{
+    return ((reinterpret_cast<uintptr_t>(block) & 15) == 0) && (N % 16 == 0);
+}
+
+cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s)
+{
+    if (n_jobs <= 0 || total_ctas <= 0) return cudaSuccess;
+    if (total_ctas > 2147483647LL) return cudaErrorInvalidValue;
+    decode_batch_kernel<<<(unsigned)total_ctas, kDecThreads, 0, s>>>(jobs, n_jobs);
     return cudaGetLastError();
 }
 

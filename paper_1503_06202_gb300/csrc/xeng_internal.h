@@ -25,6 +25,21 @@ cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N,
                           int32_t f0, int32_t nf, uint8_t *planes, int64_t t_pad,
                           int64_t n_pad, cudaStream_t s);
 
+// Batched decode: one launch over the tiles of several blocks.
+struct DecodeJob {
+    const uint8_t *block;  // [T][F][N]
+    uint8_t *planes;       // [F][2][n_pad][t_pad]
+    int64_t T, t_pad, n_pad;
+    int64_t cta0;          // first CTA of this job in the launch
+    int32_t F, N;
+    int32_t vec_ok;        // 16-byte loads allowed (see decode_vec_ok)
+    int32_t pad_;
+};
+int decode_vec_ok(const uint8_t *block, int32_t N);
+// CTAs one job takes in a batched decode launch.
+inline int64_t decode_ctas(int64_t t_pad, int64_t n_pad, int64_t F) { return (t_pad / 128) * (n_pad / 128) * F; }
+cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s);
+
 // Tensor-core correlation of decoded planes (tcgen05, FP8 E4M3, f32 in TMEM).
 // acc: int32 [nf][N(N+1)/2][2] of the channel group; accumulate = add to it.
 struct TcArgs {
@@ -38,6 +53,31 @@ struct TcArgs {
     int32_t *err;
 };
 cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s);
+
+// Batched (listed) launches: a job table, per-job tensor maps and a work list
+// partitioned by CTA, all in device memory.
+struct JobDesc {
+    int32_t *out;      // [F][N(N+1)/2][2] int32 of the job
+    int32_t n_pad;     // inputs rounded up to 128
+    int32_t N;
+    int32_t split;     // != 0: several items share a tile; the epilogue adds atomically
+    int32_t pad_;
+};
+struct WorkItem {
+    int32_t job, fl;   // job index, channel within the job
+    int16_t I, J;      // 128-input tile pair, I <= J
+    int32_t kc0, kc1;  // 128-sample chunks [kc0, kc1), at most kMaxChunkSamples / 128 of them
+};
+struct ListArgs {
+    const CUtensorMap *maps;   // [n_jobs], 64-byte aligned
+    const JobDesc *jobs;       // [n_jobs]
+    const WorkItem *items;     // [n_items]
+    const int32_t *cta_begin;  // [grid + 1]: CTA b runs items [cta_begin[b], cta_begin[b + 1])
+    int32_t *err;              // device status word
+};
+cudaError_t encode_planes_map(CUtensorMap *map, const uint8_t *planes, int64_t t_pad, int64_t rows);
+cudaError_t prepare_correlate_tc_listed();  // kernel attributes; call before any stream capture
+cudaError_t launch_correlate_tc_listed(const ListArgs &L, int grid, cudaStream_t s);
 
 // Plain CUDA-core correlation straight from the bytes (dp4a, int32).
 cudaError_t launch_correlate_dp4a(const uint8_t *block, int64_t T, int32_t F, int32_t N,

@@ -235,3 +235,131 @@ def xeng_peak_probe(kind: int, iters: int):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     rc = L.xeng_peak_probe(kind, iters, ctypes.byref(tf), ctypes.byref(ms))
     return rc, tf.value, ms.value
+
+
+# ------------------------------------------------------------------ batches --
+
+XENG_SCHED_LPT = 0
+XENG_SCHED_ROUND_ROBIN = 1
+
+
+class XengJob(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int32), ("n_freq", ctypes.c_int32), ("n_samples", ctypes.c_int64),
+                ("block", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class XengBatchOpts(ctypes.Structure):
+    _fields_ = [("max_chunks_per_item", ctypes.c_int32), ("policy", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class XengBatchInfo(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_int32), ("n_items", ctypes.c_int64), ("grid", ctypes.c_int32),
+                ("decode_ctas", ctypes.c_int64), ("planes_bytes", ctypes.c_int64),
+                ("max_chunks_per_item", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("load_imbalance", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_typed", False):
+        vp, i32 = ctypes.c_void_p, ctypes.c_int32
+        L.xeng_batch_create.argtypes = [ctypes.POINTER(XengJob), i32, ctypes.POINTER(XengBatchOpts), ctypes.POINTER(vp)]
+        L.xeng_batch_create.restype = ctypes.c_int
+        L.xeng_batch_run.argtypes = [vp, vp]
+        L.xeng_batch_run.restype = ctypes.c_int
+        L.xeng_batch_info.argtypes = [vp, ctypes.POINTER(XengBatchInfo)]
+        L.xeng_batch_info.restype = ctypes.c_int
+        L.xeng_batch_destroy.argtypes = [vp]
+        L.xeng_batch_destroy.restype = None
+        L.xeng_batch_autotune.argtypes = [ctypes.POINTER(XengJob), i32, ctypes.c_char_p, i32,
+                                          ctypes.POINTER(XengBatchOpts), ctypes.POINTER(ctypes.c_double)]
+        L.xeng_batch_autotune.restype = ctypes.c_int
+        L._batch_typed = True
+    return L
+
+
+def _jobs_array(jobs):
+    """jobs: iterable of (block, out) pairs of tensors or (N, F, T, block, out) tuples."""
+    arr = (XengJob * len(jobs))()
+    for k, jb in enumerate(jobs):
+        if len(jb) == 2:
+            block, out = jb
+            T, F, N = block.shape
+        else:
+            N, F, T, block, out = jb
+        arr[k] = XengJob(N, F, T, _ptr(block), _ptr(out))
+    return arr
+
+
+def _opts(max_chunks_per_item=0, policy=XENG_SCHED_LPT, use_graph=True):
+    return XengBatchOpts(max_chunks_per_item, policy, 1 if use_graph else 0)
+
+
+def xeng_batch_create(jobs, opts=None):
+    """Returns (status, batch handle)."""
+    arr = _jobs_array(jobs)
+    h = ctypes.c_void_p()
+    rc = _batch_lib().xeng_batch_create(arr, len(arr), ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return rc, (h.value if rc == XENG_OK else None)
+
+
+def xeng_batch_run(b, stream=None) -> int:
+    return _batch_lib().xeng_batch_run(b, _stream(stream))
+
+
+def xeng_batch_info(b):
+    info = XengBatchInfo()
+    rc = _batch_lib().xeng_batch_info(b, ctypes.byref(info))
+    return rc, info.as_dict()
+
+
+def xeng_batch_destroy(b) -> None:
+    _batch_lib().xeng_batch_destroy(b)
+
+
+def xeng_batch_autotune(jobs, cache_path=None, reps: int = 3):
+    """Returns (status, opts, ms per run); status 1 = answered from the cache."""
+    arr = _jobs_array(jobs)
+    best = XengBatchOpts()
+    ms = ctypes.c_double()
+    rc = _batch_lib().xeng_batch_autotune(arr, len(arr), cache_path.encode() if cache_path else None, reps,
+                                          ctypes.byref(best), ctypes.byref(ms))
+    return rc, best, ms.value
+
+
+class XBatch:
+    """Owning wrapper of a planned batch (xeng_batch_*)."""
+
+    def __init__(self, jobs, opts: XengBatchOpts | None = None):
+        rc, b = xeng_batch_create(jobs, opts)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_batch_create")
+        self.b = b
+
+    def run(self, stream=None) -> None:
+        rc = xeng_batch_run(self.b, stream)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_batch_run")
+
+    def info(self) -> dict:
+        rc, d = xeng_batch_info(self.b)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_batch_info")
+        return d
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            xeng_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -181,3 +181,22 @@ CHIME_FULL = Recipe("sky", T=8192, F=1024, N=2048, seed=2)
 # 16 channels of the full-CHIME shape: inputs (256 MiB) still exceed L2 while
 # the whole working set stays near 1.3 GB -- the profiling case.
 CHIME_SLICE = Recipe("sky", T=8192, F=16, N=2048, seed=2)
+
+
+BATCH_N = (64, 96, 128, 200, 256, 512, 1024, 2048)
+BATCH_F = (1, 16, 64)
+
+
+def batched_jobs(seed: int = 3, n_jobs: int = 64, t_min: int = 1024, t_max: int = 32768, t_step: int = 256):
+    """The batched workload: n_jobs independent uniform-nibble blocks, each with
+    N drawn from BATCH_N, F from BATCH_F and T log-uniform on [t_min, t_max]
+    rounded to a multiple of t_step; job j uses sub-stream j of `seed`."""
+    jobs = []
+    for j in range(n_jobs):
+        u = [key(seed, 1_000_000 + 3 * j + k) / 2.0 ** 64 for k in range(3)]
+        N = BATCH_N[min(int(u[0] * len(BATCH_N)), len(BATCH_N) - 1)]
+        F = BATCH_F[min(int(u[1] * len(BATCH_F)), len(BATCH_F) - 1)]
+        T = math.exp(math.log(t_min) + u[2] * (math.log(t_max) - math.log(t_min)))
+        T = int(min(t_max, max(t_min, round(T / t_step) * t_step)))
+        jobs.append(Recipe("uniform", T=T, F=F, N=N, seed=seed, stream=j))
+    return jobs
