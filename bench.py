@@ -32,6 +32,8 @@ WORKLOADS = {
     "pathfinder_small": ("PATHFINDER_SMALL", "Pathfinder-shaped small: N=256, 8 channels, T=4096, uniform nibbles"),
     "chime_slice": ("CHIME_SLICE", "16 channels of the full-CHIME shape (N=2048, T=8192): profiling case"),
     "batched": (None, "64 independent jobs, N in {64..2048}, F in {1,16,64}, T log-uniform 1024..32768, uniform nibbles"),
+    "serving": (None, "8 concurrent streams (3 x N=256, 3 x N=512, 2 x N=2048), 256 channels each, 256-sample blocks, "
+                      "Poisson arrivals at r x real time, dumps every 65536 samples"),
 }
 METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)"
 
@@ -39,7 +41,7 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 # one ncu capture of the 16-channel slice of the same (N, T) shape; traffic
 # grows in proportion to channels.  Keyed by (N, T); must be re-taken (or
 # removed) whenever the kernel changes.
-CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (643.938560e6 + 242.520064e6) / 16}
+CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (594.477568e6 + 238.902272e6) / 16}
 
 
 def useful_ops(T, F, N):
@@ -189,7 +191,10 @@ def run_batched(args, rank, world, local_rank):
     ops = sum(useful_ops(r.T, r.F, r.N) for r in recipes)
     cache = os.path.join(tempfile.gettempdir(), "xeng_batch_tune.txt")
     t0 = time.perf_counter()
-    rc, opts, tuned_ms = xe.xeng_batch_autotune(jobs, cache, reps=2)
+    if args.batch_max_chunks > 0:  # a fixed plan (profiling runs), no tuning
+        rc, opts, tuned_ms = 2, xe.xeng._opts(args.batch_max_chunks, args.batch_policy, True), None
+    else:
+        rc, opts, tuned_ms = xe.xeng_batch_autotune(jobs, cache, reps=2)
     tune_s = time.perf_counter() - t0
     if rc < 0:
         raise RuntimeError("autotune failed: %s" % xe.xeng_strerror(rc))
@@ -225,7 +230,7 @@ def run_batched(args, rank, world, local_rank):
             e_.close()
         return t
     per_tc_ms = per_job(xe.XENG_ENGINE_TENSOR, 3)
-    per_dp4a_ms = per_job(xe.XENG_ENGINE_DP4A, 1)
+    per_dp4a_ms = per_job(xe.XENG_ENGINE_DP4A, 1) if not args.no_per_job_dp4a else float("nan")
     b.close()
     peaks, peak_src = load_peaks()
     value = ops / (ms * 1e-3) / 1e12
@@ -237,7 +242,8 @@ def run_batched(args, rank, world, local_rank):
                        "l2": "inputs (%.1f GB) larger than L2; no flush" % (sum(r.nbytes for r in recipes) / 1e9)},
             "step_call": "xeng_batch_run (CUDA graph: 1 decode + 1 persistent tensor-core launch)",
             "gpu_launches": 2 * args.steps,
-            "autotune": {"opts": opts.as_dict(), "tuned_ms": tuned_ms, "from_cache": rc == 1, "tune_s": tune_s},
+            "autotune": {"opts": opts.as_dict(), "tuned_ms": tuned_ms, "from_cache": rc == 1, "fixed": rc == 2,
+                         "tune_s": tune_s},
             "plan": info,
             "per_job_tensor": {"ms": per_tc_ms, "tops": ops / (per_tc_ms * 1e-3) / 1e12, "launches": 2 * len(recipes)},
             "per_job_dp4a": {"ms": per_dp4a_ms, "tops": ops / (per_dp4a_ms * 1e-3) / 1e12, "launches": len(recipes)},
@@ -247,6 +253,116 @@ def run_batched(args, rank, world, local_rank):
                          "frac": value / (2.0 * peaks["bf16_tflops_sustained"]), "traffic": None,
                          "note": "whole batched run, useful ops; peak = 2 x %s sustained bf16" % peak_src},
             "clocks": clocks, "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args, rank, world, local_rank):
+    """The streaming workload through the xserve_* service: Poisson block
+    arrivals at r x the real-time rate per stream, continuous batching, dumps
+    every 65536 samples; sustained TOPS and latency percentiles per rate,
+    against one plain xeng_push per block."""
+    import threading
+    import numpy as np
+    import torch
+    import synth
+    import paper_1503_06202_gb300 as xe
+
+    torch.cuda.set_device(local_rank)
+    BS, DUMP, POOL = 256, 65536, 16
+    real_rate = 1.0 / (BS * 2.56e-6)  # blocks per second per stream at the 2.56 us sample period
+    shapes = [(256, 256)] * 3 + [(512, 256)] * 3 + [(2048, 256)] * 2
+    pools = []
+    for k, (N, F) in enumerate(shapes):
+        pools.append([synth.Recipe("uniform", T=BS, F=F, N=N, seed=4, stream=k * POOL + b).device() for b in range(POOL)])
+    torch.cuda.synchronize()
+    demand = [8.0 * BS * F * N * (N + 1) / 2 * real_rate / 1e12 for N, F in shapes]
+    results = []
+    rng = np.random.default_rng(5)
+    for rate in args.serve_rates:
+        rc, sv = xe.xserve_create(hbm_budget_bytes=120 << 30, max_blocks=args.serve_max_blocks, max_streams=16)
+        if rc != xe.XENG_OK:
+            raise RuntimeError("xserve_create: " + xe.xeng_strerror(rc))
+        ids = []
+        for (N, F) in shapes:
+            rc, sid = xe.xserve_open_stream(sv, N, F, BS, DUMP, rate * real_rate)
+            if rc != xe.XENG_OK:
+                raise RuntimeError("admission refused: " + xe.xeng_strerror(rc))
+            ids.append(sid)
+        outs = [torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda") for N, F in shapes]
+        events = []
+        for k in range(len(shapes)):
+            t = rng.exponential(1.0 / (rate * real_rate))
+            while t < args.serve_seconds:
+                events.append((t, k))
+                t += rng.exponential(1.0 / (rate * real_rate))
+        events.sort()
+        stop = threading.Event()
+        dumps = [0] * len(shapes)
+
+        def poller():
+            while not stop.is_set():
+                got = False
+                for k in range(len(shapes)):
+                    r_, _ = xe.xserve_poll_dump(sv, ids[k], outs[k])
+                    if r_ == 1:
+                        dumps[k] += 1
+                        got = True
+                if not got:
+                    time.sleep(5e-4)
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        n_sub = [0] * len(shapes)
+        t0 = xe.xserve_now()
+        for t, k in events:
+            while xe.xserve_now() - t0 < t:
+                pass
+            xe.xserve_submit(sv, ids[k], pools[k][n_sub[k] % POOL], 0.0)
+            n_sub[k] += 1
+        t_arr = xe.xserve_now() - t0
+        _, st_end = xe.xserve_stats(sv)
+        xe.xserve_drain(sv, 600.0)
+        time.sleep(0.05)
+        stop.set()
+        th.join()
+        rc, st = xe.xserve_stats(sv)
+        xe.xserve_destroy(sv)
+        results.append({"rate": rate, "offered_tops": rate * sum(demand), "arrival_window_s": t_arr,
+                        "blocks": sum(n_sub), "sustained_tops": st["useful_ops"] / st["busy_s"] / 1e12,
+                        "busy_s": st["busy_s"], "rounds": st["rounds"], "dumps": st["dumps_done"],
+                        "backlog_blocks_at_end_of_arrivals": st_end["backlog_blocks"],
+                        "block_latency_p50_ms": st["block_p50_s"] * 1e3, "block_latency_p99_ms": st["block_p99_s"] * 1e3,
+                        "dump_latency_p50_ms": st["dump_p50_s"] * 1e3, "dump_latency_p99_ms": st["dump_p99_s"] * 1e3,
+                        "gpu_decode_ms": st["gpu_decode_ms"], "gpu_correlate_ms": st["gpu_correlate_ms"],
+                        "host_plan_ms": st["host_plan_ms"]})
+        del outs
+
+    # plain comparison: one xeng_push per block, streams round-robin, closed loop
+    engs = [xe.XEngine(N, F, DUMP) for N, F in shapes]
+    nblk = 32
+    for e_, pool in zip(engs, pools):
+        e_.push(pool[0], BS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(nblk):
+        for e_, pool in zip(engs, pools):
+            e_.push(pool[b % POOL], BS)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_tops = nblk * sum(8.0 * BS * F * N * (N + 1) / 2 for N, F in shapes) / plain_s / 1e12
+    for e_ in engs:
+        e_.close()
+    head = results[0]
+    line = {"metric": METRIC, "value": head["sustained_tops"], "unit": "TOPS", "n_gpus": world, "steps": len(results),
+            "warmup": 0, "ms_per_step": head["busy_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)", "data": "synthetic (seeded on-device block pools)",
+            "config": {"workload": "serving", "description": WORKLOADS["serving"][1],
+                       "streams": ["N=%d F=%d" % sh for sh in shapes], "block_samples": BS, "dump_samples": DUMP,
+                       "max_blocks_per_round": args.serve_max_blocks, "arrival_seconds": args.serve_seconds,
+                       "real_time_blocks_per_s": real_rate, "real_time_demand_tops": sum(demand)},
+            "per_rate": results, "plain_per_block_push_tops": plain_tops,
+            "speedup_vs_plain_per_block": head["sustained_tops"] / plain_tops,
+            "e2e": None, "cpu_baseline": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -263,6 +379,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the dense-throughput probes")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
+    ap.add_argument("--serve-seconds", type=float, default=1.5)
+    ap.add_argument("--serve-max-blocks", type=int, default=16)
+    ap.add_argument("--batch-max-chunks", type=int, default=0, help="fixed batch plan instead of autotuning")
+    ap.add_argument("--batch-policy", type=int, default=1)
+    ap.add_argument("--no-per-job-dp4a", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -275,6 +397,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local_rank)
         return
 
     import torch

@@ -234,6 +234,98 @@ XENG_API void xeng_batch_destroy(xeng_batch_t b);
 XENG_API int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cache_path, int32_t reps,
                                  xeng_batch_opts_t *best, double *best_ms);
 
+/*
+ * Streaming service: frame blocks from many concurrent streams, integrated
+ * continuously into device-resident accumulators (Sec. IV-A data flow,
+ * Sec. IV-C-1 integration) and dumped on a fixed cadence.  A worker thread
+ * batches whatever blocks are queued across all streams into each round (one
+ * decode launch + one persistent tensor-core launch), with up to two rounds in
+ * flight; blocks that arrive meanwhile join the next round.  Streams are
+ * admitted against an HBM budget (accumulators, two dump buffers and two
+ * decode slices each) and, optionally, a compute budget; closing a stream
+ * frees its share for later admissions.  Results are bit-identical to
+ * integrating each stream alone.
+ */
+typedef struct xserve_s *xserve_t;
+
+typedef struct {
+    int64_t hbm_budget_bytes;    /* device memory streams may hold (default 120 GiB)             */
+    int32_t max_blocks;          /* blocks of one stream per round (default 16)                  */
+    int32_t max_streams;         /* stream slots (default 16)                                    */
+    int64_t max_items;           /* tile pairs one round may hold (default 4 Mi)                  */
+    double  compute_budget_tops; /* > 0: also refuse streams whose declared demand exceeds it     */
+} xserve_opts_t;
+
+typedef struct {
+    int64_t seq;                 /* integration number of the stream (0, 1, ...)                  */
+    int64_t samples;             /* samples integrated (= dump_samples)                           */
+    double  last_arrival_s;      /* arrival time of the integration's last block (xserve_now clock) */
+    double  ready_s;             /* time the dump was seen complete                               */
+} xserve_dump_info_t;
+
+typedef struct {
+    int64_t rounds, blocks_done, dumps_done, refused, backlog_blocks, used_bytes;
+    int32_t open_streams, pad_;
+    double  useful_ops;          /* 8 ops per complex MAC over all integrated blocks             */
+    double  busy_s;              /* first arrival -> last completed round                         */
+    double  block_p50_s, block_p99_s;  /* block arrival -> its round complete                     */
+    double  dump_p50_s, dump_p99_s;    /* last block of an integration -> dump available          */
+    double  gpu_decode_ms, gpu_correlate_ms;  /* summed device time of the rounds' two launches   */
+    double  host_plan_ms;                     /* summed host time spent building rounds           */
+} xserve_stats_t;
+
+/* xserve_now -- the server's clock (seconds, monotonic) for arrival stamps. */
+XENG_API double xserve_now(void);
+
+/* xserve_create -- start a server and its worker thread on the current device;
+ *   opts may be NULL for the defaults. */
+XENG_API int xserve_create(const xserve_opts_t *opts, xserve_t *out);
+
+/*
+ * xserve_open_stream -- admit a stream of n_inputs x n_freq blocks of
+ *   block_samples samples, dumped every dump_samples samples (a multiple of
+ *   block_samples, <= XENG_MAX_T_INTEG; block_samples rounded up to 128 times
+ *   max_blocks must be <= 65536).  rate_blocks_per_s is the declared arrival
+ *   rate, used only by the compute budget.  Returns XENG_ERR_NOMEM when the
+ *   budget (or a slot) is not available now -- retry after another stream
+ *   closes -- and sets *stream_id on success.
+ */
+XENG_API int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t block_samples,
+                                int64_t dump_samples, double rate_blocks_per_s, int32_t *stream_id);
+
+/*
+ * xserve_submit -- queue one block ([block_samples][F][N] bytes, device
+ *   memory) that arrived at arrival_s (xserve_now clock; <= 0 = now).  Never
+ *   waits for the GPU.  The caller keeps the block unchanged until
+ *   xserve_consumed reports it (blocks of a stream are consumed in order).
+ */
+XENG_API int xserve_submit(xserve_t sv, int32_t stream_id, const uint8_t *block, double arrival_s);
+
+/* xserve_consumed -- blocks of the stream whose round has completed. */
+XENG_API int64_t xserve_consumed(xserve_t sv, int32_t stream_id);
+
+/*
+ * xserve_poll_dump -- if the stream's oldest finished integration is ready,
+ *   copy its [F][N(N+1)/2][2] int32 triangle to out (host or device memory),
+ *   fill *info (may be NULL) and return 1; else return 0.  A stream whose two
+ *   dump buffers are both full waits for its dumps to be taken.
+ */
+XENG_API int xserve_poll_dump(xserve_t sv, int32_t stream_id, int32_t *out, xserve_dump_info_t *info);
+
+/* xserve_drain -- wait (up to timeout_s; <= 0 = no limit) until every queued
+ *   block that can run has been integrated. */
+XENG_API int xserve_drain(xserve_t sv, double timeout_s);
+
+/* xserve_close_stream -- drop its queued blocks, wait for its rounds in
+ *   flight, free its device memory and budget. */
+XENG_API int xserve_close_stream(xserve_t sv, int32_t stream_id);
+
+/* xserve_stats -- counters and latency percentiles so far. */
+XENG_API int xserve_stats(xserve_t sv, xserve_stats_t *out);
+
+/* xserve_destroy -- stop the worker (queued blocks are dropped) and free everything. */
+XENG_API void xserve_destroy(xserve_t sv);
+
 /* Size of the fixed device array xeng_correlate_noalloc works in (64 MiB). */
 #define XENG_NOALLOC_SCRATCH_BYTES 67108864LL
 

@@ -110,6 +110,7 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
         L.items = b->d_items;
         L.cta_begin = b->d_cta_begin;
         L.err = b->d_err;
+        L.n_items = b->n_items;
         e = launch_correlate_tc_listed(L, b->grid, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -149,12 +150,13 @@ int plan(xeng_batch_s *b)
         jd[j].out = jb.out;
         jd[j].n_pad = (int32_t)n_pad[j];
         jd[j].N = jb.n_inputs;
-        jd[j].split = ns > 1 ? 1 : 0;
+        jd[j].mode = ns > 1 ? 2 : 0;  // split tiles add atomically into zeroed outputs
         jd[j].pad_ = 0;
         dj[j].block = jb.block;
         dj[j].planes = pl;
         dj[j].T = jb.n_samples;
         dj[j].t_pad = t_pad[j];
+        dj[j].pitch = t_pad[j];
         dj[j].n_pad = n_pad[j];
         dj[j].cta0 = cta0;
         dj[j].F = jb.n_freq;

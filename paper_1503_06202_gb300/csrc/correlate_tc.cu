@@ -209,7 +209,7 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
         w.J = wi.J;
         w.kc0 = wi.kc0;
         w.kc1 = wi.kc1;
-        w.mode = jd.split ? kAtomicAdd : kStore;
+        w.mode = jd.mode;
     } else {
         w.map = tmap;
         w.out = a.acc;
@@ -244,9 +244,10 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = kListed ? L.err : a.err;
-    const int it_begin = kListed ? L.cta_begin[blockIdx.x] : (int)blockIdx.x;
-    const int it_end = kListed ? L.cta_begin[blockIdx.x + 1] : sc.n_tiles;
-    const int it_step = kListed ? 1 : (int)gridDim.x;
+    const bool strided = !kListed || L.cta_begin == nullptr;
+    const int it_begin = strided ? (int)blockIdx.x : L.cta_begin[blockIdx.x];
+    const int it_end = !kListed ? sc.n_tiles : (strided ? (int)L.n_items : L.cta_begin[blockIdx.x + 1]);
+    const int it_step = strided ? (int)gridDim.x : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -386,23 +387,33 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                 tmem_ld16(taddr + 128 + c, nim);
                 tmem_ld_wait();
                 if (row_ok) {
-                    #pragma unroll
-                    for (int e = 0; e < 16; e++) {
-                        const int64_t j = jbase + c + e;
-                        if (j >= i && j < N) {
-                            const int vr = __float2int_rn(__uint_as_float(re[e]));
-                            const int vi = -__float2int_rn(__uint_as_float(nim[e]));
-                            int2 *p = out + row_base + j;
-                            if (w.mode == kStore) {
-                                *p = make_int2(vr, vi);
-                            } else if (w.mode == kAdd) {
-                                int2 o = *p;
-                                *p = make_int2(o.x + vr, o.y + vi);
-                            } else {
-                                atomicAdd(&p->x, vr);
-                                atomicAdd(&p->y, vi);
+                    int2 *p = out + row_base + jbase + c;  // pairs j = jbase + c + e, e = 0..15
+                    const int64_t e_lo = i - (jbase + c);  // first e on or above the diagonal
+                    const int64_t e_hi = N - (jbase + c);  // first e past the last input
+                    if (w.mode == kAdd) {
+                        // all 16 loads issued before any store, so they overlap in flight
+                        int2 old[16];
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi) old[e] = p[e];
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi)
+                                p[e] = make_int2(old[e].x + __float2int_rn(__uint_as_float(re[e])),
+                                                 old[e].y - __float2int_rn(__uint_as_float(nim[e])));
+                    } else if (w.mode == kStore) {
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi)
+                                p[e] = make_int2(__float2int_rn(__uint_as_float(re[e])),
+                                                 -__float2int_rn(__uint_as_float(nim[e])));
+                    } else {
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi) {
+                                atomicAdd(&p[e].x, __float2int_rn(__uint_as_float(re[e])));
+                                atomicAdd(&p[e].y, -__float2int_rn(__uint_as_float(nim[e])));
                             }
-                        }
                     }
                 }
             }

@@ -53,9 +53,10 @@ __device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &
     im = __byte_perm(i02, i13, 0x5140);
 }
 
-// Decode one 128-sample x 128-input tile (tb, ib) of channel f0 + fl.
+// Decode one 128-sample x 128-input tile (tb, ib) of channel f0 + fl into
+// planes whose rows are `pitch` bytes apart.
 __device__ __forceinline__ void decode_tile(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N,
-                                            int32_t f0, uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad,
+                                            int32_t f0, uint8_t *__restrict__ planes, int64_t pitch, int64_t n_pad,
                                             int vec_ok, int tb, int ib, int fl, uint32_t *tile)
 {
     const int64_t t0 = (int64_t)tb * 128;
@@ -116,8 +117,8 @@ __device__ __forceinline__ void decode_tile(const uint8_t *__restrict__ block, i
     #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int64_t i = i0 + q * 4 + k;
-        uint8_t *rowre = planes + ((int64_t)fl * 2 * n_pad + i) * t_pad + tcol;
-        uint8_t *rowim = planes + ((int64_t)fl * 2 * n_pad + n_pad + i) * t_pad + tcol;
+        uint8_t *rowre = planes + ((int64_t)fl * 2 * n_pad + i) * pitch + tcol;
+        uint8_t *rowim = planes + ((int64_t)fl * 2 * n_pad + n_pad + i) * pitch + tcol;
         *reinterpret_cast<uint4 *>(rowre) = make_uint4(re[k][0], re[k][1], re[k][2], re[k][3]);
         *reinterpret_cast<uint4 *>(rowim) = make_uint4(im[k][0], im[k][1], im[k][2], im[k][3]);
     }
@@ -150,7 +151,7 @@ decode_batch_kernel(const DecodeJob *__restrict__ jobs, int n_jobs)
     const int tb = (int)(local % ntb);
     const int ib = (int)((local / ntb) % nib);
     const int fl = (int)(local / (ntb * nib));
-    decode_tile(j.block, j.T, j.F, j.N, 0, j.planes, j.t_pad, j.n_pad, j.vec_ok, tb, ib, fl, tile);
+    decode_tile(j.block, j.T, j.F, j.N, 0, j.planes, j.pitch, j.n_pad, j.vec_ok, tb, ib, fl, tile);
 }
 
 }  // namespace

@@ -28,8 +28,9 @@ cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N,
 // Batched decode: one launch over the tiles of several blocks.
 struct DecodeJob {
     const uint8_t *block;  // [T][F][N]
-    uint8_t *planes;       // [F][2][n_pad][t_pad]
+    uint8_t *planes;       // [F][2][n_pad][pitch]: this job fills columns [0, t_pad) of every row
     int64_t T, t_pad, n_pad;
+    int64_t pitch;         // bytes between plane rows (>= t_pad)
     int64_t cta0;          // first CTA of this job in the launch
     int32_t F, N;
     int32_t vec_ok;        // 16-byte loads allowed (see decode_vec_ok)
@@ -60,7 +61,7 @@ struct JobDesc {
     int32_t *out;      // [F][N(N+1)/2][2] int32 of the job
     int32_t n_pad;     // inputs rounded up to 128
     int32_t N;
-    int32_t split;     // != 0: several items share a tile; the epilogue adds atomically
+    int32_t mode;      // epilogue: 0 store, 1 add (read-modify-write), 2 atomic add (items share tiles)
     int32_t pad_;
 };
 struct WorkItem {
@@ -72,8 +73,10 @@ struct ListArgs {
     const CUtensorMap *maps;   // [n_jobs], 64-byte aligned
     const JobDesc *jobs;       // [n_jobs]
     const WorkItem *items;     // [n_items]
-    const int32_t *cta_begin;  // [grid + 1]: CTA b runs items [cta_begin[b], cta_begin[b + 1])
+    const int32_t *cta_begin;  // [grid + 1]: CTA b runs items [cta_begin[b], cta_begin[b + 1]);
+                               // nullptr: CTA b runs items b, b + grid, b + 2 grid, ... < n_items
     int32_t *err;              // device status word
+    int64_t n_items;
 };
 cudaError_t encode_planes_map(CUtensorMap *map, const uint8_t *planes, int64_t t_pad, int64_t rows);
 cudaError_t prepare_correlate_tc_listed();  // kernel attributes; call before any stream capture

@@ -363,3 +363,111 @@ class XBatch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ serving --
+
+class XserveOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_blocks", ctypes.c_int32), ("max_streams", ctypes.c_int32),
+                ("max_items", ctypes.c_int64), ("compute_budget_tops", ctypes.c_double)]
+
+
+class XserveDumpInfo(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_int64), ("samples", ctypes.c_int64), ("last_arrival_s", ctypes.c_double),
+                ("ready_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class XserveStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("blocks_done", ctypes.c_int64), ("dumps_done", ctypes.c_int64),
+                ("refused", ctypes.c_int64), ("backlog_blocks", ctypes.c_int64), ("used_bytes", ctypes.c_int64),
+                ("open_streams", ctypes.c_int32), ("pad_", ctypes.c_int32), ("useful_ops", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("block_p50_s", ctypes.c_double), ("block_p99_s", ctypes.c_double),
+                ("dump_p50_s", ctypes.c_double), ("dump_p99_s", ctypes.c_double),
+                ("gpu_decode_ms", ctypes.c_double), ("gpu_correlate_ms", ctypes.c_double),
+                ("host_plan_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+def _serve_lib():
+    L = lib()
+    if not getattr(L, "_serve_typed", False):
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.xserve_now.argtypes = []
+        L.xserve_now.restype = dbl
+        L.xserve_create.argtypes = [ctypes.POINTER(XserveOpts), ctypes.POINTER(vp)]
+        L.xserve_create.restype = ctypes.c_int
+        L.xserve_open_stream.argtypes = [vp, i32, i32, i64, i64, dbl, ctypes.POINTER(i32)]
+        L.xserve_open_stream.restype = ctypes.c_int
+        L.xserve_submit.argtypes = [vp, i32, vp, dbl]
+        L.xserve_submit.restype = ctypes.c_int
+        L.xserve_consumed.argtypes = [vp, i32]
+        L.xserve_consumed.restype = i64
+        L.xserve_poll_dump.argtypes = [vp, i32, vp, ctypes.POINTER(XserveDumpInfo)]
+        L.xserve_poll_dump.restype = ctypes.c_int
+        L.xserve_drain.argtypes = [vp, dbl]
+        L.xserve_drain.restype = ctypes.c_int
+        L.xserve_close_stream.argtypes = [vp, i32]
+        L.xserve_close_stream.restype = ctypes.c_int
+        L.xserve_stats.argtypes = [vp, ctypes.POINTER(XserveStats)]
+        L.xserve_stats.restype = ctypes.c_int
+        L.xserve_destroy.argtypes = [vp]
+        L.xserve_destroy.restype = None
+        L._serve_typed = True
+    return L
+
+
+def xserve_now() -> float:
+    return _serve_lib().xserve_now()
+
+
+def xserve_create(hbm_budget_bytes=120 << 30, max_blocks=16, max_streams=16, max_items=4 << 20,
+                  compute_budget_tops=0.0):
+    o = XserveOpts(hbm_budget_bytes, max_blocks, max_streams, max_items, compute_budget_tops)
+    h = ctypes.c_void_p()
+    rc = _serve_lib().xserve_create(ctypes.byref(o), ctypes.byref(h))
+    return rc, (h.value if rc == XENG_OK else None)
+
+
+def xserve_open_stream(sv, n_inputs, n_freq, block_samples, dump_samples, rate_blocks_per_s=0.0):
+    sid = ctypes.c_int32(-1)
+    rc = _serve_lib().xserve_open_stream(sv, n_inputs, n_freq, block_samples, dump_samples, rate_blocks_per_s,
+                                         ctypes.byref(sid))
+    return rc, (sid.value if rc == XENG_OK else None)
+
+
+def xserve_submit(sv, stream_id, block, arrival_s=0.0) -> int:
+    return _serve_lib().xserve_submit(sv, stream_id, _ptr(block), arrival_s)
+
+
+def xserve_consumed(sv, stream_id) -> int:
+    return _serve_lib().xserve_consumed(sv, stream_id)
+
+
+def xserve_poll_dump(sv, stream_id, out):
+    """Returns (status, info dict or None); status 1 = a dump was copied to out."""
+    info = XserveDumpInfo()
+    rc = _serve_lib().xserve_poll_dump(sv, stream_id, _ptr(out), ctypes.byref(info))
+    return rc, (info.as_dict() if rc == 1 else None)
+
+
+def xserve_drain(sv, timeout_s=0.0) -> int:
+    return _serve_lib().xserve_drain(sv, timeout_s)
+
+
+def xserve_close_stream(sv, stream_id) -> int:
+    return _serve_lib().xserve_close_stream(sv, stream_id)
+
+
+def xserve_stats(sv):
+    st = XserveStats()
+    rc = _serve_lib().xserve_stats(sv, ctypes.byref(st))
+    return rc, st.as_dict()
+
+
+def xserve_destroy(sv) -> None:
+    _serve_lib().xserve_destroy(sv)

@@ -1,0 +1,170 @@
+"""The streaming service (xserve_*): every stream's dumps bit-identical alone
+and in the mix and equal to the oracle; admission by HBM budget with later
+re-admission; dump back-pressure; argument checks."""
+import random
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1503_06202_gb300 as xe  # noqa: E402
+
+BS = 256             # samples per block
+PER_DUMP = 6         # blocks per integration
+STREAMS = [(64, 2), (130, 1), (256, 3)]  # (N, F)
+
+
+def make_blocks(N, F, n, seed):
+    rng = np.random.default_rng(seed)
+    host = [rng.integers(0, 256, size=(BS, F, N), dtype=np.uint8) for _ in range(n)]
+    return host, [torch.from_numpy(h).cuda() for h in host]
+
+
+def run_server(streams, schedule, max_blocks=4, jitter=True):
+    """streams: list of (N, F, device blocks); schedule: list of stream indices in
+    submission order.  Returns the dumps per stream (numpy, in order)."""
+    rc, sv = xe.xserve_create(hbm_budget_bytes=8 << 30, max_blocks=max_blocks, max_streams=8)
+    assert rc == xe.XENG_OK
+    ids = []
+    for N, F, _ in streams:
+        rc, sid = xe.xserve_open_stream(sv, N, F, BS, BS * PER_DUMP)
+        assert rc == xe.XENG_OK
+        ids.append(sid)
+    nxt = [0] * len(streams)
+    dumps = [[] for _ in streams]
+    outs = [torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda") for N, F, _ in streams]
+    rng = random.Random(7)
+    for k in schedule:
+        assert xe.xserve_submit(sv, ids[k], streams[k][2][nxt[k]]) == xe.XENG_OK
+        nxt[k] += 1
+        if jitter and rng.random() < 0.3:
+            time.sleep(rng.random() * 2e-3)  # let rounds start while others arrive
+        for s in range(len(streams)):
+            rc, info = xe.xserve_poll_dump(sv, ids[s], outs[s])
+            if rc == 1:
+                dumps[s].append((info["seq"], outs[s].cpu().numpy().copy()))
+    assert xe.xserve_drain(sv, 60.0) == xe.XENG_OK
+    for s in range(len(streams)):
+        while True:
+            rc, info = xe.xserve_poll_dump(sv, ids[s], outs[s])
+            assert rc >= 0
+            if rc != 1:
+                break
+            dumps[s].append((info["seq"], outs[s].cpu().numpy().copy()))
+    rc, st = xe.xserve_stats(sv)
+    assert rc == xe.XENG_OK and st["blocks_done"] == len(schedule)
+    for s in range(len(streams)):
+        assert xe.xserve_consumed(sv, ids[s]) == nxt[s]
+    xe.xserve_destroy(sv)
+    return [[d for _, d in sorted(ds, key=lambda x: x[0])] for ds in dumps]
+
+
+def test_serve_alone_and_in_the_mix_match_the_oracle():
+    n_int = 2
+    data = []
+    for k, (N, F) in enumerate(STREAMS):
+        host, dev = make_blocks(N, F, n_int * PER_DUMP, seed=100 + k)
+        data.append((N, F, host, dev))
+    want = [[oracle.correlate(np.concatenate(host[i * PER_DUMP:(i + 1) * PER_DUMP], axis=0)) for i in range(n_int)]
+            for (_, _, host, _) in data]
+    # each stream alone
+    for k, (N, F, host, dev) in enumerate(data):
+        got = run_server([(N, F, dev)], [0] * (n_int * PER_DUMP))[0]
+        assert len(got) == n_int
+        for i in range(n_int):
+            assert np.array_equal(got[i].astype(np.int64), want[k][i]), ("alone", k, i)
+    # all streams together, interleaved at random
+    order = [k for k in range(len(data)) for _ in range(n_int * PER_DUMP)]
+    random.Random(3).shuffle(order)
+    mixed = run_server([(N, F, dev) for (N, F, _, dev) in data], order)
+    for k in range(len(data)):
+        assert len(mixed[k]) == n_int
+        for i in range(n_int):
+            assert np.array_equal(mixed[k][i].astype(np.int64), want[k][i]), ("mix", k, i)
+
+
+def test_serve_single_block_rounds_and_partial_last_round():
+    N, F = 100, 2
+    host, dev = make_blocks(N, F, PER_DUMP, seed=9)
+    got = run_server([(N, F, dev)], [0] * PER_DUMP, max_blocks=1, jitter=False)[0]
+    assert np.array_equal(got[0].astype(np.int64), oracle.correlate(np.concatenate(host, axis=0)))
+    got = run_server([(N, F, dev)], [0] * PER_DUMP, max_blocks=5, jitter=False)[0]  # 5 + 1 blocks
+    assert np.array_equal(got[0].astype(np.int64), oracle.correlate(np.concatenate(host, axis=0)))
+
+
+def test_serve_admission_by_hbm_budget():
+    N, F = 256, 4
+    acc = F * N * (N + 1) // 2 * 8
+    planes = F * 2 * 256 * BS * 4
+    per_stream = 3 * acc + 2 * planes
+    rc, sv = xe.xserve_create(hbm_budget_bytes=2 * per_stream + per_stream // 2, max_blocks=4, max_streams=8)
+    assert rc == xe.XENG_OK
+    rc, a = xe.xserve_open_stream(sv, N, F, BS, BS * 4)
+    assert rc == xe.XENG_OK
+    rc, b = xe.xserve_open_stream(sv, N, F, BS, BS * 4)
+    assert rc == xe.XENG_OK
+    rc, c = xe.xserve_open_stream(sv, N, F, BS, BS * 4)
+    assert rc == xe.XENG_ERR_NOMEM and c is None  # over budget: refused
+    # work in flight on the admitted streams, then one closes and frees its share
+    host, dev = make_blocks(N, F, 4, seed=11)
+    for blk in dev:
+        assert xe.xserve_submit(sv, a, blk) == xe.XENG_OK
+        assert xe.xserve_submit(sv, b, blk) == xe.XENG_OK
+    assert xe.xserve_close_stream(sv, a) == xe.XENG_OK
+    rc, c = xe.xserve_open_stream(sv, N, F, BS, BS * 4)
+    assert rc == xe.XENG_OK  # admitted once memory freed up
+    assert xe.xserve_drain(sv, 60.0) == xe.XENG_OK
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    rc, info = xe.xserve_poll_dump(sv, b, out)
+    assert rc == 1 and info["samples"] == 4 * BS
+    assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.correlate(np.concatenate(host, axis=0)))
+    rc, st = xe.xserve_stats(sv)
+    assert st["refused"] == 1 and st["open_streams"] == 2
+    xe.xserve_destroy(sv)
+
+
+def test_serve_compute_budget_and_bad_args():
+    rc, sv = xe.xserve_create(compute_budget_tops=10.0, max_blocks=4)
+    assert rc == xe.XENG_OK
+    # 1000 blocks/s of N=2048, F=8, 256 samples: 8*256*8*2098176*1000 = 34 TOPS > 10
+    rc, _ = xe.xserve_open_stream(sv, 2048, 8, BS, BS * 4, 1000.0)
+    assert rc == xe.XENG_ERR_NOMEM
+    rc, s = xe.xserve_open_stream(sv, 64, 1, BS, BS * 4, 100.0)
+    assert rc == xe.XENG_OK
+    assert xe.xserve_open_stream(sv, 0, 1, BS, BS * 4)[0] == xe.XENG_ERR_RANGE
+    assert xe.xserve_open_stream(sv, 8, 1, BS, BS * 4 + 1)[0] == xe.XENG_ERR_RANGE  # not a whole number of blocks
+    assert xe.xserve_open_stream(sv, 8, 1, 32768, 65536)[0] == xe.XENG_ERR_RANGE   # a round would exceed 65536
+    assert xe.xserve_submit(sv, 99, torch.zeros(1, device="cuda")) == xe.XENG_ERR_ARG
+    assert xe.xserve_poll_dump(sv, s, None)[0] == xe.XENG_ERR_ARG
+    xe.xserve_destroy(sv)
+
+
+def test_serve_dump_backpressure():
+    N, F = 64, 1
+    host, dev = make_blocks(N, F, 3 * PER_DUMP, seed=12)
+    rc, sv = xe.xserve_create(max_blocks=4, max_streams=2)
+    rc, s = xe.xserve_open_stream(sv, N, F, BS, BS * PER_DUMP)
+    for blk in dev:
+        xe.xserve_submit(sv, s, blk)
+    assert xe.xserve_drain(sv, 60.0) == xe.XENG_OK  # returns although the third integration waits
+    rc, st = xe.xserve_stats(sv)
+    assert st["dumps_done"] == 2 and st["backlog_blocks"] > 0
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    got = []
+    for _ in range(3):
+        deadline = time.time() + 30
+        while True:
+            rc, info = xe.xserve_poll_dump(sv, s, out)
+            if rc == 1:
+                got.append(out.cpu().numpy().astype(np.int64))
+                break
+            assert time.time() < deadline
+            time.sleep(1e-3)
+    for i in range(3):
+        assert np.array_equal(got[i], oracle.correlate(np.concatenate(host[i * PER_DUMP:(i + 1) * PER_DUMP], axis=0)))
+    xe.xserve_destroy(sv)
