@@ -280,18 +280,22 @@ def run_serving(args, rank, world, local_rank):
     results = []
     rng = np.random.default_rng(5)
     for rate in args.serve_rates:
-        rc, sv = xe.xserve_create(hbm_budget_bytes=120 << 30, max_blocks=args.serve_max_blocks, max_streams=16)
+        rc, sv = xe.xserve_create(hbm_budget_bytes=120 << 30, max_blocks=args.serve_max_blocks, max_streams=16,
+                                  compute_budget_tops=args.serve_compute_budget)
         if rc != xe.XENG_OK:
             raise RuntimeError("xserve_create: " + xe.xeng_strerror(rc))
-        ids = []
-        for (N, F) in shapes:
+        ids, admitted = [], []
+        for k, (N, F) in enumerate(shapes):
             rc, sid = xe.xserve_open_stream(sv, N, F, BS, DUMP, rate * real_rate)
+            if rc == xe.XENG_ERR_NOMEM and args.serve_compute_budget > 0:
+                continue  # refused by the compute budget: this stream is not served at this rate
             if rc != xe.XENG_OK:
                 raise RuntimeError("admission refused: " + xe.xeng_strerror(rc))
             ids.append(sid)
+            admitted.append(k)
         outs = [torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda") for N, F in shapes]
         events = []
-        for k in range(len(shapes)):
+        for k in admitted:
             t = rng.exponential(1.0 / (rate * real_rate))
             while t < args.serve_seconds:
                 events.append((t, k))
@@ -299,12 +303,13 @@ def run_serving(args, rank, world, local_rank):
         events.sort()
         stop = threading.Event()
         dumps = [0] * len(shapes)
+        sid_of = dict(zip(admitted, ids))
 
         def poller():
             while not stop.is_set():
                 got = False
-                for k in range(len(shapes)):
-                    r_, _ = xe.xserve_poll_dump(sv, ids[k], outs[k])
+                for k in admitted:
+                    r_, _ = xe.xserve_poll_dump(sv, sid_of[k], outs[k])
                     if r_ == 1:
                         dumps[k] += 1
                         got = True
@@ -317,7 +322,7 @@ def run_serving(args, rank, world, local_rank):
         for t, k in events:
             while xe.xserve_now() - t0 < t:
                 pass
-            xe.xserve_submit(sv, ids[k], pools[k][n_sub[k] % POOL], 0.0)
+            xe.xserve_submit(sv, sid_of[k], pools[k][n_sub[k] % POOL], 0.0)
             n_sub[k] += 1
         t_arr = xe.xserve_now() - t0
         _, st_end = xe.xserve_stats(sv)
@@ -327,7 +332,8 @@ def run_serving(args, rank, world, local_rank):
         th.join()
         rc, st = xe.xserve_stats(sv)
         xe.xserve_destroy(sv)
-        results.append({"rate": rate, "offered_tops": rate * sum(demand), "arrival_window_s": t_arr,
+        results.append({"rate": rate, "admitted_streams": ["N=%d F=%d" % shapes[k] for k in admitted],
+                        "offered_tops": rate * sum(demand[k] for k in admitted), "arrival_window_s": t_arr,
                         "blocks": sum(n_sub), "sustained_tops": st["useful_ops"] / st["busy_s"] / 1e12,
                         "busy_s": st["busy_s"], "rounds": st["rounds"], "dumps": st["dumps_done"],
                         "backlog_blocks_at_end_of_arrivals": st_end["backlog_blocks"],
@@ -359,6 +365,7 @@ def run_serving(args, rank, world, local_rank):
             "config": {"workload": "serving", "description": WORKLOADS["serving"][1],
                        "streams": ["N=%d F=%d" % sh for sh in shapes], "block_samples": BS, "dump_samples": DUMP,
                        "max_blocks_per_round": args.serve_max_blocks, "arrival_seconds": args.serve_seconds,
+                       "compute_budget_tops": args.serve_compute_budget,
                        "real_time_blocks_per_s": real_rate, "real_time_demand_tops": sum(demand)},
             "per_rate": results, "plain_per_block_push_tops": plain_tops,
             "speedup_vs_plain_per_block": head["sustained_tops"] / plain_tops,
@@ -381,7 +388,8 @@ def main():
     ap.add_argument("--no-peaks", action="store_true", help="skip the dense-throughput probes")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
     ap.add_argument("--serve-seconds", type=float, default=1.5)
-    ap.add_argument("--serve-max-blocks", type=int, default=16)
+    ap.add_argument("--serve-max-blocks", type=int, default=32)
+    ap.add_argument("--serve-compute-budget", type=float, default=0.0, help="TOPS; > 0 admits streams by compute too")
     ap.add_argument("--batch-max-chunks", type=int, default=0, help="fixed batch plan instead of autotuning")
     ap.add_argument("--batch-policy", type=int, default=1)
     ap.add_argument("--no-per-job-dp4a", action="store_true")

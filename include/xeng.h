@@ -112,6 +112,25 @@ XENG_API int64_t xeng_dump(xeng_t h, int32_t *out, void *stream);
  */
 XENG_API int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *out, void *stream);
 
+/*
+ * xeng_correlate_gated -- one integration split into gates, with flagged
+ *   samples excluded.  Gating (Sec. IV-C-4) partitions the samples by their
+ *   time relative to a periodic source: gate[t] in [0, n_gates) names the
+ *   sub-buffer of sample t (any other value drops it).  Flags (Sec. IV-A):
+ *   valid[t][f][i] == 0 marks a missing or saturated sample, which then
+ *   contributes nothing; the usable samples are counted per gate, channel and
+ *   input for renormalising the integrated matrices downstream.
+ *     V^g_ij(f) = sum over t with gate[t] == g, valid_i(t), valid_j(t) of x_i conj(x_j)
+ *   block: device [n_samples][F][N]; gate: host int32 [n_samples];
+ *   valid: device uint8 [n_samples][F][N] or NULL (all usable);
+ *   out: device int32 [n_gates][F][N(N+1)/2][2] (overwritten);
+ *   counts: device int32 [n_gates][F][N] or NULL.
+ *   n_samples <= min(t_integ, 65536) (else XENG_ERR_OVERFLOW / XENG_ERR_RANGE);
+ *   tensor engine only.  Asynchronous on `stream` after reading `gate`.
+ */
+XENG_API int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int32_t *gate,
+                                  int32_t n_gates, const uint8_t *valid, int32_t *out, int32_t *counts, void *stream);
+
 /* xeng_destroy -- free the handle and its device memory; NULL is a no-op.
  * Synchronizes the device first. */
 XENG_API void xeng_destroy(xeng_t h);

@@ -58,7 +58,8 @@ def bind(path: str):
     lib.oracle_correlate_full.argtypes = [u8p, i64, i32, i32, i32, i32, i64p]
     lib.oracle_correlate_pairs.argtypes = [u8p, i64, i32, i32, i64, i32p, i32p, i32p, i64p]
     lib.oracle_beam_power.argtypes = [u8p, i64, i32, i32, i32, i32, i64p, i64p, i64p]
-    for fn in (lib.oracle_correlate, lib.oracle_correlate_full,
+    lib.oracle_correlate_gated.argtypes = [u8p, i64, i32, i32, i32p, i32, u8p, i64p, i64p]
+    for fn in (lib.oracle_correlate, lib.oracle_correlate_full, lib.oracle_correlate_gated,
                lib.oracle_correlate_pairs, lib.oracle_beam_power, lib.oracle_num_threads):
         fn.restype = ctypes.c_int
     return lib
@@ -149,6 +150,28 @@ def beam_power(block, w_re, w_im, f0: int = 0, nf: int | None = None, lib=None) 
                                  _ptr(out, ctypes.c_int64)) != 0:
         raise ValueError("oracle_beam_power: bad arguments")
     return out
+
+
+def correlate_gated(block, gate, n_gates: int, valid=None, lib=None):
+    """Gated, flagged visibilities (Sec. IV-C-4, Sec. IV-A): returns
+    (int64 [G][F][N(N+1)/2][2], int64 [G][F][N] valid-sample counts)."""
+    block = _check_block(block)
+    T, F, N = block.shape
+    gate = np.ascontiguousarray(gate, dtype=np.int32)
+    if gate.shape != (T,):
+        raise ValueError("gate must be int32 [T]")
+    vp = None
+    if valid is not None:
+        valid = np.ascontiguousarray(valid, dtype=np.uint8)
+        if valid.shape != block.shape:
+            raise ValueError("valid must be uint8 [T][F][N]")
+        vp = _ptr(valid, ctypes.c_uint8)
+    out = np.zeros((n_gates, F, n_baselines(N), 2), dtype=np.int64)
+    counts = np.zeros((n_gates, F, N), dtype=np.int64)
+    if _load(lib).oracle_correlate_gated(_ptr(block, ctypes.c_uint8), T, F, N, _ptr(gate, ctypes.c_int32), n_gates,
+                                         vp, _ptr(out, ctypes.c_int64), _ptr(counts, ctypes.c_int64)) != 0:
+        raise ValueError("oracle_correlate_gated: bad arguments")
+    return out, counts
 
 
 def weighted_sum(vis, w_re, w_im) -> np.ndarray:

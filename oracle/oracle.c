@@ -191,3 +191,52 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * oracle_correlate_gated: gating (Sec. IV-C-4: the integration is split into
+ * sub-buffers by the time of each sample relative to a source's period) and
+ * flagged data (Sec. IV-A: missing or saturated samples are tracked and their
+ * count is reported for renormalising the integrated matrices).
+ *
+ * gate[t] in [0, G) names the sub-buffer sample t goes to; any other value
+ * drops the sample.  valid[t][f][i] != 0 marks a usable sample; NULL means
+ * every sample is usable.  For every gate g, channel f and pair i <= j:
+ *
+ *     V^g_ij(f) = sum over t with gate[t] == g, valid_i(t), valid_j(t)
+ *                 of x_i(t, f) * conj(x_j(t, f)),
+ *     counts[g][f][i] = number of t with gate[t] == g and valid_i(t).
+ *
+ * out: int64 [G][F][N(N+1)/2][2]; counts: int64 [G][F][N] or NULL.
+ */
+int oracle_correlate_gated(const uint8_t *in, int64_t T, int32_t F, int32_t N, const int32_t *gate, int32_t G,
+                           const uint8_t *valid, int64_t *out, int64_t *counts)
+{
+    if (T < 0 || F < 1 || N < 1 || G < 1 || !gate)
+        return -1;
+    const int64_t nb = (int64_t)N * (N + 1) / 2;
+    memset(out, 0, sizeof(int64_t) * (size_t)(G * F * nb * 2));
+    if (counts)
+        memset(counts, 0, sizeof(int64_t) * (size_t)(G * F * N));
+    for (int32_t f = 0; f < F; f++) {
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < N; i++) {
+            for (int64_t t = 0; t < T; t++) {
+                const int32_t g = gate[t];
+                if (g < 0 || g >= G) continue;
+                const int64_t at = (t * F + f) * (int64_t)N;
+                if (valid && !valid[at + i]) continue;
+                if (counts) counts[((int64_t)g * F + f) * N + i] += 1;
+                const uint8_t x = in[at + i];
+                int64_t *o = out + ((int64_t)g * F + f) * nb * 2;
+                for (int64_t j = i; j < N; j++) {
+                    if (valid && !valid[at + j]) continue;
+                    const uint8_t y = in[at + j];
+                    const int64_t k = tri_index(i, j, N);
+                    o[2 * k] += sample_re(x) * sample_re(y) + sample_im(x) * sample_im(y);
+                    o[2 * k + 1] += sample_im(x) * sample_re(y) - sample_re(x) * sample_im(y);
+                }
+            }
+        }
+    }
+    return 0;
+}

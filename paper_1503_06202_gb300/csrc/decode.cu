@@ -53,6 +53,45 @@ __device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &
     im = __byte_perm(i02, i13, 0x5140);
 }
 
+// Phase 2 of a tile (after the 128 x 128 bytes sit in `tile`): thread =
+// (input quad q, 16-sample block b); transpose, decode, store both planes.
+__device__ __forceinline__ void decode_tile_store(const uint32_t *tile, uint8_t *__restrict__ planes, int64_t pitch,
+                                                  int64_t n_pad, int64_t t0, int i0, int fl)
+{
+    const int tid = threadIdx.x;
+    const int b = tid & 7;    // lanes 0..7 of a row group write one 128-byte row segment
+    const int q = tid >> 3;   // 0..31
+    uint32_t re[4][4], im[4][4];  // [input k][word g] (word g = samples 4g..4g+3)
+    #pragma unroll
+    for (int g = 0; g < 4; g++) {
+        uint32_t r[4];
+        #pragma unroll
+        for (int k = 0; k < 4; k++) r[k] = tile[row_word(b * 16 + g * 4 + k) + q];
+        // 4x4 byte transpose: r[k] byte m = (time k, input m) -> c[m] byte k
+        const uint32_t lo01 = __byte_perm(r[0], r[1], 0x5140);
+        const uint32_t hi01 = __byte_perm(r[0], r[1], 0x7362);
+        const uint32_t lo23 = __byte_perm(r[2], r[3], 0x5140);
+        const uint32_t hi23 = __byte_perm(r[2], r[3], 0x7362);
+        const uint32_t c0 = __byte_perm(lo01, lo23, 0x5410);
+        const uint32_t c1 = __byte_perm(lo01, lo23, 0x7632);
+        const uint32_t c2 = __byte_perm(hi01, hi23, 0x5410);
+        const uint32_t c3 = __byte_perm(hi01, hi23, 0x7632);
+        decode_word(c0, re[0][g], im[0][g]);
+        decode_word(c1, re[1][g], im[1][g]);
+        decode_word(c2, re[2][g], im[2][g]);
+        decode_word(c3, re[3][g], im[3][g]);
+    }
+    const int64_t tcol = t0 + b * 16;
+    #pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int64_t i = i0 + q * 4 + k;
+        uint8_t *rowre = planes + ((int64_t)fl * 2 * n_pad + i) * pitch + tcol;
+        uint8_t *rowim = planes + ((int64_t)fl * 2 * n_pad + n_pad + i) * pitch + tcol;
+        *reinterpret_cast<uint4 *>(rowre) = make_uint4(re[k][0], re[k][1], re[k][2], re[k][3]);
+        *reinterpret_cast<uint4 *>(rowim) = make_uint4(im[k][0], im[k][1], im[k][2], im[k][3]);
+    }
+}
+
 // Decode one 128-sample x 128-input tile (tb, ib) of channel f0 + fl into
 // planes whose rows are `pitch` bytes apart.
 __device__ __forceinline__ void decode_tile(const uint8_t *__restrict__ block, int64_t T, int32_t F, int32_t N,
@@ -90,38 +129,7 @@ __device__ __forceinline__ void decode_tile(const uint8_t *__restrict__ block, i
     }
     __syncthreads();
 
-    // Phase 2: thread = (input quad q, 16-sample block b).
-    const int b = tid & 7;    // lanes 0..7 of a row group write one 128-byte row segment
-    const int q = tid >> 3;   // 0..31
-    uint32_t re[4][4], im[4][4];  // [input k][word g] (word g = samples 4g..4g+3)
-    #pragma unroll
-    for (int g = 0; g < 4; g++) {
-        uint32_t r[4];
-        #pragma unroll
-        for (int k = 0; k < 4; k++) r[k] = tile[row_word(b * 16 + g * 4 + k) + q];
-        // 4x4 byte transpose: r[k] byte m = (time k, input m) -> c[m] byte k
-        const uint32_t lo01 = __byte_perm(r[0], r[1], 0x5140);
-        const uint32_t hi01 = __byte_perm(r[0], r[1], 0x7362);
-        const uint32_t lo23 = __byte_perm(r[2], r[3], 0x5140);
-        const uint32_t hi23 = __byte_perm(r[2], r[3], 0x7362);
-        const uint32_t c0 = __byte_perm(lo01, lo23, 0x5410);
-        const uint32_t c1 = __byte_perm(lo01, lo23, 0x7632);
-        const uint32_t c2 = __byte_perm(hi01, hi23, 0x5410);
-        const uint32_t c3 = __byte_perm(hi01, hi23, 0x7632);
-        decode_word(c0, re[0][g], im[0][g]);
-        decode_word(c1, re[1][g], im[1][g]);
-        decode_word(c2, re[2][g], im[2][g]);
-        decode_word(c3, re[3][g], im[3][g]);
-    }
-    const int64_t tcol = t0 + b * 16;
-    #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int64_t i = i0 + q * 4 + k;
-        uint8_t *rowre = planes + ((int64_t)fl * 2 * n_pad + i) * pitch + tcol;
-        uint8_t *rowim = planes + ((int64_t)fl * 2 * n_pad + n_pad + i) * pitch + tcol;
-        *reinterpret_cast<uint4 *>(rowre) = make_uint4(re[k][0], re[k][1], re[k][2], re[k][3]);
-        *reinterpret_cast<uint4 *>(rowim) = make_uint4(im[k][0], im[k][1], im[k][2], im[k][3]);
-    }
+    decode_tile_store(tile, planes, pitch, n_pad, t0, i0, fl);
 }
 
 __global__ void __launch_bounds__(kDecThreads)
@@ -154,6 +162,49 @@ decode_batch_kernel(const DecodeJob *__restrict__ jobs, int n_jobs)
     decode_tile(j.block, j.T, j.F, j.N, 0, j.planes, j.pitch, j.n_pad, j.vec_ok, tb, ib, fl, tile);
 }
 
+
+// Gated, flagged decode: the tile's samples are rows idx[t0 .. t0 + 127] of the
+// block (the samples of one gate, in order); a sample whose valid byte is 0 is
+// replaced by value 0 + 0i, and the usable samples per input are added to
+// counts[fl * N + i].  Rows past Tg and inputs past N decode to +0.0.
+__global__ void __launch_bounds__(kDecThreads)
+decode_gather_kernel(const uint8_t *__restrict__ block, int32_t F, int32_t N, int32_t f0,
+                     const int32_t *__restrict__ idx, int64_t Tg, const uint8_t *__restrict__ valid,
+                     uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int32_t *__restrict__ counts)
+{
+    __shared__ uint32_t tile[kTileWords];
+    __shared__ int cnt[128];
+    const int64_t t0 = (int64_t)blockIdx.x * 128;
+    const int i0 = blockIdx.y * 128;
+    const int fl = blockIdx.z;
+    const int64_t f = f0 + fl;
+    const int tid = threadIdx.x;
+    if (tid < 128) cnt[tid] = 0;
+    __syncthreads();
+    for (int ch = tid; ch < 128 * 8; ch += kDecThreads) {
+        const int t = ch >> 3, c = ch & 7;
+        const int64_t k = t0 + t;
+        const int ic = i0 + c * 16;
+        uint32_t w[4] = {0x88888888u, 0x88888888u, 0x88888888u, 0x88888888u};
+        if (k < Tg) {
+            const int64_t row = ((int64_t)idx[k] * F + f) * N;
+            for (int m = 0; m < 16; m++) {
+                const int i = ic + m;
+                if (i >= N) break;
+                uint32_t byte = block[row + i];
+                if (valid && !valid[row + i]) byte = 0x88;
+                else if (counts) atomicAdd(&cnt[c * 16 + m], 1);
+                w[m >> 2] = (w[m >> 2] & ~(0xFFu << (8 * (m & 3)))) | (byte << (8 * (m & 3)));
+            }
+        }
+        uint32_t *dst = tile + row_word(t) + c * 4;
+        dst[0] = w[0]; dst[1] = w[1]; dst[2] = w[2]; dst[3] = w[3];
+    }
+    __syncthreads();
+    decode_tile_store(tile, planes, t_pad, n_pad, t0, i0, fl);
+    if (counts && tid < 128 && i0 + tid < N && cnt[tid]) atomicAdd(&counts[(int64_t)fl * N + i0 + tid], cnt[tid]);
+}
+
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0,
@@ -176,6 +227,20 @@ cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total
     if (n_jobs <= 0 || total_ctas <= 0) return cudaSuccess;
     if (total_ctas > 2147483647LL) return cudaErrorInvalidValue;
     decode_batch_kernel<<<(unsigned)total_ctas, kDecThreads, 0, s>>>(jobs, n_jobs);
+    return cudaGetLastError();
+}
+
+}  // namespace xeng
+
+namespace xeng {
+
+cudaError_t launch_decode_gather(const uint8_t *block, int32_t F, int32_t N, int32_t f0, int32_t nf, const int32_t *idx,
+                                 int64_t Tg, const uint8_t *valid, uint8_t *planes, int64_t t_pad, int64_t n_pad,
+                                 int32_t *counts, cudaStream_t s)
+{
+    if (nf <= 0 || t_pad <= 0) return cudaSuccess;
+    dim3 grid((unsigned)(t_pad / 128), (unsigned)(n_pad / 128), (unsigned)nf);
+    decode_gather_kernel<<<grid, kDecThreads, 0, s>>>(block, F, N, f0, idx, Tg, valid, planes, t_pad, n_pad, counts);
     return cudaGetLastError();
 }
 

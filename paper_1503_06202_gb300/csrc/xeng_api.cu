@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -38,6 +39,13 @@ struct xeng_s {
     xeng_stats_t stats{};
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
+    // host-buffer pipeline: copies in, compute and copies out overlap by channel group
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_fin = nullptr, ev_in[2] = {nullptr, nullptr}, ev_cmp[2] = {nullptr, nullptr};
+    uint8_t *pstage[2] = {nullptr, nullptr};
+    int64_t pstage_bytes = 0;
+    int32_t *gidx = nullptr;       // sample indices of the gates of a gated call
+    int64_t gidx_cap = 0;
 };
 
 namespace {
@@ -195,6 +203,17 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->acc);
     cudaFree(h->planes);
     cudaFree(h->staging);
+    cudaFree(h->gidx);
+    cudaFree(h->pstage[0]);
+    cudaFree(h->pstage[1]);
+    if (h->h2d) cudaStreamDestroy(h->h2d);
+    if (h->d2h) cudaStreamDestroy(h->d2h);
+    for (int k = 0; k < 2; k++) {
+        if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+        if (h->ev_cmp[k]) cudaEventDestroy(h->ev_cmp[k]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_fin) cudaEventDestroy(h->ev_fin);
     cudaFree(h->d_err);
     if (h->h_err) cudaFreeHost(h->h_err);
     for (auto &t : h->timed) {
@@ -226,6 +245,17 @@ const uint8_t *device_block(xeng_s *h, const uint8_t *block, int64_t bytes, cuda
     if (is_device_pointer(block)) return block;
     if (h->staging_bytes < bytes) {
         cudaFree(h->staging);
+    cudaFree(h->gidx);
+    cudaFree(h->pstage[0]);
+    cudaFree(h->pstage[1]);
+    if (h->h2d) cudaStreamDestroy(h->h2d);
+    if (h->d2h) cudaStreamDestroy(h->d2h);
+    for (int k = 0; k < 2; k++) {
+        if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+        if (h->ev_cmp[k]) cudaEventDestroy(h->ev_cmp[k]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_fin) cudaEventDestroy(h->ev_fin);
         h->staging = nullptr;
         h->staging_bytes = 0;
         if (cudaMalloc(&h->staging, (size_t)bytes) != cudaSuccess) {
@@ -284,6 +314,105 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
     return e;
 }
 
+// Streams, events and staging of the host-buffer pipeline (created on first use).
+int ensure_pipeline(xeng_s *h, int64_t stage_bytes)
+{
+    cudaError_t e = cudaSuccess;
+    if (!h->h2d) {
+        e = cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+            e = cudaEventCreateWithFlags(&h->ev_in[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_cmp[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fin, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (stage_bytes > h->pstage_bytes) {
+        cudaDeviceSynchronize();  // the old staging may still be read by queued work
+        cudaFree(h->pstage[0]);
+        cudaFree(h->pstage[1]);
+        h->pstage[0] = h->pstage[1] = nullptr;
+        h->pstage_bytes = 0;
+        e = cudaMalloc(&h->pstage[0], (size_t)stage_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&h->pstage[1], (size_t)stage_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return XENG_ERR_NOMEM;
+        }
+        h->pstage_bytes = stage_bytes;
+    }
+    return XENG_OK;
+}
+
+// One integration of n <= chunk_t samples with the tensor engine, where the
+// block (`host_in`) and/or the result (`host_out`) live in host memory: the
+// channels are cut into groups; group g's pitched host-to-device copy, its
+// decode + correlation and its device-to-host copy run on three streams, so
+// transfers of neighbouring groups overlap the compute.  `src` is the block
+// (host or device), `target` the device triangle written (store when
+// `fresh`, else add).  Returns XENG_OK or an error; host_out is complete when
+// `s` passes the point this call enqueues.
+int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, int32_t *target, int32_t *host_out,
+                        bool fresh, cudaStream_t s)
+{
+    const int64_t N = h->N, F = h->F;
+    const int64_t n_pad = round_up(N, kTile), t_pad = round_up(n, kTile), nb2 = N * (N + 1);
+    int64_t pf = (F + 7) / 8;  // about eight groups
+    if (pf > h->group_f) pf = h->group_f;
+    if (pf < 1) pf = 1;
+    int st = ensure_pipeline(h, host_in ? pf * n * N : 0);
+    if (st != XENG_OK) return st;
+    cudaError_t e = cudaEventRecord(h->ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->h2d, h->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h, h->ev_start, 0);
+    int g = 0;
+    for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += pf, ++g) {
+        const int32_t nf = (int32_t)((F - f0) < pf ? (F - f0) : pf);
+        const int buf = g & 1;
+        const uint8_t *blk = src;
+        int32_t bf = (int32_t)F, bf0 = (int32_t)f0;
+        if (host_in) {
+            // staging[buf] was last read by the decode of group g - 2, which ev_cmp[buf] follows
+            if (g >= 2) e = cudaStreamWaitEvent(h->h2d, h->ev_cmp[buf], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(h->pstage[buf], (size_t)(nf * N), src + f0 * N, (size_t)(F * N), (size_t)(nf * N),
+                                      (size_t)n, cudaMemcpyHostToDevice, h->h2d);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[buf], h->h2d);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_in[buf], 0);
+            if (e != cudaSuccess) break;
+            blk = h->pstage[buf];
+            bf = nf;
+            bf0 = 0;
+        }
+        e = timed_launch(h, 0, s, [&] {
+            return launch_decode(blk, n, bf, (int32_t)N, bf0, nf, h->planes, t_pad, n_pad, s);
+        });
+        if (e != cudaSuccess) break;
+        TcArgs a;
+        a.planes = h->planes;
+        a.t_pad = t_pad;
+        a.n_pad = (int32_t)n_pad;
+        a.N = (int32_t)N;
+        a.nf = nf;
+        a.acc = target + f0 * nb2;
+        a.accumulate = fresh ? 0 : 1;
+        a.err = h->d_err;
+        e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
+        if (e == cudaSuccess && host_out) {
+            e = cudaStreamWaitEvent(h->d2h, h->ev_cmp[buf], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(host_out + f0 * nb2, target + f0 * nb2, (size_t)(nf * nb2 * 4),
+                                    cudaMemcpyDeviceToHost, h->d2h);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_fin, host_out ? h->d2h : s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_fin, 0);
+    return cuda_status(e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -298,10 +427,15 @@ int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
     if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples == 0) return XENG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const uint8_t *dblock = device_block(h, block, n_samples * h->F * h->N, s, &st);
-    if (!dblock) return st;
-    cudaError_t e = integrate(h, dblock, n_samples, h->acc, h->fresh, s);
-    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    if (h->engine == XENG_ENGINE_TENSOR && n_samples <= h->chunk_t && !is_device_pointer(block)) {
+        st = integrate_pipelined(h, block, true, n_samples, h->acc, nullptr, h->fresh, s);
+        if (st != XENG_OK) return (h->sticky = st);
+    } else {
+        const uint8_t *dblock = device_block(h, block, n_samples * h->F * h->N, s, &st);
+        if (!dblock) return st;
+        cudaError_t e = integrate(h, dblock, n_samples, h->acc, h->fresh, s);
+        if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    }
     cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     h->samples += n_samples;
     h->fresh = false;
@@ -326,6 +460,16 @@ int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *o
         memset(out, 0, (size_t)bytes);
         return cuda_status(e);
     }
+    const bool dev_in = is_device_pointer(block);
+    if (h->engine == XENG_ENGINE_TENSOR && n_samples <= h->chunk_t && (!dev_in || !dev_out)) {
+        // host buffers: copies overlap the compute, group by group
+        st = integrate_pipelined(h, block, !dev_in, n_samples, dev_out ? out : h->acc, dev_out ? nullptr : out, true, s);
+        if (st == XENG_OK) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (st == XENG_OK && e == cudaSuccess && !dev_out) e = cudaStreamSynchronize(s);
+        if (st != XENG_OK) return (h->sticky = st);
+        if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+        return dev_out ? XENG_OK : check_sticky(h);
+    }
     const uint8_t *dblock = device_block(h, block, n_samples * h->F * h->N, s, &st);
     if (!dblock) return st;
     // device output: written in place; host output: through the accumulators
@@ -337,6 +481,78 @@ int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *o
     }
     if (e != cudaSuccess) return (h->sticky = cuda_status(e));
     return dev_out ? XENG_OK : check_sticky(h);
+}
+
+int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int32_t *gate, int32_t n_gates,
+                         const uint8_t *valid, int32_t *out, int32_t *counts, void *stream)
+{
+    if (!h || !gate || !out || n_gates < 1 || n_samples < 0 || (n_samples > 0 && !block)) return XENG_ERR_ARG;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    if (n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
+    if (n_samples > h->chunk_t) return XENG_ERR_RANGE;
+    if (h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_ARG;
+    if (!is_device_pointer(out) || (counts && !is_device_pointer(counts)) || (valid && !is_device_pointer(valid)) ||
+        (n_samples > 0 && !is_device_pointer(block)))
+        return XENG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->N, F = h->F;
+    const int64_t n_pad = round_up(N, kTile), nb2 = N * (N + 1);
+    // the samples of each gate, in time order
+    std::vector<int64_t> cnt(n_gates + 1, 0);
+    for (int64_t t = 0; t < n_samples; t++)
+        if (gate[t] >= 0 && gate[t] < n_gates) cnt[gate[t] + 1]++;
+    for (int g = 0; g < n_gates; g++) cnt[g + 1] += cnt[g];
+    std::vector<int32_t> idx((size_t)std::max<int64_t>(cnt[n_gates], 1));
+    {
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t t = 0; t < n_samples; t++)
+            if (gate[t] >= 0 && gate[t] < n_gates) idx[fill[gate[t]]++] = (int32_t)t;
+    }
+    cudaError_t e = cudaSuccess;
+    if ((int64_t)idx.size() > h->gidx_cap) {
+        e = cudaStreamSynchronize(s);  // an earlier gated call may still read the old list
+        cudaFree(h->gidx);
+        h->gidx = nullptr;
+        h->gidx_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&h->gidx, idx.size() * sizeof(int32_t));
+        if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+        h->gidx_cap = (int64_t)idx.size();
+    }
+    e = cudaMemcpyAsync(h->gidx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // idx is pageable and goes out of scope
+    if (e == cudaSuccess && counts) e = cudaMemsetAsync(counts, 0, (size_t)(n_gates * F * N * 4), s);
+    for (int g = 0; g < n_gates && e == cudaSuccess; g++) {
+        const int64_t Tg = cnt[g + 1] - cnt[g];
+        int32_t *out_g = out + (int64_t)g * F * nb2;
+        if (Tg == 0) {
+            e = cudaMemsetAsync(out_g, 0, (size_t)(F * nb2 * 4), s);
+            continue;
+        }
+        const int64_t t_pad = round_up(Tg, kTile);
+        for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += h->group_f) {
+            const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
+            e = timed_launch(h, 0, s, [&] {
+                return launch_decode_gather(block, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->gidx + cnt[g], Tg, valid,
+                                            h->planes, t_pad, n_pad,
+                                            counts ? counts + ((int64_t)g * F + f0) * N : nullptr, s);
+            });
+            if (e != cudaSuccess) break;
+            TcArgs a;
+            a.planes = h->planes;
+            a.t_pad = t_pad;
+            a.n_pad = (int32_t)n_pad;
+            a.N = (int32_t)N;
+            a.nf = nf;
+            a.acc = out_g + f0 * nb2;
+            a.accumulate = 0;
+            a.err = h->d_err;
+            e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    return XENG_OK;
 }
 
 int64_t xeng_dump(xeng_t h, int32_t *out, void *stream)

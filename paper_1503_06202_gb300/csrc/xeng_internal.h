@@ -25,6 +25,13 @@ cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N,
                           int32_t f0, int32_t nf, uint8_t *planes, int64_t t_pad,
                           int64_t n_pad, cudaStream_t s);
 
+// Gated / flagged decode of channels [f0, f0 + nf): tile rows are block rows
+// idx[0 .. Tg) (one gate's samples); samples whose valid byte is 0 decode to
+// zero; usable samples per (channel, input) are added to counts[fl][N] (may be null).
+cudaError_t launch_decode_gather(const uint8_t *block, int32_t F, int32_t N, int32_t f0, int32_t nf, const int32_t *idx,
+                                 int64_t Tg, const uint8_t *valid, uint8_t *planes, int64_t t_pad, int64_t n_pad,
+                                 int32_t *counts, cudaStream_t s);
+
 // Batched decode: one launch over the tiles of several blocks.
 struct DecodeJob {
     const uint8_t *block;  // [T][F][N]

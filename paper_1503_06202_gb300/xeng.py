@@ -62,6 +62,8 @@ def lib():
         L.xeng_dump.restype = i64
         L.xeng_correlate.argtypes = [vp, vp, i64, vp, vp]
         L.xeng_correlate.restype = ctypes.c_int
+        L.xeng_correlate_gated.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, vp]
+        L.xeng_correlate_gated.restype = ctypes.c_int
         L.xeng_destroy.argtypes = [vp]
         L.xeng_destroy.restype = None
         L.xeng_strerror.argtypes = [ctypes.c_int]
@@ -120,6 +122,12 @@ def xeng_dump(h, out, stream=None) -> int:
 
 def xeng_correlate(h, block, n_samples: int, out, stream=None) -> int:
     return lib().xeng_correlate(h, _ptr(block), n_samples, _ptr(out), _stream(stream))
+
+
+def xeng_correlate_gated(h, block, n_samples, gate, n_gates, valid, out, counts, stream=None) -> int:
+    """gate: host int32 array [n_samples] (numpy); valid/counts may be None."""
+    return lib().xeng_correlate_gated(h, _ptr(block), n_samples, _ptr(gate), n_gates, _ptr(valid), _ptr(out),
+                                      _ptr(counts), _stream(stream))
 
 
 def xeng_destroy(h) -> None:

@@ -223,6 +223,40 @@ def test_one_shot_correlate():
         eng.close()
 
 
+def test_host_pipeline_many_channel_groups():
+    # 20 channels in groups of 3: copies in, compute and copies out on three streams
+    rng = np.random.default_rng(30)
+    T, F, N = 500, 20, 100
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    pinned = torch.from_numpy(blk).pin_memory()
+    hout = torch.zeros((F, N * (N + 1) // 2, 2), dtype=torch.int32).pin_memory()
+    eng = xe.XEngine(N, F, T)
+    for _ in range(2):  # the second call reuses the staging buffers
+        eng.correlate(pinned, hout)
+        assert_same(hout.numpy().astype(np.int64), want, "pipelined host in/out")
+    dout = torch.zeros((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    eng.correlate(pinned, dout)  # host in, device out
+    torch.cuda.synchronize()
+    assert_same(dout.cpu().numpy().astype(np.int64), want, "pipelined host in")
+    eng.correlate(torch.from_numpy(blk).cuda(), hout)  # device in, host out
+    assert_same(hout.numpy().astype(np.int64), want, "pipelined host out")
+    eng.push(pinned[:200])
+    eng.push(blk[200:])
+    assert eng.dump(dout) == T
+    torch.cuda.synchronize()
+    assert_same(dout.cpu().numpy().astype(np.int64), want, "pipelined pushes")
+    eng.close()
+    # longer than one round of samples: the unpipelined host path
+    T2 = 70000
+    blk2 = rng.integers(0, 256, size=(T2, 2, 64), dtype=np.uint8)
+    eng = xe.XEngine(64, 2, T2)
+    h2 = np.zeros((2, 64 * 65 // 2, 2), np.int32)
+    eng.correlate(blk2, h2)
+    assert_same(h2.astype(np.int64), oracle.correlate(blk2), "long host block")
+    eng.close()
+
+
 def test_create_rejects_bad_sizes_on_gpu():
     for args in [(0, 1, 1), (4097, 1, 1), (1, 0, 1), (1, 1, 0), (1, 1, 2 ** 24)]:
         rc, h = xe.xeng_create(*args)

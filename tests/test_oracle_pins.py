@@ -188,8 +188,47 @@ def pin_pairs_and_subsets(lib=None):
     assert np.array_equal(got, full[fs, oracle.triangle_index(i, j, N)])
 
 
+def pin_gated(lib=None):
+    """Gating and flags (Sec. IV-C-4, Sec. IV-A) reduce to the plain definition."""
+    rng = np.random.default_rng(8)
+    T, F, N, G = 90, 2, 9, 3
+    blk = _random_block(rng, T, F, N)
+    plain = oracle.correlate(blk, lib=lib)
+    # one gate, every sample usable: the plain correlation; counts = T
+    v, c = oracle.correlate_gated(blk, np.zeros(T, np.int32), 1, lib=lib)
+    assert np.array_equal(v[0], plain) and (c == T).all()
+    # gates partition the samples: the sum over gates is the plain correlation,
+    # and each gate equals the plain correlation of its own samples
+    gate = rng.integers(0, G, T).astype(np.int32)
+    v, c = oracle.correlate_gated(blk, gate, G, lib=lib)
+    assert np.array_equal(v.sum(axis=0), plain)
+    for g in range(G):
+        assert np.array_equal(v[g], oracle.correlate(blk[gate == g], lib=lib))
+        assert (c[g] == (gate == g).sum()).all()
+    # a gate outside [0, G) drops the sample
+    gate2 = gate.copy()
+    gate2[::4] = -1
+    gate2[1::7] = G
+    v2, _ = oracle.correlate_gated(blk, gate2, G, lib=lib)
+    keep = (gate2 >= 0) & (gate2 < G)
+    assert np.array_equal(v2.sum(axis=0), oracle.correlate(blk[keep], lib=lib))
+    # a flagged sample contributes exactly what a zero sample (byte 0x88) does,
+    # and the counts are the usable samples per gate and input
+    valid = (rng.random((T, F, N)) > 0.2).astype(np.uint8)
+    v3, c3 = oracle.correlate_gated(blk, gate, G, valid, lib=lib)
+    zeroed = np.where(valid.astype(bool), blk, np.uint8(0x88))
+    v4, _ = oracle.correlate_gated(zeroed, gate, G, lib=lib)
+    assert np.array_equal(v3, v4)
+    for g in range(G):
+        assert np.array_equal(c3[g], valid[gate == g].sum(axis=0))
+    # closed form: every byte 0x00 (-8-8i), every sample usable: 128 T_g per gate
+    v5, _ = oracle.correlate_gated(np.zeros((T, F, N), np.uint8), gate, G, lib=lib)
+    for g in range(G):
+        assert (v5[g][..., 0] == 128 * (gate == g).sum()).all() and (v5[g][..., 1] == 0).all()
+
+
 PINS = [pin_constant_input, pin_impulses, pin_hermitian, pin_autocorrelations, pin_matmul,
-        pin_exhaustive_pairs, pin_beam_power, pin_linearity, pin_permutation, pin_pairs_and_subsets]
+        pin_exhaustive_pairs, pin_beam_power, pin_linearity, pin_permutation, pin_pairs_and_subsets, pin_gated]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -237,6 +276,8 @@ MUTANTS = {
                     "for (int64_t j = i + 1; j < N; j++) {\n                const"),
     "short_integration": ("for (int64_t t = 0; t < T; t++) {\n                    /*",
                           "for (int64_t t = 1; t < T; t++) {\n                    /*"),
+    "flag_only_first_input": ("                    if (valid && !valid[at + j]) continue;\n", ""),
+    "gate_off_by_one": ("if (g < 0 || g >= G) continue;", "if (g < 0 || g > G - 2) continue;"),
 }
 
 
