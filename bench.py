@@ -44,6 +44,23 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (594.477568e6 + 238.902272e6) / 16}
 
 
+def max_over_ranks(x, dist=None):
+    """Largest value of x over all ranks (x itself without a process group).
+    Works on the gloo (CPU tensors) and nccl (CUDA tensors) backends."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_max, world):
+    """Throughput of the whole job: every rank processed units_per_rank in at most seconds_max."""
+    return units_per_rank * world / seconds_max
+
+
 def useful_ops(T, F, N):
     return 8.0 * T * F * N * (N + 1) / 2
 
@@ -427,6 +444,8 @@ def main():
     if not args.no_peaks:
         probes = {}
         for name, kind, iters in (("tc_f8f6f4", xe.XENG_PEAK_TC_F8F6F4, 1 << 21), ("tc_f16", xe.XENG_PEAK_TC_F16, 1 << 20),
+                                  ("tc_f8f6f4_n128", xe.XENG_PEAK_TC_F8F6F4_N128, 1 << 21),
+                                  ("tc_f8f6f4_correlator_mix", xe.XENG_PEAK_TC_F8F6F4_MIX, 1 << 20),
                                   ("mma_sync_s8", xe.XENG_PEAK_MMA_SYNC_S8, 200000), ("dp4a", xe.XENG_PEAK_DP4A, 500000)):
             rc, tf, pms = xe.xeng_peak_probe(kind, iters)
             probes[name] = round(tf, 1) if rc == 0 else None
@@ -472,12 +491,9 @@ def main():
     ev1.record(stream)
     ev1.synchronize()
     push_dump_ms = ev0.elapsed_time(ev1) / 2
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     ops = useful_ops(T, F, N)
-    value = ops * world / (ms * 1e-3) / 1e12
+    value = whole_job_rate(ops, ms * 1e-3, world) / 1e12
 
     # dominant kernel: the correlation launches, timed live over the timed region
     peaks, peak_src = load_peaks()
@@ -523,12 +539,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             eng.correlate(hblock, hout, T, stream)  # returns once the triangle is in host memory
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ops * world / dt / 1e12, "unit": "TOPS", "h2d_bytes_per_step": T * F * N,
+        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist)
+        e2e = {"value": whole_job_rate(ops, dt, world) / 1e12, "unit": "TOPS", "h2d_bytes_per_step": T * F * N,
                "d2h_bytes_per_step": F * B * 8, "ms_per_step": dt * 1e3}
         del hblock, hout
 

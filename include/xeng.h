@@ -158,6 +158,17 @@ XENG_API int xeng_set_engine(xeng_t h, int32_t engine);
 XENG_API int xeng_decode(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t n_inputs,
                          int32_t f0, int32_t nf, uint8_t *planes, void *stream);
 
+/*
+ * xeng_selftest_wait_timeout -- exercise the kernels' bounded waits without a
+ *   fault or a hang: one thread of a 64-thread kernel waits limit_ns
+ *   (<= 1 s) on a barrier nothing completes, gives up and writes the
+ *   time-out status (2) to the status word; the other 63 threads, waiting on
+ *   the same barrier with the kernels' 2 s limit, see the word and leave at
+ *   once.  Writes the final status word and the number of threads that gave
+ *   up (64).  Synchronous; allocates 8 bytes.
+ */
+XENG_API int xeng_selftest_wait_timeout(int64_t limit_ns, int32_t *status, int32_t *threads_left);
+
 /* Launch and device-time counters of one handle (see xeng_set_profiling). */
 typedef struct {
     int64_t launches;          /* kernels launched by this handle so far      */

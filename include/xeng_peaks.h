@@ -24,6 +24,9 @@ extern "C" {
 #define XENG_PEAK_TC_F16      1  /* tcgen05.mma kind::f16, M128 N256 K16, f32 accumulate          */
 #define XENG_PEAK_MMA_SYNC_S8 2  /* warp mma.sync m16n8k32 s8 x s8 -> s32 (legacy INT8 tensor)   */
 #define XENG_PEAK_DP4A        3  /* CUDA-core dp4a (4 int8 products per instruction)             */
+#define XENG_PEAK_TC_F8F6F4_N128 4  /* as XENG_PEAK_TC_F8F6F4 with N = 128                       */
+#define XENG_PEAK_TC_F8F6F4_MIX  5  /* the correlator's mix per K step: one N = 256 and two N = 128
+                                       (second with A negated) into one 256-column accumulator   */
 
 /*
  * xeng_peak_probe -- run probe `kind` with `iters` instructions per issuing

@@ -19,6 +19,8 @@ LIB = os.path.join(HERE, "libxeng.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE]
+# Build parameters, e.g. XENG_NVCC_DEFINES="XENG_TC_CHUNK=64" (rebuild with --force after changing).
+DEFINES = ["-D" + d for d in os.environ.get("XENG_NVCC_DEFINES", "").split() if d]
 
 
 def nvcc() -> str:
@@ -44,7 +46,7 @@ def compile_jobs(force: bool = False, verbose_ptxas: bool = False):
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers()):
-            cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, *FLAGS, *DEFINES, "-c", src, "-o", obj]
             if verbose_ptxas:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((cmd, obj))

@@ -35,9 +35,19 @@
 namespace xeng {
 namespace {
 
-constexpr int kStages = 3;
-constexpr int kPlaneTile = kTile * kTile;     // 16 KB: 128 rows x 128 bytes
+// Samples per pipeline stage (the K extent of one TMA box): 128 with a
+// 128-byte swizzle, or 64 with a 64-byte swizzle (twice the stages of half the
+// size in the same shared memory).  A build parameter.
+#ifndef XENG_TC_CHUNK
+#define XENG_TC_CHUNK 128
+#endif
+constexpr int kKc = XENG_TC_CHUNK;
+static_assert(kKc == 128 || kKc == 64, "XENG_TC_CHUNK must be 128 or 64");
+constexpr int kPlaneTile = kTile * kKc;       // 128 rows x kKc bytes
 constexpr int kStageBytes = 4 * kPlaneTile;   // A_a, A_b, B_a, B_b
+constexpr int kStages = (3 * 4 * kTile * 128) / kStageBytes;  // 192 KB of stages
+constexpr int kKSteps = kKc / 32;             // 32-sample MMAs per stage
+constexpr int kChunksPer128 = 128 / kKc;
 constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kNumBars = 2 * kStages + 5;     // full, empty, acc_full x2, acc_empty x2, drain
@@ -55,12 +65,13 @@ constexpr uint32_t kIdescN256 = make_idesc(256, false);
 constexpr uint32_t kIdescN128 = make_idesc(128, false);
 constexpr uint32_t kIdescN128Neg = make_idesc(128, true);
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
-// bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+// Shared-memory matrix descriptor: K-major, rows of kKc bytes swizzled over
+// kKc bytes (layout 2 = 128-byte, 4 = 64-byte swizzle), 8-row groups 8 * kKc
+// bytes apart (SBO), descriptor version 1.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * kKc) >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)(kKc == 128 ? 2 : 4) << 61);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -96,7 +107,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 // Bounded wait for the phase with the given parity to complete.  Returns
 // false if the error word is set by someone else or if the limit passes
 // (then this thread sets it to `code`).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code)
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
+                                       uint64_t limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -104,7 +116,7 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, 
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*(volatile int *)err != 0) return false;
-            if (globaltimer() - t0 > kWaitLimitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 atomicCAS(err, 0, code);
                 return false;
             }
@@ -207,8 +219,8 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
         w.fl = wi.fl;
         w.I = wi.I;
         w.J = wi.J;
-        w.kc0 = wi.kc0;
-        w.kc1 = wi.kc1;
+        w.kc0 = wi.kc0 * kChunksPer128;
+        w.kc1 = wi.kc1 * kChunksPer128;
         w.mode = jd.mode;
     } else {
         w.map = tmap;
@@ -291,11 +303,11 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     }
                     const uint32_t st = sbase + stage * kStageBytes;
                     mbar_expect_tx(full_bar(stage), diag ? 2 * kPlaneTile : 4 * kPlaneTile);
-                    tma_load_2d(st, w.map, kc * kTile, rowA, full_bar(stage));
-                    tma_load_2d(st + kPlaneTile, w.map, kc * kTile, rowA + w.n_pad, full_bar(stage));
+                    tma_load_2d(st, w.map, kc * kKc, rowA, full_bar(stage));
+                    tma_load_2d(st + kPlaneTile, w.map, kc * kKc, rowA + w.n_pad, full_bar(stage));
                     if (!diag) {
-                        tma_load_2d(st + 2 * kPlaneTile, w.map, kc * kTile, rowB, full_bar(stage));
-                        tma_load_2d(st + 3 * kPlaneTile, w.map, kc * kTile, rowB + w.n_pad, full_bar(stage));
+                        tma_load_2d(st + 2 * kPlaneTile, w.map, kc * kKc, rowB, full_bar(stage));
+                        tma_load_2d(st + 3 * kPlaneTile, w.map, kc * kKc, rowB + w.n_pad, full_bar(stage));
                     }
                     ++issued;
                     if (++stage == kStages) {
@@ -340,7 +352,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     const uint32_t b_re = diag ? a_re : st + 2 * kPlaneTile;
                     const uint32_t b_im = b_re + kPlaneTile;
                     #pragma unroll
-                    for (int kk = 0; kk < 4; kk++) {
+                    for (int kk = 0; kk < kKSteps; kk++) {
                         const uint32_t off = kk * 32;
                         mma_f8(d, sw128_desc(a_re + off), sw128_desc(b_re + off), kIdescN256,
                                (kc != w.kc0 || kk != 0) ? 1u : 0u);
@@ -431,6 +443,22 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
     }
 }
 
+// Self-test of the bounded wait: thread 0 waits `limit_ns` on a barrier that
+// nothing arrives on and records kDevTimeoutMma; the other threads wait with
+// the full limit and leave as soon as they see the status word set.
+__global__ void wait_selftest_kernel(int *err, uint64_t limit_ns, int *left)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(b, 0u, err, kDevTimeoutMma, threadIdx.x == 0 ? limit_ns : kWaitLimitNs);
+    if (!ok) atomicAdd(left, 1);
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -461,12 +489,13 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
     CUtensorMap map;
     const cuuint64_t dims[2] = {(cuuint64_t)a.t_pad, (cuuint64_t)a.nf * 2 * a.n_pad};
     const cuuint64_t strides[1] = {(cuuint64_t)a.t_pad};
-    const cuuint32_t box[2] = {kTile, kTile};
+    const cuuint32_t box[2] = {(cuuint32_t)kKc, kTile};
     const cuuint32_t estr[2] = {1, 1};
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)a.planes, dims, strides,
-                                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        kKc == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(correlate_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -477,7 +506,7 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
     sc.tiles_per_ch = sc.nt * (sc.nt + 1) / 2;
     sc.n_tiles = a.nf * sc.tiles_per_ch;
     const int grid = sc.n_tiles < num_sms ? sc.n_tiles : num_sms;
-    correlate_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kTile), ListArgs{});
+    correlate_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kKc), ListArgs{});
     return cudaGetLastError();
 }
 
@@ -487,12 +516,31 @@ cudaError_t encode_planes_map(CUtensorMap *map, const uint8_t *planes, int64_t t
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)t_pad, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)t_pad};
-    const cuuint32_t box[2] = {kTile, kTile};
+    const cuuint32_t box[2] = {(cuuint32_t)kKc, kTile};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)planes, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, kKc == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t selftest_wait_timeout(int64_t limit_ns, int *status, int *left)
+{
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(d, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 64>>>(d, (uint64_t)limit_ns, d + 1);
+        e = cudaGetLastError();
+    }
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    *status = h[0];
+    *left = h[1];
+    return e;
 }
 
 cudaError_t prepare_correlate_tc_listed()

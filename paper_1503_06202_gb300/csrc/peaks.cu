@@ -22,8 +22,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// M = 128, N = 256 per instruction; K = 32 (8-bit) or 16 (16-bit).
-template <bool kF8>
+// M = 128 per instruction; K = 32 (8-bit) or 16 (16-bit).  kMix 0: N = 256;
+// 1: N = 128; 2: the correlator's pattern -- N = 256, then two N = 128 (the
+// second with A negated) into the two halves of the same 256 columns.
+template <bool kF8, int kMix>
 __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sink)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -49,13 +51,22 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sin
     const uint32_t tmem = tmem_slot;
     if (threadIdx.x == 0) {
         const uint32_t a = base, b = base + 16384;
-        const uint32_t idesc = (1u << 4) | (kF8 ? 0u : 0u) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        const uint32_t idesc = (1u << 4) | ((uint32_t)((kMix == 1 ? 128 : 256) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        const uint32_t idesc128 = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         for (int64_t i = 0; i < iters; i++) {
             const uint32_t off = (uint32_t)(i & 3) * 32;
             if (kF8) {
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
                              ::"r"(tmem), "l"(desc_sw128(a + off)), "l"(desc_sw128(b + off)), "r"(idesc), "r"(1));
+                if (kMix == 2) {
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                                 ::"r"(tmem), "l"(desc_sw128(a + off)), "l"(desc_sw128(b + 16384 + off)), "r"(idesc128), "r"(1));
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                                 ::"r"(tmem + 128), "l"(desc_sw128(a + off)), "l"(desc_sw128(b + off)), "r"(idesc128 | (1u << 13)), "r"(1));
+                }
             } else {
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
@@ -143,13 +154,23 @@ extern "C" int xeng_peak_probe(int32_t kind, int64_t iters, double *tflops, doub
         cudaEventRecord(e0);
         switch (kind) {
         case XENG_PEAK_TC_F8F6F4:
-            cudaFuncSetAttribute(tc_peak_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            tc_peak_kernel<true><<<sms, 128, smem>>>(iters, sink);
+            cudaFuncSetAttribute(tc_peak_kernel<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 0><<<sms, 128, smem>>>(iters, sink);
             flops = 2.0 * 128 * 256 * 32 * (double)iters * sms;
             break;
+        case XENG_PEAK_TC_F8F6F4_N128:
+            cudaFuncSetAttribute(tc_peak_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 1><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 128 * 32 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_MIX:
+            cudaFuncSetAttribute(tc_peak_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 2><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 512 * 32 * (double)iters * sms;
+            break;
         case XENG_PEAK_TC_F16:
-            cudaFuncSetAttribute(tc_peak_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            tc_peak_kernel<false><<<sms, 128, smem>>>(iters, sink);
+            cudaFuncSetAttribute(tc_peak_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<false, 0><<<sms, 128, smem>>>(iters, sink);
             flops = 2.0 * 128 * 256 * 16 * (double)iters * sms;
             break;
         case XENG_PEAK_MMA_SYNC_S8:
@@ -175,7 +196,7 @@ extern "C" int xeng_peak_probe(int32_t kind, int64_t iters, double *tflops, doub
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (err != cudaSuccess) return err == cudaErrorInvalidValue ? -1 : -5;
-    if (flag && (kind == XENG_PEAK_TC_F8F6F4 || kind == XENG_PEAK_TC_F16)) return -6;
+    if (flag) return -6;
     *ms = t;
     *tflops = flops / (t * 1e-3) / 1e12;
     return 0;

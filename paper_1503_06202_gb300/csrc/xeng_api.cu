@@ -602,6 +602,20 @@ int xeng_decode(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t
     return cuda_status(e);
 }
 
+int xeng_selftest_wait_timeout(int64_t limit_ns, int32_t *status, int32_t *threads_left)
+{
+    if (!status || !threads_left || limit_ns < 0 || limit_ns > 1000000000LL) return XENG_ERR_ARG;
+    int st = 0, left = 0;
+    cudaError_t e = selftest_wait_timeout(limit_ns, &st, &left);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return XENG_ERR_CUDA;
+    }
+    *status = st;
+    *threads_left = left;
+    return XENG_OK;
+}
+
 int xeng_set_profiling(xeng_t h, int32_t on)
 {
     if (!h) return XENG_ERR_ARG;

@@ -86,7 +86,10 @@ struct ListArgs {
     int64_t n_items;
 };
 cudaError_t encode_planes_map(CUtensorMap *map, const uint8_t *planes, int64_t t_pad, int64_t rows);
-cudaError_t prepare_correlate_tc_listed();  // kernel attributes; call before any stream capture
+cudaError_t prepare_correlate_tc_listed();
+// Bounded-wait self-test (no fault, no hang): *status = device status word
+// after one thread's wait ran out, *left = threads that gave up (all of them).
+cudaError_t selftest_wait_timeout(int64_t limit_ns, int *status, int *left);  // kernel attributes; call before any stream capture
 cudaError_t launch_correlate_tc_listed(const ListArgs &L, int grid, cudaStream_t s);
 
 // Plain CUDA-core correlation straight from the bytes (dp4a, int32).

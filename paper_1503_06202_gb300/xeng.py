@@ -142,6 +142,16 @@ def xeng_decode(block, n_samples, n_freq, n_inputs, f0, nf, planes, stream=None)
     return lib().xeng_decode(_ptr(block), n_samples, n_freq, n_inputs, f0, nf, _ptr(planes), _stream(stream))
 
 
+def xeng_selftest_wait_timeout(limit_ns: int):
+    """Returns (status, device status word, threads that gave up)."""
+    L = lib()
+    L.xeng_selftest_wait_timeout.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.xeng_selftest_wait_timeout.restype = ctypes.c_int
+    st, left = ctypes.c_int32(), ctypes.c_int32()
+    rc = L.xeng_selftest_wait_timeout(limit_ns, ctypes.byref(st), ctypes.byref(left))
+    return rc, st.value, left.value
+
+
 def xeng_set_profiling(h, on: bool) -> int:
     return lib().xeng_set_profiling(h, 1 if on else 0)
 
@@ -230,6 +240,7 @@ def xeng_correlate_noalloc(block, n_samples, n_freq, n_inputs, out, stream=None)
 
 
 XENG_PEAK_TC_F8F6F4, XENG_PEAK_TC_F16, XENG_PEAK_MMA_SYNC_S8, XENG_PEAK_DP4A = 0, 1, 2, 3
+XENG_PEAK_TC_F8F6F4_N128, XENG_PEAK_TC_F8F6F4_MIX = 4, 5
 
 
 def xeng_peak_probe(kind: int, iters: int):

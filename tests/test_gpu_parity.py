@@ -333,3 +333,17 @@ def test_full_size_workload(name):
         lhs = beam_power_gpu(block, w)
         rhs = weighted_sum_gpu(out, w)
         assert torch.equal(lhs, rhs), "beam-power identity fails on %d channels" % int((lhs != rhs).sum())
+
+
+def test_bounded_wait_times_out_with_status_and_context_stays_usable():
+    import time as _t
+    t0 = _t.perf_counter()
+    rc, status, left = xe.xeng_selftest_wait_timeout(50_000_000)  # 50 ms
+    dt = _t.perf_counter() - t0
+    assert rc == xe.XENG_OK
+    assert status == 2 and left == 64  # the MMA-wait status; every waiter gave up
+    assert dt < 1.5  # the other threads left on the status word, not after their 2 s limit
+    # the context is still usable: a normal correlation runs and is exact
+    rng = np.random.default_rng(31)
+    blk = rng.integers(0, 256, size=(200, 1, 40), dtype=np.uint8)
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "after time-out self-test")
