@@ -46,6 +46,8 @@ struct xeng_s {
     int64_t pstage_bytes = 0;
     int32_t *gidx = nullptr;       // sample indices of the gates of a gated call
     int64_t gidx_cap = 0;
+    struct PairList { int nt, nf, n; PairItem *dev; };
+    std::vector<PairList> pair_lists;  // device pair lists of the 2-CTA launches, by (nt, nf)
 };
 
 namespace {
@@ -97,6 +99,40 @@ cudaEvent_t take_event(xeng_s *h)
     cudaEvent_t e = nullptr;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
+}
+
+// Correlation launches use one CTA per tile, or (build parameter
+// XENG_TC_PAIRS=1) 2-CTA clusters in which neighbouring tiles of a tile row
+// share their A operand through TMA multicast.  Both give the same bits; on
+// GB300 the pairs were no faster (the feed is bound by shared-memory traffic,
+// not by L2 reads), so they are off by default.
+#ifndef XENG_TC_PAIRS
+#define XENG_TC_PAIRS 0
+#endif
+
+cudaError_t run_correlate(xeng_s *h, TcArgs a, cudaStream_t s)
+{
+    if (!XENG_TC_PAIRS) return launch_correlate_tc(a, h->num_sms, s);
+    const int nt = a.n_pad / kTile;
+    const xeng_s::PairList *pl = nullptr;
+    for (auto &p : h->pair_lists)
+        if (p.nt == nt && p.nf == a.nf) pl = &p;
+    if (!pl) {
+        std::vector<PairItem> v;
+        build_pair_list(nt, a.nf, v);
+        PairItem *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, v.size() * sizeof(PairItem));
+        if (e == cudaSuccess) e = cudaMemcpy(d, v.data(), v.size() * sizeof(PairItem), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return e;
+        }
+        h->pair_lists.push_back({nt, a.nf, (int)v.size(), d});
+        pl = &h->pair_lists.back();
+    }
+    a.pairs = pl->dev;
+    a.n_pairs = pl->n;
+    return launch_correlate_tc_pairs(a, h->num_sms, s);
 }
 
 // Run one kernel launch, bracketed by events when profiling.
@@ -204,6 +240,7 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->planes);
     cudaFree(h->staging);
     cudaFree(h->gidx);
+    for (auto &pl : h->pair_lists) cudaFree(pl.dev);
     cudaFree(h->pstage[0]);
     cudaFree(h->pstage[1]);
     if (h->h2d) cudaStreamDestroy(h->h2d);
@@ -246,6 +283,7 @@ const uint8_t *device_block(xeng_s *h, const uint8_t *block, int64_t bytes, cuda
     if (h->staging_bytes < bytes) {
         cudaFree(h->staging);
     cudaFree(h->gidx);
+    for (auto &pl : h->pair_lists) cudaFree(pl.dev);
     cudaFree(h->pstage[0]);
     cudaFree(h->pstage[1]);
     if (h->h2d) cudaStreamDestroy(h->h2d);
@@ -308,7 +346,7 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
             a.acc = target + f0 * nb2;
             a.accumulate = accumulate;
             a.err = h->d_err;
-            e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+            e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
         }
     }
     return e;
@@ -399,7 +437,7 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
         a.acc = target + f0 * nb2;
         a.accumulate = fresh ? 0 : 1;
         a.err = h->d_err;
-        e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+        e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
         if (e == cudaSuccess && host_out) {
             e = cudaStreamWaitEvent(h->d2h, h->ev_cmp[buf], 0);
@@ -547,7 +585,7 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
             a.acc = out_g + f0 * nb2;
             a.accumulate = 0;
             a.err = h->d_err;
-            e = timed_launch(h, 1, s, [&] { return launch_correlate_tc(a, h->num_sms, s); });
+            e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
         }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -1,6 +1,7 @@
 // xeng_internal.h -- declarations shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -48,6 +49,16 @@ int decode_vec_ok(const uint8_t *block, int32_t N);
 inline int64_t decode_ctas(int64_t t_pad, int64_t n_pad, int64_t F) { return (t_pad / 128) * (n_pad / 128) * F; }
 cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s);
 
+// Two tiles run together by the two CTAs of a cluster (CTA r takes tile r).
+// flags bit 0: same (channel, I) -- the CTAs share the A operand, each loading
+// one of its two planes into both CTAs' shared memory (TMA multicast);
+// bit 1: tile 1 repeats tile 0 to keep the pair in step (CTA 1 writes nothing).
+struct PairItem {
+    int32_t fl[2];
+    int16_t I[2], J[2];
+    int32_t flags;
+};
+
 // Tensor-core correlation of decoded planes (tcgen05, FP8 E4M3, f32 in TMEM).
 // acc: int32 [nf][N(N+1)/2][2] of the channel group; accumulate = add to it.
 struct TcArgs {
@@ -59,8 +70,14 @@ struct TcArgs {
     int32_t *acc;
     int32_t accumulate;
     int32_t *err;
+    const PairItem *pairs = nullptr;  // launch_correlate_tc_pairs: the pair list
+    int32_t n_pairs = 0;
 };
 cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s);
+// The same correlation by 2-CTA clusters over a pair list (see PairItem).
+cudaError_t launch_correlate_tc_pairs(const TcArgs &a, int num_sms, cudaStream_t s);
+// Pair list of nf channels of nt x nt tile grids, channel-major.
+void build_pair_list(int nt, int nf, std::vector<PairItem> &out);
 
 // Batched (listed) launches: a job table, per-job tensor maps and a work list
 // partitioned by CTA, all in device memory.
