@@ -446,6 +446,7 @@ def main():
         for name, kind, iters in (("tc_f8f6f4", xe.XENG_PEAK_TC_F8F6F4, 1 << 21), ("tc_f16", xe.XENG_PEAK_TC_F16, 1 << 20),
                                   ("tc_f8f6f4_n128", xe.XENG_PEAK_TC_F8F6F4_N128, 1 << 21),
                                   ("tc_f8f6f4_correlator_mix", xe.XENG_PEAK_TC_F8F6F4_MIX, 1 << 20),
+                                  ("tc_f8f6f4_live_data", xe.XENG_PEAK_TC_F8F6F4_LIVE, 1 << 21),
                                   ("mma_sync_s8", xe.XENG_PEAK_MMA_SYNC_S8, 200000), ("dp4a", xe.XENG_PEAK_DP4A, 500000)):
             rc, tf, pms = xe.xeng_peak_probe(kind, iters)
             probes[name] = round(tf, 1) if rc == 0 else None
@@ -517,6 +518,10 @@ def main():
             executed = nt * (nt + 1) // 2 * 128 * 128 / (N * (N + 1) / 2)
             roof["executed_over_useful"] = executed
             roof["frac_executed_of_probe_fp8"] = roof["achieved"] * executed / probes["tc_f8f6f4"]
+        if probes and probes.get("tc_f8f6f4_live_data"):
+            roof["peak_probe_fp8_live_data"] = probes["tc_f8f6f4_live_data"]
+            roof["frac_executed_of_probe_fp8_live_data"] = (roof["achieved"] * roof.get("executed_over_useful", 1.0)
+                                                           / probes["tc_f8f6f4_live_data"])
         if probes and probes.get("mma_sync_s8"):
             roof["frac_of_probe_int8_mma_sync"] = roof["achieved"] / probes["mma_sync_s8"]
     else:

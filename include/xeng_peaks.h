@@ -25,6 +25,8 @@ extern "C" {
 #define XENG_PEAK_MMA_SYNC_S8 2  /* warp mma.sync m16n8k32 s8 x s8 -> s32 (legacy INT8 tensor)   */
 #define XENG_PEAK_DP4A        3  /* CUDA-core dp4a (4 int8 products per instruction)             */
 #define XENG_PEAK_TC_F8F6F4_N128 4  /* as XENG_PEAK_TC_F8F6F4 with N = 128                       */
+#define XENG_PEAK_TC_F8F6F4_LIVE 6  /* as XENG_PEAK_TC_F8F6F4 with random codes of -8..7 instead of
+                                       zeros (the power the tensor core draws depends on the data) */
 #define XENG_PEAK_TC_F8F6F4_MIX  5  /* the correlator's mix per K step: one N = 256 and two N = 128
                                        (second with A negated) into one 256-column accumulator   */
 

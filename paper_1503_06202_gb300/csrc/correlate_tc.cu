@@ -548,6 +548,259 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
+// ---------------------------------------------------------------------------
+// cta_group::2 variant: a cluster of two CTAs computes a 256 x 256 complex
+// tile (inputs i in I2*256 + [0, 256), j in J2*256 + [0, 256), I2 <= J2) with
+// M = 256, N = 256 pair MMAs.  CTA r holds the A planes of rows
+// I2*256 + r*128 + [0, 128) and the B planes of j rows J2*256 + r*128 + [0, 128);
+// each pair MMA reads A rows from both CTAs and B's N halves from both, so a
+// CTA supplies half the B operand and the operand bytes per MAC halve.  Per
+// 32-sample K step the leader issues
+//     Re += A_a B_a^T,  Re += A_b B_b^T,  Im += A_b B_a^T,  Im += (-A_a) B_b^T
+// into two 256-column accumulators (all 512 TMEM columns, so the epilogue of
+// a tile does not overlap the next tile's MMAs).  Both CTAs' TMA copies
+// complete on the leader's barriers; the leader's commits reach both CTAs.
+constexpr int kThreads2 = 320;                  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 epilogue
+constexpr int kEpiThreads2 = 256;               // per CTA
+constexpr int kNumBars2 = 2 * kStages + 3;      // full, empty, acc_full, acc_empty, drain
+constexpr size_t kSmemBytes2 = 1024 + (size_t)kStages * kStageBytes + kNumBars2 * 8 + 16;
+
+__host__ __device__ constexpr uint32_t make_idesc_m256(bool neg_a)
+{
+    return (1u << 4) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+constexpr uint32_t kIdesc2 = make_idesc_m256(false);
+constexpr uint32_t kIdesc2Neg = make_idesc_m256(true);
+
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar_cluster)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8_cg2(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit_cg2(uint32_t bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(mask)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+struct Sched2 {
+    int nt2, tiles_per_ch, n_tiles;
+    __device__ __forceinline__ void decode(int tile, int &fl, int &I, int &J) const
+    {
+        fl = tile / tiles_per_ch;
+        tile_pair(tile - fl * tiles_per_ch, nt2, I, J);
+    }
+};
+
+__global__ void __launch_bounds__(kThreads2, 1)
+correlate_tc2_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, const Sched2 sc, const int n_k)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    const uint32_t bars = sbase + kStages * kStageBytes;
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (kStages + s); };
+    const uint32_t accf_bar = bars + 8u * (2 * kStages);
+    const uint32_t acce_bar = bars + 8u * (2 * kStages + 1);
+    const uint32_t drain_bar = bars + 8u * (2 * kStages + 2);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * kNumBars2 - raw));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    int *err = a.err;
+    const int it_begin = (int)(blockIdx.x >> 1), it_step = (int)(gridDim.x >> 1);
+    const uint16_t kBoth = 0x3;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(accf_bar, 1);
+        mbar_init(acce_bar, 2 * kEpiThreads2);  // both CTAs' epilogue threads
+        mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap) : "memory");
+    }
+    if (warp == 1) {  // one collective allocation for the pair: both CTAs issue it
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync();  // the peer's barriers and TMEM exist before anything targets them
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both CTAs) ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int tile = it_begin; ok && tile < sc.n_tiles; tile += it_step) {
+                int fl, I2, J2;
+                sc.decode(tile, fl, I2, J2);
+                const bool diag = (I2 == J2);
+                const int rowA = fl * 2 * a.n_pad + I2 * 256 + (int)rank * kTile;
+                const int rowB = fl * 2 * a.n_pad + J2 * 256 + (int)rank * kTile;
+                for (int kc = 0; kc < n_k; kc++) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + stage * kStageBytes;
+                    const uint32_t fb = mapa_rank(full_bar(stage), 0);  // the leader's barrier
+                    if (leader) mbar_expect_tx(full_bar(stage), 2u * (diag ? 2 * kPlaneTile : 4 * kPlaneTile));
+                    tma_load_2d_cg2(st, &tmap, kc * kKc, rowA, fb);
+                    tma_load_2d_cg2(st + kPlaneTile, &tmap, kc * kKc, rowA + a.n_pad, fb);
+                    if (!diag) {
+                        tma_load_2d_cg2(st + 2 * kPlaneTile, &tmap, kc * kKc, rowB, fb);
+                        tma_load_2d_cg2(st + 3 * kPlaneTile, &tmap, kc * kKc, rowB + a.n_pad, fb);
+                    }
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------- MMA issuer (leader CTA) ----------------
+            int stage = 0;
+            uint32_t phase = 0, uses = 0;
+            bool ok = true;
+            const uint32_t d_re = tmem, d_im = tmem + 256u;
+            for (int tile = it_begin; ok && tile < sc.n_tiles; tile += it_step) {
+                int fl, I2, J2;
+                sc.decode(tile, fl, I2, J2);
+                const bool diag = (I2 == J2);
+                if (!mbar_wait(acce_bar, (uses & 1u) ^ 1u, err, kDevTimeoutMma)) break;
+                ++uses;
+                fence_after();
+                for (int kc = 0; kc < n_k; kc++) {
+                    if (!mbar_wait(full_bar(stage), phase, err, kDevTimeoutMma)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t st = sbase + stage * kStageBytes;
+                    const uint32_t a_a = st, a_b = st + kPlaneTile;
+                    const uint32_t b_a = diag ? a_a : st + 2 * kPlaneTile;
+                    const uint32_t b_b = b_a + kPlaneTile;
+                    #pragma unroll
+                    for (int kk = 0; kk < kKSteps; kk++) {
+                        const uint32_t off = kk * 32;
+                        const uint32_t acc = (kc != 0 || kk != 0) ? 1u : 0u;
+                        mma_f8_cg2(d_re, sw128_desc(a_a + off), sw128_desc(b_a + off), kIdesc2, acc);
+                        mma_f8_cg2(d_re, sw128_desc(a_b + off), sw128_desc(b_b + off), kIdesc2, 1u);
+                        mma_f8_cg2(d_im, sw128_desc(a_b + off), sw128_desc(b_a + off), kIdesc2, acc);
+                        mma_f8_cg2(d_im, sw128_desc(a_a + off), sw128_desc(b_b + off), kIdesc2Neg, 1u);
+                    }
+                    mma_commit_cg2(empty_bar(stage), kBoth);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit_cg2(accf_bar, kBoth);
+            }
+            // Drain: every MMA issued above has finished once this completes.
+            mma_commit_cg2(drain_bar, 0x1);
+            (void)mbar_wait(drain_bar, 0u, err, kDevTimeoutMma);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9 of both CTAs) ----------------
+        const int q = warp & 3;                 // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;       // which 128 of the 256 columns
+        const int row = q * 32 + lane;
+        const uint32_t acce_leader = mapa_rank(acce_bar, 0);
+        uint32_t uses = 0;
+        const int64_t N = a.N;
+        for (int tile = it_begin; tile < sc.n_tiles; tile += it_step) {
+            int fl, I2, J2;
+            sc.decode(tile, fl, I2, J2);
+            const bool ok = mbar_wait(accf_bar, uses & 1u, err, kDevTimeoutEpilogue);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            ++uses;
+            fence_after();
+            const int64_t i = (int64_t)I2 * 256 + rank * kTile + row;
+            const bool row_ok = i < N;
+            const int64_t row_base = i * N - i * (i - 1) / 2 - i;
+            int2 *out = reinterpret_cast<int2 *>(a.acc + (int64_t)fl * N * (N + 1));
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+            for (int c = half * 128; c < half * 128 + 128; c += 16) {
+                uint32_t re[16], im[16];
+                tmem_ld16(taddr + c, re);
+                tmem_ld16(taddr + 256 + c, im);
+                tmem_ld_wait();
+                if (row_ok) {
+                    const int64_t j0 = (int64_t)J2 * 256 + c;
+                    int2 *p = out + row_base + j0;
+                    const int64_t e_lo = i - j0, e_hi = N - j0;
+                    if (a.accumulate) {
+                        int2 old[16];
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi) old[e] = p[e];
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi)
+                                p[e] = make_int2(old[e].x + __float2int_rn(__uint_as_float(re[e])),
+                                                 old[e].y + __float2int_rn(__uint_as_float(im[e])));
+                    } else {
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            if (e >= e_lo && e < e_hi)
+                                p[e] = make_int2(__float2int_rn(__uint_as_float(re[e])),
+                                                 __float2int_rn(__uint_as_float(im[e])));
+                    }
+                }
+            }
+            fence_before();
+            mbar_arrive_cluster(acce_leader);
+        }
+    }
+
+    __syncwarp();
+    fence_before();
+    __syncthreads();
+    cluster_sync();  // no copy, commit or arrival of the peer may still target this CTA
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
@@ -647,6 +900,35 @@ cudaError_t launch_correlate_tc_pairs(const TcArgs &a, int num_sms, cudaStream_t
     cfg.numAttrs = 1;
     Sched sc{};
     return cudaLaunchKernelEx(&cfg, correlate_tc_kernel<false, true>, map, a, sc, (int)(a.t_pad / kKc), ListArgs{});
+}
+
+cudaError_t launch_correlate_tc2(const TcArgs &a, int num_sms, cudaStream_t s)
+{
+    if (a.nf <= 0) return cudaSuccess;
+    if (a.t_pad % kTile != 0 || a.n_pad % 256 != 0 || a.t_pad > kMaxChunkSamples) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    cudaError_t e = encode_planes_map(&map, a.planes, a.t_pad, (int64_t)a.nf * 2 * a.n_pad);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(correlate_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes2);
+    if (e != cudaSuccess) return e;
+    Sched2 sc;
+    sc.nt2 = a.n_pad / 256;
+    sc.tiles_per_ch = sc.nt2 * (sc.nt2 + 1) / 2;
+    sc.n_tiles = a.nf * sc.tiles_per_ch;
+    const int clusters = sc.n_tiles < num_sms / 2 ? sc.n_tiles : num_sms / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters, 1, 1);
+    cfg.blockDim = dim3(kThreads2, 1, 1);
+    cfg.dynamicSmemBytes = kSmemBytes2;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, correlate_tc2_kernel, map, a, sc, (int)(a.t_pad / kKc));
 }
 
 cudaError_t encode_planes_map(CUtensorMap *map, const uint8_t *planes, int64_t t_pad, int64_t rows)

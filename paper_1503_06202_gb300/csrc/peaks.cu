@@ -25,7 +25,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 // M = 128 per instruction; K = 32 (8-bit) or 16 (16-bit).  kMix 0: N = 256;
 // 1: N = 128; 2: the correlator's pattern -- N = 256, then two N = 128 (the
 // second with A negated) into the two halves of the same 256 columns.
-template <bool kF8, int kMix>
+// kRandom: operands are E4M3 codes of pseudo-random integers in [-8, 7] (the
+// correlator's operand values) instead of zeros -- the tensor core draws more
+// power on live data, which matters under the board's power cap.
+template <bool kF8, int kMix, bool kRandom = false>
 __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sink)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -34,7 +37,14 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sin
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    for (int k = threadIdx.x; k < 48 * 1024 / 4; k += blockDim.x) reinterpret_cast<uint32_t *>(gbase)[k] = 0;
+    // E4M3 codes of -8..7
+    const uint8_t codes[16] = {0xD0, 0xCE, 0xCC, 0xCA, 0xC8, 0xC4, 0xC0, 0xB8,
+                               0x00, 0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E};
+    for (int k = threadIdx.x; k < 48 * 1024; k += blockDim.x) {
+        uint32_t h = (uint32_t)k * 2654435761u + blockIdx.x * 40503u;
+        h ^= h >> 15;
+        gbase[k] = kRandom ? codes[h & 15] : (uint8_t)0;
+    }
     const uint32_t bar_a = smem_u32(&bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
@@ -167,6 +177,11 @@ extern "C" int xeng_peak_probe(int32_t kind, int64_t iters, double *tflops, doub
             cudaFuncSetAttribute(tc_peak_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             tc_peak_kernel<true, 2><<<sms, 128, smem>>>(iters, sink);
             flops = 2.0 * 128 * 512 * 32 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_LIVE:
+            cudaFuncSetAttribute(tc_peak_kernel<true, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 0, true><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 256 * 32 * (double)iters * sms;
             break;
         case XENG_PEAK_TC_F16:
             cudaFuncSetAttribute(tc_peak_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

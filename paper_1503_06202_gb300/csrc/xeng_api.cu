@@ -101,17 +101,24 @@ cudaEvent_t take_event(xeng_s *h)
     return e;
 }
 
-// Correlation launches use one CTA per tile, or (build parameter
-// XENG_TC_PAIRS=1) 2-CTA clusters in which neighbouring tiles of a tile row
-// share their A operand through TMA multicast.  Both give the same bits; on
-// GB300 the pairs were no faster (the feed is bound by shared-memory traffic,
-// not by L2 reads), so they are off by default.
+// Correlation launches of a handle: one CTA per 128 x 128 tile (default), or
+// (build parameter XENG_TC_2CTA=1) cta_group::2 clusters computing 256 x 256
+// tiles, or (XENG_TC_PAIRS=1) 2-CTA clusters in which neighbouring 128 x 128
+// tiles of a tile row share their A operand through TMA multicast.  All give
+// the same bits; the alternatives measured no faster on GB300.
+#ifndef XENG_TC_2CTA
+#define XENG_TC_2CTA 0
+#endif
 #ifndef XENG_TC_PAIRS
 #define XENG_TC_PAIRS 0
 #endif
 
+// Rows of the decoded planes per channel and plane: N rounded up to the tile.
+int64_t planes_rows(int64_t N) { return round_up(N, XENG_TC_2CTA ? 256 : kTile); }
+
 cudaError_t run_correlate(xeng_s *h, TcArgs a, cudaStream_t s)
 {
+    if (XENG_TC_2CTA) return launch_correlate_tc2(a, h->num_sms, s);
     if (!XENG_TC_PAIRS) return launch_correlate_tc(a, h->num_sms, s);
     const int nt = a.n_pad / kTile;
     const xeng_s::PairList *pl = nullptr;
@@ -203,7 +210,7 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
 
     // Decode buffer: rounds of (group_f channels x chunk_t samples); the
     // budget bounds it at 16 GiB or a quarter of the free memory.
-    const int64_t n_pad = round_up(n_inputs, kTile);
+    const int64_t n_pad = planes_rows(n_inputs);
     h->chunk_t = round_up(t_integ < kMaxChunkSamples ? t_integ : kMaxChunkSamples, kTile);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -318,7 +325,7 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
                       cudaStream_t s)
 {
     const int64_t N = h->N, F = h->F;
-    const int64_t n_pad = round_up(N, kTile);
+    const int64_t n_pad = planes_rows(N);
     const int64_t nb2 = N * (N + 1);
     if (h->engine == XENG_ENGINE_DP4A) {
         return timed_launch(h, 1, s, [&] {
@@ -396,7 +403,7 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
                         bool fresh, cudaStream_t s)
 {
     const int64_t N = h->N, F = h->F;
-    const int64_t n_pad = round_up(N, kTile), t_pad = round_up(n, kTile), nb2 = N * (N + 1);
+    const int64_t n_pad = planes_rows(N), t_pad = round_up(n, kTile), nb2 = N * (N + 1);
     int64_t pf = (F + 7) / 8;  // about eight groups
     if (pf > h->group_f) pf = h->group_f;
     if (pf < 1) pf = 1;
@@ -535,7 +542,7 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
         return XENG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = h->N, F = h->F;
-    const int64_t n_pad = round_up(N, kTile), nb2 = N * (N + 1);
+    const int64_t n_pad = planes_rows(N), nb2 = N * (N + 1);
     // the samples of each gate, in time order
     std::vector<int64_t> cnt(n_gates + 1, 0);
     for (int64_t t = 0; t < n_samples; t++)

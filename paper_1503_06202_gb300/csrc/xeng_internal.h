@@ -74,6 +74,9 @@ struct TcArgs {
     int32_t n_pairs = 0;
 };
 cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s);
+// The same correlation with cta_group::2: clusters of two CTAs compute
+// 256 x 256 tiles (a.n_pad must be a multiple of 256).
+cudaError_t launch_correlate_tc2(const TcArgs &a, int num_sms, cudaStream_t s);
 // The same correlation by 2-CTA clusters over a pair list (see PairItem).
 cudaError_t launch_correlate_tc_pairs(const TcArgs &a, int num_sms, cudaStream_t s);
 // Pair list of nf channels of nt x nt tile grids, channel-major.
