@@ -403,6 +403,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the dense-throughput probes")
+    ap.add_argument("--no-shift", action="store_true", help="skip the time-shift measurement")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-max-blocks", type=int, default=32)
@@ -485,13 +486,37 @@ def main():
     eng.set_profiling(False)
     clocks = clk.summary()
     # the same integration through xeng_push + xeng_dump (adds the triangle copy)
-    ev0.record(stream)
-    for _ in range(2):
-        eng.push(block, T, stream)
-        eng.dump(out, stream)
-    ev1.record(stream)
-    ev1.synchronize()
-    push_dump_ms = ev0.elapsed_time(ev1) / 2
+    def push_dump(reps=2):
+        eng.set_profiling(True)
+        eng.stats(reset=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            eng.push(block, T, stream)
+            eng.dump(out, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        s2 = eng.stats(reset=True)
+        eng.set_profiling(False)
+        return ev0.elapsed_time(ev1) / reps, s2["decode_ms"] / reps
+
+    push_dump_ms, push_dump_decode_ms = push_dump()
+    # time shifting (Sec. IV-C-5): two inputs of an outlying station delayed by
+    # 168 ms (65,625 samples), the rest undelayed; the stream history carries
+    # across the pushes
+    shift = None
+    if args.engine == "tensor" and not args.no_shift:
+        import numpy as np
+        d = np.zeros(N, np.int32)
+        d[N - 2:] = 65625
+        eng.set_delays(d)
+        push_dump(1)
+        sh_ms, sh_dec = push_dump()
+        eng.set_delays(None)
+        shift = {"delayed_inputs": 2, "delay_samples": 65625, "push_dump_ms_per_step": sh_ms,
+                 "decode_ms_per_step": sh_dec, "unshifted_push_dump_ms_per_step": push_dump_ms,
+                 "unshifted_decode_ms_per_step": push_dump_decode_ms,
+                 "value": whole_job_rate(useful_ops(T, F, N), max_over_ranks(sh_ms, dist) * 1e-3, world) / 1e12,
+                 "unit": "TOPS"}
     ms = max_over_ranks(ms, dist)
     ops = useful_ops(T, F, N)
     value = whole_job_rate(ops, ms * 1e-3, world) / 1e12
@@ -564,7 +589,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
-                "push_dump_ms_per_step": push_dump_ms,
+                "push_dump_ms_per_step": push_dump_ms, "time_shift": shift,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}
         print(json.dumps(line), flush=True)

@@ -131,6 +131,30 @@ XENG_API int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, i
 XENG_API int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int32_t *gate,
                                   int32_t n_gates, const uint8_t *valid, int32_t *out, int32_t *counts, void *stream);
 
+/*
+ * xeng_set_delays -- time shifting (Sec. IV-C-5).  The signal of an outlying
+ *   station reaches the correlator early relative to the other inputs, which
+ *   decorrelates it from them; delaying that input by a whole number of
+ *   samples restores the correlation.  With delays d_i set, every later
+ *   xeng_push integrates
+ *     V_ij(f) += sum_t y_i(t, f) conj(y_j(t, f)),   y_i(t, f) = x_i(t - d_i, f),
+ *   where t counts the samples of the handle's stream (every push since this
+ *   call, in order) and x_i(t) = 0 + 0i for t < 0.  Between pushes the handle
+ *   keeps the last max(d) samples of each delayed input on the device
+ *   (2 * max(d) * n_freq * #{i : d_i > 0} bytes); xeng_dump does not reset
+ *   that history.
+ *   delays: host int32 [n_inputs], each in [0, XENG_MAX_DELAY]; NULL, or all
+ *   zero, removes the delays.  The history restarts empty (zeros) with every
+ *   call.  Synchronizes the device: a set-up call, not for the streaming loop.
+ *   Errors: XENG_ERR_ARG (NULL handle), XENG_ERR_RANGE (a delay out of range),
+ *   XENG_ERR_UNSUPPORTED (handle on the dp4a engine), XENG_ERR_NOMEM (delays
+ *   removed).  While delays are set, xeng_correlate, xeng_correlate_gated and
+ *   xeng_set_engine(XENG_ENGINE_DP4A) return XENG_ERR_UNSUPPORTED: they have
+ *   no stream history to shift against.
+ */
+#define XENG_MAX_DELAY 131072  /* samples; 168 ms at 2.56 us per sample is 65,625 */
+XENG_API int xeng_set_delays(xeng_t h, const int32_t *delays);
+
 /* xeng_destroy -- free the handle and its device memory; NULL is a no-op.
  * Synchronizes the device first. */
 XENG_API void xeng_destroy(xeng_t h);

@@ -18,7 +18,10 @@ arithmetic, so the oracle is that definition written out in ``oracle.c``.
 Pinned by ``tests/test_oracle_pins.py`` against closed forms (constant and
 impulse inputs), Hermitian symmetry, autocorrelation sums, brute force in
 Python integers on small N, exhaustive two-input cases, the beam-power
-identity, linearity in time and input-permutation covariance.
+identity, linearity in time and input-permutation covariance; the time shift
+(Sec. IV-C-5) and the beamformer (Sec. IV-C-3) against the plain correlation of
+shifted streams built in numpy, numpy complex matmul and the beam-power
+identity.
 """
 from __future__ import annotations
 
@@ -59,7 +62,10 @@ def bind(path: str):
     lib.oracle_correlate_pairs.argtypes = [u8p, i64, i32, i32, i64, i32p, i32p, i32p, i64p]
     lib.oracle_beam_power.argtypes = [u8p, i64, i32, i32, i32, i32, i64p, i64p, i64p]
     lib.oracle_correlate_gated.argtypes = [u8p, i64, i32, i32, i32p, i32, u8p, i64p, i64p]
+    lib.oracle_correlate_shifted.argtypes = [u8p, i64, i32, i32, i32p, i64, i64, i64p]
+    lib.oracle_beamform.argtypes = [u8p, i64, i32, i32, i32p, i32p, i32, i64p]
     for fn in (lib.oracle_correlate, lib.oracle_correlate_full, lib.oracle_correlate_gated,
+               lib.oracle_correlate_shifted, lib.oracle_beamform,
                lib.oracle_correlate_pairs, lib.oracle_beam_power, lib.oracle_num_threads):
         fn.restype = ctypes.c_int
     return lib
@@ -172,6 +178,40 @@ def correlate_gated(block, gate, n_gates: int, valid=None, lib=None):
                                          vp, _ptr(out, ctypes.c_int64), _ptr(counts, ctypes.c_int64)) != 0:
         raise ValueError("oracle_correlate_gated: bad arguments")
     return out, counts
+
+
+def correlate_shifted(block, delays, t_a: int = 0, t_b: int | None = None, lib=None) -> np.ndarray:
+    """Time-shifted visibilities (Sec. IV-C-5) over the window t_a <= t < t_b of
+    the stream ``block``: input i delayed by delays[i] >= 0 samples, zero before
+    the stream's first sample.  int64 [F][N(N+1)/2][2]."""
+    block = _check_block(block)
+    T, F, N = block.shape
+    t_b = T if t_b is None else t_b
+    delays = np.ascontiguousarray(delays, dtype=np.int32)
+    if delays.shape != (N,):
+        raise ValueError("delays must be int32 [N]")
+    out = np.zeros((F, n_baselines(N), 2), dtype=np.int64)
+    if _load(lib).oracle_correlate_shifted(_ptr(block, ctypes.c_uint8), T, F, N, _ptr(delays, ctypes.c_int32),
+                                           t_a, t_b, _ptr(out, ctypes.c_int64)) != 0:
+        raise ValueError("oracle_correlate_shifted: bad arguments")
+    return out
+
+
+def beamform(block, w_re, w_im, lib=None) -> np.ndarray:
+    """Formed beams (Sec. IV-C-3): y_b(t, f) = sum_i w_{f,b,i} x_i(t, f) with
+    Gaussian-integer weights w_re, w_im [F][B][N].  int64 [T][F][B][2]."""
+    block = _check_block(block)
+    T, F, N = block.shape
+    w_re = np.ascontiguousarray(w_re, dtype=np.int32)
+    w_im = np.ascontiguousarray(w_im, dtype=np.int32)
+    if w_re.ndim != 3 or w_re.shape[0] != F or w_re.shape[2] != N or w_im.shape != w_re.shape:
+        raise ValueError("weights must be int32 [F][B][N]")
+    B = w_re.shape[1]
+    out = np.zeros((T, F, B, 2), dtype=np.int64)
+    if _load(lib).oracle_beamform(_ptr(block, ctypes.c_uint8), T, F, N, _ptr(w_re, ctypes.c_int32),
+                                  _ptr(w_im, ctypes.c_int32), B, _ptr(out, ctypes.c_int64)) != 0:
+        raise ValueError("oracle_beamform: bad arguments")
+    return out
 
 
 def weighted_sum(vis, w_re, w_im) -> np.ndarray:

@@ -240,3 +240,88 @@ int oracle_correlate_gated(const uint8_t *in, int64_t T, int32_t F, int32_t N, c
     }
     return 0;
 }
+
+/*
+ * oracle_correlate_shifted: time shifting (Sec. IV-C-5: an input from an
+ * outlying station is delayed inside the correlator so that its signal lines
+ * up with the others again).  Input i is delayed by delays[i] >= 0 samples:
+ *
+ *     y_i(t, f) = x_i(t - delays[i], f),  and 0 where t - delays[i] < 0
+ *
+ * (nothing precedes the stream's first sample).  For the window
+ * t_a <= t < t_b of the stream in[T][F][N] and every channel f, pair i <= j:
+ *
+ *     V_ij(f) = sum_{t = t_a}^{t_b - 1} y_i(t, f) * conj(y_j(t, f)).
+ *
+ * out: int64 [F][N(N+1)/2][2].  Returns 0, or -1 on bad arguments / no memory.
+ */
+int oracle_correlate_shifted(const uint8_t *in, int64_t T, int32_t F, int32_t N, const int32_t *delays, int64_t t_a,
+                             int64_t t_b, int64_t *out)
+{
+    if (T < 0 || F < 1 || N < 1 || !delays || t_a < 0 || t_b < t_a || t_b > T)
+        return -1;
+    for (int32_t i = 0; i < N; i++)
+        if (delays[i] < 0)
+            return -1;
+    const int64_t W = t_b - t_a, nb = (int64_t)N * (N + 1) / 2;
+    int64_t *re = malloc(sizeof(int64_t) * (size_t)(N * W + 1));
+    int64_t *im = malloc(sizeof(int64_t) * (size_t)(N * W + 1));
+    if (!re || !im) { free(re); free(im); return -1; }
+    for (int32_t f = 0; f < F; f++) {
+        /* the delayed series y_i over the window */
+        for (int64_t i = 0; i < N; i++)
+            for (int64_t w = 0; w < W; w++) {
+                const int64_t s = t_a + w - delays[i];
+                re[i * W + w] = s >= 0 ? sample_re(in[(s * F + f) * (int64_t)N + i]) : 0;
+                im[i * W + w] = s >= 0 ? sample_im(in[(s * F + f) * (int64_t)N + i]) : 0;
+            }
+        int64_t *o = out + (int64_t)f * nb * 2;
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < N; i++)
+            for (int64_t j = i; j < N; j++) {
+                int64_t vr = 0, vi = 0;
+                for (int64_t w = 0; w < W; w++) {
+                    vr += re[i * W + w] * re[j * W + w] + im[i * W + w] * im[j * W + w];
+                    vi += im[i * W + w] * re[j * W + w] - re[i * W + w] * im[j * W + w];
+                }
+                o[2 * tri_index(i, j, N)] = vr;
+                o[2 * tri_index(i, j, N) + 1] = vi;
+            }
+    }
+    free(re);
+    free(im);
+    return 0;
+}
+
+/*
+ * oracle_beamform: discrete beamforming (Sec. IV-C-3: the data of all inputs
+ * are phase-shifted and summed, which points a beam at one region of the sky;
+ * the beam is written out at the full sample cadence).  With Gaussian-integer
+ * weights w_{f,b,i} = w_re + i w_im, for every sample t, channel f, beam b:
+ *
+ *     y_b(t, f) = sum_i w_{f,b,i} * x_i(t, f).
+ *
+ * w_re, w_im: int32 [F][B][N].  out: int64 [T][F][B][2].
+ */
+int oracle_beamform(const uint8_t *in, int64_t T, int32_t F, int32_t N, const int32_t *w_re, const int32_t *w_im,
+                    int32_t B, int64_t *out)
+{
+    if (T < 0 || F < 1 || N < 1 || B < 1 || !w_re || !w_im)
+        return -1;
+    #pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < T; t++)
+        for (int64_t f = 0; f < F; f++)
+            for (int64_t b = 0; b < B; b++) {
+                int64_t yr = 0, yi = 0;
+                for (int64_t i = 0; i < N; i++) {
+                    const uint8_t x = in[(t * F + f) * (int64_t)N + i];
+                    const int64_t wr = w_re[(f * B + b) * N + i], wi = w_im[(f * B + b) * N + i];
+                    /* (wr + i wi) (xr + i xi) */
+                    yr += wr * sample_re(x) - wi * sample_im(x);
+                    yi += wr * sample_im(x) + wi * sample_re(x);
+                }
+                out[((t * F + f) * B + b) * 2] = yr;
+                out[((t * F + f) * B + b) * 2 + 1] = yi;
+            }
+    return 0;
+}

@@ -17,8 +17,7 @@
 // 1024.0, so the half value is 1024 + u, minus 1032 gives u - 8 exactly) and
 // packs pairs to E4M3 with the hardware converter.  HBM-bound: 1 byte read,
 // 2 bytes written per (input, sample).
-#include <cuda_fp16.h>
-#include <cuda_fp8.h>
+#include "nibble.cuh"
 #include "xeng_internal.h"
 
 namespace xeng {
@@ -30,28 +29,6 @@ constexpr int kRowWords = 33;  // 128 bytes + 4 bytes of padding per sample row
 // skew per 16-row group keeps the column reads of phase 2 conflict-free.
 __device__ __forceinline__ int row_word(int t) { return t * kRowWords + (t >> 4) * 4; }
 constexpr int kTileWords = 128 * kRowWords + 8 * 4;
-
-// Two offset nibbles (in bits 0-3 and 16-19 of x) to two E4M3 codes.
-__device__ __forceinline__ uint32_t nib2_to_e4m3(uint32_t x)
-{
-    __half2_raw h;
-    uint32_t v = (x & 0x000F000Fu) | 0x64006400u;  // half2(1024 + u_lo, 1024 + u_hi)
-    __half2 hv = *reinterpret_cast<__half2 *>(&v);
-    hv = __hsub2(hv, __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408)));  // - 1032
-    h = *reinterpret_cast<__half2_raw *>(&hv);
-    return (uint32_t)__nv_cvt_halfraw2_to_fp8x2(h, __NV_SATFINITE, __NV_E4M3);
-}
-
-// Word of 4 samples (bytes = times t..t+3 of one input) -> (real codes, imag codes).
-__device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &im)
-{
-    uint32_t r02 = nib2_to_e4m3(c >> 4);   // high nibbles of bytes 0 and 2
-    uint32_t r13 = nib2_to_e4m3(c >> 12);  // high nibbles of bytes 1 and 3
-    uint32_t i02 = nib2_to_e4m3(c);        // low nibbles of bytes 0 and 2
-    uint32_t i13 = nib2_to_e4m3(c >> 8);   // low nibbles of bytes 1 and 3
-    re = __byte_perm(r02, r13, 0x5140);
-    im = __byte_perm(i02, i13, 0x5140);
-}
 
 // Phase 2 of a tile (after the 128 x 128 bytes sit in `tile`): thread =
 // (input quad q, 16-sample block b); transpose, decode, store both planes.
@@ -205,7 +182,87 @@ decode_gather_kernel(const uint8_t *__restrict__ block, int32_t F, int32_t N, in
     if (counts && tid < 128 && i0 + tid < N && cnt[tid]) atomicAdd(&counts[(int64_t)fl * N + i0 + tid], cnt[tid]);
 }
 
+// Shifted decode (Sec. IV-C-5): plane column t of input i holds the sample
+// t0 + t - d_i of the block, or of the history when that index is negative.
+// A 16-input chunk whose inputs share one delay keeps the 16-byte load.
+__global__ void __launch_bounds__(kDecThreads)
+decode_shifted_kernel(const uint8_t *__restrict__ block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
+                      const ShiftArgs sa, uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int vec_ok)
+{
+    __shared__ uint32_t tile[kTileWords];
+    const int64_t tr0 = (int64_t)blockIdx.x * 128;  // first plane column of the tile
+    const int i0 = blockIdx.y * 128;
+    const int fl = blockIdx.z;
+    const int64_t f = f0 + fl;
+    const int tid = threadIdx.x;
+    for (int ch = tid; ch < 128 * 8; ch += kDecThreads) {
+        const int t = ch >> 3, c = ch & 7;
+        const int64_t tt = t0 + tr0 + t;  // sample of the block before the shift
+        const int ic = i0 + c * 16;
+        uint32_t w[4] = {0x88888888u, 0x88888888u, 0x88888888u, 0x88888888u};
+        if (tr0 + t < nt) {
+            const int cd = (vec_ok && ic + 16 <= N) ? sa.chunk_delay[ic >> 4] : -1;
+            if (cd >= 0 && tt - cd >= 0) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(block + ((tt - cd) * F + f) * N + ic);
+                w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+            } else {
+                for (int m = 0; m < 16; m++) {
+                    const int i = ic + m;
+                    if (i >= N) break;
+                    const int64_t src = tt - sa.delay[i];
+                    const uint32_t byte = src >= 0 ? block[(src * F + f) * N + i]
+                                                   : sa.hist[((sa.H + src) * F + f) * sa.S + sa.slot[i]];
+                    w[m >> 2] = (w[m >> 2] & ~(0xFFu << (8 * (m & 3)))) | (byte << (8 * (m & 3)));
+                }
+            }
+        }
+        uint32_t *dst = tile + row_word(t) + c * 4;
+        dst[0] = w[0]; dst[1] = w[1]; dst[2] = w[2]; dst[3] = w[3];
+    }
+    __syncthreads();
+    decode_tile_store(tile, planes, t_pad, n_pad, tr0, i0, fl);
+}
+
+// History after a block of n samples, [H][F][S]: entry (h, f, s) is sample
+// n - H + h of input inputs[s] -- from the block when that index is >= 0,
+// else entry n + h of the old history.
+__global__ void shift_history_kernel(const uint8_t *__restrict__ hist_old, const uint8_t *__restrict__ block,
+                                     int64_t n, int32_t F, int32_t N, const int32_t *__restrict__ inputs, int32_t S,
+                                     int64_t H, uint8_t *__restrict__ hist_new)
+{
+    const int64_t total = H * F * S;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t sl = (int32_t)(k % S);
+        const int64_t f = (k / S) % F;
+        const int64_t h = k / ((int64_t)S * F);
+        const int64_t src = n - H + h;
+        hist_new[k] = src >= 0 ? block[(src * F + f) * N + inputs[sl]] : hist_old[((n + h) * F + f) * S + sl];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
+                                  int32_t nf, const ShiftArgs &sa, uint8_t *planes, int64_t t_pad, int64_t n_pad,
+                                  cudaStream_t s)
+{
+    if (nf <= 0 || t_pad <= 0) return cudaSuccess;
+    const int vec_ok = decode_vec_ok(block, N);
+    dim3 grid((unsigned)(t_pad / 128), (unsigned)(n_pad / 128), (unsigned)nf);
+    decode_shifted_kernel<<<grid, kDecThreads, 0, s>>>(block, t0, nt, F, N, f0, sa, planes, t_pad, n_pad, vec_ok);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, int64_t n, int32_t F, int32_t N,
+                                 const int32_t *inputs, int32_t S, int64_t H, uint8_t *hist_new, cudaStream_t s)
+{
+    const int64_t total = H * F * S;
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    shift_history_kernel<<<(unsigned)blocks, 256, 0, s>>>(hist_old, block, n, F, N, inputs, S, H, hist_new);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0,
                           int32_t nf, uint8_t *planes, int64_t t_pad, int64_t n_pad, cudaStream_t s)

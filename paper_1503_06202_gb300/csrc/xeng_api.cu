@@ -48,11 +48,34 @@ struct xeng_s {
     int64_t gidx_cap = 0;
     struct PairList { int nt, nf, n; PairItem *dev; };
     std::vector<PairList> pair_lists;  // device pair lists of the 2-CTA launches, by (nt, nf)
+    // time shifting: delays, history of the delayed inputs (ping-pong), their list
+    bool shifted = false;
+    int32_t *d_delay = nullptr, *d_slot = nullptr, *d_chunk_delay = nullptr, *d_shift_inputs = nullptr;
+    uint8_t *hist[2] = {nullptr, nullptr};
+    int hist_cur = 0;
+    int64_t hist_H = 0;
+    int32_t hist_S = 0;
 };
 
 namespace {
 
 int64_t acc_bytes(const xeng_s *h) { return (int64_t)h->F * n_baselines(h->N) * 8; }
+
+void free_shift(xeng_s *h)
+{
+    cudaFree(h->d_delay);
+    cudaFree(h->d_slot);
+    cudaFree(h->d_chunk_delay);
+    cudaFree(h->d_shift_inputs);
+    cudaFree(h->hist[0]);
+    cudaFree(h->hist[1]);
+    h->d_delay = h->d_slot = h->d_chunk_delay = h->d_shift_inputs = nullptr;
+    h->hist[0] = h->hist[1] = nullptr;
+    h->shifted = false;
+    h->hist_H = 0;
+    h->hist_S = 0;
+    h->hist_cur = 0;
+}
 
 int cuda_status(cudaError_t e)
 {
@@ -258,6 +281,7 @@ void xeng_destroy(xeng_t h)
     }
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     if (h->ev_fin) cudaEventDestroy(h->ev_fin);
+    free_shift(h);
     cudaFree(h->d_err);
     if (h->h_err) cudaFreeHost(h->h_err);
     for (auto &t : h->timed) {
@@ -273,7 +297,60 @@ int xeng_set_engine(xeng_t h, int32_t engine)
 {
     if (!h) return XENG_ERR_ARG;
     if (engine != XENG_ENGINE_TENSOR && engine != XENG_ENGINE_DP4A) return XENG_ERR_ARG;
+    if (engine == XENG_ENGINE_DP4A && h->shifted) return XENG_ERR_UNSUPPORTED;
     h->engine = engine;
+    return XENG_OK;
+}
+
+int xeng_set_delays(xeng_t h, const int32_t *delays)
+{
+    if (!h) return XENG_ERR_ARG;
+    const int32_t N = h->N;
+    int32_t H = 0;
+    if (delays)
+        for (int32_t i = 0; i < N; i++) {
+            if (delays[i] < 0 || delays[i] > XENG_MAX_DELAY) return XENG_ERR_RANGE;
+            if (delays[i] > H) H = delays[i];
+        }
+    if (H > 0 && h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_UNSUPPORTED;
+    cudaDeviceSynchronize();  // queued pushes may still read the old delays and history
+    free_shift(h);
+    if (H == 0) return cuda_status(cudaGetLastError());
+    std::vector<int32_t> slot(N, -1), inputs, chunk((N + 15) / 16, -1);
+    for (int32_t i = 0; i < N; i++)
+        if (delays[i] > 0) {
+            slot[i] = (int32_t)inputs.size();
+            inputs.push_back(i);
+        }
+    for (int32_t c = 0; c * 16 < N; c++) {
+        bool same = c * 16 + 16 <= N;
+        for (int32_t i = c * 16 + 1; same && i < c * 16 + 16; i++) same = delays[i] == delays[c * 16];
+        if (same) chunk[c] = delays[c * 16];
+    }
+    const int32_t S = (int32_t)inputs.size();
+    const int64_t hist_bytes = (int64_t)H * h->F * S;
+    cudaError_t e = cudaMalloc(&h->d_delay, sizeof(int32_t) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_slot, sizeof(int32_t) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_chunk_delay, sizeof(int32_t) * chunk.size());
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_shift_inputs, sizeof(int32_t) * S);
+    if (e == cudaSuccess) e = cudaMalloc(&h->hist[0], (size_t)hist_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->hist[1], (size_t)hist_bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_delay, delays, sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_slot, slot.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_chunk_delay, chunk.data(), sizeof(int32_t) * chunk.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_shift_inputs, inputs.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->hist[0], 0x88, (size_t)hist_bytes);  // value 0 + 0i
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_shift(h);
+        return e == cudaErrorMemoryAllocation ? XENG_ERR_NOMEM : XENG_ERR_CUDA;
+    }
+    h->hist_H = H;
+    h->hist_S = S;
+    h->shifted = true;
     return XENG_OK;
 }
 
@@ -322,7 +399,7 @@ const uint8_t *device_block(xeng_s *h, const uint8_t *block, int64_t bytes, cuda
 // the first launch stores when `fresh`, every later one adds.  Work is
 // ordered after earlier work on `s` and before later work on `s`.
 cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32_t *target, bool fresh,
-                      cudaStream_t s)
+                      cudaStream_t s, bool apply_shift = false)
 {
     const int64_t N = h->N, F = h->F;
     const int64_t n_pad = planes_rows(N);
@@ -340,9 +417,23 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
         for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += h->group_f) {
             const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
             const uint8_t *src = dblock + t0 * F * N;
-            e = timed_launch(h, 0, s, [&] {
-                return launch_decode(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes, t_pad, n_pad, s);
-            });
+            if (apply_shift) {
+                ShiftArgs sa;
+                sa.delay = h->d_delay;
+                sa.slot = h->d_slot;
+                sa.chunk_delay = h->d_chunk_delay;
+                sa.hist = h->hist[h->hist_cur];
+                sa.H = h->hist_H;
+                sa.S = h->hist_S;
+                e = timed_launch(h, 0, s, [&] {
+                    return launch_decode_shifted(dblock, t0, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, sa, h->planes,
+                                                 t_pad, n_pad, s);
+                });
+            } else {
+                e = timed_launch(h, 0, s, [&] {
+                    return launch_decode(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes, t_pad, n_pad, s);
+                });
+            }
             if (e != cudaSuccess) break;
             TcArgs a;
             a.planes = h->planes;
@@ -355,6 +446,11 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
             a.err = h->d_err;
             e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
         }
+    }
+    if (e == cudaSuccess && apply_shift) {
+        e = launch_shift_history(h->hist[h->hist_cur], dblock, n_samples, (int32_t)F, (int32_t)N, h->d_shift_inputs,
+                                 h->hist_S, h->hist_H, h->hist[h->hist_cur ^ 1], s);
+        if (e == cudaSuccess) h->hist_cur ^= 1;
     }
     return e;
 }
@@ -472,13 +568,13 @@ int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
     if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples == 0) return XENG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->engine == XENG_ENGINE_TENSOR && n_samples <= h->chunk_t && !is_device_pointer(block)) {
+    if (h->engine == XENG_ENGINE_TENSOR && n_samples <= h->chunk_t && !is_device_pointer(block) && !h->shifted) {
         st = integrate_pipelined(h, block, true, n_samples, h->acc, nullptr, h->fresh, s);
         if (st != XENG_OK) return (h->sticky = st);
     } else {
         const uint8_t *dblock = device_block(h, block, n_samples * h->F * h->N, s, &st);
         if (!dblock) return st;
-        cudaError_t e = integrate(h, dblock, n_samples, h->acc, h->fresh, s);
+        cudaError_t e = integrate(h, dblock, n_samples, h->acc, h->fresh, s, h->shifted);
         if (e != cudaSuccess) return (h->sticky = cuda_status(e));
     }
     cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -494,6 +590,7 @@ int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *o
     int st = check_sticky(h);
     if (st != XENG_OK) return st;
     if (n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
+    if (h->shifted) return XENG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     const bool dev_out = is_device_pointer(out);
     if (!dev_out && (h->samples > 0 || !h->fresh)) return XENG_ERR_ARG;  // would clobber an open integration
@@ -537,6 +634,7 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
     if (n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples > h->chunk_t) return XENG_ERR_RANGE;
     if (h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_ARG;
+    if (h->shifted) return XENG_ERR_UNSUPPORTED;
     if (!is_device_pointer(out) || (counts && !is_device_pointer(counts)) || (valid && !is_device_pointer(valid)) ||
         (n_samples > 0 && !is_device_pointer(block)))
         return XENG_ERR_ARG;

@@ -47,6 +47,26 @@ struct DecodeJob {
 int decode_vec_ok(const uint8_t *block, int32_t N);
 // CTAs one job takes in a batched decode launch.
 inline int64_t decode_ctas(int64_t t_pad, int64_t n_pad, int64_t F) { return (t_pad / 128) * (n_pad / 128) * F; }
+// Time shifting (Sec. IV-C-5): input i of the pushed block is read d_i
+// samples late; the samples before the block come from the history.
+struct ShiftArgs {
+    const int32_t *delay = nullptr;        // [N] delay of input i, samples
+    const int32_t *slot = nullptr;         // [N] history column of input i (-1: not delayed)
+    const int32_t *chunk_delay = nullptr;  // [ceil(N/16)] delay shared by inputs 16c..16c+15, or -1
+    const uint8_t *hist = nullptr;         // [H][F][S] the H samples before the block, delayed inputs only
+    int64_t H = 0;
+    int32_t S = 0;
+};
+// Decode samples t0 .. t0 + nt - 1 of the block (T_block samples) with the
+// shift applied, channels f0 .. f0 + nf - 1, into planes as launch_decode.
+cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
+                                  int32_t nf, const ShiftArgs &sa, uint8_t *planes, int64_t t_pad, int64_t n_pad,
+                                  cudaStream_t s);
+// New history after a block of n samples: the last H samples of (old history,
+// block) for the S delayed inputs listed in `inputs`.
+cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, int64_t n, int32_t F, int32_t N,
+                                 const int32_t *inputs, int32_t S, int64_t H, uint8_t *hist_new, cudaStream_t s);
+
 cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s);
 
 // Two tiles run together by the two CTAs of a cluster (CTA r takes tile r).

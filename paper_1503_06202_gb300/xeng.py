@@ -25,6 +25,7 @@ XENG_MAX_INPUTS = 4096
 XENG_MAX_T_INTEG = 16777215
 XENG_ENGINE_TENSOR = 0
 XENG_ENGINE_DP4A = 1
+XENG_MAX_DELAY = 131072
 
 
 class XengStats(ctypes.Structure):
@@ -70,6 +71,8 @@ def lib():
         L.xeng_strerror.restype = ctypes.c_char_p
         L.xeng_set_engine.argtypes = [vp, i32]
         L.xeng_set_engine.restype = ctypes.c_int
+        L.xeng_set_delays.argtypes = [vp, vp]
+        L.xeng_set_delays.restype = ctypes.c_int
         L.xeng_decode.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp]
         L.xeng_decode.restype = ctypes.c_int
         L.xeng_set_profiling.argtypes = [vp, i32]
@@ -138,6 +141,14 @@ def xeng_set_engine(h, engine: int) -> int:
     return lib().xeng_set_engine(h, engine)
 
 
+def xeng_set_delays(h, delays) -> int:
+    """delays: host int32 numpy array [n_inputs], or None to remove them."""
+    if delays is not None:
+        import numpy as np
+        delays = np.ascontiguousarray(delays, dtype=np.int32)
+    return lib().xeng_set_delays(h, _ptr(delays))
+
+
 def xeng_decode(block, n_samples, n_freq, n_inputs, f0, nf, planes, stream=None) -> int:
     return lib().xeng_decode(_ptr(block), n_samples, n_freq, n_inputs, f0, nf, _ptr(planes), _stream(stream))
 
@@ -182,6 +193,11 @@ class XEngine:
         rc = xeng_set_engine(self.h, engine)
         if rc != XENG_OK:
             raise XengError(rc, "xeng_set_engine")
+
+    def set_delays(self, delays) -> None:
+        rc = xeng_set_delays(self.h, delays)
+        if rc != XENG_OK:
+            raise XengError(rc, "xeng_set_delays")
 
     def push(self, block, n_samples: int | None = None, stream=None) -> None:
         if n_samples is None:

@@ -50,6 +50,7 @@ def test_null_handles_and_pointers():
     assert xe.xeng_push(None, None, 0) == xe.XENG_ERR_ARG
     assert xe.xeng_dump(None, None) == xe.XENG_ERR_ARG
     assert xe.xeng_set_engine(None, 0) == xe.XENG_ERR_ARG
+    assert xe.xeng_set_delays(None, None) == xe.XENG_ERR_ARG
     assert xe.xeng_set_profiling(None, True) == xe.XENG_ERR_ARG
     xe.xeng_destroy(None)
     assert xe.xeng_decode(None, 1, 1, 1, 0, 1, None) == xe.XENG_ERR_ARG

@@ -227,8 +227,80 @@ def pin_gated(lib=None):
         assert (v5[g][..., 0] == 128 * (gate == g).sum()).all() and (v5[g][..., 1] == 0).all()
 
 
+def _shifted_stream(blk, delays, t_a, t_b):
+    """The delayed stream y over [t_a, t_b) built by numpy indexing: column i
+    of sample w is row t_a + w - delays[i] of blk, byte 0x88 (value 0) before
+    the stream's start."""
+    T, F, N = blk.shape
+    W = t_b - t_a
+    y = np.full((W, F, N), 0x88, np.uint8)
+    for i in range(N):
+        src = np.arange(t_a, t_b) - int(delays[i])
+        ok = src >= 0
+        y[ok, :, i] = blk[src[ok], :, i]
+    return y
+
+
+def pin_shifted(lib=None):
+    """Time shifting (Sec. IV-C-5) reduces to the plain correlation of a stream
+    whose columns were moved in numpy."""
+    rng = np.random.default_rng(21)
+    T, F, N = 120, 2, 11
+    blk = _random_block(rng, T, F, N)
+    zero = np.zeros(N, np.int32)
+    assert np.array_equal(oracle.correlate_shifted(blk, zero, lib=lib), oracle.correlate(blk, lib=lib))
+    # one delay for every input: the window slides back by d, zeros before t = 0
+    for d, (t_a, t_b) in [(5, (0, T)), (17, (30, 90)), (200, (0, T))]:
+        want = oracle.correlate(blk[max(t_a - d, 0):max(t_b - d, 0)], lib=lib)
+        assert np.array_equal(oracle.correlate_shifted(blk, np.full(N, d, np.int32), t_a, t_b, lib=lib), want), d
+    # per-input delays, windows starting before and after the largest delay
+    delays = rng.integers(0, 40, N).astype(np.int32)
+    delays[3] = 0
+    for t_a, t_b in [(0, T), (7, 61), (45, T), (0, 1), (10, 10)]:
+        want = oracle.correlate(_shifted_stream(blk, delays, t_a, t_b), lib=lib)
+        got = oracle.correlate_shifted(blk, delays, t_a, t_b, lib=lib)
+        assert np.array_equal(got, want), (t_a, t_b)
+    # windows add up
+    parts = sum(oracle.correlate_shifted(blk, delays, a, b, lib=lib) for a, b in [(0, 33), (33, 34), (34, T)])
+    assert np.array_equal(parts, oracle.correlate_shifted(blk, delays, lib=lib))
+
+
+def pin_beamform(lib=None):
+    """Beamforming (Sec. IV-C-3) against numpy complex matmul, unit weights,
+    a closed form and the beam-power identity through the correlation."""
+    rng = np.random.default_rng(22)
+    T, F, N, B = 40, 3, 13, 4
+    blk = _random_block(rng, T, F, N)
+    w_re = rng.integers(-128, 128, (F, B, N))
+    w_im = rng.integers(-128, 128, (F, B, N))
+    y = oracle.beamform(blk, w_re, w_im, lib=lib)
+    x = _decode_complex(blk)                                    # [T][F][N]
+    want = np.einsum("fbi,tfi->tfb", w_re + 1j * w_im, x)       # exact in complex128 here
+    assert np.array_equal(y[..., 0], want.real.astype(np.int64))
+    assert np.array_equal(y[..., 1], want.imag.astype(np.int64))
+    # unit weight on input k: the beam is x_k itself
+    e_re = np.zeros((F, 1, N), np.int64)
+    e_re[:, 0, 5] = 1
+    y1 = oracle.beamform(blk, e_re, np.zeros_like(e_re), lib=lib)
+    assert np.array_equal(y1[:, :, 0, 0], (blk[:, :, 5].astype(np.int64) >> 4) - 8)
+    assert np.array_equal(y1[:, :, 0, 1], (blk[:, :, 5].astype(np.int64) & 15) - 8)
+    # weight i on input k: (xr + i xi) i = -xi + i xr
+    y2 = oracle.beamform(blk, np.zeros_like(e_re), e_re, lib=lib)
+    assert np.array_equal(y2[..., 0, 0], -y1[..., 0, 1]) and np.array_equal(y2[..., 0, 1], y1[..., 0, 0])
+    # every byte 0x00 (x = -8 - 8i), every weight 1: y = N (-8 - 8i)
+    y3 = oracle.beamform(np.zeros((3, 1, N), np.uint8), np.ones((1, 2, N)), np.zeros((1, 2, N)), lib=lib)
+    assert (y3[..., 0] == -8 * N).all() and (y3[..., 1] == -8 * N).all()
+    # sum_t |y_b|^2 = sum_ij w_i conj(w_j) V_ij, V from the correlation oracle
+    vis = oracle.correlate(blk, lib=lib)
+    power = (y.astype(np.int64) ** 2).sum(axis=(0, 3))          # [F][B]
+    for f in range(F):
+        for b in range(B):
+            assert power[f, b] == oracle.weighted_sum(vis[f:f + 1], w_re[f, b], w_im[f, b])[0], (f, b)
+
+
 PINS = [pin_constant_input, pin_impulses, pin_hermitian, pin_autocorrelations, pin_matmul,
-        pin_exhaustive_pairs, pin_beam_power, pin_linearity, pin_permutation, pin_pairs_and_subsets, pin_gated]
+        pin_exhaustive_pairs, pin_beam_power, pin_linearity, pin_permutation, pin_pairs_and_subsets, pin_gated,
+        pin_shifted, pin_beamform]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -261,6 +333,13 @@ def test_paper_constants():
     # the int32 bound per integration: |Re| <= 128 T must stay below 2^31 for
     # the paper's default 2^23-sample integration (and up to 2^24 - 1 samples)
     assert 128 * it["value"] < 2 ** 31 and 128 * (2 ** 24 - 1) < 2 ** 31 <= 128 * 2 ** 24
+    # 168 ms of shift at one sample per 2.56 us is 65,625 samples: the library's
+    # delay limit must cover it
+    shift = round(g["max_time_shift"]["seconds"] / period)
+    assert shift == 65625
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "xeng.h")).read()
+    limit = int(hdr.split("#define XENG_MAX_DELAY")[1].split()[0].rstrip("LlUu"))
+    assert limit >= shift
 
 
 MUTANTS = {
@@ -278,6 +357,12 @@ MUTANTS = {
                           "for (int64_t t = 1; t < T; t++) {\n                    /*"),
     "flag_only_first_input": ("                    if (valid && !valid[at + j]) continue;\n", ""),
     "gate_off_by_one": ("if (g < 0 || g >= G) continue;", "if (g < 0 || g > G - 2) continue;"),
+    "shift_ignores_window_start": ("const int64_t s = t_a + w - delays[i];", "const int64_t s = w - delays[i];"),
+    "shift_missing_on_imag": ("im[i * W + w] = s >= 0 ? sample_im(in[(s * F + f) * (int64_t)N + i]) : 0;",
+                              "im[i * W + w] = sample_im(in[((t_a + w) * F + f) * (int64_t)N + i]);"),
+    "beam_conjugated_weight": ("yi += wr * sample_im(x) + wi * sample_re(x);",
+                               "yi += wr * sample_im(x) - wi * sample_re(x);"),
+    "beam_dropped_cross_term": ("yr += wr * sample_re(x) - wi * sample_im(x);", "yr += wr * sample_re(x);"),
 }
 
 
