@@ -404,6 +404,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the dense-throughput probes")
     ap.add_argument("--no-shift", action="store_true", help="skip the time-shift measurement")
+    ap.add_argument("--no-beam", action="store_true", help="skip the beamforming measurement")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-max-blocks", type=int, default=32)
@@ -517,6 +518,35 @@ def main():
                  "unshifted_decode_ms_per_step": push_dump_decode_ms,
                  "value": whole_job_rate(useful_ops(T, F, N), max_over_ranks(sh_ms, dist) * 1e-3, world) / 1e12,
                  "unit": "TOPS"}
+    # beamforming (Sec. IV-C-3): 16 beams over the same block, int8 weights;
+    # HBM-bound: reads the block once, writes T x F x 16 complex int32
+    beam = None
+    if args.engine == "tensor" and not args.no_beam:
+        nb = 16
+        bf = xe.XBeam(N, F, nb)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        with torch.cuda.stream(stream):
+            w_re = torch.randint(-128, 128, (F, nb, N), dtype=torch.int8, device="cuda", generator=g)
+            w_im = torch.randint(-128, 128, (F, nb, N), dtype=torch.int8, device="cuda", generator=g)
+            bout = torch.empty((T, F, nb, 2), dtype=torch.int32, device="cuda")
+        bf.set_weights(w_re, w_im, stream)
+        for _ in range(3):
+            bf.run(block, bout, T, stream)
+        reps = 10
+        ev0.record(stream)
+        for _ in range(reps):
+            bf.run(block, bout, T, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        bms = ev0.elapsed_time(ev1) / reps
+        peaks_b, src_b = load_peaks()
+        bytes_alg = T * F * N + T * F * nb * 8
+        beam = {"n_beams": nb, "ms_per_step": bms, "bound": "hbm", "algorithmic_bytes": bytes_alg,
+                "achieved": bytes_alg / (bms * 1e-3) / 1e9, "peak": peaks_b["hbm_gbs"], "unit": "GB/s",
+                "cmac_per_s": T * F * N * nb / (bms * 1e-3), "kernel": "beamform_kernel<16>"}
+        beam["frac"] = beam["achieved"] / beam["peak"]
+        bf.close()
+        del w_re, w_im, bout
     ms = max_over_ranks(ms, dist)
     ops = useful_ops(T, F, N)
     value = whole_job_rate(ops, ms * 1e-3, world) / 1e12
@@ -589,7 +619,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
-                "push_dump_ms_per_step": push_dump_ms, "time_shift": shift,
+                "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "beamform": beam,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}
         print(json.dumps(line), flush=True)

@@ -155,6 +155,34 @@ XENG_API int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samp
 #define XENG_MAX_DELAY 131072  /* samples; 168 ms at 2.56 us per sample is 65,625 */
 XENG_API int xeng_set_delays(xeng_t h, const int32_t *delays);
 
+/*
+ * Beamforming (Sec. IV-C-3).  The telescope cannot point physically; a beam is
+ * formed digitally by phase-shifting the inputs and summing them, so that
+ * signals from one region of the sky add in phase, and is written out at the
+ * full sample cadence.  For every sample t, channel f and beam b:
+ *     y_b(t, f) = sum_i w_{f,b,i} x_i(t, f),   w = w_re + i w_im, int8 parts,
+ * exact in int32 (|y| <= 2 * 128 * 8 * N < 2^31).
+ *
+ *   xbeam_create(n_inputs, n_freq, n_beams, &b): 16 <= n_inputs <= XENG_MAX_INPUTS
+ *     with n_inputs a multiple of 16 (the block's rows are read by TMA, whose
+ *     strides must be multiples of 16 bytes), 1 <= n_beams <= XBEAM_MAX_BEAMS;
+ *     else XENG_ERR_RANGE.  All weights start at zero.
+ *   xbeam_set_weights(b, w_re, w_im, stream): int8 [n_freq][n_beams][n_inputs]
+ *     each, host or device memory (host: returns once they are copied).
+ *   xbeam_run(b, block, n_samples, out, stream): block device uint8
+ *     [n_samples][n_freq][n_inputs], 16-byte aligned; out device int32
+ *     [n_samples][n_freq][n_beams][2] (Re, Im), 8-byte aligned, overwritten.
+ *     Asynchronous on `stream`; a device-side time-out is reported by the next
+ *     call as XENG_ERR_TIMEOUT (sticky).
+ *   xbeam_destroy(b): synchronizes the device, frees the handle; NULL is a no-op.
+ */
+typedef struct xbeam_s *xbeam_t;
+#define XBEAM_MAX_BEAMS 64
+XENG_API int xbeam_create(int32_t n_inputs, int32_t n_freq, int32_t n_beams, xbeam_t *out);
+XENG_API int xbeam_set_weights(xbeam_t b, const int8_t *w_re, const int8_t *w_im, void *stream);
+XENG_API int xbeam_run(xbeam_t b, const uint8_t *block, int64_t n_samples, int32_t *out, void *stream);
+XENG_API void xbeam_destroy(xbeam_t b);
+
 /* xeng_destroy -- free the handle and its device memory; NULL is a no-op.
  * Synchronizes the device first. */
 XENG_API void xeng_destroy(xeng_t h);

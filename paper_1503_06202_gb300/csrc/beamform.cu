@@ -1,0 +1,572 @@
+// beamform.cu -- discrete beamforming on the tensor cores (paper Sec. IV-C-3:
+// the data of all inputs are phase-shifted and summed, so that signals from
+// one region of the sky add in phase; the beam is written out at the full
+// sample cadence).
+//
+// For every sample t, channel f and beam b
+//     y_b(t, f) = sum_i w_{f,b,i} x_i(t, f),
+// x_i decoded from the 4+4-bit offset bytes (Sec. II-A), w = w_re + i w_im
+// with int8 parts.  As real GEMMs with M = 128 samples and K = inputs:
+//     Re y = X_re W_re^T - X_im W_im^T,   Im y = X_re W_im^T + X_im W_re^T.
+// E4M3 holds -8..15 exactly but not all of int8, so a weight part v is split
+// into v = 16 hi + lo, hi = v >> 4 in [-8, 8], lo = v & 15 in [0, 15].  The B
+// operand of the X_re MMA stacks the rows [hi W_re; hi W_im; lo W_re; lo W_im]
+// (4 Bp rows, Bp = beams rounded up), that of the X_im MMA
+// [hi(-W_im); hi W_re; lo(-W_im); lo W_re], so one 128 x 4Bp f32 accumulator
+// collects the hi and lo parts of Re y and Im y side by side and the
+// epilogue forms y = 16 hi + lo in int32.  Products are integers of
+// magnitude <= 8 * 15 and partial sums stay below 240 N <= 2^20, so the f32
+// accumulation is exact.
+//
+// One persistent CTA per SM; work items = (channel, 128-sample tile):
+//   warp 0        TMA producer: raw byte tiles (128 samples x 128 inputs of one
+//                 channel, read straight from the block) into a raw ring, and
+//                 the matching 128-input slices of both weight operands
+//   warp 1        TMEM allocation and the single-thread MMA issuer
+//   warps 2..9    converters: raw bytes -> E4M3 planes X_re, X_im, written in
+//                 the 128-byte-swizzled K-major layout the MMA reads
+//   warps 10..13  epilogue: TMEM -> int32 beams [T][F][B][2] in HBM
+// Two TMEM accumulators let the epilogue of one item overlap the next item's
+// MMAs.  Every wait is bounded; on time-out the roles leave their loops, the
+// producer lets its issued copies land, the MMA thread drains and TMEM is
+// freed before exit.
+#include <cstring>
+#include <new>
+
+#include "../../include/xeng.h"
+#include "nibble.cuh"
+#include "tc_ptx.cuh"
+#include "xeng_internal.h"
+
+namespace xeng {
+namespace {
+
+constexpr int kBfThreads = 448;        // 14 warps
+constexpr int kConvThreads = 256;      // warps 2..9
+constexpr int kConvFirst = 64;         // first converter thread
+constexpr int kRawBytes = 128 * 128;   // 128 samples x 128 inputs, one byte each
+constexpr int kPlaneBytes = 128 * 128; // 128 samples x 128 inputs, one E4M3 code each
+
+template <int kBp>
+struct BfCfg {
+    static constexpr int kN = 4 * kBp;                           // MMA N: hi/lo x Re/Im x beams
+    static constexpr int kWBytes = kN * 128;                     // one weight operand slice
+    static constexpr int kStageBytes = 2 * kPlaneBytes + 2 * kWBytes;
+    static constexpr int kS = kBp <= 16 ? 3 : 2;                 // MMA ring stages
+    static constexpr int kR = kBp <= 32 ? 4 : 2;                 // raw ring stages
+    static constexpr uint32_t kTmemCols = 8 * kBp;               // two accumulators (a power of 2 >= 32)
+    static constexpr int kBars = 2 * kR + 3 * kS + 5;
+    static constexpr size_t kSmem = 1024 + (size_t)kR * kRawBytes + (size_t)kS * kStageBytes + kBars * 8 + 16;
+    // kind::f8f6f4, D f32, A and B E4M3 K-major, N and M = 128
+    static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static_assert(kTmemCols >= 32 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation must be a power of 2");
+    static_assert(kSmem <= 232448, "shared memory over the per-CTA limit");
+};
+
+// K-major operand with 128-byte rows, 128-byte swizzle, 8-row groups 1 KB apart.
+__device__ __forceinline__ uint64_t bf_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void bf_item(const BfArgs &a, int64_t it, int &f, int &tt)
+{
+    if (a.f_fastest) {
+        f = (int)(it % a.F);
+        tt = (int)(it / a.F);
+    } else {
+        tt = (int)(it % a.n_tt);
+        f = (int)(it / a.n_tt);
+    }
+}
+
+template <int kBp>
+__global__ void __launch_bounds__(kBfThreads, 1)
+beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ CUtensorMap w_map, const BfArgs a)
+{
+    using C = BfCfg<kBp>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t *sgen = smem_raw + (sbase - raw);  // generic view of the aligned base
+    const uint32_t stbase = sbase + C::kR * kRawBytes;
+    const uint32_t bars = stbase + C::kS * C::kStageBytes;
+    auto rawf = [&](int r) { return bars + 8u * r; };                          // raw tile landed
+    auto rawe = [&](int r) { return bars + 8u * (C::kR + r); };                // raw tile read
+    auto wf = [&](int s) { return bars + 8u * (2 * C::kR + s); };             // weight slices landed
+    auto xf = [&](int s) { return bars + 8u * (2 * C::kR + C::kS + s); };     // planes written
+    auto ste = [&](int s) { return bars + 8u * (2 * C::kR + 2 * C::kS + s); };  // stage consumed by the MMAs
+    auto accf = [&](int b) { return bars + 8u * (2 * C::kR + 3 * C::kS + b); };
+    auto acce = [&](int b) { return bars + 8u * (2 * C::kR + 3 * C::kS + 2 + b); };
+    const uint32_t drain_bar = bars + 8u * (2 * C::kR + 3 * C::kS + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * C::kBars - raw));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *err = a.err;
+
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < C::kR; r++) {
+            mbar_init(rawf(r), 1);
+            mbar_init(rawe(r), kConvThreads);
+        }
+        for (int s = 0; s < C::kS; s++) {
+            mbar_init(wf(s), 1);
+            mbar_init(xf(s), kConvThreads);
+            mbar_init(ste(s), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), 128);
+        }
+        mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&w_map) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int r = 0, s = 0, issued_r = 0, issued_s = 0;
+            uint32_t pr = 0, ps = 0;
+            bool ok = true;
+            for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x) {
+                int f, tt;
+                bf_item(a, it, f, tt);
+                for (int k = 0; k < a.n_kc; k++) {
+                    if (!mbar_wait(rawe(r), pr ^ 1u, err, kDevTimeoutProducer)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(rawf(r), kRawBytes);
+                    tma_load_3d(sbase + r * kRawBytes, &raw_map, k * 128, f, tt * 128, rawf(r));
+                    ++issued_r;
+                    if (++r == C::kR) {
+                        r = 0;
+                        pr ^= 1u;
+                    }
+                    if (!mbar_wait(ste(s), ps ^ 1u, err, kDevTimeoutProducer)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t w0 = stbase + s * C::kStageBytes + 2 * kPlaneBytes;
+                    mbar_expect_tx(wf(s), 2 * C::kWBytes);
+                    tma_load_2d(w0, &w_map, k * 128, (f * 2 + 0) * C::kN, wf(s));
+                    tma_load_2d(w0 + C::kWBytes, &w_map, k * 128, (f * 2 + 1) * C::kN, wf(s));
+                    ++issued_s;
+                    if (++s == C::kS) {
+                        s = 0;
+                        ps ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the copies already issued land before the CTA can exit.
+                for (int k = 1; k <= C::kR && k <= issued_r; k++) {
+                    int q = r - k, p = (int)pr;
+                    if (q < 0) { q += C::kR; p ^= 1; }
+                    (void)mbar_wait(rawf(q), (uint32_t)p, err, kDevTimeoutProducer);
+                }
+                for (int k = 1; k <= C::kS && k <= issued_s; k++) {
+                    int q = s - k, p = (int)ps;
+                    if (q < 0) { q += C::kS; p ^= 1; }
+                    (void)mbar_wait(wf(q), (uint32_t)p, err, kDevTimeoutProducer);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int s = 0, local = 0;
+            uint32_t ps = 0, uses[2] = {0, 0};
+            bool ok = true;
+            for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x, ++local) {
+                const int ab = local & 1;
+                if (!mbar_wait(acce(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma)) break;
+                ++uses[ab];
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * C::kN);
+                for (int k = 0; k < a.n_kc; k++) {
+                    if (!mbar_wait(wf(s), ps, err, kDevTimeoutMma) || !mbar_wait(xf(s), ps, err, kDevTimeoutMma)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t xre = stbase + s * C::kStageBytes, xim = xre + kPlaneBytes;
+                    const uint32_t w0 = xre + 2 * kPlaneBytes, w1 = w0 + C::kWBytes;
+                    #pragma unroll
+                    for (int kk = 0; kk < 4; kk++) {
+                        const uint32_t off = kk * 32;
+                        mma_f8(d, bf_desc(xre + off), bf_desc(w0 + off), C::kIdesc, (k != 0 || kk != 0) ? 1u : 0u);
+                        mma_f8(d, bf_desc(xim + off), bf_desc(w1 + off), C::kIdesc, 1u);
+                    }
+                    mma_commit(ste(s));
+                    if (++s == C::kS) {
+                        s = 0;
+                        ps ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(accf(ab));
+            }
+            // Drain: every MMA issued above has finished once this completes.
+            mma_commit(drain_bar);
+            (void)mbar_wait(drain_bar, 0u, err, kDevTimeoutMma);
+        }
+    } else if (warp < 10) {
+        // ---------------- converters ----------------
+        const int ct = threadIdx.x - kConvFirst;  // 0..255
+        int r = 0, s = 0;
+        uint32_t pr = 0, ps = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x) {
+            for (int k = 0; k < a.n_kc; k++) {
+                ok = mbar_wait(rawf(r), pr, err, kDevTimeoutProducer) &&
+                     mbar_wait(ste(s), ps ^ 1u, err, kDevTimeoutProducer);
+                if (!ok) break;
+                const uint8_t *rt = sgen + r * kRawBytes;
+                uint8_t *xre = sgen + (stbase - sbase) + s * C::kStageBytes;
+                uint8_t *xim = xre + kPlaneBytes;
+                uint4 v[4];
+                #pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int q = j * kConvThreads + ct, t = q >> 3, c = q & 7;
+                    v[j] = *reinterpret_cast<const uint4 *>(rt + t * 128 + c * 16);
+                }
+                #pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int q = j * kConvThreads + ct, t = q >> 3, c = q & 7;
+                    uint32_t re[4], im[4];
+                    decode_word(v[j].x, re[0], im[0]);
+                    decode_word(v[j].y, re[1], im[1]);
+                    decode_word(v[j].z, re[2], im[2]);
+                    decode_word(v[j].w, re[3], im[3]);
+                    // row t, 16-byte chunk c of a 128-byte-swizzled tile
+                    const int off = t * 128 + ((c ^ (t & 7)) << 4);
+                    *reinterpret_cast<uint4 *>(xre + off) = make_uint4(re[0], re[1], re[2], re[3]);
+                    *reinterpret_cast<uint4 *>(xim + off) = make_uint4(im[0], im[1], im[2], im[3]);
+                }
+                mbar_arrive(rawe(r));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the MMA
+                mbar_arrive(xf(s));
+                if (++r == C::kR) {
+                    r = 0;
+                    pr ^= 1u;
+                }
+                if (++s == C::kS) {
+                    s = 0;
+                    ps ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 10..13) ----------------
+        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row = q * 32 + lane;
+        constexpr int G = kBp < 16 ? kBp : 16;
+        uint32_t uses[2] = {0, 0};
+        int local = 0;
+        for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x, ++local) {
+            int f, tt;
+            bf_item(a, it, f, tt);
+            const int ab = local & 1;
+            const bool ok = mbar_wait(accf(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue);
+            if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
+            ++uses[ab];
+            fence_after();
+            const int64_t t = (int64_t)tt * 128 + row;
+            int2 *o = reinterpret_cast<int2 *>(a.out) + (t * a.F + f) * a.B;
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::kN);
+            #pragma unroll
+            for (int b0 = 0; b0 < kBp; b0 += G) {
+                uint32_t hre[G], him[G], lre[G], lim[G];
+                #pragma unroll
+                for (int c = 0; c < G; c += 4) {
+                    tmem_ld4(ta + b0 + c, *reinterpret_cast<uint32_t(*)[4]>(hre + c));
+                    tmem_ld4(ta + kBp + b0 + c, *reinterpret_cast<uint32_t(*)[4]>(him + c));
+                    tmem_ld4(ta + 2 * kBp + b0 + c, *reinterpret_cast<uint32_t(*)[4]>(lre + c));
+                    tmem_ld4(ta + 3 * kBp + b0 + c, *reinterpret_cast<uint32_t(*)[4]>(lim + c));
+                }
+                tmem_ld_wait();
+                if (t < a.T) {
+                    #pragma unroll
+                    for (int e = 0; e < G; e++)
+                        if (b0 + e < a.B)
+                            o[b0 + e] = make_int2(16 * __float2int_rn(__uint_as_float(hre[e])) +
+                                                      __float2int_rn(__uint_as_float(lre[e])),
+                                                  16 * __float2int_rn(__uint_as_float(him[e])) +
+                                                      __float2int_rn(__uint_as_float(lim[e])));
+                }
+            }
+            fence_before();
+            mbar_arrive(acce(ab));
+        }
+    }
+
+    __syncwarp();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols));
+    }
+}
+
+// Weight operands from int8 weights [F][B][N] (re, im): [F][2][4 Bp][n_pad]
+// E4M3 codes, operand m = 0 multiplies X_re, m = 1 multiplies X_im; row
+// g * Bp + b holds the hi (g = 0, 1) or lo (g = 2, 3) part of the Re-y (g even)
+// or Im-y (g odd) weight of beam b.  Rows b >= B and columns i >= N are zero.
+__global__ void beam_weights_kernel(const int8_t *__restrict__ w_re, const int8_t *__restrict__ w_im, int32_t F,
+                                    int32_t B, int32_t N, int32_t bp, int32_t n_pad, uint8_t *__restrict__ wdev)
+{
+    const int64_t total = (int64_t)F * 2 * 4 * bp * n_pad;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % n_pad);
+        const int64_t rowk = k / n_pad;
+        const int rr = (int)(rowk % (4 * bp));
+        const int m = (int)((rowk / (4 * bp)) % 2);
+        const int64_t f = rowk / (8 * bp);
+        const int g = rr / bp, b = rr % bp;
+        int v = 0;
+        if (b < B && i < N) {
+            const int64_t src = (f * B + b) * N + i;
+            const int wr = w_re[src], wi = w_im[src];
+            // m = 0: Re y += x_re w_re, Im y += x_re w_im;  m = 1: Re y += x_im (-w_im), Im y += x_im w_re
+            const int base = (m == 0) ? ((g & 1) ? wi : wr) : ((g & 1) ? wr : -wi);
+            v = g < 2 ? (base >> 4) : (base & 15);
+        }
+        wdev[k] = (uint8_t)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+template <int kBp>
+cudaError_t launch_bf(const CUtensorMap &rm, const CUtensorMap &wm, const BfArgs &a, int grid, cudaStream_t s)
+{
+    using C = BfCfg<kBp>;
+    cudaError_t e = cudaFuncSetAttribute(beamform_kernel<kBp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::kSmem);
+    if (e != cudaSuccess) return e;
+    beamform_kernel<kBp><<<grid, kBfThreads, C::kSmem, s>>>(rm, wm, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int beam_padded(int32_t n_beams)
+{
+    return n_beams <= 4 ? 4 : n_beams <= 8 ? 8 : n_beams <= 16 ? 16 : n_beams <= 32 ? 32 : 64;
+}
+
+cudaError_t launch_beam_weights(const int8_t *w_re, const int8_t *w_im, int32_t F, int32_t B, int32_t N,
+                                uint8_t *wdev, cudaStream_t s)
+{
+    const int bp = beam_padded(B);
+    const int n_pad = (int)round_up(N, 128);
+    const int64_t total = (int64_t)F * 8 * bp * n_pad;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    beam_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(w_re, w_im, F, B, N, bp, n_pad, wdev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a, int num_sms, cudaStream_t s)
+{
+    if (a.T <= 0) return cudaSuccess;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const int bp = beam_padded(a.B);
+    const int n_pad = (int)round_up(a.N, 128);
+    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x 128 samples
+    CUtensorMap rm, wm;
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)a.N, (cuuint64_t)a.F, (cuuint64_t)a.T};
+        cuuint64_t strides[2] = {(cuuint64_t)a.N, (cuuint64_t)a.N * a.F};
+        cuuint32_t box[3] = {128, 1, 128}, estr[3] = {1, 1, 1};
+        if (enc(&rm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)a.F * 8 * bp};
+        cuuint64_t strides[1] = {(cuuint64_t)n_pad};
+        cuuint32_t box[2] = {128, (cuuint32_t)(4 * bp)}, estr[2] = {1, 1};
+        if (enc(&wm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)wdev, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    a.n_kc = n_pad / 128;
+    a.n_tt = (int32_t)((a.T + 127) / 128);
+    a.n_items = (int64_t)a.F * a.n_tt;
+    // channel-fastest order reads neighbouring channels' rows together; it
+    // needs every channel's weights in L2, else one channel at a time
+    a.f_fastest = ((int64_t)a.F * 8 * bp * n_pad <= ((int64_t)48 << 20)) ? 1 : 0;
+    const int grid = (int)(a.n_items < num_sms ? a.n_items : num_sms);
+    switch (bp) {
+        case 4: return launch_bf<4>(rm, wm, a, grid, s);
+        case 8: return launch_bf<8>(rm, wm, a, grid, s);
+        case 16: return launch_bf<16>(rm, wm, a, grid, s);
+        case 32: return launch_bf<32>(rm, wm, a, grid, s);
+        default: return launch_bf<64>(rm, wm, a, grid, s);
+    }
+}
+
+}  // namespace xeng
+
+// ---------------------------------------------------------------------------
+// C ABI
+struct xbeam_s {
+    int32_t N = 0, F = 0, B = 0;
+    int device = 0, num_sms = 0;
+    uint8_t *wdev = nullptr;    // [F][2][4 Bp][n_pad] E4M3 weight operands
+    int64_t wdev_bytes = 0;
+    int8_t *wstage = nullptr;   // device copy of host weights
+    int *d_err = nullptr;       // device status word of the kernels
+    int *h_err = nullptr;       // pinned mirror, refreshed after each run
+    int sticky = XENG_OK;
+};
+
+namespace {
+
+bool bf_is_device_pointer(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int bf_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return XENG_OK;
+    if (e == cudaErrorMemoryAllocation) return XENG_ERR_NOMEM;
+    return XENG_ERR_CUDA;
+}
+
+int bf_check_sticky(xbeam_s *b)
+{
+    if (b->sticky != XENG_OK) return b->sticky;
+    if (*b->h_err != 0) b->sticky = XENG_ERR_TIMEOUT;
+    return b->sticky;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xbeam_create(int32_t n_inputs, int32_t n_freq, int32_t n_beams, xbeam_t *out)
+{
+    if (!out) return XENG_ERR_ARG;
+    *out = nullptr;
+    if (n_inputs < 16 || n_inputs > XENG_MAX_INPUTS || n_inputs % 16 != 0 || n_freq < 1 || n_beams < 1 ||
+        n_beams > XBEAM_MAX_BEAMS)
+        return XENG_ERR_RANGE;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return XENG_ERR_UNSUPPORTED;
+    }
+    if (prop.major != 10 || prop.minor != 3) return XENG_ERR_UNSUPPORTED;
+    xbeam_s *b = new (std::nothrow) xbeam_s;
+    if (!b) return XENG_ERR_NOMEM;
+    b->N = n_inputs;
+    b->F = n_freq;
+    b->B = n_beams;
+    b->device = dev;
+    b->num_sms = prop.multiProcessorCount;
+    b->wdev_bytes = (int64_t)n_freq * 8 * xeng::beam_padded(n_beams) * xeng::round_up(n_inputs, 128);
+    cudaError_t e = cudaMalloc(&b->wdev, (size_t)b->wdev_bytes);
+    if (e == cudaSuccess) e = cudaMemset(b->wdev, 0, (size_t)b->wdev_bytes);  // E4M3 +0: all weights zero
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        xbeam_destroy(b);
+        return bf_status(e);
+    }
+    *b->h_err = 0;
+    *out = b;
+    return XENG_OK;
+}
+
+int xbeam_set_weights(xbeam_t b, const int8_t *w_re, const int8_t *w_im, void *stream)
+{
+    if (!b || !w_re || !w_im) return XENG_ERR_ARG;
+    int st = bf_check_sticky(b);
+    if (st != XENG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = (int64_t)b->F * b->B * b->N;
+    const bool dre = bf_is_device_pointer(w_re), dim = bf_is_device_pointer(w_im);
+    cudaError_t e = cudaSuccess;
+    if (!dre || !dim) {
+        if (!b->wstage) {
+            e = cudaMalloc(&b->wstage, (size_t)(2 * n));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                b->wstage = nullptr;
+                return XENG_ERR_NOMEM;
+            }
+        }
+        if (!dre) e = cudaMemcpyAsync(b->wstage, w_re, (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !dim) e = cudaMemcpyAsync(b->wstage + n, w_im, (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return (b->sticky = bf_status(e));
+    }
+    e = xeng::launch_beam_weights(dre ? w_re : b->wstage, dim ? w_im : b->wstage + n, b->F, b->B, b->N, b->wdev, s);
+    // host weights may be reused by the caller at once
+    if (e == cudaSuccess && (!dre || !dim)) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return (b->sticky = bf_status(e));
+    return XENG_OK;
+}
+
+int xbeam_run(xbeam_t b, const uint8_t *block, int64_t n_samples, int32_t *out, void *stream)
+{
+    if (!b || n_samples < 0) return XENG_ERR_ARG;
+    int st = bf_check_sticky(b);
+    if (st != XENG_OK) return st;
+    if (n_samples == 0) return XENG_OK;
+    if (n_samples > ((int64_t)1 << 31) - 128) return XENG_ERR_RANGE;
+    if (!block || !out || !bf_is_device_pointer(block) || !bf_is_device_pointer(out)) return XENG_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(block) & 15) != 0 || (reinterpret_cast<uintptr_t>(out) & 7) != 0)
+        return XENG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    xeng::BfArgs a;
+    a.T = n_samples;
+    a.F = b->F;
+    a.N = b->N;
+    a.B = b->B;
+    a.out = out;
+    a.err = b->d_err;
+    cudaError_t e = xeng::launch_beamform(block, b->wdev, a, b->num_sms, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return (b->sticky = bf_status(e));
+    return XENG_OK;
+}
+
+void xbeam_destroy(xbeam_t b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    cudaFree(b->wdev);
+    cudaFree(b->wstage);
+    cudaFree(b->d_err);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

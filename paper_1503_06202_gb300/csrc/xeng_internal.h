@@ -67,6 +67,23 @@ cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, 
 cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, int64_t n, int32_t F, int32_t N,
                                  const int32_t *inputs, int32_t S, int64_t H, uint8_t *hist_new, cudaStream_t s);
 
+// Beamforming (Sec. IV-C-3).  The host fills T, F, N, B, out and err; the
+// launcher fills the rest.
+struct BfArgs {
+    int64_t T = 0;
+    int32_t F = 0, N = 0, B = 0;
+    int32_t n_kc = 0;       // 128-input K chunks
+    int32_t n_tt = 0;       // 128-sample tiles
+    int64_t n_items = 0;    // F * n_tt
+    int32_t f_fastest = 0;  // item order: channel fastest, else sample tile fastest
+    int32_t *out = nullptr; // [T][F][B][2]
+    int *err = nullptr;
+};
+int beam_padded(int32_t n_beams);  // 4, 8, 16, 32 or 64
+cudaError_t launch_beam_weights(const int8_t *w_re, const int8_t *w_im, int32_t F, int32_t B, int32_t N,
+                                uint8_t *wdev, cudaStream_t s);
+cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a, int num_sms, cudaStream_t s);
+
 cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s);
 
 // Two tiles run together by the two CTAs of a cluster (CTA r takes tile r).

@@ -26,6 +26,7 @@ XENG_MAX_T_INTEG = 16777215
 XENG_ENGINE_TENSOR = 0
 XENG_ENGINE_DP4A = 1
 XENG_MAX_DELAY = 131072
+XBEAM_MAX_BEAMS = 64
 
 
 class XengStats(ctypes.Structure):
@@ -73,6 +74,14 @@ def lib():
         L.xeng_set_engine.restype = ctypes.c_int
         L.xeng_set_delays.argtypes = [vp, vp]
         L.xeng_set_delays.restype = ctypes.c_int
+        L.xbeam_create.argtypes = [i32, i32, i32, ctypes.POINTER(vp)]
+        L.xbeam_create.restype = ctypes.c_int
+        L.xbeam_set_weights.argtypes = [vp, vp, vp, vp]
+        L.xbeam_set_weights.restype = ctypes.c_int
+        L.xbeam_run.argtypes = [vp, vp, i64, vp, vp]
+        L.xbeam_run.restype = ctypes.c_int
+        L.xbeam_destroy.argtypes = [vp]
+        L.xbeam_destroy.restype = None
         L.xeng_decode.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp]
         L.xeng_decode.restype = ctypes.c_int
         L.xeng_set_profiling.argtypes = [vp, i32]
@@ -231,6 +240,59 @@ class XEngine:
     def close(self) -> None:
         if getattr(self, "h", None):
             xeng_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def xbeam_create(n_inputs: int, n_freq: int, n_beams: int):
+    """Returns (status, beamformer handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().xbeam_create(n_inputs, n_freq, n_beams, ctypes.byref(h))
+    return rc, (h.value if rc == XENG_OK else None)
+
+
+def xbeam_set_weights(b, w_re, w_im, stream=None) -> int:
+    """w_re, w_im: int8 [n_freq][n_beams][n_inputs], torch (device) or numpy (host)."""
+    return lib().xbeam_set_weights(b, _ptr(w_re), _ptr(w_im), _stream(stream))
+
+
+def xbeam_run(b, block, n_samples: int, out, stream=None) -> int:
+    return lib().xbeam_run(b, _ptr(block), n_samples, _ptr(out), _stream(stream))
+
+
+def xbeam_destroy(b) -> None:
+    lib().xbeam_destroy(b)
+
+
+class XBeam:
+    """Beamformer (Sec. IV-C-3): y_b(t, f) = sum_i w_{f,b,i} x_i(t, f) in int32."""
+
+    def __init__(self, n_inputs: int, n_freq: int, n_beams: int):
+        rc, self.h = xbeam_create(n_inputs, n_freq, n_beams)
+        if rc != XENG_OK:
+            raise XengError(rc, "xbeam_create")
+        self.n_inputs, self.n_freq, self.n_beams = n_inputs, n_freq, n_beams
+
+    def set_weights(self, w_re, w_im, stream=None) -> None:
+        rc = xbeam_set_weights(self.h, w_re, w_im, stream)
+        if rc != XENG_OK:
+            raise XengError(rc, "xbeam_set_weights")
+
+    def run(self, block, out, n_samples: int | None = None, stream=None) -> None:
+        if n_samples is None:
+            n_samples = block.shape[0]
+        rc = xbeam_run(self.h, block, n_samples, out, stream)
+        if rc != XENG_OK:
+            raise XengError(rc, "xbeam_run")
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            xbeam_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -51,9 +51,19 @@ def test_null_handles_and_pointers():
     assert xe.xeng_dump(None, None) == xe.XENG_ERR_ARG
     assert xe.xeng_set_engine(None, 0) == xe.XENG_ERR_ARG
     assert xe.xeng_set_delays(None, None) == xe.XENG_ERR_ARG
+    assert xe.lib().xbeam_create(16, 1, 1, None) == xe.XENG_ERR_ARG
+    assert xe.xbeam_set_weights(None, None, None) == xe.XENG_ERR_ARG
+    assert xe.xbeam_run(None, None, 0, None) == xe.XENG_ERR_ARG
+    xe.xbeam_destroy(None)
     assert xe.xeng_set_profiling(None, True) == xe.XENG_ERR_ARG
     xe.xeng_destroy(None)
     assert xe.xeng_decode(None, 1, 1, 1, 0, 1, None) == xe.XENG_ERR_ARG
+
+
+@pytest.mark.parametrize("args", [(0, 1, 1), (8, 1, 1), (200, 1, 1), (4112, 1, 1), (16, 0, 1), (16, 1, 0), (16, 1, 65)])
+def test_beam_create_range_checked_before_cuda(args):
+    rc, h = xe.xbeam_create(*args)
+    assert rc == xe.XENG_ERR_RANGE and h is None
 
 
 def test_strerror_covers_codes():
