@@ -19,15 +19,23 @@
 // accumulation is exact.
 //
 // One persistent CTA per SM; work items = (channel, 128-sample tile):
-//   warp 0        TMA producer: raw byte tiles (128 samples x 128 inputs of one
-//                 channel, read straight from the block) into a raw ring, and
-//                 the matching 128-input slices of both weight operands
-//   warp 1        TMEM allocation and the single-thread MMA issuer
-//   warps 2..9    converters: raw bytes -> E4M3 planes X_re, X_im, written in
-//                 the 128-byte-swizzled K-major layout the MMA reads
-//   warps 10..13  epilogue: TMEM -> int32 beams [T][F][B][2] in HBM
-// Two TMEM accumulators let the epilogue of one item overlap the next item's
-// MMAs.  Every wait is bounded; on time-out the roles leave their loops, the
+//   warp 0        TMA producer of the 128-input slices of both weight
+//                 operands (L2-resident) into a deep shared-memory ring
+//   warp 1        TMEM allocation and the single-thread MMA issuer; the MMA
+//                 reads its A operand (the decoded samples) from tensor memory
+//                 and only B (the weights) from shared memory
+//   warps 2..13   converters in three groups of four warps (one per TMEM lane
+//                 quadrant); group g takes the steps g, g + 3, ...: each thread
+//                 reads one sample row (128 inputs) of the step's raw tile from
+//                 shared memory, decodes it to E4M3 codes and writes X_re, X_im
+//                 into the group's TMEM slot with tcgen05.st
+//   warps 14..17  epilogue: TMEM -> int32 beams [T][F][B][2] in HBM
+//   warp 18       TMA producer of the raw tiles (128 samples x 128 inputs of one
+//                 channel, 128-byte swizzle) into a six-slot ring
+// Shared memory then carries only the weight slices; decoded planes written to
+// and read back from shared memory made the MMAs shared-memory bound at small
+// beam counts.  Two TMEM accumulators (one above 32 beams) let the epilogue of
+// one item overlap the next item's MMAs.  Every wait is bounded; on time-out the roles leave their loops, the
 // producer lets its issued copies land, the MMA thread drains and TMEM is
 // freed before exit.
 #include <cstring>
@@ -41,25 +49,38 @@
 namespace xeng {
 namespace {
 
-constexpr int kBfThreads = 448;        // 14 warps
-constexpr int kConvThreads = 256;      // warps 2..9
-constexpr int kConvFirst = 64;         // first converter thread
-constexpr int kRawBytes = 128 * 128;   // 128 samples x 128 inputs, one byte each
-constexpr int kPlaneBytes = 128 * 128; // 128 samples x 128 inputs, one E4M3 code each
+// Converter groups: four warps each, one per TMEM lane quadrant; group g
+// converts the steps n = g, g + kGroups, ... into its own TMEM slot g (a slot
+// used by one group only, in order, so its barriers never run two phases apart).
+constexpr int kGroups = 3;
+constexpr int kConvWarps = 4 * kGroups;              // warps 2 .. 13
+constexpr int kEpiWarp0 = 2 + kConvWarps;            // 4 epilogue warps (one per TMEM lane quadrant)
+constexpr int kRawProdWarp = kEpiWarp0 + 4;          // TMA producer of the raw tiles
+constexpr int kBfThreads = 32 * (kRawProdWarp + 1);
+constexpr int kRawBytes = 128 * 128;                 // 128 samples x 128 inputs of one channel
+constexpr int kR = 2 * kGroups;                      // raw ring: a multiple of the groups, so each slot has one user
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kXCols = 64;                      // one K chunk: X_re in 32 columns (4 codes each), X_im in 32
 
 template <int kBp>
 struct BfCfg {
     static constexpr int kN = 4 * kBp;                           // MMA N: hi/lo x Re/Im x beams
     static constexpr int kWBytes = kN * 128;                     // one weight operand slice
-    static constexpr int kStageBytes = 2 * kPlaneBytes + 2 * kWBytes;
-    static constexpr int kS = kBp <= 16 ? 3 : 2;                 // MMA ring stages
-    static constexpr int kR = kBp <= 32 ? 4 : 2;                 // raw ring stages
-    static constexpr uint32_t kTmemCols = 8 * kBp;               // two accumulators (a power of 2 >= 32)
-    static constexpr int kBars = 2 * kR + 3 * kS + 5;
-    static constexpr size_t kSmem = 1024 + (size_t)kR * kRawBytes + (size_t)kS * kStageBytes + kBars * 8 + 16;
+    static constexpr int kWStageBytes = 2 * kWBytes;             // both weight operands of one K chunk
+    static constexpr int kAcc = (8 * kBp <= 256) ? 2 : 1;        // accumulators (2: epilogue overlaps MMAs)
+    static constexpr uint32_t kXCol0 = kAcc * kN;                // first TMEM column of the X slots
+    // X slots per group: two where TMEM has room (the group converts its next
+    // step while the MMAs of the previous one run), else one
+    static constexpr int kSlots = (kTmemCols - kXCol0) / (kGroups * kXCols) >= 2 ? 2 : 1;
+    static_assert(kXCol0 + kGroups * kSlots * kXCols <= kTmemCols, "TMEM: accumulators + X slots");
+    static constexpr int kSWFit = (232448 - 1024 - 512 - kR * kRawBytes) / kWStageBytes;
+    static constexpr int kSW = kSWFit > 8 ? 8 : kSWFit;          // weight ring stages (L2 latency off the path)
+    static_assert(kSW >= 2, "weight ring needs two stages");
+    static constexpr int kXS = kGroups * kSlots;                 // X slots in all
+    static constexpr int kBars = 2 * kR + 2 * kXS + 2 * kSW + 2 * kAcc + 1;
+    static constexpr size_t kSmem = 1024 + (size_t)kR * kRawBytes + (size_t)kSW * kWStageBytes + kBars * 8 + 16;
     // kind::f8f6f4, D f32, A and B E4M3 K-major, N and M = 128
     static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    static_assert(kTmemCols >= 32 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation must be a power of 2");
     static_assert(kSmem <= 232448, "shared memory over the per-CTA limit");
 };
 
@@ -68,6 +89,22 @@ __device__ __forceinline__ uint64_t bf_desc(uint32_t saddr)
 {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// MMA with A (M = 128 rows x K = 32 codes) read from tensor memory.
+__device__ __forceinline__ void mma_f8_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(d), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ void bf_item(const BfArgs &a, int64_t it, int &f, int &tt)
@@ -88,45 +125,54 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     using C = BfCfg<kBp>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t sbase = (raw + 1023u) & ~1023u;
-    uint8_t *sgen = smem_raw + (sbase - raw);  // generic view of the aligned base
-    const uint32_t stbase = sbase + C::kR * kRawBytes;
-    const uint32_t bars = stbase + C::kS * C::kStageBytes;
-    auto rawf = [&](int r) { return bars + 8u * r; };                          // raw tile landed
-    auto rawe = [&](int r) { return bars + 8u * (C::kR + r); };                // raw tile read
-    auto wf = [&](int s) { return bars + 8u * (2 * C::kR + s); };             // weight slices landed
-    auto xf = [&](int s) { return bars + 8u * (2 * C::kR + C::kS + s); };     // planes written
-    auto ste = [&](int s) { return bars + 8u * (2 * C::kR + 2 * C::kS + s); };  // stage consumed by the MMAs
-    auto accf = [&](int b) { return bars + 8u * (2 * C::kR + 3 * C::kS + b); };
-    auto acce = [&](int b) { return bars + 8u * (2 * C::kR + 3 * C::kS + 2 + b); };
-    const uint32_t drain_bar = bars + 8u * (2 * C::kR + 3 * C::kS + 4);
+    const uint32_t rbase = (raw + 1023u) & ~1023u;                  // raw ring
+    const uint8_t *rgen = smem_raw + (rbase - raw);                 // generic view of it
+    const uint32_t wbase = rbase + kR * kRawBytes;                  // weight ring
+    const uint32_t bars = wbase + C::kSW * C::kWStageBytes;
+    auto xf = [&](int x) { return bars + 8u * x; };                           // X slot x written
+    auto xe = [&](int x) { return bars + 8u * (C::kXS + x); };                // X slot x consumed
+    auto wf = [&](int s) { return bars + 8u * (2 * C::kXS + s); };            // weight slices landed
+    auto we = [&](int s) { return bars + 8u * (2 * C::kXS + C::kSW + s); };   // weight slices consumed
+    auto accf = [&](int b) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + b); };
+    auto acce = [&](int b) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + C::kAcc + b); };
+    const uint32_t drain_bar = bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc);
+    auto rawf = [&](int r) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc + 1 + r); };       // tile landed
+    auto rawe = [&](int r) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc + 1 + kR + r); };  // tile read
+    // step n of this CTA belongs to group n % kGroups, which uses its slots in
+    // turn: slot (n / kGroups) % kSlots of the group, phase (n / kGroups / kSlots) & 1
+    auto xslot = [&](int64_t n) { return (int)(n % kGroups) * C::kSlots + (int)((n / kGroups) % C::kSlots); };
+    auto xphase = [&](int64_t n) { return (uint32_t)((n / kGroups / C::kSlots) & 1); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * C::kBars - raw));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = a.err;
+    const int64_t n_seq = ((a.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x) * a.n_kc;
 
     if (threadIdx.x == 0) {
-        for (int r = 0; r < C::kR; r++) {
-            mbar_init(rawf(r), 1);
-            mbar_init(rawe(r), kConvThreads);
+        for (int x = 0; x < C::kXS; x++) {
+            mbar_init(xf(x), 128);
+            mbar_init(xe(x), 1);
         }
-        for (int s = 0; s < C::kS; s++) {
+        for (int s = 0; s < C::kSW; s++) {
             mbar_init(wf(s), 1);
-            mbar_init(xf(s), kConvThreads);
-            mbar_init(ste(s), 1);
+            mbar_init(we(s), 1);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < C::kAcc; b++) {
             mbar_init(accf(b), 1);
             mbar_init(acce(b), 128);
         }
         mbar_init(drain_bar, 1);
+        for (int r = 0; r < kR; r++) {
+            mbar_init(rawf(r), 1);
+            mbar_init(rawe(r), 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&w_map) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(C::kTmemCols));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before();
@@ -136,35 +182,24 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer ----------------
-            int r = 0, s = 0, issued_r = 0, issued_s = 0;
-            uint32_t pr = 0, ps = 0;
+            // ---------------- TMA producer: weight slices ----------------
+            int s = 0, issued = 0;
+            uint32_t ps = 0;
             bool ok = true;
             for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x) {
                 int f, tt;
                 bf_item(a, it, f, tt);
                 for (int k = 0; k < a.n_kc; k++) {
-                    if (!mbar_wait(rawe(r), pr ^ 1u, err, kDevTimeoutProducer)) {
+                    if (!mbar_wait(we(s), ps ^ 1u, err, kDevTimeoutProducer)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(rawf(r), kRawBytes);
-                    tma_load_3d(sbase + r * kRawBytes, &raw_map, k * 128, f, tt * 128, rawf(r));
-                    ++issued_r;
-                    if (++r == C::kR) {
-                        r = 0;
-                        pr ^= 1u;
-                    }
-                    if (!mbar_wait(ste(s), ps ^ 1u, err, kDevTimeoutProducer)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t w0 = stbase + s * C::kStageBytes + 2 * kPlaneBytes;
+                    const uint32_t w0 = wbase + s * C::kWStageBytes;
                     mbar_expect_tx(wf(s), 2 * C::kWBytes);
                     tma_load_2d(w0, &w_map, k * 128, (f * 2 + 0) * C::kN, wf(s));
                     tma_load_2d(w0 + C::kWBytes, &w_map, k * 128, (f * 2 + 1) * C::kN, wf(s));
-                    ++issued_s;
-                    if (++s == C::kS) {
+                    ++issued;
+                    if (++s == C::kSW) {
                         s = 0;
                         ps ^= 1u;
                     }
@@ -172,14 +207,9 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             }
             if (!ok) {
                 // Let the copies already issued land before the CTA can exit.
-                for (int k = 1; k <= C::kR && k <= issued_r; k++) {
-                    int q = r - k, p = (int)pr;
-                    if (q < 0) { q += C::kR; p ^= 1; }
-                    (void)mbar_wait(rawf(q), (uint32_t)p, err, kDevTimeoutProducer);
-                }
-                for (int k = 1; k <= C::kS && k <= issued_s; k++) {
+                for (int k = 1; k <= C::kSW && k <= issued; k++) {
                     int q = s - k, p = (int)ps;
-                    if (q < 0) { q += C::kS; p ^= 1; }
+                    if (q < 0) { q += C::kSW; p ^= 1; }
                     (void)mbar_wait(wf(q), (uint32_t)p, err, kDevTimeoutProducer);
                 }
             }
@@ -187,33 +217,43 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            int s = 0, local = 0;
-            uint32_t ps = 0, uses[2] = {0, 0};
+            // Per step: two waits, eight MMAs, two commits; the bookkeeping is
+            // kept to a few integer operations since each step carries little
+            // tensor work (N = 4 Bp).
+            int sw = 0, local = 0, c = 0;  // c = step index modulo the X slots
+            uint32_t pw = 0, pxs = 0, uses[2] = {0, 0};
             bool ok = true;
             for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x, ++local) {
-                const int ab = local & 1;
-                if (!mbar_wait(acce(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma)) break;
+                const int ab = C::kAcc == 2 ? (local & 1) : 0;
+                if (!mbar_wait_backoff(acce(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma, 0)) break;
                 ++uses[ab];
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(ab * C::kN);
                 for (int k = 0; k < a.n_kc; k++) {
-                    if (!mbar_wait(wf(s), ps, err, kDevTimeoutMma) || !mbar_wait(xf(s), ps, err, kDevTimeoutMma)) {
+                    const int x = (c % kGroups) * C::kSlots + c / kGroups;
+                    if (!mbar_wait_backoff(wf(sw), pw, err, kDevTimeoutMma, 0) ||
+                        !mbar_wait_backoff(xf(x), pxs, err, kDevTimeoutMma, 0)) {
                         ok = false;
                         break;
                     }
                     fence_after();
-                    const uint32_t xre = stbase + s * C::kStageBytes, xim = xre + kPlaneBytes;
-                    const uint32_t w0 = xre + 2 * kPlaneBytes, w1 = w0 + C::kWBytes;
+                    const uint32_t xre = tmem + C::kXCol0 + (uint32_t)x * kXCols, xim = xre + 32;
+                    const uint32_t w0 = wbase + sw * C::kWStageBytes;
+                    const uint64_t b0 = bf_desc(w0), b1 = bf_desc(w0 + C::kWBytes);
                     #pragma unroll
-                    for (int kk = 0; kk < 4; kk++) {
-                        const uint32_t off = kk * 32;
-                        mma_f8(d, bf_desc(xre + off), bf_desc(w0 + off), C::kIdesc, (k != 0 || kk != 0) ? 1u : 0u);
-                        mma_f8(d, bf_desc(xim + off), bf_desc(w1 + off), C::kIdesc, 1u);
+                    for (int kk = 0; kk < 4; kk++) {  // +32 bytes along K = +2 in the descriptor's address field
+                        mma_f8_ta(d, xre + kk * 8, b0 + 2 * kk, C::kIdesc, (k != 0 || kk != 0) ? 1u : 0u);
+                        mma_f8_ta(d, xim + kk * 8, b1 + 2 * kk, C::kIdesc, 1u);
                     }
-                    mma_commit(ste(s));
-                    if (++s == C::kS) {
-                        s = 0;
-                        ps ^= 1u;
+                    mma_commit(xe(x));
+                    mma_commit(we(sw));
+                    if (++sw == C::kSW) {
+                        sw = 0;
+                        pw ^= 1u;
+                    }
+                    if (++c == C::kXS) {
+                        c = 0;
+                        pxs ^= 1u;
                     }
                 }
                 if (!ok) break;
@@ -223,54 +263,49 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             mma_commit(drain_bar);
             (void)mbar_wait(drain_bar, 0u, err, kDevTimeoutMma);
         }
-    } else if (warp < 10) {
-        // ---------------- converters ----------------
-        const int ct = threadIdx.x - kConvFirst;  // 0..255
-        int r = 0, s = 0;
-        uint32_t pr = 0, ps = 0;
-        bool ok = true;
-        for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x) {
-            for (int k = 0; k < a.n_kc; k++) {
-                ok = mbar_wait(rawf(r), pr, err, kDevTimeoutProducer) &&
-                     mbar_wait(ste(s), ps ^ 1u, err, kDevTimeoutProducer);
-                if (!ok) break;
-                const uint8_t *rt = sgen + r * kRawBytes;
-                uint8_t *xre = sgen + (stbase - sbase) + s * C::kStageBytes;
-                uint8_t *xim = xre + kPlaneBytes;
-                uint4 v[4];
+    } else if (warp < kEpiWarp0) {
+        // ---------------- converters: raw tile (smem) -> E4M3 codes in TMEM ----------------
+        // Thread = one sample row of a step (its TMEM lane): the row's 128
+        // bytes from the 128-byte-swizzled raw tile (conflict-free: lanes t and
+        // t + 8 share a chunk position, the minimum for 16-byte reads).
+        const int g = (warp - 2) >> 2;
+        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row = q * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + C::kXCol0;
+        for (int64_t n = g; n < n_seq; n += kGroups) {
+            const int r = (int)(n % kR);
+            const uint32_t pr = (uint32_t)((n / kR) & 1);
+            const int x = xslot(n);
+            const bool ok = mbar_wait_backoff(rawf(r), pr, err, kDevTimeoutProducer, 0) &&
+                            mbar_wait_backoff(xe(x), xphase(n) ^ 1u, err, kDevTimeoutProducer, 0);
+            if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.st
+            fence_after();
+            const uint8_t *rt = rgen + r * kRawBytes + row * 128;
+            uint4 v[8];
+            #pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = *reinterpret_cast<const uint4 *>(rt + ((j ^ (row & 7)) << 4));
+            mbar_arrive(rawe(r));
+            const uint32_t xre = lane_base + (uint32_t)x * kXCols;
+            #pragma unroll
+            for (int h = 0; h < 4; h++) {  // 32 inputs = 8 columns per store
+                uint32_t re[8], im[8];
                 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int q = j * kConvThreads + ct, t = q >> 3, c = q & 7;
-                    v[j] = *reinterpret_cast<const uint4 *>(rt + t * 128 + c * 16);
+                for (int j = 0; j < 2; j++) {
+                    const uint4 w = v[2 * h + j];
+                    decode_word(w.x, re[4 * j + 0], im[4 * j + 0]);
+                    decode_word(w.y, re[4 * j + 1], im[4 * j + 1]);
+                    decode_word(w.z, re[4 * j + 2], im[4 * j + 2]);
+                    decode_word(w.w, re[4 * j + 3], im[4 * j + 3]);
                 }
-                #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int q = j * kConvThreads + ct, t = q >> 3, c = q & 7;
-                    uint32_t re[4], im[4];
-                    decode_word(v[j].x, re[0], im[0]);
-                    decode_word(v[j].y, re[1], im[1]);
-                    decode_word(v[j].z, re[2], im[2]);
-                    decode_word(v[j].w, re[3], im[3]);
-                    // row t, 16-byte chunk c of a 128-byte-swizzled tile
-                    const int off = t * 128 + ((c ^ (t & 7)) << 4);
-                    *reinterpret_cast<uint4 *>(xre + off) = make_uint4(re[0], re[1], re[2], re[3]);
-                    *reinterpret_cast<uint4 *>(xim + off) = make_uint4(im[0], im[1], im[2], im[3]);
-                }
-                mbar_arrive(rawe(r));
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the MMA
-                mbar_arrive(xf(s));
-                if (++r == C::kR) {
-                    r = 0;
-                    pr ^= 1u;
-                }
-                if (++s == C::kS) {
-                    s = 0;
-                    ps ^= 1u;
-                }
+                tmem_st8(xre + h * 8, re);
+                tmem_st8(xre + 32 + h * 8, im);
             }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            fence_before();
+            mbar_arrive(xf(x));
         }
-    } else {
-        // ---------------- epilogue (warps 10..13) ----------------
+    } else if (warp < kRawProdWarp) {
+        // ---------------- epilogue (warps 14..17) ----------------
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
         const int row = q * 32 + lane;
         constexpr int G = kBp < 16 ? kBp : 16;
@@ -279,13 +314,14 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
         for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x, ++local) {
             int f, tt;
             bf_item(a, it, f, tt);
-            const int ab = local & 1;
-            const bool ok = mbar_wait(accf(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue);
+            const int ab = C::kAcc == 2 ? (local & 1) : 0;
+            const bool ok = mbar_wait_backoff(accf(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue, 256);
             if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
             ++uses[ab];
             fence_after();
             const int64_t t = (int64_t)tt * 128 + row;
             int2 *o = reinterpret_cast<int2 *>(a.out) + (t * a.F + f) * a.B;
+            int4 *o4 = reinterpret_cast<int4 *>(o);  // two beams per store when B is even
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::kN);
             #pragma unroll
             for (int b0 = 0; b0 < kBp; b0 += G) {
@@ -299,17 +335,48 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
                 }
                 tmem_ld_wait();
                 if (t < a.T) {
+                    int2 y[G];
                     #pragma unroll
                     for (int e = 0; e < G; e++)
-                        if (b0 + e < a.B)
-                            o[b0 + e] = make_int2(16 * __float2int_rn(__uint_as_float(hre[e])) +
-                                                      __float2int_rn(__uint_as_float(lre[e])),
-                                                  16 * __float2int_rn(__uint_as_float(him[e])) +
-                                                      __float2int_rn(__uint_as_float(lim[e])));
+                        y[e] = make_int2(16 * __float2int_rn(__uint_as_float(hre[e])) +
+                                             __float2int_rn(__uint_as_float(lre[e])),
+                                         16 * __float2int_rn(__uint_as_float(him[e])) +
+                                             __float2int_rn(__uint_as_float(lim[e])));
+                    if (a.vec16) {
+                        #pragma unroll
+                        for (int e = 0; e < G; e += 2)
+                            if (b0 + e < a.B) o4[(b0 + e) >> 1] = make_int4(y[e].x, y[e].y, y[e + 1].x, y[e + 1].y);
+                    } else {
+                        #pragma unroll
+                        for (int e = 0; e < G; e++)
+                            if (b0 + e < a.B) o[b0 + e] = y[e];
+                    }
                 }
             }
             fence_before();
             mbar_arrive(acce(ab));
+        }
+    } else if (lane == 0) {
+        // ---------------- TMA producer: raw tiles (warp 18) ----------------
+        int issued = 0;
+        bool ok = true;
+        for (int64_t n = 0; n < n_seq; n++) {
+            const int r = (int)(n % kR);
+            if (!mbar_wait(rawe(r), (uint32_t)((n / kR) & 1) ^ 1u, err, kDevTimeoutProducer)) {
+                ok = false;
+                break;
+            }
+            const int64_t it = blockIdx.x + (n / a.n_kc) * (int64_t)gridDim.x;
+            int f, tt;
+            bf_item(a, it, f, tt);
+            mbar_expect_tx(rawf(r), kRawBytes);
+            tma_load_3d(rbase + r * kRawBytes, &raw_map, (int)(n % a.n_kc) * 128, f, tt * 128, rawf(r));
+            ++issued;
+        }
+        if (!ok) {
+            // Let the copies already issued land before the CTA can exit.
+            for (int64_t n = issued - 1; n >= 0 && n >= issued - kR; n--)
+                (void)mbar_wait(rawf((int)(n % kR)), (uint32_t)((n / kR) & 1), err, kDevTimeoutProducer);
         }
     }
 
@@ -318,7 +385,7 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     __syncthreads();
     fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
 
@@ -386,14 +453,15 @@ cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a,
     if (!enc) return cudaErrorNotSupported;
     const int bp = beam_padded(a.B);
     const int n_pad = (int)round_up(a.N, 128);
-    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x 128 samples
+    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel
+    // x 128 samples, 128-byte swizzle (conflict-free row reads by the converters)
     CUtensorMap rm, wm;
     {
         cuuint64_t dims[3] = {(cuuint64_t)a.N, (cuuint64_t)a.F, (cuuint64_t)a.T};
         cuuint64_t strides[2] = {(cuuint64_t)a.N, (cuuint64_t)a.N * a.F};
         cuuint32_t box[3] = {128, 1, 128}, estr[3] = {1, 1, 1};
         if (enc(&rm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
@@ -412,6 +480,8 @@ cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a,
     // channel-fastest order reads neighbouring channels' rows together; it
     // needs every channel's weights in L2, else one channel at a time
     a.f_fastest = ((int64_t)a.F * 8 * bp * n_pad <= ((int64_t)48 << 20)) ? 1 : 0;
+    a.block = block;
+    a.vec16 = (a.B % 2 == 0 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0) ? 1 : 0;
     const int grid = (int)(a.n_items < num_sms ? a.n_items : num_sms);
     switch (bp) {
         case 4: return launch_bf<4>(rm, wm, a, grid, s);

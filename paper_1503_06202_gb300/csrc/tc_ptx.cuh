@@ -62,6 +62,26 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, 
     }
 }
 
+// As mbar_wait, but sleeping `sleep_ns` between polls: for roles with many
+// warps waiting, whose spinning would take issue slots from the warps at work.
+// Inlined: a call would make the caller's loads still in flight complete
+// before it (their registers are saved across the call).
+__device__ __forceinline__ bool mbar_wait_backoff(uint32_t bar, uint32_t parity, int *err, int code, uint32_t sleep_ns,
+                                               uint64_t limit_ns = kWaitLimitNs)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (sleep_ns) __nanosleep(sleep_ns);
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)err != 0) return false;
+        if (globaltimer() - t0 > limit_ns) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");

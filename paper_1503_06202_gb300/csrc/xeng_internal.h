@@ -76,6 +76,8 @@ struct BfArgs {
     int32_t n_tt = 0;       // 128-sample tiles
     int64_t n_items = 0;    // F * n_tt
     int32_t f_fastest = 0;  // item order: channel fastest, else sample tile fastest
+    int32_t vec16 = 0;      // B even and out 16-byte aligned: two beams per store
+    const uint8_t *block = nullptr;  // [T][F][N]
     int32_t *out = nullptr; // [T][F][B][2]
     int *err = nullptr;
 };
