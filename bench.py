@@ -513,6 +513,8 @@ def main():
         push_dump(1)
         sh_ms, sh_dec = push_dump()
         eng.set_delays(None)
+        eng.correlate(block, out, T, stream)  # `out` holds the unshifted result again for the CPU check
+        stream.synchronize()
         shift = {"delayed_inputs": 2, "delay_samples": 65625, "push_dump_ms_per_step": sh_ms,
                  "decode_ms_per_step": sh_dec, "unshifted_push_dump_ms_per_step": push_dump_ms,
                  "unshifted_decode_ms_per_step": push_dump_decode_ms,
