@@ -136,6 +136,19 @@ cudaEvent_t take_event(xeng_s *h)
 #define XENG_TC_PAIRS 0
 #endif
 
+// Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
+// either end (the first group's upload and the last group's download overlap
+// nothing), but each group's pitched upload copies T rows of (channels x N)
+// bytes, and narrow rows cost the copy engine time per row (measured on GB300:
+// 207 GB/s at 512 KB rows, 152 at 256 KB, 102 at 128 KB, 212 for a flat copy).
+// So the groups are sized for rows of about XENG_PIPE_ROW_BYTES (a build
+// parameter), one to eight of them; full CHIME (1024 channels x 2048 inputs)
+// gets five (measured: 4 / 5 / 6 / 8 groups -> 130.5 / 128.4 / 133.7 / 144.4 ms
+// end to end).
+#ifndef XENG_PIPE_ROW_BYTES
+#define XENG_PIPE_ROW_BYTES 409600
+#endif
+
 // Rows of the decoded planes per channel and plane: N rounded up to the tile.
 int64_t planes_rows(int64_t N) { return round_up(N, XENG_TC_2CTA ? 256 : kTile); }
 
@@ -500,7 +513,9 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
 {
     const int64_t N = h->N, F = h->F;
     const int64_t n_pad = planes_rows(N), t_pad = round_up(n, kTile), nb2 = N * (N + 1);
-    int64_t pf = (F + 7) / 8;  // about eight groups
+    int64_t groups = (F * N + XENG_PIPE_ROW_BYTES / 2) / XENG_PIPE_ROW_BYTES;
+    groups = groups < 1 ? 1 : groups > 8 ? 8 : groups;
+    int64_t pf = (F + groups - 1) / groups;  // channels per group
     if (pf > h->group_f) pf = h->group_f;
     if (pf < 1) pf = 1;
     int st = ensure_pipeline(h, host_in ? pf * n * N : 0);
@@ -517,9 +532,13 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
         if (host_in) {
             // staging[buf] was last read by the decode of group g - 2, which ev_cmp[buf] follows
             if (g >= 2) e = cudaStreamWaitEvent(h->h2d, h->ev_cmp[buf], 0);
-            if (e == cudaSuccess)
-                e = cudaMemcpy2DAsync(h->pstage[buf], (size_t)(nf * N), src + f0 * N, (size_t)(F * N), (size_t)(nf * N),
-                                      (size_t)n, cudaMemcpyHostToDevice, h->h2d);
+            if (e == cudaSuccess) {
+                if (nf == F)  // every channel: the block is contiguous
+                    e = cudaMemcpyAsync(h->pstage[buf], src, (size_t)(n * F * N), cudaMemcpyHostToDevice, h->h2d);
+                else
+                    e = cudaMemcpy2DAsync(h->pstage[buf], (size_t)(nf * N), src + f0 * N, (size_t)(F * N),
+                                          (size_t)(nf * N), (size_t)n, cudaMemcpyHostToDevice, h->h2d);
+            }
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[buf], h->h2d);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_in[buf], 0);
             if (e != cudaSuccess) break;
