@@ -261,11 +261,13 @@ typedef struct {
 
 #define XENG_SCHED_LPT         0  /* longest items first onto the least-loaded CTA */
 #define XENG_SCHED_ROUND_ROBIN 1  /* items dealt round-robin in job order          */
+#define XENG_SCHED_ORDERED     2  /* items in job order, each to the CTA expected to be
+                                     free first: CTAs stay on neighbouring tiles       */
 
 typedef struct {
     int32_t max_chunks_per_item; /* split a tile's integration into items of at most this many
                                     128-sample chunks (1..512; <= 0 means 512)            */
-    int32_t policy;              /* XENG_SCHED_LPT or XENG_SCHED_ROUND_ROBIN              */
+    int32_t policy;              /* XENG_SCHED_LPT, _ROUND_ROBIN or _ORDERED               */
     int32_t use_graph;           /* != 0: capture the run in a CUDA graph once, replay it */
 } xeng_batch_opts_t;
 

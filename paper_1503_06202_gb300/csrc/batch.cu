@@ -10,10 +10,10 @@
 // work items; a tile whose integration is longer than `max_chunks` 128-sample
 // chunks is split along time into several items whose int32 results are added
 // with atomics (exact: integer addition is order-independent).  Items are
-// assigned to one persistent CTA per SM either longest-first onto the
-// least-loaded CTA (LPT) or round-robin in job order; each CTA then runs its
-// items in job/channel order so CTAs sweep the jobs together and operands stay
-// in L2.
+// assigned to one persistent CTA per SM longest-first onto the least-loaded
+// CTA (LPT), round-robin in job order, or in job order onto the CTA expected
+// to be free first (ORDERED: the CTAs move through the list together and share
+// each channel's operands in L2); each CTA runs its items in job/channel order.
 #include <algorithm>
 #include <cinttypes>
 #include <cstdio>
@@ -191,16 +191,31 @@ int plan(xeng_batch_s *b)
     const int P = (int)std::max<int64_t>(1, std::min<int64_t>(b->num_sms, (int64_t)cand.size()));
     std::vector<std::vector<int64_t>> per(P);
     std::vector<double> load(P, 0.0);
+    typedef std::pair<double, int> LoadCta;
     if (b->opts.policy == XENG_SCHED_ROUND_ROBIN) {
         for (size_t k = 0; k < cand.size(); k++) {
             per[k % P].push_back((int64_t)k);
             load[k % P] += cand[k].cost;
         }
+    } else if (b->opts.policy == XENG_SCHED_ORDERED) {
+        // items in job / channel / tile order, each to the CTA expected to be
+        // free first: the CTAs advance through the list together, as with a
+        // shared work queue, so at any time they work on neighbouring tiles of
+        // the same channel and share its operands in L2
+        std::priority_queue<LoadCta, std::vector<LoadCta>, std::greater<LoadCta>> heap;
+        for (int c = 0; c < P; c++) heap.push({0.0, c});
+        for (size_t k = 0; k < cand.size(); k++) {
+            LoadCta t = heap.top();
+            heap.pop();
+            per[t.second].push_back((int64_t)k);
+            t.first += cand[k].cost;
+            load[t.second] = t.first;
+            heap.push(t);
+        }
     } else {
         std::vector<int64_t> idx(cand.size());
         for (size_t k = 0; k < idx.size(); k++) idx[k] = (int64_t)k;
         std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return cand[x].cost > cand[y].cost; });
-        typedef std::pair<double, int> LoadCta;
         std::priority_queue<LoadCta, std::vector<LoadCta>, std::greater<LoadCta>> heap;
         for (int c = 0; c < P; c++) heap.push({0.0, c});
         for (int64_t k : idx) {
@@ -278,7 +293,8 @@ int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_o
         o = *opts;
         if (o.max_chunks_per_item <= 0 || o.max_chunks_per_item > kMaxChunkSamples / kTile)
             o.max_chunks_per_item = kMaxChunkSamples / kTile;
-        if (o.policy != XENG_SCHED_LPT && o.policy != XENG_SCHED_ROUND_ROBIN) return XENG_ERR_ARG;
+        if (o.policy != XENG_SCHED_LPT && o.policy != XENG_SCHED_ROUND_ROBIN && o.policy != XENG_SCHED_ORDERED)
+            return XENG_ERR_ARG;
     }
     for (int j = 0; j < n_jobs; j++) {
         const xeng_job_t &jb = jobs[j];
@@ -383,7 +399,7 @@ int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cach
     }
     if (reps < 1) reps = 3;
     const int chunks[] = {16, 32, 64, 128, 256, 512};
-    const int policies[] = {XENG_SCHED_LPT, XENG_SCHED_ROUND_ROBIN};
+    const int policies[] = {XENG_SCHED_LPT, XENG_SCHED_ROUND_ROBIN, XENG_SCHED_ORDERED};
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return XENG_ERR_CUDA;
     cudaEvent_t e0, e1;

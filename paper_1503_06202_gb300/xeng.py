@@ -338,6 +338,7 @@ def xeng_peak_probe(kind: int, iters: int):
 
 XENG_SCHED_LPT = 0
 XENG_SCHED_ROUND_ROBIN = 1
+XENG_SCHED_ORDERED = 2
 
 
 class XengJob(ctypes.Structure):

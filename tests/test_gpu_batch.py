@@ -58,7 +58,9 @@ def test_batch_matches_oracle_and_alone():
 @pytest.mark.parametrize("max_chunks,policy,graph", [(0, xe.XENG_SCHED_LPT, True), (1, xe.XENG_SCHED_LPT, True),
                                                       (3, xe.XENG_SCHED_ROUND_ROBIN, True),
                                                       (7, xe.XENG_SCHED_ROUND_ROBIN, False),
-                                                      (512, xe.XENG_SCHED_LPT, False)])
+                                                      (512, xe.XENG_SCHED_LPT, False),
+                                                      (2, xe.XENG_SCHED_ORDERED, True),
+                                                      (512, xe.XENG_SCHED_ORDERED, True)])
 def test_batch_plans_agree(max_chunks, policy, graph):
     host, jobs = make_jobs(SMALL_MIX[:7], seed=41)
     b = xe.XBatch(jobs, xe.xeng._opts(max_chunks, policy, graph))
