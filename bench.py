@@ -31,6 +31,7 @@ WORKLOADS = {
     "pathfinder_full": ("PATHFINDER_FULL", "full Pathfinder rate: N=256, 1024 channels, T=32768, sky+noise (rho 0.1, sigma 2.5)"),
     "pathfinder_small": ("PATHFINDER_SMALL", "Pathfinder-shaped small: N=256, 8 channels, T=4096, uniform nibbles"),
     "chime_slice": ("CHIME_SLICE", "16 channels of the full-CHIME shape (N=2048, T=8192): profiling case"),
+    "pathfinder_slice": ("PATHFINDER_SLICE", "64 channels of the Pathfinder shape (N=256, T=32768): profiling case"),
     "batched": (None, "64 independent jobs, N in {64..2048}, F in {1,16,64}, T log-uniform 1024..32768, uniform nibbles"),
     "serving": (None, "8 concurrent streams (3 x N=256, 3 x N=512, 2 x N=2048), 256 channels each, 256-sample blocks, "
                       "Poisson arrivals at r x real time, dumps every 65536 samples"),

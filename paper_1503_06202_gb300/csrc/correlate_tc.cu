@@ -111,17 +111,7 @@ struct Work {
     bool dup;        // pair launch: this CTA repeats the peer's tile, writes nothing
 };
 
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
 
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 // TMA load whose box lands at the same offset in the shared memory of every
 // CTA of the cluster in `mask`, completing bytes on each one's barrier there.
@@ -454,12 +444,6 @@ __host__ __device__ constexpr uint32_t make_idesc_m256(bool neg_a)
 constexpr uint32_t kIdesc2 = make_idesc_m256(false);
 constexpr uint32_t kIdesc2Neg = make_idesc_m256(true);
 
-__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-    return r;
-}
 
 __device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar_cluster)
 {
@@ -469,25 +453,8 @@ __device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap 
         : "memory");
 }
 
-__device__ __forceinline__ void mma_f8_cg2(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 
-__device__ __forceinline__ void mma_commit_cg2(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
-                 : "memory");
-}
 
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
-}
 
 struct Sched2 {
     int nt2, tiles_per_ch, n_tiles;

@@ -135,6 +135,10 @@ cudaEvent_t take_event(xeng_s *h)
 #ifndef XENG_TC_PAIRS
 #define XENG_TC_PAIRS 0
 #endif
+// Up to 256 inputs: decode fused into the correlation (no planes in HBM).
+#ifndef XENG_FUSED_SMALL
+#define XENG_FUSED_SMALL 1
+#endif
 
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
 // either end (the first group's upload and the last group's download overlap
@@ -423,6 +427,17 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
         });
     }
     cudaError_t e = cudaSuccess;
+    if (XENG_FUSED_SMALL && !apply_shift && fused256_ok(dblock, (int32_t)N)) {
+        for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
+            const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
+            const int accumulate = (fresh && t0 == 0) ? 0 : 1;
+            e = timed_launch(h, 1, s, [&] {
+                return launch_correlate_fused256(dblock, n_samples, t0, nt, (int32_t)F, (int32_t)N, 0, (int32_t)F,
+                                                 target, accumulate, h->d_err, h->num_sms, s);
+            });
+        }
+        return e;
+    }
     for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
         const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
         const int64_t t_pad = round_up(nt, kTile);
@@ -545,6 +560,20 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
             blk = h->pstage[buf];
             bf = nf;
             bf0 = 0;
+        }
+        if (XENG_FUSED_SMALL && fused256_ok(blk, (int32_t)N)) {
+            e = timed_launch(h, 1, s, [&] {
+                return launch_correlate_fused256(blk, n, 0, n, bf, (int32_t)N, bf0, nf, target + f0 * nb2,
+                                                 fresh ? 0 : 1, h->d_err, h->num_sms, s);
+            });
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
+            if (e == cudaSuccess && host_out) {
+                e = cudaStreamWaitEvent(h->d2h, h->ev_cmp[buf], 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(host_out + f0 * nb2, target + f0 * nb2, (size_t)(nf * nb2 * 4),
+                                        cudaMemcpyDeviceToHost, h->d2h);
+            }
+            continue;
         }
         e = timed_launch(h, 0, s, [&] {
             return launch_decode(blk, n, bf, (int32_t)N, bf0, nf, h->planes, t_pad, n_pad, s);

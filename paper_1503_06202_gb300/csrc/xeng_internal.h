@@ -67,6 +67,15 @@ cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, 
 cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, int64_t n, int32_t F, int32_t N,
                                  const int32_t *inputs, int32_t S, int64_t H, uint8_t *hist_new, cudaStream_t s);
 
+// Decode fused into the correlation for N <= 256 (N % 16 == 0, block 16-byte
+// aligned): samples t0 .. t0 + nt - 1 (nt <= 65536) of the block (T_block
+// samples), channels f0 .. f0 + nf - 1, stored (accumulate = 0) or added into
+// acc [nf][N(N+1)/2][2]; no decoded planes.
+bool fused256_ok(const uint8_t *block, int32_t N);
+cudaError_t launch_correlate_fused256(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
+                                      int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
+                                      int num_sms, cudaStream_t s);
+
 // Beamforming (Sec. IV-C-3).  The host fills T, F, N, B, out and err; the
 // launcher fills the rest.
 struct BfArgs {

@@ -181,6 +181,8 @@ CHIME_FULL = Recipe("sky", T=8192, F=1024, N=2048, seed=2)
 # 16 channels of the full-CHIME shape: inputs (256 MiB) still exceed L2 while
 # the whole working set stays near 1.3 GB -- the profiling case.
 CHIME_SLICE = Recipe("sky", T=8192, F=16, N=2048, seed=2)
+# 64 channels of the Pathfinder shape (512 MiB of input): its profiling case.
+PATHFINDER_SLICE = Recipe("sky", T=32768, F=64, N=256, seed=1)
 
 
 BATCH_N = (64, 96, 128, 200, 256, 512, 1024, 2048)
