@@ -1,0 +1,67 @@
+"""The fused decode + correlation used for up to 256 inputs (N a multiple of
+16): bit-exact against the oracle for tiny N (the second CTA of the cluster
+reads only padding), ragged sample counts, one sample, several launches
+adding into int32, pushes in pieces, host buffers, and many channels per
+cluster."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1503_06202_gb300 as xe  # noqa: E402
+
+
+def correlate(blk, pieces=None, host=False, t_integ=None):
+    T, F, N = blk.shape
+    eng = xe.XEngine(N, F, t_integ or max(T, 1))
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    src = blk if host else torch.from_numpy(blk).cuda()
+    if pieces:
+        t = 0
+        for p in pieces + [T - sum(pieces)]:
+            eng.push(src[t:t + p], p)
+            t += p
+        eng.dump(out)
+    else:
+        eng.correlate(src, out, T)
+    torch.cuda.synchronize()
+    eng.close()
+    return out.cpu().numpy().astype(np.int64)
+
+
+@pytest.mark.parametrize("T,F,N", [(1, 1, 16), (127, 2, 16), (129, 3, 32), (1000, 2, 96), (300, 1, 128),
+                                   (4097, 2, 144), (513, 2, 240), (1, 1, 256), (2049, 3, 256)])
+def test_fused_shapes(T, F, N):
+    rng = np.random.default_rng(T * 131 + F * 17 + N)
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    assert np.array_equal(correlate(blk), oracle.correlate(blk)), (T, F, N)
+
+
+def test_fused_several_launches_and_pieces():
+    # 140,000 samples = three launches of <= 65,536 adding into int32
+    rng = np.random.default_rng(5)
+    T, F, N = 140000, 2, 256
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    assert np.array_equal(correlate(blk), want)
+    assert np.array_equal(correlate(blk, pieces=[100, 65536, 3]), want)
+
+
+def test_fused_int32_beyond_f32_range():
+    # every sample -8-8i over 140,000 samples: Re = 17,920,000 > 2^24
+    T, F, N = 140000, 1, 64
+    out = correlate(np.zeros((T, F, N), np.uint8))
+    assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
+
+
+def test_fused_host_buffers_and_many_channels():
+    # 300 channels over the 76 clusters: several channels per cluster
+    rng = np.random.default_rng(6)
+    T, F, N = 640, 300, 256
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    assert np.array_equal(correlate(blk), want)
+    assert np.array_equal(correlate(blk, host=True), want)
