@@ -61,6 +61,18 @@ namespace {
 
 int64_t acc_bytes(const xeng_s *h) { return (int64_t)h->F * n_baselines(h->N) * 8; }
 
+// The decode buffer, allocated on first use.  Synchronizes the device then.
+cudaError_t ensure_planes(xeng_s *h)
+{
+    if (h->planes) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&h->planes, (size_t)h->planes_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->planes = nullptr;
+    }
+    return e;
+}
+
 void free_shift(xeng_s *h)
 {
     cudaFree(h->d_delay);
@@ -249,7 +261,8 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
     h->num_sms = prop.multiProcessorCount;
 
     // Decode buffer: rounds of (group_f channels x chunk_t samples); the
-    // budget bounds it at 16 GiB or a quarter of the free memory.
+    // budget bounds it at 16 GiB or a quarter of the free memory.  Allocated on
+    // first use: handles with up to 256 inputs correlate without it.
     const int64_t n_pad = planes_rows(n_inputs);
     h->chunk_t = round_up(t_integ < kMaxChunkSamples ? t_integ : kMaxChunkSamples, kTile);
     size_t free_b = 0, total_b = 0;
@@ -265,7 +278,6 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
     h->planes_bytes = g * per_ch;
 
     cudaError_t e = cudaMalloc(&h->acc, (size_t)acc_bytes(h));
-    if (e == cudaSuccess) e = cudaMalloc(&h->planes, (size_t)h->planes_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, sizeof(int));
@@ -438,6 +450,7 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
         }
         return e;
     }
+    e = ensure_planes(h);
     for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
         const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
         const int64_t t_pad = round_up(nt, kTile);
@@ -575,6 +588,8 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
             }
             continue;
         }
+        e = ensure_planes(h);
+        if (e != cudaSuccess) break;
         e = timed_launch(h, 0, s, [&] {
             return launch_decode(blk, n, bf, (int32_t)N, bf0, nf, h->planes, t_pad, n_pad, s);
         });
@@ -710,6 +725,8 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
         if (e != cudaSuccess) return (h->sticky = cuda_status(e));
         h->gidx_cap = (int64_t)idx.size();
     }
+    e = ensure_planes(h);
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
     e = cudaMemcpyAsync(h->gidx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // idx is pageable and goes out of scope
     if (e == cudaSuccess && counts) e = cudaMemsetAsync(counts, 0, (size_t)(n_gates * F * N * 4), s);
