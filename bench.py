@@ -212,7 +212,7 @@ def run_batched(args, rank, world, local_rank):
     if args.batch_max_chunks > 0:  # a fixed plan (profiling runs), no tuning
         rc, opts, tuned_ms = 2, xe.xeng._opts(args.batch_max_chunks, args.batch_policy, True), None
     else:
-        rc, opts, tuned_ms = xe.xeng_batch_autotune(jobs, cache, reps=2)
+        rc, opts, tuned_ms = xe.xeng_batch_autotune(jobs, cache, reps=3)
     tune_s = time.perf_counter() - t0
     if rc < 0:
         raise RuntimeError("autotune failed: %s" % xe.xeng_strerror(rc))

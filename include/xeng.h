@@ -309,7 +309,8 @@ XENG_API void xeng_batch_destroy(xeng_batch_t b);
 /*
  * xeng_batch_autotune -- pick xeng_batch_opts_t for these jobs by timing every
  *   (max_chunks_per_item in {16, 32, 64, 128, 256, 512}) x (policy) candidate
- *   for `reps` runs each (overwriting the jobs' outputs).  With a cache_path,
+ *   for `reps` runs each, in two passes (forward, then reverse order; each
+ *   candidate keeps its better time), overwriting the jobs' outputs.  With a cache_path,
  *   a text file of "signature max_chunks policy ms" lines keyed by the jobs'
  *   (N, F, T) list and the SM count is read first (hit: returns 1 without
  *   timing) and the winner appended after tuning (returns 0).  *best_ms (may
