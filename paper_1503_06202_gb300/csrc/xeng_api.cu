@@ -546,6 +546,39 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
     int64_t pf = (F + groups - 1) / groups;  // channels per group
     if (pf > h->group_f) pf = h->group_f;
     if (pf < 1) pf = 1;
+    if (host_in && pf >= F && n >= 2 * kTile) {
+        // One channel group (short rows per sample): pipeline over time
+        // instead.  Time chunks of the block are contiguous, so each is one flat
+        // copy; their correlations add into the int32 triangle (exact in any
+        // order), and the download follows the last chunk.
+        const int64_t tc = round_up((n + 7) / 8, kTile);
+        int st = ensure_pipeline(h, tc * F * N);
+        if (st != XENG_OK) return st;
+        cudaError_t e = cudaEventRecord(h->ev_start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->h2d, h->ev_start, 0);
+        int k = 0;
+        for (int64_t t0 = 0; t0 < n && e == cudaSuccess; t0 += tc, ++k) {
+            const int64_t nt = (n - t0) < tc ? (n - t0) : tc;
+            const int buf = k & 1;
+            if (k >= 2) e = cudaStreamWaitEvent(h->h2d, h->ev_cmp[buf], 0);  // staging reused
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->pstage[buf], src + t0 * F * N, (size_t)(nt * F * N), cudaMemcpyHostToDevice,
+                                    h->h2d);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[buf], h->h2d);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_in[buf], 0);
+            if (e == cudaSuccess) e = integrate(h, h->pstage[buf], nt, target, fresh && k == 0, s);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
+        }
+        if (e == cudaSuccess && host_out) {
+            e = cudaEventRecord(h->ev_fin, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h, h->ev_fin, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(host_out, target, (size_t)(F * nb2 * 4), cudaMemcpyDeviceToHost, h->d2h);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_fin, h->d2h);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_fin, 0);
+        }
+        return cuda_status(e);
+    }
     int st = ensure_pipeline(h, host_in ? pf * n * N : 0);
     if (st != XENG_OK) return st;
     cudaError_t e = cudaEventRecord(h->ev_start, s);
