@@ -205,7 +205,10 @@ XENG_API int xeng_set_engine(xeng_t h, int32_t engine);
  *     planes [nf][2][n_pad][t_pad]   (plane 0 = real parts, 1 = imaginary)
  *   with n_pad = N rounded up to 128 and t_pad = n_samples rounded up to 128;
  *   padding is written as code 0x00 (+0.0).  planes is device memory of
- *   nf * 2 * n_pad * t_pad bytes.  Asynchronous on `stream`.
+ *   nf * 2 * n_pad * t_pad bytes.  Where N is a multiple of 16 and block is
+ *   16-byte aligned the stage runs as the engine's TMA pipeline and the call
+ *   synchronizes `stream`, returning XENG_ERR_TIMEOUT if the pipeline stalled
+ *   (bounded waits, 2 s); otherwise it is asynchronous on `stream`.
  */
 XENG_API int xeng_decode(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t n_inputs,
                          int32_t f0, int32_t nf, uint8_t *planes, void *stream);

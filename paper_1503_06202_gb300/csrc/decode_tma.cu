@@ -1,0 +1,299 @@
+// decode_tma.cu -- the decode stage (paper Sec. II-A: nibble = value + 8,
+// high nibble real, low nibble imaginary) as a persistent TMA pipeline: the
+// same planes as decode_kernel ([nf][2][n_pad][t_pad] E4M3 codes, K-major,
+// +0.0 outside the block), for blocks whose rows TMA can address (N a multiple
+// of 16, block 16-byte aligned).
+//
+// Per CTA (one per SM), tiles of 128 samples x 128 inputs of one channel in
+// order input block fastest, then channel, then sample block:
+//   warp 0        TMA loads of raw tiles into a ring of slots (no per-thread
+//                 address arithmetic)
+//   warps 1..16   converters, in independent groups that take alternate tiles:
+//                 transpose + decode into the group's two plane tiles in
+//                 shared memory (128-byte swizzle), conflict-free mapping: a
+//                 unit is 4 inputs x 8 samples; (virtual) warp w, lane q takes
+//                 inputs 4q .. 4q + 3, sample block b = (w + q) mod 8 and half
+//                 h = ((q >> 3) & 1) ^ (w >> 3) -- raw reads hit 32 banks,
+//                 8-byte plane writes 16 slots per half-warp
+//   one thread    of each group TMA-stores its plane tiles and recycles the
+//                 raw slot; a plane buffer is rewritten only after its store
+//                 has finished reading shared memory
+#include "nibble.cuh"
+#include "tc_ptx.cuh"
+#include "xeng_internal.h"
+
+namespace xeng {
+namespace {
+
+constexpr int kDTConvWarps = 16;
+constexpr int kDTConvThreads = 32 * kDTConvWarps;
+constexpr int kDTThreads = 32 + kDTConvThreads;
+constexpr int kDTRaw = 128 * 128;
+constexpr int kDTPlane = 128 * 128;
+// Pipeline shape, measured on GB300 (full-CHIME decode, 16 GiB in, 32 GiB out):
+// one converter group of 16 warps spends its time in the per-tile chain (wait,
+// convert, fence, store issue) and reaches 4.2 TB/s whatever the ring depth;
+// two groups of 8 warps, each with one plane buffer, and an 8-slot raw ring
+// reach 5.5-5.8 TB/s (4 groups: 5.2; two groups with two plane buffers and a
+// shallower ring: 5.1-5.4; two CTAs per SM of one group: 4.9).
+constexpr int kDTSlots = 8;
+constexpr int kDTGroups = 2;
+constexpr int kDTPlaneBufs = 1;
+
+// shared memory: a ring of raw tiles, then kP plane-tile pairs per converter group, then the barriers
+constexpr size_t dt_smem(int stages, int groups, int pbufs)
+{
+    return 1024 + (size_t)stages * kDTRaw + (size_t)groups * pbufs * 2 * kDTPlane + 2 * stages * 8 + 16;
+}
+
+struct DecTmaArgs {
+    int64_t T;             // samples to decode (t0 .. t0 + T - 1 of the map's block)
+    int32_t n_ib, n_tb;    // input blocks, sample blocks per channel
+    int64_t n_tiles;
+    int32_t N, nf, n_pad;
+    int32_t f0;            // first channel of the map's block
+    int64_t t0;            // first sample of the map's block
+    int *err;
+};
+
+// Tile order: input block fastest, then channel, then sample block, so the
+// CTAs working at the same time read neighbouring bytes of the same sample rows.
+__device__ __forceinline__ void tile_coords(const DecTmaArgs &a, int64_t tile, int &ib, int &fl, int &tb)
+{
+    ib = (int)(tile % a.n_ib);
+    fl = (int)((tile / a.n_ib) % a.nf);
+    tb = (int)(tile / ((int64_t)a.n_ib * a.nf));
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(map), "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+template <int kStages, int kGroups, int kP>
+__global__ void __launch_bounds__(kDTThreads, 1)
+decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ CUtensorMap plane_map,
+                  const DecTmaArgs a)
+{
+    // Each raw slot must belong to one group (kStages a multiple of kGroups):
+    // a group waits on a slot's "full" barrier by phase parity, which is only
+    // unambiguous if the slot's previous tile was the same group's (then it is
+    // consumed, so its load is complete).  A slot shared by groups could still
+    // be in an earlier tile's phase of the same parity as awaited.
+    static_assert(kDTConvWarps % kGroups == 0 && kStages % kGroups == 0, "groups of whole warps, owning whole slots");
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t *sgen = smem_raw + (sbase - raw);
+    const uint32_t pbase = sbase + kStages * kDTRaw;                 // plane buffers
+    const uint32_t bars = pbase + kGroups * kP * 2 * kDTPlane;
+    auto rawf = [&](int s) { return bars + 8u * s; };               // raw tile landed
+    auto rawe = [&](int s) { return bars + 8u * (kStages + s); };  // raw tile converted
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *err = a.err;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(rawf(s), 1);
+            mbar_init(rawe(s), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&plane_map) : "memory");
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0, issued = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+                int ib, fl, tb;
+                tile_coords(a, tile, ib, fl, tb);
+                if (!mbar_wait(rawe(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(rawf(stage), kDTRaw);
+                tma_load_3d(sbase + stage * kDTRaw, &raw_map, ib * 128, a.f0 + fl, (int)(a.t0 + tb * 128),
+                            rawf(stage));
+                ++issued;
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            // whether or not the converters consumed them (they stop early on an
+            // error), the last loads must land before the CTA exits: wait for
+            // each, bounded in time but not cut short by the error word
+            (void)ok;
+            for (int k = 1; k <= kStages && k <= issued; k++) {
+                int s = stage - k, p = (int)phase;
+                if (s < 0) {
+                    s += kStages;
+                    p ^= 1;
+                }
+                const uint64_t t_start = globaltimer();
+                while (!mbar_try_wait(rawf(s), (uint32_t)p) && globaltimer() - t_start < kWaitLimitNs) {
+                }
+            }
+        }
+    } else {
+        // ---------------- converters ----------------
+        // kGroups independent groups of kGW warps; group g converts the CTA's
+        // tiles n = g, g + kGroups, ... (raw slot n mod kStages) into its own
+        // kP plane buffers in turn, so several tiles are in conversion at once.
+        // Each thread covers the units of kGroups "virtual warps" of the
+        // 16-warp mapping.
+        constexpr int kGW = kDTConvWarps / kGroups;
+        constexpr int kGThreads = 32 * kGW;
+        const int cw = warp - 1;
+        const int grp = cw / kGW, wl = cw % kGW;
+        const int q = lane;  // inputs 4q .. 4q + 3
+        const bool storer = wl == 0 && lane == 0;
+        const uint32_t bar_a = 1 + 2 * grp, bar_b = 2 + 2 * grp;
+        for (int64_t n = grp;; n += kGroups) {
+            const int64_t tile = blockIdx.x + n * gridDim.x;
+            if (tile >= a.n_tiles) break;
+            int ib, fl, tb;
+            tile_coords(a, tile, ib, fl, tb);
+            const int stage = (int)(n % kStages);
+            const uint32_t phase = (uint32_t)((n / kStages) & 1);
+            const bool ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, 0);
+            const int pslot = (int)((n / kGroups) % kP);
+            const uint32_t pre_s = pbase + (uint32_t)((grp * kP + pslot) * 2 * kDTPlane);
+            // the store that last read this plane buffer (the group's kP-th last) is done reading
+            if (storer) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kP - 1) : "memory");
+            // every thread of the group has its raw tile, and the plane buffer is free
+            asm volatile("bar.sync %0, %1;" ::"r"(bar_a), "n"(kGThreads) : "memory");
+            const uint32_t *rt = reinterpret_cast<const uint32_t *>(sgen + stage * kDTRaw);
+            uint8_t *pre = sgen + (pre_s - sbase);
+            uint8_t *pim = pre + kDTPlane;
+            const int ibase = ib * 128;
+            if (ok) {
+                #pragma unroll
+                for (int k = 0; k < kGroups; k++) {
+                    const int vw = wl + kGW * k;                  // virtual warp 0..15
+                    const int b = ((vw & 7) + lane) & 7;          // sample block of this lane
+                    const int h = ((lane >> 3) & 1) ^ (vw >> 3);  // which 8 samples of the block
+                    const int64_t tbase = (int64_t)tb * 128 + b * 16 + h * 8;  // first sample of the unit
+                    uint32_t re[4][2], im[4][2];  // [input m][word g] (samples 4g .. 4g + 3 of the half)
+                    #pragma unroll
+                    for (int g = 0; g < 2; g++) {
+                        uint32_t r[4];
+                        #pragma unroll
+                        for (int kk = 0; kk < 4; kk++) {
+                            const int t = b * 16 + h * 8 + g * 4 + kk;
+                            r[kk] = (tbase + g * 4 + kk < a.T) ? rt[t * 32 + q] : 0x88888888u;  // past the end: 0
+                        }
+                        const uint32_t lo01 = __byte_perm(r[0], r[1], 0x5140);
+                        const uint32_t hi01 = __byte_perm(r[0], r[1], 0x7362);
+                        const uint32_t lo23 = __byte_perm(r[2], r[3], 0x5140);
+                        const uint32_t hi23 = __byte_perm(r[2], r[3], 0x7362);
+                        decode_word(__byte_perm(lo01, lo23, 0x5410), re[0][g], im[0][g]);
+                        decode_word(__byte_perm(lo01, lo23, 0x7632), re[1][g], im[1][g]);
+                        decode_word(__byte_perm(hi01, hi23, 0x5410), re[2][g], im[2][g]);
+                        decode_word(__byte_perm(hi01, hi23, 0x7632), re[3][g], im[3][g]);
+                    }
+                    #pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int i = 4 * q + m;
+                        const int off = i * 128 + ((b ^ (i & 7)) << 4) + h * 8;  // row i, chunk b, half h
+                        const bool row_ok = ibase + i < a.N;                     // rows past N are +0.0
+                        *reinterpret_cast<uint2 *>(pre + off) =
+                            row_ok ? make_uint2(re[m][0], re[m][1]) : make_uint2(0u, 0u);
+                        *reinterpret_cast<uint2 *>(pim + off) =
+                            row_ok ? make_uint2(im[m][0], im[m][1]) : make_uint2(0u, 0u);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the TMA store
+            // the second barrier also ORs the group's failure flags, so that all
+            // of its threads leave the loop in the same iteration (a named
+            // barrier that some threads never reach would not return)
+            uint32_t any_fail;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                "bar.red.or.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(any_fail)
+                : "r"(ok ? 0u : 1u), "r"(bar_b), "n"(kGThreads)
+                : "memory");
+            if (storer) {
+                if (!any_fail) {
+                    const int y = (fl * 2) * a.n_pad + ib * 128;
+                    tma_store_2d(&plane_map, tb * 128, y, pre_s);
+                    tma_store_2d(&plane_map, tb * 128, y + a.n_pad, pre_s + kDTPlane);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+                mbar_arrive(rawe(stage));  // the raw slot may be refilled
+            }
+            if (any_fail) break;
+        }
+        // every store has finished writing before the CTA exits
+        if (storer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+}
+
+}  // namespace
+
+bool decode_tma_ok(const uint8_t *block, int32_t N)
+{
+    return N % 16 == 0 && (reinterpret_cast<uintptr_t>(block) & 15) == 0;
+}
+
+cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0, int32_t nf,
+                              uint8_t *planes, int64_t t_pad, int64_t n_pad, int *err, int num_sms, cudaStream_t s)
+{
+    if (nf <= 0 || t_pad <= 0) return cudaSuccess;
+    if (!decode_tma_ok(block, N) || T <= 0 || t_pad % 128 != 0 || n_pad % 128 != 0 || t_pad < T || n_pad < N ||
+        t_pad > 2147483647LL || (int64_t)nf * 2 * n_pad > 2147483647LL || num_sms <= 0)
+        return cudaErrorInvalidValue;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap rm, pm;
+    {
+        // raw block [T][F][N] bytes: box of 128 inputs x 1 channel x 128 samples; reads past N or T fill 0
+        const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T};
+        const cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};
+        const cuuint32_t box[3] = {128, 1, 128}, estr[3] = {1, 1, 1};
+        if (enc(&rm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        // planes [nf * 2 * n_pad][t_pad]: box of 128 samples x 128 rows, 128-byte swizzle (the
+        // layout the converters write in shared memory)
+        const cuuint64_t dims[2] = {(cuuint64_t)t_pad, (cuuint64_t)nf * 2 * n_pad};
+        const cuuint64_t strides[1] = {(cuuint64_t)t_pad};
+        const cuuint32_t box[2] = {128, 128}, estr[2] = {1, 1};
+        if (enc(&pm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)planes, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    auto kern = decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs>;
+    const size_t smem = dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    DecTmaArgs a;
+    a.T = T;
+    a.n_ib = (int32_t)(n_pad / 128);
+    a.n_tb = (int32_t)(t_pad / 128);
+    a.n_tiles = (int64_t)a.n_ib * nf * a.n_tb;
+    a.N = N;
+    a.nf = nf;
+    a.n_pad = (int32_t)n_pad;
+    a.f0 = f0;
+    a.t0 = 0;
+    a.err = err;
+    const int grid = (int)(a.n_tiles < num_sms ? a.n_tiles : num_sms);
+    kern<<<grid, kDTThreads, smem, s>>>(rm, pm, a);
+    return cudaGetLastError();
+}
+
+}  // namespace xeng

@@ -116,7 +116,10 @@ extern "C" int xeng_correlate_noalloc(const uint8_t *block, int64_t n_samples, i
     if (group > 65535) group = 65535;
     for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += group) {
         const int32_t nf = (int32_t)((F - f0) < group ? (F - f0) : group);
-        e = launch_decode(block, n_samples, (int32_t)F, (int32_t)N, (int32_t)f0, nf, planes, t_pad, n_pad, s);
+        e = decode_tma_ok(block, (int32_t)N)
+                ? launch_decode_tma(block, n_samples, (int32_t)F, (int32_t)N, (int32_t)f0, nf, planes, t_pad, n_pad,
+                                    status, sms, s)
+                : launch_decode(block, n_samples, (int32_t)F, (int32_t)N, (int32_t)f0, nf, planes, t_pad, n_pad, s);
         if (e != cudaSuccess) break;
         TcArgs a;
         a.planes = planes;

@@ -55,6 +55,7 @@ struct xeng_s {
     int hist_cur = 0;
     int64_t hist_H = 0;
     int32_t hist_S = 0;
+    bool decode_tma = false;       // decode through the TMA pipeline where the block allows it
 };
 
 namespace {
@@ -194,6 +195,22 @@ cudaError_t run_correlate(xeng_s *h, TcArgs a, cudaStream_t s)
     return launch_correlate_tc_pairs(a, h->num_sms, s);
 }
 
+// Decode launches of a handle: the persistent TMA pipeline where TMA can
+// address the block's rows (N a multiple of 16, 16-byte aligned), else the
+// thread-per-row kernel.  Both write the same planes.  The environment variable
+// XENG_DECODE_THREADS=1 (read at handle creation) keeps the thread kernel.
+#ifndef XENG_DECODE_TMA
+#define XENG_DECODE_TMA 1
+#endif
+
+cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int32_t N, int32_t f0, int32_t nf,
+                       int64_t t_pad, int64_t n_pad, cudaStream_t s)
+{
+    if (h->decode_tma && decode_tma_ok(src, N))
+        return launch_decode_tma(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, h->d_err, h->num_sms, s);
+    return launch_decode(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, s);
+}
+
 // Run one kernel launch, bracketed by events when profiling.
 template <class F>
 cudaError_t timed_launch(xeng_s *h, int kind, cudaStream_t s, F &&fn)
@@ -259,6 +276,10 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
     h->t_integ = t_integ;
     h->device = dev;
     h->num_sms = prop.multiProcessorCount;
+    {
+        const char *env = getenv("XENG_DECODE_THREADS");
+        h->decode_tma = XENG_DECODE_TMA && !(env && env[0] == '1');
+    }
 
     // Decode buffer: rounds of (group_f channels x chunk_t samples); the
     // budget bounds it at 16 GiB or a quarter of the free memory.  Allocated on
@@ -472,7 +493,7 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
                 });
             } else {
                 e = timed_launch(h, 0, s, [&] {
-                    return launch_decode(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes, t_pad, n_pad, s);
+                    return run_decode(h, src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, t_pad, n_pad, s);
                 });
             }
             if (e != cudaSuccess) break;
@@ -624,7 +645,7 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
         e = ensure_planes(h);
         if (e != cudaSuccess) break;
         e = timed_launch(h, 0, s, [&] {
-            return launch_decode(blk, n, bf, (int32_t)N, bf0, nf, h->planes, t_pad, n_pad, s);
+            return run_decode(h, blk, n, bf, (int32_t)N, bf0, nf, t_pad, n_pad, s);
         });
         if (e != cudaSuccess) break;
         TcArgs a;
@@ -838,9 +859,26 @@ int xeng_decode(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t
     const int64_t t_pad = round_up(n_samples, kTile);
     const int64_t n_pad = round_up(n_inputs, kTile);
     if (t_pad / kTile > 2147483647LL) return XENG_ERR_RANGE;
-    cudaError_t e = launch_decode(block, n_samples, n_freq, n_inputs, f0, nf, planes, t_pad, n_pad,
-                                  (cudaStream_t)stream);
-    return cuda_status(e);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!decode_tma_ok(block, n_inputs)) return cuda_status(launch_decode(block, n_samples, n_freq, n_inputs, f0, nf,
+                                                                          planes, t_pad, n_pad, s));
+    // the TMA pipeline: its status word lives on the stream for this call only
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int *d_status = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_status), sizeof(int), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h_status = 0;
+    e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = launch_decode_tma(block, n_samples, n_freq, n_inputs, f0, nf, planes, t_pad, n_pad, d_status, sms, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t ef = cudaFreeAsync(d_status, s);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return h_status != 0 ? XENG_ERR_TIMEOUT : XENG_OK;
 }
 
 int xeng_selftest_wait_timeout(int64_t limit_ns, int32_t *status, int32_t *threads_left)

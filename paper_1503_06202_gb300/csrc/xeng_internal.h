@@ -26,6 +26,13 @@ cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N,
                           int32_t f0, int32_t nf, uint8_t *planes, int64_t t_pad,
                           int64_t n_pad, cudaStream_t s);
 
+// The same decode as a persistent TMA pipeline (one CTA per SM): needs N a
+// multiple of 16 and a 16-byte aligned block (decode_tma_ok), t_pad and n_pad
+// multiples of 128.  A stalled pipeline sets *err and returns.
+bool decode_tma_ok(const uint8_t *block, int32_t N);
+cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0, int32_t nf,
+                              uint8_t *planes, int64_t t_pad, int64_t n_pad, int *err, int num_sms, cudaStream_t s);
+
 // Gated / flagged decode of channels [f0, f0 + nf): tile rows are block rows
 // idx[0 .. Tg) (one gate's samples); samples whose valid byte is 0 decode to
 // zero; usable samples per (channel, input) are added to counts[fl][N] (may be null).

@@ -47,11 +47,14 @@ def assert_same(got, want, what=""):
 
 # --------------------------------------------------------------- decode ----
 
-def test_decode_stage_codes():
-    rng = np.random.default_rng(20)
-    T, F, N, f0, nf = 300, 3, 200, 1, 2
+# N = 200 takes the thread-per-row decode; N a multiple of 16 the TMA pipeline
+# (ragged sample and input blocks, a block shorter than one sample tile)
+@pytest.mark.parametrize("T,F,N,f0,nf", [(300, 3, 200, 1, 2), (300, 3, 272, 1, 2), (5, 2, 16, 0, 2),
+                                         (1000, 4, 400, 1, 3)])
+def test_decode_stage_codes(T, F, N, f0, nf):
+    rng = np.random.default_rng(20 + N)
     blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
-    t_pad, n_pad = 384, 256
+    t_pad, n_pad = -(-T // 128) * 128, -(-N // 128) * 128
     planes = torch.full((nf, 2, n_pad, t_pad), 0x55, dtype=torch.uint8, device="cuda")
     assert xe.xeng_decode(to_dev(blk), T, F, N, f0, nf, planes) == xe.XENG_OK
     torch.cuda.synchronize()
@@ -70,7 +73,9 @@ def test_decode_stage_codes():
 # ------------------------------------------------------------ small/ragged --
 
 SHAPES = [(1, 1, 1), (5, 3, 2), (129, 2, 7), (300, 2, 127), (128, 1, 128), (257, 2, 129), (1000, 3, 200),
-          (700, 2, 300), (1024, 1, 513), (64, 2, 1024)]
+          (700, 2, 300), (1024, 1, 513), (64, 2, 1024),
+          # N > 256 and a multiple of 16: the TMA decode pipeline, ragged tiles
+          (1000, 3, 272), (129, 2, 400), (5, 2, 288)]
 
 
 @pytest.mark.parametrize("engine", sorted(ENGINES))
