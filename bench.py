@@ -613,6 +613,15 @@ def main():
                 "traffic": None, "frac": None}
     roof["avg_launch_ms"] = corr_ms
     roof["decode_ms_per_step"] = st["decode_ms"] / args.steps
+    # the decode stage (HBM-bound): 1 byte read + 2 plane bytes written per (input, sample, channel)
+    decode_roof = None
+    if args.engine == "tensor" and st["decode_ms"] > 0:
+        dec_ms = st["decode_ms"] / args.steps
+        dec_bytes = 3 * T * F * N
+        decode_roof = {"kernel": "decode_tma_kernel" if N % 16 == 0 else "decode_kernel", "bound": "hbm",
+                       "ms_per_step": dec_ms, "algorithmic_bytes": dec_bytes,
+                       "achieved": dec_bytes / (dec_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": dec_bytes / (dec_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src}
 
     # end to end through the ABI with host buffers: H2D of the block, D2H of the triangle
     e2e = None
@@ -649,7 +658,8 @@ def main():
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
                 "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "beamform": beam,
                 "pathfinder_rate": secondary,
-                "gpu_launches": int(st["launches"]), "roofline": roof, "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": int(st["launches"]), "roofline": roof, "decode_roofline": decode_roof,
+                "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}
         print(json.dumps(line), flush=True)
     eng.close()
