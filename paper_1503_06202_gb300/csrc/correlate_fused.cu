@@ -217,15 +217,11 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
                         const int t = b * 16 + h * 8 + g * 4 + k;
                         r[k] = (tb + g * 4 + k < a.nt) ? rt[t * 32 + q] : 0x88888888u;  // past the end: value 0
                     }
-                    // 4x4 byte transpose: r[k] byte m = (sample k, input m) -> c[m] byte k
-                    const uint32_t lo01 = __byte_perm(r[0], r[1], 0x5140);
-                    const uint32_t hi01 = __byte_perm(r[0], r[1], 0x7362);
-                    const uint32_t lo23 = __byte_perm(r[2], r[3], 0x5140);
-                    const uint32_t hi23 = __byte_perm(r[2], r[3], 0x7362);
-                    decode_word(__byte_perm(lo01, lo23, 0x5410), re[0][g], im[0][g]);
-                    decode_word(__byte_perm(lo01, lo23, 0x7632), re[1][g], im[1][g]);
-                    decode_word(__byte_perm(hi01, hi23, 0x5410), re[2][g], im[2][g]);
-                    decode_word(__byte_perm(hi01, hi23, 0x7632), re[3][g], im[3][g]);
+                    // transpose + decode: r[k] byte m = (sample k, input m) -> input m's codes of samples 0..3
+                    decode_input4(r, 0, re[0][g], im[0][g]);
+                    decode_input4(r, 1, re[1][g], im[1][g]);
+                    decode_input4(r, 2, re[2][g], im[2][g]);
+                    decode_input4(r, 3, re[3][g], im[3][g]);
                 }
                 #pragma unroll
                 for (int m = 0; m < 4; m++) {

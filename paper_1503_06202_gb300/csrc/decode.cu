@@ -44,19 +44,11 @@ __device__ __forceinline__ void decode_tile_store(const uint32_t *tile, uint8_t 
         uint32_t r[4];
         #pragma unroll
         for (int k = 0; k < 4; k++) r[k] = tile[row_word(b * 16 + g * 4 + k) + q];
-        // 4x4 byte transpose: r[k] byte m = (time k, input m) -> c[m] byte k
-        const uint32_t lo01 = __byte_perm(r[0], r[1], 0x5140);
-        const uint32_t hi01 = __byte_perm(r[0], r[1], 0x7362);
-        const uint32_t lo23 = __byte_perm(r[2], r[3], 0x5140);
-        const uint32_t hi23 = __byte_perm(r[2], r[3], 0x7362);
-        const uint32_t c0 = __byte_perm(lo01, lo23, 0x5410);
-        const uint32_t c1 = __byte_perm(lo01, lo23, 0x7632);
-        const uint32_t c2 = __byte_perm(hi01, hi23, 0x5410);
-        const uint32_t c3 = __byte_perm(hi01, hi23, 0x7632);
-        decode_word(c0, re[0][g], im[0][g]);
-        decode_word(c1, re[1][g], im[1][g]);
-        decode_word(c2, re[2][g], im[2][g]);
-        decode_word(c3, re[3][g], im[3][g]);
+        // transpose + decode: r[k] byte m = (sample k, input m) -> input m's codes of samples 0..3
+        decode_input4(r, 0, re[0][g], im[0][g]);
+        decode_input4(r, 1, re[1][g], im[1][g]);
+        decode_input4(r, 2, re[2][g], im[2][g]);
+        decode_input4(r, 3, re[3][g], im[3][g]);
     }
     const int64_t tcol = t0 + b * 16;
     #pragma unroll
