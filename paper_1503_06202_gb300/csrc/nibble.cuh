@@ -12,31 +12,38 @@
 namespace xeng {
 namespace {
 
-// Two offset nibbles (in bits 0-3 and 16-19 of x) to two E4M3 codes (bits
-// 0-7 and 8-15 of the result).
-__device__ __forceinline__ uint32_t nib2_to_e4m3(uint32_t x)
+// Two offset nibbles (in bits 0-3 and 16-19 of x) to the half2 of their
+// values u - 8.
+__device__ __forceinline__ uint32_t nib2_lo_half2(uint32_t x)
 {
-    __half2_raw h;
     uint32_t v = (x & 0x000F000Fu) | 0x64006400u;  // half2(1024 + u_lo, 1024 + u_hi)
     __half2 hv = *reinterpret_cast<__half2 *>(&v);
     hv = __hsub2(hv, __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408)));  // - 1032
-    h = *reinterpret_cast<__half2_raw *>(&hv);
-    return (uint32_t)__nv_cvt_halfraw2_to_fp8x2(h, __NV_SATFINITE, __NV_E4M3);
+    return *reinterpret_cast<uint32_t *>(&hv);
 }
 
 // The same for nibbles in bits 4-7 and 20-23, without shifting them down:
 // they land in mantissa bits 4-7 (1024 + 16 u), and (1024 + 16 u) / 16 - 72 =
 // u - 8, one exact half-precision FMA.
-__device__ __forceinline__ uint32_t nib2_hi_to_e4m3(uint32_t x)
+__device__ __forceinline__ uint32_t nib2_hi_half2(uint32_t x)
 {
-    __half2_raw h;
     uint32_t v = (x & 0x00F000F0u) | 0x64006400u;  // half2(1024 + 16 u_lo, 1024 + 16 u_hi)
     __half2 hv = *reinterpret_cast<__half2 *>(&v);
     hv = __hfma2(hv, __halves2half2(__ushort_as_half(0x2C00), __ushort_as_half(0x2C00)),   // x 1/16
                  __halves2half2(__ushort_as_half(0xD480), __ushort_as_half(0xD480)));  // - 72
-    h = *reinterpret_cast<__half2_raw *>(&hv);
+    return *reinterpret_cast<uint32_t *>(&hv);
+}
+
+__device__ __forceinline__ uint32_t half2_to_e4m3x2(uint32_t v)
+{
+    __half2_raw h = *reinterpret_cast<__half2_raw *>(&v);
     return (uint32_t)__nv_cvt_halfraw2_to_fp8x2(h, __NV_SATFINITE, __NV_E4M3);
 }
+
+// Two offset nibbles (bits 0-3 and 16-19, or 4-7 and 20-23) to two E4M3 codes
+// (bits 0-7 and 8-15 of the result).
+__device__ __forceinline__ uint32_t nib2_to_e4m3(uint32_t x) { return half2_to_e4m3x2(nib2_lo_half2(x)); }
+__device__ __forceinline__ uint32_t nib2_hi_to_e4m3(uint32_t x) { return half2_to_e4m3x2(nib2_hi_half2(x)); }
 
 // Word of 4 samples (bytes = times t..t+3 of one input) -> (real codes, imag codes).
 __device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &im)
