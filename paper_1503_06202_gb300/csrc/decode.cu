@@ -215,6 +215,31 @@ decode_shifted_kernel(const uint8_t *__restrict__ block, int64_t t0, int64_t nt,
     decode_tile_store(tile, planes, t_pad, n_pad, tr0, i0, fl);
 }
 
+// Shift fix-up after a plain decode of samples t0 .. t0 + nt - 1: the plane
+// rows of the S delayed inputs (inputs[s], delay d) are rewritten with the
+// codes of x_i(t - d) -- from the block when t - d >= 0, else from the
+// history -- leaving every other row (and the padding past nt) as decoded.
+// One thread per (channel, delayed input, sample): writes are contiguous
+// along the sample, and the gathers run with the whole GPU's parallelism.
+__global__ void shift_fixup_kernel(const uint8_t *__restrict__ block, int64_t t0, int64_t nt, int32_t F, int32_t N,
+                                   int32_t f0, int32_t nf, const ShiftArgs sa, const int32_t *__restrict__ inputs,
+                                   uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad)
+{
+    const int64_t total = (int64_t)nf * sa.S * nt;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = k % nt;
+        const int32_t sl = (int32_t)((k / nt) % sa.S);
+        const int64_t fl = k / (nt * sa.S);
+        const int64_t f = f0 + fl;
+        const int32_t i = inputs[sl];
+        const int64_t src = t0 + t - sa.delay[i];
+        const uint32_t byte = src >= 0 ? block[(src * F + f) * N + i] : sa.hist[((sa.H + src) * F + f) * sa.S + sl];
+        const uint32_t codes = nib2_to_e4m3(byte | (byte << 12));  // low nibble -> byte 0, high nibble -> byte 1
+        planes[((fl * 2 + 0) * n_pad + i) * t_pad + t] = (uint8_t)(codes >> 8);  // real part: high nibble
+        planes[((fl * 2 + 1) * n_pad + i) * t_pad + t] = (uint8_t)(codes & 0xFFu);
+    }
+}
+
 // History after a block of n samples, [H][F][S]: entry (h, f, s) is sample
 // n - H + h of input inputs[s] -- from the block when that index is >= 0,
 // else entry n + h of the old history.
@@ -242,6 +267,18 @@ cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, 
     const int vec_ok = decode_vec_ok(block, N);
     dim3 grid((unsigned)(t_pad / 128), (unsigned)(n_pad / 128), (unsigned)nf);
     decode_shifted_kernel<<<grid, kDecThreads, 0, s>>>(block, t0, nt, F, N, f0, sa, planes, t_pad, n_pad, vec_ok);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_fixup(const uint8_t *block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
+                               int32_t nf, const ShiftArgs &sa, const int32_t *inputs, uint8_t *planes, int64_t t_pad,
+                               int64_t n_pad, cudaStream_t s)
+{
+    const int64_t total = (int64_t)nf * sa.S * nt;
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    shift_fixup_kernel<<<(unsigned)blocks, 256, 0, s>>>(block, t0, nt, F, N, f0, nf, sa, inputs, planes, t_pad, n_pad);
     return cudaGetLastError();
 }
 

@@ -488,6 +488,14 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
                 sa.H = h->hist_H;
                 sa.S = h->hist_S;
                 e = timed_launch(h, 0, s, [&] {
+                    if (h->decode_tma && decode_tma_ok(src, (int32_t)N)) {
+                        // plain TMA decode, then the delayed inputs' rows rewritten
+                        cudaError_t e2 = launch_decode_tma(src, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->planes,
+                                                           t_pad, n_pad, h->d_err, h->num_sms, s);
+                        if (e2 != cudaSuccess) return e2;
+                        return launch_shift_fixup(dblock, t0, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, sa,
+                                                  h->d_shift_inputs, h->planes, t_pad, n_pad, s);
+                    }
                     return launch_decode_shifted(dblock, t0, nt, (int32_t)F, (int32_t)N, (int32_t)f0, nf, sa, h->planes,
                                                  t_pad, n_pad, s);
                 });

@@ -69,6 +69,12 @@ struct ShiftArgs {
 cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
                                   int32_t nf, const ShiftArgs &sa, uint8_t *planes, int64_t t_pad, int64_t n_pad,
                                   cudaStream_t s);
+// After a plain decode of samples t0 .. t0 + nt - 1 into planes: rewrite the
+// rows of the S delayed inputs (inputs[s] has history column s) with their
+// shifted samples, as launch_decode_shifted computes them.
+cudaError_t launch_shift_fixup(const uint8_t *block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
+                               int32_t nf, const ShiftArgs &sa, const int32_t *inputs, uint8_t *planes, int64_t t_pad,
+                               int64_t n_pad, cudaStream_t s);
 // New history after a block of n samples: the last H samples of (old history,
 // block) for the S delayed inputs listed in `inputs`.
 cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, int64_t n, int32_t F, int32_t N,

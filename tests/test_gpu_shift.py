@@ -68,6 +68,21 @@ def test_shift_uniform_and_mixed_chunks_host_blocks():
     check(stream, delays, got)
 
 
+def test_shift_tma_decode_ragged_blocks():
+    # N = 272 (a multiple of 16: the TMA decode, with a last block of 16
+    # inputs): delayed inputs in a mixed chunk, in the last block, and one
+    # delayed longer than the pushes; pushes with ragged sample tiles
+    N, F = 272, 2
+    delays = np.zeros(N, np.int32)
+    delays[0] = 2000
+    delays[140:144] = 9
+    delays[260] = 50
+    delays[271] = 1
+    pushes = [300, 129, 1000, 64]
+    stream, got = run_stream(N, F, 4096, delays, pushes, {1, 3}, seed=6)
+    check(stream, delays, got)
+
+
 def test_shift_multi_chunk_push_and_max_delay():
     # a push longer than one 65,536-sample round, and the largest delay
     N, F = 32, 1
