@@ -405,6 +405,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the dense-throughput probes")
     ap.add_argument("--no-shift", action="store_true", help="skip the time-shift measurement")
+    ap.add_argument("--no-gate", action="store_true", help="skip the gating + flags measurement")
     ap.add_argument("--no-beam", action="store_true", help="skip the beamforming measurement")
     ap.add_argument("--no-secondary", action="store_true", help="skip the Pathfinder-rate measurement")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
@@ -522,6 +523,45 @@ def main():
                  "unshifted_decode_ms_per_step": push_dump_decode_ms,
                  "value": whole_job_rate(useful_ops(T, F, N), max_over_ranks(sh_ms, dist) * 1e-3, world) / 1e12,
                  "unit": "TOPS"}
+    # gating and flags (Sec. IV-C-4, Sec. IV-A): the samples split into two phase
+    # gates (on / off, alternating every 64 samples) and 1% of the (sample,
+    # channel, input) bytes flagged; the counts of usable samples come back too
+    gating = None
+    if args.engine == "tensor" and not args.no_gate:
+        import numpy as np
+        G = 2
+        gate = ((np.arange(T) // 64) % G).astype(np.int32)
+        valid = torch.randint(0, 100, (T, F, N), dtype=torch.uint8, device="cuda")
+        valid.clamp_(max=1)  # 0 (1 in 100: flagged) or 1
+        gout = torch.empty((G, F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+        gcounts = torch.empty((G, F, N), dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+
+        def gated():
+            rc = xe.xeng_correlate_gated(eng.h, block, T, gate, G, valid, gout, gcounts, stream)
+            if rc != xe.XENG_OK:
+                raise xe.XengError(rc, "xeng_correlate_gated")
+
+        gated()
+        eng.set_profiling(True)
+        eng.stats(reset=True)
+        greps = 2
+        ev0.record(stream)
+        for _ in range(greps):
+            gated()
+        ev1.record(stream)
+        ev1.synchronize()
+        gst = eng.stats(reset=True)
+        eng.set_profiling(False)
+        g_ms = ev0.elapsed_time(ev1) / greps
+        gating = {"gates": G, "gate_period_samples": 128, "flagged_fraction": 0.01, "ms_per_step": g_ms,
+                  "decode_ms_per_step": gst["decode_ms"] / greps,
+                  "correlate_ms_per_step": gst["correlate_ms"] / greps,
+                  "value": whole_job_rate(useful_ops(T, F, N), max_over_ranks(g_ms, dist) * 1e-3, world) / 1e12,
+                  "unit": "TOPS", "ungated_ms_per_step": ms,
+                  "kernels": "decode_gather_kernel (gate rows, flags, counts) + correlate_tc_kernel per gate"}
+        del valid, gout, gcounts
+        torch.cuda.synchronize()
     # beamforming (Sec. IV-C-3): 16 beams over the same block, int8 weights;
     # HBM-bound: reads the block once, writes T x F x 16 complex int32
     beam = None
@@ -656,7 +696,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
-                "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "beamform": beam,
+                "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "gating": gating, "beamform": beam,
                 "pathfinder_rate": secondary,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "decode_roofline": decode_roof,
                 "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,

@@ -139,7 +139,8 @@ decode_batch_kernel(const DecodeJob *__restrict__ jobs, int n_jobs)
 __global__ void __launch_bounds__(kDecThreads)
 decode_gather_kernel(const uint8_t *__restrict__ block, int32_t F, int32_t N, int32_t f0,
                      const int32_t *__restrict__ idx, int64_t Tg, const uint8_t *__restrict__ valid,
-                     uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int32_t *__restrict__ counts)
+                     uint8_t *__restrict__ planes, int64_t t_pad, int64_t n_pad, int32_t *__restrict__ counts,
+                     int vec_ok)
 {
     __shared__ uint32_t tile[kTileWords];
     __shared__ int cnt[128];
@@ -150,6 +151,9 @@ decode_gather_kernel(const uint8_t *__restrict__ block, int32_t F, int32_t N, in
     const int tid = threadIdx.x;
     if (tid < 128) cnt[tid] = 0;
     __syncthreads();
+    // usable-sample counters of this thread's 16 inputs (its chunk c = tid & 7
+    // is the same for all its rows), one byte each, four to a word
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
     for (int ch = tid; ch < 128 * 8; ch += kDecThreads) {
         const int t = ch >> 3, c = ch & 7;
         const int64_t k = t0 + t;
@@ -157,17 +161,54 @@ decode_gather_kernel(const uint8_t *__restrict__ block, int32_t F, int32_t N, in
         uint32_t w[4] = {0x88888888u, 0x88888888u, 0x88888888u, 0x88888888u};
         if (k < Tg) {
             const int64_t row = ((int64_t)idx[k] * F + f) * N;
-            for (int m = 0; m < 16; m++) {
-                const int i = ic + m;
-                if (i >= N) break;
-                uint32_t byte = block[row + i];
-                if (valid && !valid[row + i]) byte = 0x88;
-                else if (counts) atomicAdd(&cnt[c * 16 + m], 1);
-                w[m >> 2] = (w[m >> 2] & ~(0xFFu << (8 * (m & 3)))) | (byte << (8 * (m & 3)));
+            if (vec_ok && ic + 16 <= N) {
+                // 16 bytes of samples and 16 validity bytes at once; a flagged
+                // byte becomes 0x88 (value 0 + 0i)
+                const uint4 x = *reinterpret_cast<const uint4 *>(block + row + ic);
+                w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+                if (valid) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(valid + row + ic);
+                    const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+                    #pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const uint32_t z = __vcmpeq4(vw[j], 0u);  // 0xFF in each flagged byte
+                        w[j] = (w[j] & ~z) | (0x88888888u & z);
+                        acc[j] += ~z & 0x01010101u;
+                    }
+                } else {
+                    #pragma unroll
+                    for (int j = 0; j < 4; j++) acc[j] += 0x01010101u;
+                }
+            } else {
+                for (int m = 0; m < 16; m++) {
+                    const int i = ic + m;
+                    if (i >= N) break;
+                    uint32_t byte = block[row + i];
+                    if (valid && !valid[row + i]) byte = 0x88;
+                    else acc[m >> 2] += 1u << (8 * (m & 3));
+                    w[m >> 2] = (w[m >> 2] & ~(0xFFu << (8 * (m & 3)))) | (byte << (8 * (m & 3)));
+                }
             }
         }
         uint32_t *dst = tile + row_word(t) + c * 4;
         dst[0] = w[0]; dst[1] = w[1]; dst[2] = w[2]; dst[3] = w[3];
+    }
+    if (counts) {
+        // lanes l, l ^ 8, l ^ 16, l ^ 24 hold the same chunk: sum them (each byte
+        // counter stays <= 16), then one lane per chunk adds into shared memory
+        const int lane = tid & 31;
+        #pragma unroll
+        for (int j = 0; j < 4; j++) {
+            acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 8);
+            acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 16);
+        }
+        if (lane < 8) {
+            #pragma unroll
+            for (int m = 0; m < 16; m++) {
+                const int n = (int)((acc[m >> 2] >> (8 * (m & 3))) & 0xFFu);
+                if (n) atomicAdd(&cnt[(tid & 7) * 16 + m], n);
+            }
+        }
     }
     __syncthreads();
     decode_tile_store(tile, planes, t_pad, n_pad, t0, i0, fl);
@@ -326,7 +367,9 @@ cudaError_t launch_decode_gather(const uint8_t *block, int32_t F, int32_t N, int
 {
     if (nf <= 0 || t_pad <= 0) return cudaSuccess;
     dim3 grid((unsigned)(t_pad / 128), (unsigned)(n_pad / 128), (unsigned)nf);
-    decode_gather_kernel<<<grid, kDecThreads, 0, s>>>(block, F, N, f0, idx, Tg, valid, planes, t_pad, n_pad, counts);
+    const int vec_ok = decode_vec_ok(block, N) && (!valid || (reinterpret_cast<uintptr_t>(valid) & 15) == 0);
+    decode_gather_kernel<<<grid, kDecThreads, 0, s>>>(block, F, N, f0, idx, Tg, valid, planes, t_pad, n_pad, counts,
+                                                      vec_ok);
     return cudaGetLastError();
 }
 

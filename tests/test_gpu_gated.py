@@ -21,7 +21,8 @@ def gated(eng, block_dev, gate, G, valid_dev=None, want_counts=True):
     return out.cpu().numpy().astype(np.int64), (counts.cpu().numpy().astype(np.int64) if want_counts else None)
 
 
-@pytest.mark.parametrize("T,F,N,G", [(1000, 2, 200, 3), (300, 3, 129, 1), (4096, 2, 256, 8), (777, 1, 60, 5)])
+@pytest.mark.parametrize("T,F,N,G", [(1000, 2, 200, 3), (300, 3, 129, 1), (4096, 2, 256, 8), (777, 1, 60, 5),
+                                     (500, 2, 272, 2)])
 def test_gated_flagged_matches_oracle(T, F, N, G):
     rng = np.random.default_rng(T + N + G)
     blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
