@@ -258,8 +258,9 @@ def run_batched(args, rank, world, local_rank):
             "config": {"workload": "batched", "description": WORKLOADS["batched"][1], "n_jobs": len(recipes),
                        "input_gb": sum(r.nbytes for r in recipes) / 1e9, "useful_ops": ops,
                        "l2": "inputs (%.1f GB) larger than L2; no flush" % (sum(r.nbytes for r in recipes) / 1e9)},
-            "step_call": "xeng_batch_run (CUDA graph: 1 decode + 1 persistent tensor-core launch)",
-            "gpu_launches": 2 * args.steps,
+            "step_call": "xeng_batch_run (CUDA graph: TMA decode (+ thread-per-row decode for N % 16 != 0 jobs) "
+                         "+ 1 persistent tensor-core launch)",
+            "gpu_launches": (2 + (1 if any(r.N % 16 for r in recipes) else 0)) * args.steps,
             "autotune": {"opts": opts.as_dict(), "tuned_ms": tuned_ms, "from_cache": rc == 1, "fixed": rc == 2,
                          "tune_s": tune_s},
             "plan": info,

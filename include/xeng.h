@@ -251,8 +251,9 @@ XENG_API int xeng_get_stats(xeng_t h, xeng_stats_t *stats, int32_t reset);
 /*
  * Batches: many independent whole integrations (Sec. IV-C-1) of uneven
  * sizes -- different N, F and T per job -- planned once and then run as one
- * decode launch plus one persistent tensor-core launch, captured in a CUDA
- * graph.  Every job's result is bit-identical to correlating it alone.
+ * persistent decode launch (a second one only for jobs with N not a multiple
+ * of 16 or an unaligned block) plus one persistent tensor-core launch,
+ * captured in a CUDA graph.  Every job's result is bit-identical to correlating it alone.
  */
 typedef struct {
     int32_t n_inputs;       /* N of this job, 1..XENG_MAX_INPUTS                  */
@@ -278,7 +279,7 @@ typedef struct {
     int32_t n_jobs;
     int64_t n_items;             /* work items of the persistent launch                  */
     int32_t grid;                /* persistent CTAs (one per SM)                         */
-    int64_t decode_ctas;         /* CTAs of the decode launch                            */
+    int64_t decode_ctas;         /* 128 x 128 tiles the decode launches convert per run  */
     int64_t planes_bytes;        /* decode scratch owned by the batch                    */
     int32_t max_chunks_per_item;
     int32_t policy;

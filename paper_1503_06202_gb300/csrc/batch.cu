@@ -1,7 +1,8 @@
 // batch.cu -- many independent correlations (uneven N, F, T) in one pass:
-// one decode launch over every job's tiles, then one persistent tensor-core
-// launch over a host-planned work list, both captured once in a CUDA graph
-// and replayed per run.  Each job is a whole integration (paper Sec. IV-C-1)
+// one persistent TMA decode launch over every job's tiles (plus a
+// thread-per-row decode launch for jobs whose rows TMA cannot address), then
+// one persistent tensor-core launch over a host-planned work list, all
+// captured once in a CUDA graph and replayed per run.  Each job is a whole integration (paper Sec. IV-C-1)
 // written to its own output; results are bit-identical to correlating each
 // job alone.
 //
@@ -38,8 +39,13 @@ struct xeng_batch_s {
     JobDesc *d_jobs = nullptr;
     WorkItem *d_items = nullptr;
     int32_t *d_cta_begin = nullptr;
-    DecodeJob *d_dec = nullptr;
+    DecodeJob *d_dec = nullptr;    // jobs whose rows TMA cannot address: thread-per-row decode
+    int n_dec = 0;
     int64_t dec_ctas = 0;
+    CUtensorMap *d_dmaps = nullptr;  // the other jobs: TMA decode (raw map, plane map per job)
+    DecTmaJob *d_djobs = nullptr;
+    int n_djobs = 0;
+    int64_t dtiles = 0;
     int grid = 0;
     int64_t n_items = 0;
     double max_load = 0, mean_load = 0;
@@ -90,6 +96,8 @@ void free_batch(xeng_batch_s *b)
     cudaFree(b->d_items);
     cudaFree(b->d_cta_begin);
     cudaFree(b->d_dec);
+    cudaFree(b->d_dmaps);
+    cudaFree(b->d_djobs);
     cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     cudaGetLastError();
@@ -102,7 +110,9 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
     for (auto &z : b->zero_outs)
         if (e == cudaSuccess) e = cudaMemsetAsync(z.first, 0, z.second, s);
-    if (e == cudaSuccess) e = launch_decode_batch(b->d_dec, (int)b->jobs.size(), b->dec_ctas, s);
+    if (e == cudaSuccess) e = launch_decode_tma_batch(b->d_dmaps, b->d_djobs, b->n_djobs, b->dtiles, b->d_err,
+                                                      b->num_sms, s);
+    if (e == cudaSuccess && b->n_dec > 0) e = launch_decode_batch(b->d_dec, b->n_dec, b->dec_ctas, s);
     if (e == cudaSuccess) {
         ListArgs L;
         L.maps = b->d_maps;
@@ -135,7 +145,10 @@ int plan(xeng_batch_s *b)
 
     std::vector<CUtensorMap> maps(n);
     std::vector<JobDesc> jd(n);
-    std::vector<DecodeJob> dj(n);
+    std::vector<DecodeJob> dj;
+    std::vector<CUtensorMap> dmaps;
+    std::vector<DecTmaJob> djobs;
+    int64_t dtiles = 0;
     const int maxc = b->opts.max_chunks_per_item;
     struct Cand { WorkItem w; double cost; int64_t order; };
     std::vector<Cand> cand;
@@ -152,18 +165,38 @@ int plan(xeng_batch_s *b)
         jd[j].N = jb.n_inputs;
         jd[j].mode = ns > 1 ? 2 : 0;  // split tiles add atomically into zeroed outputs
         jd[j].pad_ = 0;
-        dj[j].block = jb.block;
-        dj[j].planes = pl;
-        dj[j].T = jb.n_samples;
-        dj[j].t_pad = t_pad[j];
-        dj[j].pitch = t_pad[j];
-        dj[j].n_pad = n_pad[j];
-        dj[j].cta0 = cta0;
-        dj[j].F = jb.n_freq;
-        dj[j].N = jb.n_inputs;
-        dj[j].vec_ok = decode_vec_ok(jb.block, jb.n_inputs);
-        dj[j].pad_ = 0;
-        cta0 += decode_ctas(t_pad[j], n_pad[j], jb.n_freq);
+        CUtensorMap rmap, pmap;
+        if (encode_decode_tma_maps(jb.block, jb.n_samples, jb.n_freq, jb.n_inputs, pl, t_pad[j], n_pad[j], &rmap,
+                                   &pmap)) {
+            DecTmaJob dt;
+            dt.tile0 = dtiles;
+            dt.T = jb.n_samples;
+            dt.n_ib = (int32_t)(n_pad[j] / kTile);
+            dt.n_tb = (int32_t)(t_pad[j] / kTile);
+            dt.F = jb.n_freq;
+            dt.N = jb.n_inputs;
+            dt.n_pad = (int32_t)n_pad[j];
+            dt.pad_ = 0;
+            dtiles += (int64_t)dt.n_ib * dt.F * dt.n_tb;
+            djobs.push_back(dt);
+            dmaps.push_back(rmap);
+            dmaps.push_back(pmap);
+        } else {
+            DecodeJob d;
+            d.block = jb.block;
+            d.planes = pl;
+            d.T = jb.n_samples;
+            d.t_pad = t_pad[j];
+            d.pitch = t_pad[j];
+            d.n_pad = n_pad[j];
+            d.cta0 = cta0;
+            d.F = jb.n_freq;
+            d.N = jb.n_inputs;
+            d.vec_ok = decode_vec_ok(jb.block, jb.n_inputs);
+            d.pad_ = 0;
+            dj.push_back(d);
+            cta0 += decode_ctas(t_pad[j], n_pad[j], jb.n_freq);
+        }
         if (ns > 1) b->zero_outs.push_back({jb.out, (size_t)jb.n_freq * n_baselines(jb.n_inputs) * 8});
         const int nt = (int)(n_pad[j] / kTile);
         for (int f = 0; f < jb.n_freq; f++)
@@ -184,6 +217,9 @@ int plan(xeng_batch_s *b)
                     }
     }
     b->dec_ctas = cta0;
+    b->n_dec = (int)dj.size();
+    b->n_djobs = (int)djobs.size();
+    b->dtiles = dtiles;
     b->n_items = (int64_t)cand.size();
     if (cand.size() > 2147483647ull) return XENG_ERR_RANGE;
 
@@ -248,6 +284,8 @@ int plan(xeng_batch_s *b)
     if (e == cudaSuccess) e = upload(&b->d_items, items);
     if (e == cudaSuccess) e = upload(&b->d_cta_begin, begin);
     if (e == cudaSuccess) e = upload(&b->d_dec, dj);
+    if (e == cudaSuccess) e = upload(&b->d_dmaps, dmaps);
+    if (e == cudaSuccess) e = upload(&b->d_djobs, djobs);
     return status_of(e);
 }
 
@@ -315,6 +353,7 @@ int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_o
     if (st == XENG_OK) e = cudaMalloc(&b->d_err, sizeof(int));
     if (st == XENG_OK && e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(int));
     if (st == XENG_OK && e == cudaSuccess) e = prepare_correlate_tc_listed();
+    if (st == XENG_OK && e == cudaSuccess) e = prepare_decode_tma_batch();
     if (st == XENG_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (st == XENG_OK && e == cudaSuccess && o.use_graph) {
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
@@ -352,7 +391,7 @@ int xeng_batch_info(xeng_batch_t b, xeng_batch_info_t *info)
     info->n_jobs = (int32_t)b->jobs.size();
     info->n_items = b->n_items;
     info->grid = b->grid;
-    info->decode_ctas = b->dec_ctas;
+    info->decode_ctas = b->dec_ctas + b->dtiles;
     info->planes_bytes = b->planes_bytes;
     info->max_chunks_per_item = b->opts.max_chunks_per_item;
     info->policy = b->opts.policy;

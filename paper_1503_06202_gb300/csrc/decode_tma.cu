@@ -18,6 +18,8 @@
 //   one thread    of each group TMA-stores its plane tiles and recycles the
 //                 raw slot; a plane buffer is rewritten only after its store
 //                 has finished reading shared memory
+#include <cstring>
+
 #include "nibble.cuh"
 #include "tc_ptx.cuh"
 #include "xeng_internal.h"
@@ -54,15 +56,60 @@ struct DecTmaArgs {
     int32_t f0;            // first channel of the map's block
     int64_t t0;            // first sample of the map's block
     int *err;
+    // batched launches: job j's raw and plane maps are maps[2j], maps[2j + 1]
+    const CUtensorMap *maps;
+    const DecTmaJob *jobs;
+    int32_t n_jobs;
 };
 
-// Tile order: input block fastest, then channel, then sample block, so the
-// CTAs working at the same time read neighbouring bytes of the same sample rows.
-__device__ __forceinline__ void tile_coords(const DecTmaArgs &a, int64_t tile, int &ib, int &fl, int &tb)
+// One tile as every role sees it.
+struct DtTile {
+    const CUtensorMap *rm, *pm;
+    int ib, fl, tb, f, N, n_pad;
+    int64_t T, t0;
+};
+
+// Tile order within a block (job): input block fastest, then channel, then
+// sample block, so the CTAs working at the same time read neighbouring bytes
+// of the same sample rows.  Batched: tiles of job j are tile0[j] ..
+// tile0[j + 1] - 1.
+template <bool kBatch>
+__device__ __forceinline__ DtTile dt_tile(const DecTmaArgs &a, const CUtensorMap *rm, const CUtensorMap *pm,
+                                          int64_t tile)
 {
-    ib = (int)(tile % a.n_ib);
-    fl = (int)((tile / a.n_ib) % a.nf);
-    tb = (int)(tile / ((int64_t)a.n_ib * a.nf));
+    DtTile t;
+    if (!kBatch) {
+        t.rm = rm;
+        t.pm = pm;
+        t.ib = (int)(tile % a.n_ib);
+        t.fl = (int)((tile / a.n_ib) % a.nf);
+        t.tb = (int)(tile / ((int64_t)a.n_ib * a.nf));
+        t.f = a.f0 + t.fl;
+        t.N = a.N;
+        t.n_pad = a.n_pad;
+        t.T = a.T;
+        t.t0 = a.t0;
+    } else {
+        int lo = 0, hi = a.n_jobs - 1;
+        while (lo < hi) {  // last job whose first tile is <= tile
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.jobs[mid].tile0 <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const DecTmaJob &j = a.jobs[lo];
+        const int64_t local = tile - j.tile0;
+        t.rm = a.maps + 2 * lo;
+        t.pm = a.maps + 2 * lo + 1;
+        t.ib = (int)(local % j.n_ib);
+        t.fl = (int)((local / j.n_ib) % j.F);
+        t.tb = (int)(local / ((int64_t)j.n_ib * j.F));
+        t.f = t.fl;
+        t.N = j.N;
+        t.n_pad = j.n_pad;
+        t.T = j.T;
+        t.t0 = 0;
+    }
+    return t;
 }
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src)
@@ -72,7 +119,7 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
                  : "memory");
 }
 
-template <int kStages, int kGroups, int kP>
+template <int kStages, int kGroups, int kP, bool kBatch>
 __global__ void __launch_bounds__(kDTThreads, 1)
 decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ CUtensorMap plane_map,
                   const DecTmaArgs a)
@@ -100,8 +147,10 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             mbar_init(rawe(s), 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(&plane_map) : "memory");
+        if (!kBatch) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&plane_map) : "memory");
+        }
     }
     __syncthreads();
 
@@ -112,15 +161,13 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             uint32_t phase = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-                int ib, fl, tb;
-                tile_coords(a, tile, ib, fl, tb);
+                const DtTile t = dt_tile<kBatch>(a, &raw_map, &plane_map, tile);
                 if (!mbar_wait(rawe(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
                     ok = false;
                     break;
                 }
                 mbar_expect_tx(rawf(stage), kDTRaw);
-                tma_load_3d(sbase + stage * kDTRaw, &raw_map, ib * 128, a.f0 + fl, (int)(a.t0 + tb * 128),
-                            rawf(stage));
+                tma_load_3d(sbase + stage * kDTRaw, t.rm, t.ib * 128, t.f, (int)(t.t0 + t.tb * 128), rawf(stage));
                 ++issued;
                 if (++stage == kStages) {
                     stage = 0;
@@ -159,8 +206,8 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
         for (int64_t n = grp;; n += kGroups) {
             const int64_t tile = blockIdx.x + n * gridDim.x;
             if (tile >= a.n_tiles) break;
-            int ib, fl, tb;
-            tile_coords(a, tile, ib, fl, tb);
+            const DtTile tl = dt_tile<kBatch>(a, &raw_map, &plane_map, tile);
+            const int ib = tl.ib, fl = tl.fl, tb = tl.tb;
             const int stage = (int)(n % kStages);
             const uint32_t phase = (uint32_t)((n / kStages) & 1);
             const bool ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, 0);
@@ -188,7 +235,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                         #pragma unroll
                         for (int kk = 0; kk < 4; kk++) {
                             const int t = b * 16 + h * 8 + g * 4 + kk;
-                            r[kk] = (tbase + g * 4 + kk < a.T) ? rt[t * 32 + q] : 0x88888888u;  // past the end: 0
+                            r[kk] = (tbase + g * 4 + kk < tl.T) ? rt[t * 32 + q] : 0x88888888u;  // past the end: 0
                         }
                         // transpose + decode: r[k] byte m = (sample k, input m) -> input m's codes of samples 0..3
                         decode_input4(r, 0, re[0][g], im[0][g]);
@@ -200,7 +247,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                     for (int m = 0; m < 4; m++) {
                         const int i = 4 * q + m;
                         const int off = i * 128 + ((b ^ (i & 7)) << 4) + h * 8;  // row i, chunk b, half h
-                        const bool row_ok = ibase + i < a.N;                     // rows past N are +0.0
+                        const bool row_ok = ibase + i < tl.N;                    // rows past N are +0.0
                         *reinterpret_cast<uint2 *>(pre + off) =
                             row_ok ? make_uint2(re[m][0], re[m][1]) : make_uint2(0u, 0u);
                         *reinterpret_cast<uint2 *>(pim + off) =
@@ -221,9 +268,9 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                 : "memory");
             if (storer) {
                 if (!any_fail) {
-                    const int y = (fl * 2) * a.n_pad + ib * 128;
-                    tma_store_2d(&plane_map, tb * 128, y, pre_s);
-                    tma_store_2d(&plane_map, tb * 128, y + a.n_pad, pre_s + kDTPlane);
+                    const int y = (fl * 2) * tl.n_pad + ib * 128;
+                    tma_store_2d(tl.pm, tb * 128, y, pre_s);
+                    tma_store_2d(tl.pm, tb * 128, y + tl.n_pad, pre_s + kDTPlane);
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
                 mbar_arrive(rawe(stage));  // the raw slot may be refilled
@@ -273,7 +320,7 @@ cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    auto kern = decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs>;
+    auto kern = decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, false>;
     const size_t smem = dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -288,8 +335,59 @@ cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_
     a.f0 = f0;
     a.t0 = 0;
     a.err = err;
+    a.maps = nullptr;
+    a.jobs = nullptr;
+    a.n_jobs = 0;
     const int grid = (int)(a.n_tiles < num_sms ? a.n_tiles : num_sms);
     kern<<<grid, kDTThreads, smem, s>>>(rm, pm, a);
+    return cudaGetLastError();
+}
+
+bool encode_decode_tma_maps(const uint8_t *block, int64_t T, int32_t F, int32_t N, uint8_t *planes, int64_t t_pad,
+                            int64_t n_pad, CUtensorMap *raw_map, CUtensorMap *plane_map)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || !decode_tma_ok(block, N) || t_pad % 128 != 0 || n_pad % 128 != 0 || t_pad > 2147483647LL ||
+        (int64_t)F * 2 * n_pad > 2147483647LL || T > 2147483647LL)
+        return false;
+    const cuuint64_t rdims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T};
+    const cuuint64_t rstrides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};
+    const cuuint32_t rbox[3] = {128, 1, 128}, estr3[3] = {1, 1, 1};
+    if (enc(raw_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, rdims, rstrides, rbox, estr3,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t pdims[2] = {(cuuint64_t)t_pad, (cuuint64_t)F * 2 * n_pad};
+    const cuuint64_t pstrides[1] = {(cuuint64_t)t_pad};
+    const cuuint32_t pbox[2] = {128, 128}, estr2[2] = {1, 1};
+    return enc(plane_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)planes, pdims, pstrides, pbox, estr2,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t prepare_decode_tma_batch()
+{
+    return cudaFuncSetAttribute(decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs));
+}
+
+cudaError_t launch_decode_tma_batch(const CUtensorMap *maps, const DecTmaJob *jobs, int n_jobs, int64_t n_tiles,
+                                    int *err, int num_sms, cudaStream_t s)
+{
+    if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
+    CUtensorMap unused;
+    memset(&unused, 0, sizeof(unused));
+    DecTmaArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_tiles = n_tiles;
+    a.err = err;
+    a.maps = maps;
+    a.jobs = jobs;
+    a.n_jobs = n_jobs;
+    const int grid = (int)(n_tiles < num_sms ? n_tiles : num_sms);
+    decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, true>
+        <<<grid, kDTThreads, dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs), s>>>(unused, unused, a);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,22 @@ struct ShiftArgs {
 cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, int32_t F, int32_t N, int32_t f0,
                                   int32_t nf, const ShiftArgs &sa, uint8_t *planes, int64_t t_pad, int64_t n_pad,
                                   cudaStream_t s);
+// Batched TMA decode: job j's block [T][F][N] into its planes [F][2][n_pad][t_pad]
+// through the maps encode_decode_tma_maps writes (device array: raw map 2j,
+// plane map 2j + 1); tiles tile0[j] .. tile0[j] + n_ib * F * n_tb - 1 are job
+// j's.  prepare_decode_tma_batch sets the kernel's shared-memory limit (call
+// it before capturing a launch in a graph).
+struct DecTmaJob {
+    int64_t tile0;
+    int64_t T;
+    int32_t n_ib, n_tb, F, N, n_pad, pad_;
+};
+bool encode_decode_tma_maps(const uint8_t *block, int64_t T, int32_t F, int32_t N, uint8_t *planes, int64_t t_pad,
+                            int64_t n_pad, CUtensorMap *raw_map, CUtensorMap *plane_map);
+cudaError_t prepare_decode_tma_batch();
+cudaError_t launch_decode_tma_batch(const CUtensorMap *maps, const DecTmaJob *jobs, int n_jobs, int64_t n_tiles,
+                                    int *err, int num_sms, cudaStream_t s);
+
 // After a plain decode of samples t0 .. t0 + nt - 1 into planes: rewrite the
 // rows of the S delayed inputs (inputs[s] has history column s) with their
 // shifted samples, as launch_decode_shifted computes them.
