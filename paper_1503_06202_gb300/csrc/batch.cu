@@ -176,7 +176,7 @@ int plan(xeng_batch_s *b)
             dt.F = jb.n_freq;
             dt.N = jb.n_inputs;
             dt.n_pad = (int32_t)n_pad[j];
-            dt.pad_ = 0;
+            dt.x0 = 0;
             dtiles += (int64_t)dt.n_ib * dt.F * dt.n_tb;
             djobs.push_back(dt);
             dmaps.push_back(rmap);

@@ -65,7 +65,7 @@ struct DecTmaArgs {
 // One tile as every role sees it.
 struct DtTile {
     const CUtensorMap *rm, *pm;
-    int ib, fl, tb, f, N, n_pad;
+    int ib, fl, tb, f, N, n_pad, x0;
     int64_t T, t0;
 };
 
@@ -85,6 +85,7 @@ __device__ __forceinline__ DtTile dt_tile(const DecTmaArgs &a, const CUtensorMap
         t.fl = (int)((tile / a.n_ib) % a.nf);
         t.tb = (int)(tile / ((int64_t)a.n_ib * a.nf));
         t.f = a.f0 + t.fl;
+        t.x0 = 0;
         t.N = a.N;
         t.n_pad = a.n_pad;
         t.T = a.T;
@@ -104,6 +105,7 @@ __device__ __forceinline__ DtTile dt_tile(const DecTmaArgs &a, const CUtensorMap
         t.fl = (int)((local / j.n_ib) % j.F);
         t.tb = (int)(local / ((int64_t)j.n_ib * j.F));
         t.f = t.fl;
+        t.x0 = j.x0;
         t.N = j.N;
         t.n_pad = j.n_pad;
         t.T = j.T;
@@ -269,8 +271,8 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             if (storer) {
                 if (!any_fail) {
                     const int y = (fl * 2) * tl.n_pad + ib * 128;
-                    tma_store_2d(tl.pm, tb * 128, y, pre_s);
-                    tma_store_2d(tl.pm, tb * 128, y + tl.n_pad, pre_s + kDTPlane);
+                    tma_store_2d(tl.pm, tl.x0 + tb * 128, y, pre_s);
+                    tma_store_2d(tl.pm, tl.x0 + tb * 128, y + tl.n_pad, pre_s + kDTPlane);
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
                 mbar_arrive(rawe(stage));  // the raw slot may be refilled

@@ -11,7 +11,9 @@
 // A worker thread runs the loop.  Each round it takes, from every stream with
 // queued blocks, up to `max_blocks` of them (never across a dump boundary) --
 // blocks that arrived while earlier rounds were on the GPU join the next round
-// -- decodes them with one launch into the streams' plane slices and
+// -- decodes them with one persistent TMA launch (per-block tensor maps; a
+// thread-per-row launch only for blocks TMA cannot address) into the streams'
+// plane slices and
 // correlates all streams' tiles with one persistent tensor-core launch that
 // adds into each stream's accumulators (or stores, for the first round of an
 // integration).  A stream whose integration reaches `dump_samples` gets a
@@ -105,7 +107,9 @@ struct xserve_s {
     WorkItem *h_items[2] = {nullptr, nullptr};
     CUtensorMap *d_maps[2] = {nullptr, nullptr}, *h_maps[2] = {nullptr, nullptr};
     JobDesc *d_jobs[2] = {nullptr, nullptr}, *h_jobs[2] = {nullptr, nullptr};
-    DecodeJob *d_dec[2] = {nullptr, nullptr}, *h_dec[2] = {nullptr, nullptr};
+    DecodeJob *d_dec[2] = {nullptr, nullptr}, *h_dec[2] = {nullptr, nullptr};  // blocks TMA cannot address
+    CUtensorMap *d_dmaps[2] = {nullptr, nullptr}, *h_dmaps[2] = {nullptr, nullptr};  // TMA decode: 2 maps per block
+    DecTmaJob *d_djobs[2] = {nullptr, nullptr}, *h_djobs[2] = {nullptr, nullptr};
     int *d_err = nullptr, *h_err = nullptr;
     std::deque<Round> inflight;
     int next_slot = 0;
@@ -241,7 +245,7 @@ bool launch_round(xserve_s *sv)
 
     Round r;
     r.slot = slot;
-    int64_t n_items = 0, n_dec = 0, dec_ctas = 0;
+    int64_t n_items = 0, n_dec = 0, dec_ctas = 0, n_djobs = 0, dtiles = 0;
     int jobi = 0;
     for (auto &pk : picks) {
         SStream &st = sv->streams[pk.stream];
@@ -256,19 +260,35 @@ bool launch_round(xserve_s *sv)
             st.queue.pop_front();
             part.arrivals.push_back(qb.arrival);
             st.last_arrival = std::max(st.last_arrival, qb.arrival);
-            DecodeJob &dj = sv->h_dec[slot][n_dec++];
-            dj.block = qb.ptr;
-            dj.planes = pl + b * st.bs_pad;
-            dj.T = st.block_samples;
-            dj.t_pad = st.bs_pad;
-            dj.pitch = pitch;
-            dj.n_pad = st.n_pad;
-            dj.cta0 = dec_ctas;
-            dj.F = st.F;
-            dj.N = st.N;
-            dj.vec_ok = decode_vec_ok(qb.ptr, st.N);
-            dj.pad_ = 0;
-            dec_ctas += decode_ctas(st.bs_pad, st.n_pad, st.F);
+            // the TMA decode where the block's rows allow it: the block's raw
+            // map and the slice's plane map, the block at column b * bs_pad
+            CUtensorMap *mp = sv->h_dmaps[slot] + 2 * n_djobs;
+            if (encode_decode_tma_maps(qb.ptr, st.block_samples, st.F, st.N, pl, pitch, st.n_pad, mp, mp + 1)) {
+                DecTmaJob &dt = sv->h_djobs[slot][n_djobs++];
+                dt.tile0 = dtiles;
+                dt.T = st.block_samples;
+                dt.n_ib = (int32_t)(st.n_pad / kTile);
+                dt.n_tb = (int32_t)(st.bs_pad / kTile);
+                dt.F = st.F;
+                dt.N = st.N;
+                dt.n_pad = (int32_t)st.n_pad;
+                dt.x0 = (int32_t)(b * st.bs_pad);
+                dtiles += (int64_t)dt.n_ib * dt.F * dt.n_tb;
+            } else {
+                DecodeJob &dj = sv->h_dec[slot][n_dec++];
+                dj.block = qb.ptr;
+                dj.planes = pl + b * st.bs_pad;
+                dj.T = st.block_samples;
+                dj.t_pad = st.bs_pad;
+                dj.pitch = pitch;
+                dj.n_pad = st.n_pad;
+                dj.cta0 = dec_ctas;
+                dj.F = st.F;
+                dj.N = st.N;
+                dj.vec_ok = decode_vec_ok(qb.ptr, st.N);
+                dj.pad_ = 0;
+                dec_ctas += decode_ctas(st.bs_pad, st.n_pad, st.F);
+            }
         }
         if (encode_planes_map(&sv->h_maps[slot][jobi], pl, pitch, (int64_t)st.F * 2 * st.n_pad) != cudaSuccess) {
             sv->sticky = XENG_ERR_CUDA;  // never launch with a descriptor that failed to encode
@@ -318,12 +338,20 @@ bool launch_round(xserve_s *sv)
     r.t0 = take_timer(sv);
     r.t1 = take_timer(sv);
     r.t2 = take_timer(sv);
-    cudaError_t e = cudaMemcpyAsync(sv->d_dec[slot], sv->h_dec[slot], n_dec * sizeof(DecodeJob), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    if (n_dec > 0) e = cudaMemcpyAsync(sv->d_dec[slot], sv->h_dec[slot], n_dec * sizeof(DecodeJob), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_djobs > 0)
+        e = cudaMemcpyAsync(sv->d_dmaps[slot], sv->h_dmaps[slot], 2 * n_djobs * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess && n_djobs > 0)
+        e = cudaMemcpyAsync(sv->d_djobs[slot], sv->h_djobs[slot], n_djobs * sizeof(DecTmaJob), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_maps[slot], sv->h_maps[slot], jobi * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_jobs[slot], sv->h_jobs[slot], jobi * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_items[slot], sv->h_items[slot], n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && r.t0) e = cudaEventRecord(r.t0, s);
-    if (e == cudaSuccess) e = launch_decode_batch(sv->d_dec[slot], (int)n_dec, dec_ctas, s);
+    if (e == cudaSuccess)
+        e = launch_decode_tma_batch(sv->d_dmaps[slot], sv->d_djobs[slot], (int)n_djobs, dtiles, sv->d_err, sv->num_sms, s);
+    if (e == cudaSuccess && n_dec > 0) e = launch_decode_batch(sv->d_dec[slot], (int)n_dec, dec_ctas, s);
     if (e == cudaSuccess && r.t1) e = cudaEventRecord(r.t1, s);
     if (e == cudaSuccess) {
         ListArgs L;
@@ -429,6 +457,7 @@ int xserve_create(const xserve_opts_t *opts, xserve_t *out)
     sv->streams.resize(o.max_streams);
     for (int k = 0; k < o.max_streams; k++) sv->streams[k].id = k;
     cudaError_t e = prepare_correlate_tc_listed();
+    if (e == cudaSuccess) e = prepare_decode_tma_batch();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking);
     for (int k = 0; k < 2 && e == cudaSuccess; k++) {
         e = cudaMalloc(&sv->d_items[k], (size_t)o.max_items * sizeof(WorkItem));
@@ -439,6 +468,13 @@ int xserve_create(const xserve_opts_t *opts, xserve_t *out)
         if (e == cudaSuccess) e = cudaMallocHost(&sv->h_jobs[k], (size_t)o.max_streams * sizeof(JobDesc));
         if (e == cudaSuccess) e = cudaMalloc(&sv->d_dec[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecodeJob));
         if (e == cudaSuccess) e = cudaMallocHost(&sv->h_dec[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecodeJob));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&sv->d_dmaps[k], (size_t)o.max_streams * o.max_blocks * 2 * sizeof(CUtensorMap));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sv->h_dmaps[k], (size_t)o.max_streams * o.max_blocks * 2 * sizeof(CUtensorMap));
+        if (e == cudaSuccess) e = cudaMalloc(&sv->d_djobs[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecTmaJob));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sv->h_djobs[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecTmaJob));
     }
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(sv->d_err, 0, sizeof(int));
@@ -661,6 +697,10 @@ void xserve_destroy(xserve_t sv)
         cudaFreeHost(sv->h_jobs[k]);
         cudaFree(sv->d_dec[k]);
         cudaFreeHost(sv->h_dec[k]);
+        cudaFree(sv->d_dmaps[k]);
+        cudaFreeHost(sv->h_dmaps[k]);
+        cudaFree(sv->d_djobs[k]);
+        cudaFreeHost(sv->h_djobs[k]);
     }
     cudaFree(sv->d_err);
     if (sv->h_err) cudaFreeHost(sv->h_err);

@@ -77,7 +77,8 @@ cudaError_t launch_decode_shifted(const uint8_t *block, int64_t t0, int64_t nt, 
 struct DecTmaJob {
     int64_t tile0;
     int64_t T;
-    int32_t n_ib, n_tb, F, N, n_pad, pad_;
+    int32_t n_ib, n_tb, F, N, n_pad;
+    int32_t x0;  // first plane column of the job in its plane map (a multiple of 128)
 };
 bool encode_decode_tma_maps(const uint8_t *block, int64_t T, int32_t F, int32_t N, uint8_t *planes, int64_t t_pad,
                             int64_t n_pad, CUtensorMap *raw_map, CUtensorMap *plane_map);
