@@ -142,7 +142,9 @@ def cpu_oracle_sample(rec, T, F, N, out_dev=None):
     """Time the oracle (as it stands) on a bounded sample; check the GPU output on it."""
     import numpy as np
     import oracle
-    nf = {2048: 1, 256: 8}.get(N, 1)
+    # about 10 s of oracle work on 16 cores: 8 channels at N = 2048 (T = 8192),
+    # 128 at N = 256 (T = 32768)
+    nf = {2048: 8, 256: 128}.get(N, 8)
     nf = min(nf, F)
     host = rec.host(f0=0, nf=nf)
     t0 = time.perf_counter()
