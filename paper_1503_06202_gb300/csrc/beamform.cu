@@ -276,8 +276,8 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             const int r = (int)(n % kR);
             const uint32_t pr = (uint32_t)((n / kR) & 1);
             const int x = xslot(n);
-            const bool ok = mbar_wait_backoff(rawf(r), pr, err, kDevTimeoutProducer, 0) &&
-                            mbar_wait_backoff(xe(x), xphase(n) ^ 1u, err, kDevTimeoutProducer, 0);
+            const bool ok = mbar_wait_backoff(rawf(r), pr, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS) &&
+                            mbar_wait_backoff(xe(x), xphase(n) ^ 1u, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
             if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.st
             fence_after();
             const uint8_t *rt = rgen + r * kRawBytes + row * 128;

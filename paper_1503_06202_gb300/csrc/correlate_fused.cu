@@ -199,7 +199,7 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
         for (int it = it_begin; it < a.nf; it += it_step) {
             bool ok = true;
             for (int kc = 0; kc < n_k; kc++) {
-                ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, 0);
+                ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
                     break;

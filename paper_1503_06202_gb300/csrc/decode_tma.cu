@@ -212,7 +212,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             const int ib = tl.ib, fl = tl.fl, tb = tl.tb;
             const int stage = (int)(n % kStages);
             const uint32_t phase = (uint32_t)((n / kStages) & 1);
-            const bool ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, 0);
+            const bool ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
             const int pslot = (int)((n / kGroups) % kP);
             const uint32_t pre_s = pbase + (uint32_t)((grp * kP + pslot) * 2 * kDTPlane);
             // the store that last read this plane buffer (the group's kP-th last) is done reading
