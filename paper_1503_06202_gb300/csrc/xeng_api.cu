@@ -42,6 +42,7 @@ struct xeng_s {
     // host-buffer pipeline: copies in, compute and copies out overlap by channel group
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_start = nullptr, ev_fin = nullptr, ev_in[2] = {nullptr, nullptr}, ev_cmp[2] = {nullptr, nullptr};
+    cudaEvent_t ev_sub = nullptr;  // a channel sub-range correlated: its download may start
     uint8_t *pstage[2] = {nullptr, nullptr};
     int64_t pstage_bytes = 0;
     int32_t *gidx = nullptr;       // sample indices of the gates of a gated call
@@ -164,6 +165,11 @@ cudaEvent_t take_event(xeng_s *h)
 // end to end).
 #ifndef XENG_PIPE_ROW_BYTES
 #define XENG_PIPE_ROW_BYTES 409600
+#endif
+// Correlation launches (each followed by its download) per channel group when
+// the result goes to host memory.
+#ifndef XENG_PIPE_SUBGROUPS
+#define XENG_PIPE_SUBGROUPS 4
 #endif
 
 // Rows of the decoded planes per channel and plane: N rounded up to the tile.
@@ -331,6 +337,7 @@ void xeng_destroy(xeng_t h)
     }
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     if (h->ev_fin) cudaEventDestroy(h->ev_fin);
+    if (h->ev_sub) cudaEventDestroy(h->ev_sub);
     free_shift(h);
     cudaFree(h->d_err);
     if (h->h_err) cudaFreeHost(h->h_err);
@@ -428,6 +435,7 @@ const uint8_t *device_block(xeng_s *h, const uint8_t *block, int64_t bytes, cuda
     }
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     if (h->ev_fin) cudaEventDestroy(h->ev_fin);
+    if (h->ev_sub) cudaEventDestroy(h->ev_sub);
         h->staging = nullptr;
         h->staging_bytes = 0;
         if (cudaMalloc(&h->staging, (size_t)bytes) != cudaSuccess) {
@@ -538,6 +546,7 @@ int ensure_pipeline(xeng_s *h, int64_t stage_bytes)
         }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fin, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sub, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (stage_bytes > h->pstage_bytes) {
@@ -655,23 +664,34 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
         e = timed_launch(h, 0, s, [&] {
             return run_decode(h, blk, n, bf, (int32_t)N, bf0, nf, t_pad, n_pad, s);
         });
-        if (e != cudaSuccess) break;
-        TcArgs a;
-        a.planes = h->planes;
-        a.t_pad = t_pad;
-        a.n_pad = (int32_t)n_pad;
-        a.N = (int32_t)N;
-        a.nf = nf;
-        a.acc = target + f0 * nb2;
-        a.accumulate = fresh ? 0 : 1;
-        a.err = h->d_err;
-        e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
+        // the decode was the staging buffer's last reader
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
-        if (e == cudaSuccess && host_out) {
-            e = cudaStreamWaitEvent(h->d2h, h->ev_cmp[buf], 0);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(host_out + f0 * nb2, target + f0 * nb2, (size_t)(nf * nb2 * 4),
-                                    cudaMemcpyDeviceToHost, h->d2h);
+        if (e != cudaSuccess) break;
+        // Correlate the group in channel sub-ranges, each downloaded as soon as
+        // it is done: the downloads, the bottleneck of a host-to-host step,
+        // start a fraction of a group's correlation earlier and end as much
+        // sooner after the last one.
+        const int32_t subs = host_out ? std::min<int32_t>(XENG_PIPE_SUBGROUPS, nf) : 1;
+        const int32_t per = (nf + subs - 1) / subs;
+        for (int32_t c0 = 0; c0 < nf && e == cudaSuccess; c0 += per) {
+            const int32_t nc = std::min<int32_t>(per, nf - c0);
+            TcArgs a;
+            a.planes = h->planes + (int64_t)c0 * 2 * n_pad * t_pad;
+            a.t_pad = t_pad;
+            a.n_pad = (int32_t)n_pad;
+            a.N = (int32_t)N;
+            a.nf = nc;
+            a.acc = target + (f0 + c0) * nb2;
+            a.accumulate = fresh ? 0 : 1;
+            a.err = h->d_err;
+            e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
+            if (e == cudaSuccess && host_out) {
+                e = cudaEventRecord(h->ev_sub, s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h, h->ev_sub, 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(host_out + (f0 + c0) * nb2, target + (f0 + c0) * nb2, (size_t)(nc * nb2 * 4),
+                                        cudaMemcpyDeviceToHost, h->d2h);
+            }
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_fin, host_out ? h->d2h : s);
