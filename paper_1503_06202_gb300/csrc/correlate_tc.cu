@@ -301,7 +301,9 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)ab * 256u;
                 for (int kc = w.kc0; kc < w.kc1; kc++) {
-                    if (!mbar_wait(full_bar(stage), phase, err, kDevTimeoutMma)) {
+                    // inline probe first: the out-of-line bounded wait only when the stage is not there yet
+                    if (!mbar_try_wait(full_bar(stage), phase) &&
+                        !mbar_wait(full_bar(stage), phase, err, kDevTimeoutMma)) {
                         ok = false;
                         break;
                     }
@@ -310,13 +312,16 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     const uint32_t a_re = st, a_im = st + kPlaneTile;
                     const uint32_t b_re = diag ? a_re : st + 2 * kPlaneTile;
                     const uint32_t b_im = b_re + kPlaneTile;
+                    // descriptors built once per stage; +32 bytes along K is +2 in their address field
+                    const uint64_t dar = sw128_desc(a_re), dai = sw128_desc(a_im);
+                    const uint64_t dbr = sw128_desc(b_re), dbi = sw128_desc(b_im);
+                    const uint32_t acc0 = kc != w.kc0 ? 1u : 0u;
                     #pragma unroll
                     for (int kk = 0; kk < kKSteps; kk++) {
-                        const uint32_t off = kk * 32;
-                        mma_f8(d, sw128_desc(a_re + off), sw128_desc(b_re + off), kIdescN256,
-                               (kc != w.kc0 || kk != 0) ? 1u : 0u);
-                        mma_f8(d, sw128_desc(a_im + off), sw128_desc(b_im + off), kIdescN128, 1u);
-                        mma_f8(d + 128u, sw128_desc(a_im + off), sw128_desc(b_re + off), kIdescN128Neg, 1u);
+                        const uint64_t k2 = 2u * kk;
+                        mma_f8(d, dar + k2, dbr + k2, kIdescN256, kk != 0 ? 1u : acc0);
+                        mma_f8(d, dai + k2, dbi + k2, kIdescN128, 1u);
+                        mma_f8(d + 128u, dai + k2, dbr + k2, kIdescN128Neg, 1u);
                     }
                     if (kPair) mma_commit_mc(empty_bar(stage), kBoth);
                     else mma_commit(empty_bar(stage));
