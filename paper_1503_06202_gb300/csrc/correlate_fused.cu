@@ -158,7 +158,7 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
                 ++uses;
                 fence_after();
                 for (int kc = 0; kc < n_k; kc++) {
-                    if (!mbar_wait(full(stage), phase, err, kDevTimeoutMma)) {
+                    if (!mbar_try_wait(full(stage), phase) && !mbar_wait(full(stage), phase, err, kDevTimeoutMma)) {
                         ok = false;
                         break;
                     }

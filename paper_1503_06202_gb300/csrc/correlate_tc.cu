@@ -249,7 +249,8 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                 const int rowA = w.fl * 2 * w.n_pad + w.I * kTile;
                 const int rowB = w.fl * 2 * w.n_pad + w.J * kTile;
                 for (int kc = w.kc0; kc < w.kc1; kc++) {
-                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
+                    if (!mbar_try_wait(empty_bar(stage), phase ^ 1u) &&
+                        !mbar_wait(empty_bar(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
                         ok = false;
                         break;
                     }

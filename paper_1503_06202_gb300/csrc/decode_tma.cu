@@ -164,7 +164,8 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
                 const DtTile t = dt_tile<kBatch>(a, &raw_map, &plane_map, tile);
-                if (!mbar_wait(rawe(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
+                if (!mbar_try_wait(rawe(stage), phase ^ 1u) &&
+                    !mbar_wait(rawe(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
                     ok = false;
                     break;
                 }
