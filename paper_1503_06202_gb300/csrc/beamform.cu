@@ -9,12 +9,14 @@
 // with int8 parts.  As real GEMMs with M = 128 samples and K = inputs:
 //     Re y = X_re W_re^T - X_im W_im^T,   Im y = X_re W_im^T + X_im W_re^T.
 // E4M3 holds -8..15 exactly but not all of int8, so a weight part v is split
-// into v = 16 hi + lo, hi = v >> 4 in [-8, 8], lo = v & 15 in [0, 15].  The B
-// operand of the X_re MMA stacks the rows [hi W_re; hi W_im; lo W_re; lo W_im]
-// (4 Bp rows, Bp = beams rounded up), that of the X_im MMA
-// [hi(-W_im); hi W_re; lo(-W_im); lo W_re], so one 128 x 4Bp f32 accumulator
-// collects the hi and lo parts of Re y and Im y side by side and the
-// epilogue forms y = 16 hi + lo in int32.  Products are integers of
+// into v = 16 hi + lo, hi = v >> 4 in [-8, 8], lo = v & 15 in [0, 15].  The A
+// operand interleaves the parts of each input along K (K position 2i holds
+// Im x_i, 2i + 1 holds Re x_i: the order the nibble lookup produces them in),
+// so one MMA per 32 K positions covers both; the B operand's rows are the hi
+// parts of the Re-y weights (-w_im, w_re interleaved), of the Im-y weights
+// (w_re, w_im), then the lo parts of both (4 Bp rows, Bp = beams rounded up),
+// and one 128 x 4Bp f32 accumulator collects the hi and lo parts of Re y and
+// Im y side by side; the epilogue forms y = 16 hi + lo in int32.  Products are integers of
 // magnitude <= 8 * 15 and partial sums stay below 240 N <= 2^20, so the f32
 // accumulation is exact.
 //
@@ -27,8 +29,9 @@
 //   warps 2..13   converters in three groups of four warps (one per TMEM lane
 //                 quadrant); group g takes the steps g, g + 3, ...: each thread
 //                 reads one sample row (128 inputs) of the step's raw tile from
-//                 shared memory, decodes it to E4M3 codes and writes X_re, X_im
-//                 into the group's TMEM slot with tcgen05.st
+//                 shared memory, decodes it to E4M3 codes and writes them,
+//                 real and imaginary parts interleaved along K, into the
+//                 group's TMEM slot with tcgen05.st
 //   warps 14..17  epilogue: TMEM -> int32 beams [T][F][B][2] in HBM
 //   warp 18       TMA producer of the raw tiles (128 samples x 128 inputs of one
 //                 channel, 128-byte swizzle) into a six-slot ring
@@ -60,13 +63,13 @@ constexpr int kBfThreads = 32 * (kRawProdWarp + 1);
 constexpr int kRawBytes = 128 * 128;                 // 128 samples x 128 inputs of one channel
 constexpr int kR = 2 * kGroups;                      // raw ring: a multiple of the groups, so each slot has one user
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kXCols = 64;                      // one K chunk: X_re in 32 columns (4 codes each), X_im in 32
+constexpr uint32_t kXCols = 64;                      // one K chunk of 128 inputs: 256 codes, 4 to a column
 
 template <int kBp>
 struct BfCfg {
     static constexpr int kN = 4 * kBp;                           // MMA N: hi/lo x Re/Im x beams
-    static constexpr int kWBytes = kN * 128;                     // one weight operand slice
-    static constexpr int kWStageBytes = 2 * kWBytes;             // both weight operands of one K chunk
+    static constexpr int kWBytes = kN * 128;                     // one 128-byte-wide box of the weight operand
+    static constexpr int kWStageBytes = 2 * kWBytes;             // the weight operand of one K chunk (256 K positions)
     static constexpr int kAcc = (8 * kBp <= 256) ? 2 : 1;        // accumulators (2: epilogue overlaps MMAs)
     static constexpr uint32_t kXCol0 = kAcc * kN;                // first TMEM column of the X slots
     // X slots per group: two where TMEM has room (the group converts its next
@@ -194,10 +197,12 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
                         ok = false;
                         break;
                     }
+                    // K positions 256k .. 256k + 255 (inputs 128k .. 128k + 127) as two
+                    // 128-byte-swizzled boxes
                     const uint32_t w0 = wbase + s * C::kWStageBytes;
                     mbar_expect_tx(wf(s), 2 * C::kWBytes);
-                    tma_load_2d(w0, &w_map, k * 128, (f * 2 + 0) * C::kN, wf(s));
-                    tma_load_2d(w0 + C::kWBytes, &w_map, k * 128, (f * 2 + 1) * C::kN, wf(s));
+                    tma_load_2d(w0, &w_map, k * 256, f * C::kN, wf(s));
+                    tma_load_2d(w0 + C::kWBytes, &w_map, k * 256 + 128, f * C::kN, wf(s));
                     ++issued;
                     if (++s == C::kSW) {
                         s = 0;
@@ -237,13 +242,13 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
                         break;
                     }
                     fence_after();
-                    const uint32_t xre = tmem + C::kXCol0 + (uint32_t)x * kXCols, xim = xre + 32;
+                    const uint32_t xs = tmem + C::kXCol0 + (uint32_t)x * kXCols;
                     const uint32_t w0 = wbase + sw * C::kWStageBytes;
                     const uint64_t b0 = bf_desc(w0), b1 = bf_desc(w0 + C::kWBytes);
                     #pragma unroll
-                    for (int kk = 0; kk < 4; kk++) {  // +32 bytes along K = +2 in the descriptor's address field
-                        mma_f8_ta(d, xre + kk * 8, b0 + 2 * kk, C::kIdesc, (k != 0 || kk != 0) ? 1u : 0u);
-                        mma_f8_ta(d, xim + kk * 8, b1 + 2 * kk, C::kIdesc, 1u);
+                    for (int kk = 0; kk < 8; kk++) {  // +32 bytes along K = +2 in the descriptor's address field
+                        const uint64_t bk = (kk < 4 ? b0 : b1) + 2 * (kk & 3);
+                        mma_f8_ta(d, xs + kk * 8, bk, C::kIdesc, (k != 0 || kk != 0) ? 1u : 0u);
                     }
                     mma_commit(xe(x));
                     mma_commit(we(sw));
@@ -285,20 +290,18 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             #pragma unroll
             for (int j = 0; j < 8; j++) v[j] = *reinterpret_cast<const uint4 *>(rt + ((j ^ (row & 7)) << 4));
             mbar_arrive(rawe(r));
-            const uint32_t xre = lane_base + (uint32_t)x * kXCols;
+            const uint32_t xs = lane_base + (uint32_t)x * kXCols;
             #pragma unroll
-            for (int h = 0; h < 4; h++) {  // 32 inputs = 8 columns per store
-                uint32_t re[8], im[8];
+            for (int h = 0; h < 8; h++) {  // 16 inputs = 8 columns of (Im, Re) codes per store
+                const uint4 w = v[h];
+                const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+                uint32_t col[8];
                 #pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const uint4 w = v[2 * h + j];
-                    decode_word(w.x, re[4 * j + 0], im[4 * j + 0]);
-                    decode_word(w.y, re[4 * j + 1], im[4 * j + 1]);
-                    decode_word(w.z, re[4 * j + 2], im[4 * j + 2]);
-                    decode_word(w.w, re[4 * j + 3], im[4 * j + 3]);
+                for (int j = 0; j < 4; j++) {  // inputs 4j .. 4j + 3 of the 16
+                    col[2 * j] = nib4_to_e4m3(wd[j]);            // Im, Re of inputs 4j, 4j + 1
+                    col[2 * j + 1] = nib4_to_e4m3(wd[j] >> 16);  // Im, Re of inputs 4j + 2, 4j + 3
                 }
-                tmem_st8(xre + h * 8, re);
-                tmem_st8(xre + 32 + h * 8, im);
+                tmem_st8(xs + h * 8, col);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             fence_before();
@@ -389,27 +392,28 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     }
 }
 
-// Weight operands from int8 weights [F][B][N] (re, im): [F][2][4 Bp][n_pad]
-// E4M3 codes, operand m = 0 multiplies X_re, m = 1 multiplies X_im; row
-// g * Bp + b holds the hi (g = 0, 1) or lo (g = 2, 3) part of the Re-y (g even)
-// or Im-y (g odd) weight of beam b.  Rows b >= B and columns i >= N are zero.
+// Weight operand from int8 weights [F][B][N] (re, im): [F][4 Bp][2 n_pad] E4M3
+// codes; row g * Bp + b holds the hi (g = 0, 1) or lo (g = 2, 3) part of the
+// Re-y (g even) or Im-y (g odd) weights of beam b, K position 2i the factor of
+// Im x_i and 2i + 1 that of Re x_i.  Rows b >= B and inputs i >= N are zero.
 __global__ void beam_weights_kernel(const int8_t *__restrict__ w_re, const int8_t *__restrict__ w_im, int32_t F,
                                     int32_t B, int32_t N, int32_t bp, int32_t n_pad, uint8_t *__restrict__ wdev)
 {
-    const int64_t total = (int64_t)F * 2 * 4 * bp * n_pad;
+    const int64_t total = (int64_t)F * 4 * bp * 2 * n_pad;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(k % n_pad);
-        const int64_t rowk = k / n_pad;
+        const int kp = (int)(k % (2 * n_pad));
+        const int i = kp >> 1;
+        const bool of_re = (kp & 1) != 0;  // multiplies Re x_i (else Im x_i)
+        const int64_t rowk = k / (2 * n_pad);
         const int rr = (int)(rowk % (4 * bp));
-        const int m = (int)((rowk / (4 * bp)) % 2);
-        const int64_t f = rowk / (8 * bp);
+        const int64_t f = rowk / (4 * bp);
         const int g = rr / bp, b = rr % bp;
         int v = 0;
         if (b < B && i < N) {
             const int64_t src = (f * B + b) * N + i;
             const int wr = w_re[src], wi = w_im[src];
-            // m = 0: Re y += x_re w_re, Im y += x_re w_im;  m = 1: Re y += x_im (-w_im), Im y += x_im w_re
-            const int base = (m == 0) ? ((g & 1) ? wi : wr) : ((g & 1) ? wr : -wi);
+            // Re y += Re x w_re - Im x w_im;  Im y += Re x w_im + Im x w_re
+            const int base = (g & 1) ? (of_re ? wi : wr) : (of_re ? wr : -wi);
             v = g < 2 ? (base >> 4) : (base & 15);
         }
         wdev[k] = (uint8_t)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
@@ -439,7 +443,7 @@ cudaError_t launch_beam_weights(const int8_t *w_re, const int8_t *w_im, int32_t 
 {
     const int bp = beam_padded(B);
     const int n_pad = (int)round_up(N, 128);
-    const int64_t total = (int64_t)F * 8 * bp * n_pad;
+    const int64_t total = (int64_t)F * 8 * bp * n_pad;  // F x 4 Bp rows x 2 n_pad K positions
     int64_t blocks = (total + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     beam_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(w_re, w_im, F, B, N, bp, n_pad, wdev);
@@ -466,8 +470,9 @@ cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a,
             return cudaErrorInvalidValue;
     }
     {
-        cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)a.F * 8 * bp};
-        cuuint64_t strides[1] = {(cuuint64_t)n_pad};
+        // weights [F][4 Bp][2 n_pad]: boxes of 128 K positions x 4 Bp rows
+        cuuint64_t dims[2] = {(cuuint64_t)(2 * n_pad), (cuuint64_t)a.F * 4 * bp};
+        cuuint64_t strides[1] = {(cuuint64_t)(2 * n_pad)};
         cuuint32_t box[2] = {128, (cuuint32_t)(4 * bp)}, estr[2] = {1, 1};
         if (enc(&wm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)wdev, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -499,7 +504,7 @@ cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a,
 struct xbeam_s {
     int32_t N = 0, F = 0, B = 0;
     int device = 0, num_sms = 0;
-    uint8_t *wdev = nullptr;    // [F][2][4 Bp][n_pad] E4M3 weight operands
+    uint8_t *wdev = nullptr;    // [F][4 Bp][2 n_pad] E4M3 weight operand
     int64_t wdev_bytes = 0;
     int8_t *wstage = nullptr;   // device copy of host weights
     int *d_err = nullptr;       // device status word of the kernels
