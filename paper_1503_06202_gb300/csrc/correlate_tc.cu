@@ -359,6 +359,9 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             int2 *out = reinterpret_cast<int2 *>(w.out + (int64_t)w.fl * N * (N + 1));
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u;
             const int64_t jbase = (int64_t)w.J * kTile;
+            // the triangle is written once and not read again here: streaming
+            // stores keep it from evicting the operand planes other tiles
+            // still read from L2
             for (int c = 0; c < kTile; c += 16) {
                 uint32_t re[16], nim[16];
                 tmem_ld16(taddr + c, re);
@@ -373,18 +376,18 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                         int2 old[16];
                         #pragma unroll
                         for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi) old[e] = p[e];
+                            if (e >= e_lo && e < e_hi) old[e] = __ldcs(p + e);
                         #pragma unroll
                         for (int e = 0; e < 16; e++)
                             if (e >= e_lo && e < e_hi)
-                                p[e] = make_int2(old[e].x + __float2int_rn(__uint_as_float(re[e])),
-                                                 old[e].y - __float2int_rn(__uint_as_float(nim[e])));
+                                __stcs(p + e, make_int2(old[e].x + __float2int_rn(__uint_as_float(re[e])),
+                                                        old[e].y - __float2int_rn(__uint_as_float(nim[e]))));
                     } else if (w.mode == kStore) {
                         #pragma unroll
                         for (int e = 0; e < 16; e++)
                             if (e >= e_lo && e < e_hi)
-                                p[e] = make_int2(__float2int_rn(__uint_as_float(re[e])),
-                                                 -__float2int_rn(__uint_as_float(nim[e])));
+                                __stcs(p + e, make_int2(__float2int_rn(__uint_as_float(re[e])),
+                                                        -__float2int_rn(__uint_as_float(nim[e]))));
                     } else {
                         #pragma unroll
                         for (int e = 0; e < 16; e++)
