@@ -382,6 +382,27 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                             if (e >= e_lo && e < e_hi)
                                 __stcs(p + e, make_int2(old[e].x + __float2int_rn(__uint_as_float(re[e])),
                                                         old[e].y - __float2int_rn(__uint_as_float(nim[e]))));
+                    } else if (w.mode == kStore && e_lo <= 0 && e_hi >= 16) {
+                        // interior chunk: 16-byte stores of two pairs where the row allows
+                        int v[32];
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++) {
+                            v[2 * e] = __float2int_rn(__uint_as_float(re[e]));
+                            v[2 * e + 1] = -__float2int_rn(__uint_as_float(nim[e]));
+                        }
+                        if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+                            #pragma unroll
+                            for (int e = 0; e < 16; e += 2)
+                                __stcs(reinterpret_cast<int4 *>(p + e), make_int4(v[2 * e], v[2 * e + 1], v[2 * e + 2],
+                                                                                   v[2 * e + 3]));
+                        } else {
+                            __stcs(p, make_int2(v[0], v[1]));
+                            #pragma unroll
+                            for (int e = 1; e < 15; e += 2)
+                                __stcs(reinterpret_cast<int4 *>(p + e), make_int4(v[2 * e], v[2 * e + 1], v[2 * e + 2],
+                                                                                   v[2 * e + 3]));
+                            __stcs(p + 15, make_int2(v[30], v[31]));
+                        }
                     } else if (w.mode == kStore) {
                         #pragma unroll
                         for (int e = 0; e < 16; e++)
