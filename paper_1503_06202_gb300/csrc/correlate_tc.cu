@@ -371,7 +371,43 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     int2 *p = out + row_base + jbase + c;  // pairs j = jbase + c + e, e = 0..15
                     const int64_t e_lo = i - (jbase + c);  // first e on or above the diagonal
                     const int64_t e_hi = N - (jbase + c);  // first e past the last input
-                    if (w.mode == kAdd) {
+                    if (w.mode == kAdd && e_lo <= 0 && e_hi >= 16) {
+                        // interior chunk: 16-byte loads and stores of two pairs where the row allows;
+                        // all loads issued before any store, so they overlap in flight
+                        const bool al = (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+                        const int e0 = al ? 0 : 1;  // first element of the 16-byte pieces
+                        int4 o4[8];
+                        int2 head = make_int2(0, 0), tail = make_int2(0, 0);
+                        if (!al) {
+                            head = __ldcs(p);
+                            tail = __ldcs(p + 15);
+                        }
+                        #pragma unroll
+                        for (int k = 0; k < 8; k++)
+                            o4[k] = (al || k < 7) ? __ldcs(reinterpret_cast<const int4 *>(p + e0 + 2 * k))
+                                                  : make_int4(0, 0, 0, 0);
+                        int v[32];
+                        #pragma unroll
+                        for (int e = 0; e < 16; e++) {
+                            v[2 * e] = __float2int_rn(__uint_as_float(re[e]));
+                            v[2 * e + 1] = -__float2int_rn(__uint_as_float(nim[e]));
+                        }
+                        if (al) {
+                            #pragma unroll
+                            for (int k = 0; k < 8; k++)
+                                __stcs(reinterpret_cast<int4 *>(p + 2 * k),
+                                       make_int4(o4[k].x + v[4 * k], o4[k].y + v[4 * k + 1], o4[k].z + v[4 * k + 2],
+                                                 o4[k].w + v[4 * k + 3]));
+                        } else {
+                            __stcs(p, make_int2(head.x + v[0], head.y + v[1]));
+                            #pragma unroll
+                            for (int k = 0; k < 7; k++)
+                                __stcs(reinterpret_cast<int4 *>(p + 1 + 2 * k),
+                                       make_int4(o4[k].x + v[4 * k + 2], o4[k].y + v[4 * k + 3], o4[k].z + v[4 * k + 4],
+                                                 o4[k].w + v[4 * k + 5]));
+                            __stcs(p + 15, make_int2(tail.x + v[30], tail.y + v[31]));
+                        }
+                    } else if (w.mode == kAdd) {
                         // all 16 loads issued before any store, so they overlap in flight
                         int2 old[16];
                         #pragma unroll
