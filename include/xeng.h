@@ -104,8 +104,8 @@ XENG_API int64_t xeng_dump(xeng_t h, int32_t *out, void *stream);
  *   visibilities of exactly these n_samples samples, written to `out`
  *   ([F][N(N+1)/2][2] int32), as xeng_push + xeng_dump on a fresh handle
  *   would give, but straight into `out` when it is device memory (no copy of
- *   the triangle).  block as for xeng_push; n_samples <= t_integ (else
- *   XENG_ERR_OVERFLOW).  With device `out` the call is asynchronous on
+ *   the triangle; device `out` must be 8-byte aligned, else XENG_ERR_ARG).
+ *   block as for xeng_push; n_samples <= t_integ (else XENG_ERR_OVERFLOW).  With device `out` the call is asynchronous on
  *   `stream` and leaves any integration in progress on the handle untouched;
  *   with host `out` it returns once the data is there, and needs the handle
  *   to have no integration in progress (else XENG_ERR_ARG).
@@ -123,7 +123,7 @@ XENG_API int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, i
  *     V^g_ij(f) = sum over t with gate[t] == g, valid_i(t), valid_j(t) of x_i conj(x_j)
  *   block: device [n_samples][F][N]; gate: host int32 [n_samples];
  *   valid: device uint8 [n_samples][F][N] or NULL (all usable);
- *   out: device int32 [n_gates][F][N(N+1)/2][2] (overwritten);
+ *   out: device int32 [n_gates][F][N(N+1)/2][2] (overwritten, 8-byte aligned);
  *   counts: device int32 [n_gates][F][N] or NULL.
  *   n_samples <= min(t_integ, 65536) (else XENG_ERR_OVERFLOW / XENG_ERR_RANGE);
  *   tensor engine only.  Asynchronous on `stream` after reading `gate`.
@@ -260,7 +260,7 @@ typedef struct {
     int32_t n_freq;         /* F of this job, >= 1                                */
     int64_t n_samples;      /* T of this job, 1..XENG_MAX_T_INTEG                 */
     const uint8_t *block;   /* device memory [T][F][N], caller-owned              */
-    int32_t *out;           /* device memory [F][N(N+1)/2][2] int32, caller-owned */
+    int32_t *out;           /* device memory [F][N(N+1)/2][2] int32, caller-owned, 8-byte aligned */
 } xeng_job_t;
 
 #define XENG_SCHED_LPT         0  /* longest items first onto the least-loaded CTA */
@@ -428,8 +428,8 @@ XENG_API void xserve_destroy(xserve_t sv);
  *   the device-wide synchronization cudaMalloc / cudaFree may cause.
  *
  *   block: [n_samples][n_freq][n_inputs] bytes, device memory (caller-owned).
- *   out:   [n_freq][N(N+1)/2][2] int32, device memory (caller-owned);
- *          overwritten (n_samples == 0 writes zeros).
+ *   out:   [n_freq][N(N+1)/2][2] int32, device memory (caller-owned),
+ *          8-byte aligned; overwritten (n_samples == 0 writes zeros).
  *   Working memory is one library-owned __device__ array of
  *   XENG_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until
  *   the process exits.  Sizes beyond what it holds are rejected with

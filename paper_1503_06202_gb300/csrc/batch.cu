@@ -336,7 +336,7 @@ int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_o
     }
     for (int j = 0; j < n_jobs; j++) {
         const xeng_job_t &jb = jobs[j];
-        if (!jb.block || !jb.out) return XENG_ERR_ARG;
+        if (!jb.block || !jb.out || (reinterpret_cast<uintptr_t>(jb.out) & 7) != 0) return XENG_ERR_ARG;
         if (jb.n_inputs < 1 || jb.n_inputs > XENG_MAX_INPUTS || jb.n_freq < 1 || jb.n_samples < 1 ||
             jb.n_samples > XENG_MAX_T_INTEG)
             return XENG_ERR_RANGE;

@@ -426,18 +426,33 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                             v[2 * e] = __float2int_rn(__uint_as_float(re[e]));
                             v[2 * e + 1] = -__float2int_rn(__uint_as_float(nim[e]));
                         }
-                        if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-                            #pragma unroll
-                            for (int e = 0; e < 16; e += 2)
-                                __stcs(reinterpret_cast<int4 *>(p + e), make_int4(v[2 * e], v[2 * e + 1], v[2 * e + 2],
-                                                                                   v[2 * e + 3]));
-                        } else {
-                            __stcs(p, make_int2(v[0], v[1]));
-                            #pragma unroll
-                            for (int e = 1; e < 15; e += 2)
-                                __stcs(reinterpret_cast<int4 *>(p + e), make_int4(v[2 * e], v[2 * e + 1], v[2 * e + 2],
-                                                                                   v[2 * e + 3]));
-                            __stcs(p + 15, make_int2(v[30], v[31]));
+                        // 32-byte stores of four pairs, with 8- and 16-byte pieces at the ends by the
+                        // row start's offset in a 32-byte sector
+                        auto st8 = [&](int e) { __stcs(p + e, make_int2(v[2 * e], v[2 * e + 1])); };
+                        auto st16 = [&](int e) {
+                            __stcs(reinterpret_cast<int4 *>(p + e), make_int4(v[2 * e], v[2 * e + 1], v[2 * e + 2],
+                                                                             v[2 * e + 3]));
+                        };
+                        auto st32 = [&](int e) {
+                            asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                                         ::"l"(p + e), "r"(v[2 * e]), "r"(v[2 * e + 1]), "r"(v[2 * e + 2]),
+                                         "r"(v[2 * e + 3]), "r"(v[2 * e + 4]), "r"(v[2 * e + 5]), "r"(v[2 * e + 6]),
+                                         "r"(v[2 * e + 7])
+                                         : "memory");
+                        };
+                        switch ((reinterpret_cast<uintptr_t>(p) >> 3) & 3) {
+                            case 0:
+                                st32(0); st32(4); st32(8); st32(12);
+                                break;
+                            case 1:
+                                st8(0); st16(1); st32(3); st32(7); st32(11); st8(15);
+                                break;
+                            case 2:
+                                st16(0); st32(2); st32(6); st32(10); st16(14);
+                                break;
+                            default:
+                                st8(0); st32(1); st32(5); st32(9); st16(13); st8(15);
+                                break;
                         }
                     } else if (w.mode == kStore) {
                         #pragma unroll

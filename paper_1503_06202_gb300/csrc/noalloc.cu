@@ -72,7 +72,7 @@ bool on_device(const void *p)
 extern "C" int xeng_correlate_noalloc(const uint8_t *block, int64_t n_samples, int32_t n_freq, int32_t n_inputs,
                                       int32_t *out, void *stream)
 {
-    if (!block || !out) return XENG_ERR_ARG;
+    if (!block || !out || (reinterpret_cast<uintptr_t>(out) & 7) != 0) return XENG_ERR_ARG;
     if (n_inputs < 1 || n_inputs > XENG_MAX_INPUTS || n_freq < 1 || n_samples < 0) return XENG_ERR_RANGE;
     const int64_t n_pad = round_up(n_inputs, kTile);
     const int64_t t_pad = round_up(n_samples > 0 ? n_samples : 1, kTile);

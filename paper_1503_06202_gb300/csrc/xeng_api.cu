@@ -739,6 +739,7 @@ int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *o
     cudaStream_t s = (cudaStream_t)stream;
     const bool dev_out = is_device_pointer(out);
     if (!dev_out && (h->samples > 0 || !h->fresh)) return XENG_ERR_ARG;  // would clobber an open integration
+    if (dev_out && (reinterpret_cast<uintptr_t>(out) & 7) != 0) return XENG_ERR_ARG;  // kernels store (Re, Im) pairs
     const int64_t bytes = acc_bytes(h);
     cudaError_t e = cudaSuccess;
     if (n_samples == 0) {
@@ -781,7 +782,7 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
     if (h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_ARG;
     if (h->shifted) return XENG_ERR_UNSUPPORTED;
     if (!is_device_pointer(out) || (counts && !is_device_pointer(counts)) || (valid && !is_device_pointer(valid)) ||
-        (n_samples > 0 && !is_device_pointer(block)))
+        (n_samples > 0 && !is_device_pointer(block)) || (reinterpret_cast<uintptr_t>(out) & 7) != 0)
         return XENG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = h->N, F = h->F;

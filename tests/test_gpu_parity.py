@@ -352,3 +352,20 @@ def test_bounded_wait_times_out_with_status_and_context_stays_usable():
     rng = np.random.default_rng(31)
     blk = rng.integers(0, 256, size=(200, 1, 40), dtype=np.uint8)
     assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "after time-out self-test")
+
+
+def test_misaligned_device_output_is_refused():
+    # the kernels store (Re, Im) pairs of int32: a device `out` that is not
+    # 8-byte aligned is an argument error, not a fault
+    rng = np.random.default_rng(77)
+    T, F, N = 64, 1, 32
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    eng = xe.XEngine(N, F, T)
+    base = torch.zeros(F * N * (N + 1) + 2, dtype=torch.int32, device="cuda")
+    out = base[1:]  # 4 bytes past an aligned start
+    assert xe.xeng_correlate(eng.h, to_dev(blk), T, out) == xe.XENG_ERR_ARG
+    assert xe.xeng_correlate(eng.h, to_dev(blk), T, base[2:]) == xe.XENG_OK
+    torch.cuda.synchronize()
+    got = base[2:].view(F, N * (N + 1) // 2, 2).cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, oracle.correlate(blk))
+    eng.close()
