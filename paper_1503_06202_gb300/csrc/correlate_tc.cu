@@ -372,40 +372,64 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     const int64_t e_lo = i - (jbase + c);  // first e on or above the diagonal
                     const int64_t e_hi = N - (jbase + c);  // first e past the last input
                     if (w.mode == kAdd && e_lo <= 0 && e_hi >= 16) {
-                        // interior chunk: 16-byte loads and stores of two pairs where the row allows;
-                        // all loads issued before any store, so they overlap in flight
-                        const bool al = (reinterpret_cast<uintptr_t>(p) & 15) == 0;
-                        const int e0 = al ? 0 : 1;  // first element of the 16-byte pieces
-                        int4 o4[8];
-                        int2 head = make_int2(0, 0), tail = make_int2(0, 0);
-                        if (!al) {
-                            head = __ldcs(p);
-                            tail = __ldcs(p + 15);
-                        }
-                        #pragma unroll
-                        for (int k = 0; k < 8; k++)
-                            o4[k] = (al || k < 7) ? __ldcs(reinterpret_cast<const int4 *>(p + e0 + 2 * k))
-                                                  : make_int4(0, 0, 0, 0);
-                        int v[32];
+                        // interior chunk: the 16 pairs read and written in 32-byte pieces of four
+                        // pairs, 8- and 16-byte pieces at the ends by the row start's offset in a
+                        // 32-byte sector; all loads issued before any store
+                        int v[32], o[32];
                         #pragma unroll
                         for (int e = 0; e < 16; e++) {
                             v[2 * e] = __float2int_rn(__uint_as_float(re[e]));
                             v[2 * e + 1] = -__float2int_rn(__uint_as_float(nim[e]));
                         }
-                        if (al) {
-                            #pragma unroll
-                            for (int k = 0; k < 8; k++)
-                                __stcs(reinterpret_cast<int4 *>(p + 2 * k),
-                                       make_int4(o4[k].x + v[4 * k], o4[k].y + v[4 * k + 1], o4[k].z + v[4 * k + 2],
-                                                 o4[k].w + v[4 * k + 3]));
-                        } else {
-                            __stcs(p, make_int2(head.x + v[0], head.y + v[1]));
-                            #pragma unroll
-                            for (int k = 0; k < 7; k++)
-                                __stcs(reinterpret_cast<int4 *>(p + 1 + 2 * k),
-                                       make_int4(o4[k].x + v[4 * k + 2], o4[k].y + v[4 * k + 3], o4[k].z + v[4 * k + 4],
-                                                 o4[k].w + v[4 * k + 5]));
-                            __stcs(p + 15, make_int2(tail.x + v[30], tail.y + v[31]));
+                        auto ld8 = [&](int e) {
+                            const int2 x = __ldcs(p + e);
+                            o[2 * e] = x.x;
+                            o[2 * e + 1] = x.y;
+                        };
+                        auto ld16 = [&](int e) {
+                            const int4 x = __ldcs(reinterpret_cast<const int4 *>(p + e));
+                            o[2 * e] = x.x;
+                            o[2 * e + 1] = x.y;
+                            o[2 * e + 2] = x.z;
+                            o[2 * e + 3] = x.w;
+                        };
+                        auto ld32 = [&](int e) {
+                            asm volatile("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                         : "=r"(o[2 * e]), "=r"(o[2 * e + 1]), "=r"(o[2 * e + 2]), "=r"(o[2 * e + 3]),
+                                           "=r"(o[2 * e + 4]), "=r"(o[2 * e + 5]), "=r"(o[2 * e + 6]), "=r"(o[2 * e + 7])
+                                         : "l"(p + e));
+                        };
+                        auto st8 = [&](int e) { __stcs(p + e, make_int2(o[2 * e] + v[2 * e], o[2 * e + 1] + v[2 * e + 1])); };
+                        auto st16 = [&](int e) {
+                            __stcs(reinterpret_cast<int4 *>(p + e),
+                                   make_int4(o[2 * e] + v[2 * e], o[2 * e + 1] + v[2 * e + 1], o[2 * e + 2] + v[2 * e + 2],
+                                             o[2 * e + 3] + v[2 * e + 3]));
+                        };
+                        auto st32 = [&](int e) {
+                            asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                                         ::"l"(p + e), "r"(o[2 * e] + v[2 * e]), "r"(o[2 * e + 1] + v[2 * e + 1]),
+                                         "r"(o[2 * e + 2] + v[2 * e + 2]), "r"(o[2 * e + 3] + v[2 * e + 3]),
+                                         "r"(o[2 * e + 4] + v[2 * e + 4]), "r"(o[2 * e + 5] + v[2 * e + 5]),
+                                         "r"(o[2 * e + 6] + v[2 * e + 6]), "r"(o[2 * e + 7] + v[2 * e + 7])
+                                         : "memory");
+                        };
+                        switch ((reinterpret_cast<uintptr_t>(p) >> 3) & 3) {
+                            case 0:
+                                ld32(0); ld32(4); ld32(8); ld32(12);
+                                st32(0); st32(4); st32(8); st32(12);
+                                break;
+                            case 1:
+                                ld8(0); ld16(1); ld32(3); ld32(7); ld32(11); ld8(15);
+                                st8(0); st16(1); st32(3); st32(7); st32(11); st8(15);
+                                break;
+                            case 2:
+                                ld16(0); ld32(2); ld32(6); ld32(10); ld16(14);
+                                st16(0); st32(2); st32(6); st32(10); st16(14);
+                                break;
+                            default:
+                                ld8(0); ld32(1); ld32(5); ld32(9); ld16(13); ld8(15);
+                                st8(0); st32(1); st32(5); st32(9); st16(13); st8(15);
+                                break;
                         }
                     } else if (w.mode == kAdd) {
                         // all 16 loads issued before any store, so they overlap in flight
