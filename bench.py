@@ -42,7 +42,7 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 # one ncu capture of the 16-channel slice of the same (N, T) shape; traffic
 # grows in proportion to channels.  Keyed by (N, T); must be re-taken (or
 # removed) whenever the kernel changes.
-CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (660.2048e6 + 242.233344e6) / 16}
+CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (606.144e6 + 243.47008e6) / 16}
 
 
 def max_over_ranks(x, dist=None):
