@@ -411,6 +411,7 @@ def main():
     ap.add_argument("--no-gate", action="store_true", help="skip the gating + flags measurement")
     ap.add_argument("--no-beam", action="store_true", help="skip the beamforming measurement")
     ap.add_argument("--no-secondary", action="store_true", help="skip the Pathfinder-rate measurement")
+    ap.add_argument("--no-dp4a", action="store_true", help="skip the plain dp4a comparison")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-max-blocks", type=int, default=32)
@@ -618,9 +619,36 @@ def main():
                      "steps": reps2, "kernel": "correlate_fused256_kernel (decode fused into the correlation)"}
         eng2.close()
         del blk2, out2
+    # the plain single-instance CUDA-core (dp4a) correlator on the same GPU, on
+    # a channel sample of the same block (its full step takes seconds): its
+    # rate, and whether its output equals the tensor path's for those channels
+    plain_dp4a = None
+    if args.engine == "tensor" and not args.no_dp4a:
+        fs = min(F, 16)
+        with torch.cuda.stream(stream):
+            blk_s = block[:, :fs, :].contiguous()
+            out_s = torch.empty((fs, B, 2), dtype=torch.int32, device="cuda")
+        eng_d = xe.XEngine(N, fs, T, xe.XENG_ENGINE_DP4A)
+        eng_d.correlate(blk_s, out_s, T, stream)
+        reps_d = 3
+        ev0.record(stream)
+        for _ in range(reps_d):
+            eng_d.correlate(blk_s, out_s, T, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        d_ms = ev0.elapsed_time(ev1) / reps_d
+        d_full_ms = d_ms * F / fs
+        plain_dp4a = {"kernel": "correlate_dp4a_kernel", "sample": "channels 0..%d of the same block, %d runs" % (fs - 1, reps_d),
+                      "ms_per_sample_run": d_ms, "ms_per_step_extrapolated": d_full_ms,
+                      "value": useful_ops(T, fs, N) / (d_ms * 1e-3) / 1e12, "unit": "TOPS",
+                      "equals_tensor_output": bool(torch.equal(out_s, out[:fs]))}
+        eng_d.close()
+        del blk_s, out_s
     ms = max_over_ranks(ms, dist)
     ops = useful_ops(T, F, N)
     value = whole_job_rate(ops, ms * 1e-3, world) / 1e12
+    if plain_dp4a:
+        plain_dp4a["tensor_path_speedup"] = plain_dp4a["ms_per_step_extrapolated"] / ms
 
     # dominant kernel: the correlation launches, timed live over the timed region
     peaks, peak_src = load_peaks()
@@ -700,7 +728,7 @@ def main():
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
                 "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "gating": gating, "beamform": beam,
-                "pathfinder_rate": secondary,
+                "pathfinder_rate": secondary, "plain_dp4a": plain_dp4a,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "decode_roofline": decode_roof,
                 "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}

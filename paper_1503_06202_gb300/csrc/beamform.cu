@@ -8,17 +8,24 @@
 // x_i decoded from the 4+4-bit offset bytes (Sec. II-A), w = w_re + i w_im
 // with int8 parts.  As real GEMMs with M = 128 samples and K = inputs:
 //     Re y = X_re W_re^T - X_im W_im^T,   Im y = X_re W_im^T + X_im W_re^T.
-// E4M3 holds -8..15 exactly but not all of int8, so a weight part v is split
-// into v = 16 hi + lo, hi = v >> 4 in [-8, 8], lo = v & 15 in [0, 15].  The A
-// operand interleaves the parts of each input along K (K position 2i holds
-// Im x_i, 2i + 1 holds Re x_i: the order the nibble lookup produces them in),
-// so one MMA per 32 K positions covers both; the B operand's rows are the hi
-// parts of the Re-y weights (-w_im, w_re interleaved), of the Im-y weights
-// (w_re, w_im), then the lo parts of both (4 Bp rows, Bp = beams rounded up),
-// and one 128 x 4Bp f32 accumulator collects the hi and lo parts of Re y and
-// Im y side by side; the epilogue forms y = 16 hi + lo in int32.  Products are integers of
-// magnitude <= 8 * 15 and partial sums stay below 240 N <= 2^20, so the f32
-// accumulation is exact.
+// The samples enter undecoded: each nibble u (0..15) is the FP6 E2M3 code of
+// u / 8 (see raw4_to_e2m3_pairs), and with x = u - 8
+//     Re y = sum_i (w_re u_re - w_im u_im) - 8 sum_i (w_re - w_im),
+//     Im y = sum_i (w_re u_im + w_im u_re) - 8 sum_i (w_re + w_im),
+// whose second terms, one pair per (channel, beam), are computed once with
+// the weights.  E2M3 holds the integers -15..15 / 8 but not all of int8, so a
+// weight part v is split into v = 16 hi + lo, hi = v >> 4 in [-8, 8], lo =
+// v & 15 in [0, 15], each the E2M3 code of part / 8.  The A operand
+// interleaves the parts of each input along K (K position 2i holds Im u_i,
+// 2i + 1 holds Re u_i: the order of the bytes' nibbles), so one MMA per 32 K
+// positions covers both; the B operand's rows are the hi parts of the Re-y
+// weights (-w_im, w_re interleaved), of the Im-y weights (w_re, w_im), then
+// the lo parts of both (4 Bp rows, Bp = beams rounded up), and one 128 x 4Bp
+// f32 accumulator collects the hi and lo parts of Re y and Im y side by side;
+// the epilogue scales them by 64 and forms y = 16 hi + lo - correction in
+// int32.  Products are u v / 64 with u v an integer of magnitude <= 15 * 15
+// and partial sums stay below 450 N / 64 (N <= 4096: 450 N < 2^24), so the
+// f32 accumulation is exact.
 //
 // One persistent CTA per SM; work items = (channel, 128-sample tile):
 //   warp 0        TMA producer of the 128-input slices of both weight
@@ -29,7 +36,7 @@
 //   warps 2..13   converters in three groups of four warps (one per TMEM lane
 //                 quadrant); group g takes the steps g, g + 3, ...: each thread
 //                 reads one sample row (128 inputs) of the step's raw tile from
-//                 shared memory, decodes it to E4M3 codes and writes them,
+//                 shared memory, splits it into E2M3 nibble codes and writes them,
 //                 real and imaginary parts interleaved along K, into the
 //                 group's TMEM slot with tcgen05.st
 //   warps 14..17  epilogue: TMEM -> int32 beams [T][F][B][2] in HBM
@@ -82,8 +89,9 @@ struct BfCfg {
     static constexpr int kXS = kGroups * kSlots;                 // X slots in all
     static constexpr int kBars = 2 * kR + 2 * kXS + 2 * kSW + 2 * kAcc + 1;
     static constexpr size_t kSmem = 1024 + (size_t)kR * kRawBytes + (size_t)kSW * kWStageBytes + kBars * 8 + 16;
-    // kind::f8f6f4, D f32, A and B E4M3 K-major, N and M = 128
-    static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // kind::f8f6f4, D f32, A and B E2M3 (type 3) K-major, N and M = 128
+    static constexpr uint32_t kIdesc = (1u << 4) | (3u << 7) | (3u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                                       ((uint32_t)(128 >> 4) << 24);
     static_assert(kSmem <= 232448, "shared memory over the per-CTA limit");
 };
 
@@ -269,7 +277,7 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             (void)mbar_wait(drain_bar, 0u, err, kDevTimeoutMma);
         }
     } else if (warp < kEpiWarp0) {
-        // ---------------- converters: raw tile (smem) -> E4M3 codes in TMEM ----------------
+        // ---------------- converters: raw tile (smem) -> E2M3 nibble codes in TMEM ----------------
         // Thread = one sample row of a step (its TMEM lane): the row's 128
         // bytes from the 128-byte-swizzled raw tile (conflict-free: lanes t and
         // t + 8 share a chunk position, the minimum for 16-byte reads).
@@ -297,10 +305,8 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
                 const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
                 uint32_t col[8];
                 #pragma unroll
-                for (int j = 0; j < 4; j++) {  // inputs 4j .. 4j + 3 of the 16
-                    col[2 * j] = nib4_to_e4m3(wd[j]);            // Im, Re of inputs 4j, 4j + 1
-                    col[2 * j + 1] = nib4_to_e4m3(wd[j] >> 16);  // Im, Re of inputs 4j + 2, 4j + 3
-                }
+                for (int j = 0; j < 4; j++)  // inputs 4j .. 4j + 3 of the 16: (Im, Re) of 4j, 4j + 1 | 4j + 2, 4j + 3
+                    raw4_to_e2m3_pairs(wd[j], col[2 * j], col[2 * j + 1]);
                 tmem_st8(xs + h * 8, col);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -325,6 +331,7 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             const int64_t t = (int64_t)tt * 128 + row;
             int2 *o = reinterpret_cast<int2 *>(a.out) + (t * a.F + f) * a.B;
             int4 *o4 = reinterpret_cast<int4 *>(o);  // two beams per store when B is even
+            const int2 *corr = reinterpret_cast<const int2 *>(a.corr) + (int64_t)f * kBp;  // offset terms of the beams
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::kN);
             #pragma unroll
             for (int b0 = 0; b0 < kBp; b0 += G) {
@@ -338,13 +345,16 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
                 }
                 tmem_ld_wait();
                 if (t < a.T) {
+                    // accumulators hold sums of u v / 64: x 64 is exact
                     int2 y[G];
                     #pragma unroll
-                    for (int e = 0; e < G; e++)
-                        y[e] = make_int2(16 * __float2int_rn(__uint_as_float(hre[e])) +
-                                             __float2int_rn(__uint_as_float(lre[e])),
-                                         16 * __float2int_rn(__uint_as_float(him[e])) +
-                                             __float2int_rn(__uint_as_float(lim[e])));
+                    for (int e = 0; e < G; e++) {
+                        const int2 c = __ldg(corr + b0 + e);
+                        y[e] = make_int2(16 * __float2int_rn(64.0f * __uint_as_float(hre[e])) +
+                                             __float2int_rn(64.0f * __uint_as_float(lre[e])) - c.x,
+                                         16 * __float2int_rn(64.0f * __uint_as_float(him[e])) +
+                                             __float2int_rn(64.0f * __uint_as_float(lim[e])) - c.y);
+                    }
                     if (a.vec16) {
                         #pragma unroll
                         for (int e = 0; e < G; e += 2)
@@ -392,31 +402,87 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     }
 }
 
-// Weight operand from int8 weights [F][B][N] (re, im): [F][4 Bp][2 n_pad] E4M3
-// codes; row g * Bp + b holds the hi (g = 0, 1) or lo (g = 2, 3) part of the
+// Weight operand from int8 weights [F][B][N] (re, im): [F][4 Bp][2 n_pad]
+// bytes; row g * Bp + b holds the hi (g = 0, 1) or lo (g = 2, 3) part of the
 // Re-y (g even) or Im-y (g odd) weights of beam b, K position 2i the factor of
 // Im x_i and 2i + 1 that of Re x_i.  Rows b >= B and inputs i >= N are zero.
+// Each part v (|v| <= 15) is the E2M3 code of v / 8 (sign bit 5, |v| in bits
+// 0..3).  In shared memory the tensor core reads an FP6 operand as 16 codes
+// packed in the first 12 bytes of each 16-byte chunk (code j in bits 6j ..
+// 6j + 5, little-endian) followed by 4 unused bytes -- measured on GB300 --
+// so each thread packs one chunk of 16 K positions; the chunk grid, and so
+// the tensor-map boxes and the swizzle, are those of one byte per element.
 __global__ void beam_weights_kernel(const int8_t *__restrict__ w_re, const int8_t *__restrict__ w_im, int32_t F,
-                                    int32_t B, int32_t N, int32_t bp, int32_t n_pad, uint8_t *__restrict__ wdev)
+                                    int32_t B, int32_t N, int32_t bp, int32_t n_pad, uint4 *__restrict__ wdev)
 {
-    const int64_t total = (int64_t)F * 4 * bp * 2 * n_pad;
+    const int chunks_per_row = (2 * n_pad) / 16;
+    const int64_t total = (int64_t)F * 4 * bp * chunks_per_row;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-        const int kp = (int)(k % (2 * n_pad));
-        const int i = kp >> 1;
-        const bool of_re = (kp & 1) != 0;  // multiplies Re x_i (else Im x_i)
-        const int64_t rowk = k / (2 * n_pad);
+        const int ch = (int)(k % chunks_per_row);
+        const int64_t rowk = k / chunks_per_row;
         const int rr = (int)(rowk % (4 * bp));
         const int64_t f = rowk / (4 * bp);
         const int g = rr / bp, b = rr % bp;
-        int v = 0;
-        if (b < B && i < N) {
-            const int64_t src = (f * B + b) * N + i;
-            const int wr = w_re[src], wi = w_im[src];
-            // Re y += Re x w_re - Im x w_im;  Im y += Re x w_im + Im x w_re
-            const int base = (g & 1) ? (of_re ? wi : wr) : (of_re ? wr : -wi);
-            v = g < 2 ? (base >> 4) : (base & 15);
+        uint64_t lo = 0, hi = 0;  // bits 0..63 and 64..95 of the packed chunk
+        for (int j = 0; j < 16; j++) {
+            const int kp = ch * 16 + j;
+            const int i = kp >> 1;
+            const bool of_re = (kp & 1) != 0;  // multiplies Re x_i (else Im x_i)
+            int v = 0;
+            if (b < B && i < N) {
+                const int64_t src = (f * B + b) * N + i;
+                const int wr = w_re[src], wi = w_im[src];
+                // Re y += Re x w_re - Im x w_im;  Im y += Re x w_im + Im x w_re
+                const int base = (g & 1) ? (of_re ? wi : wr) : (of_re ? wr : -wi);
+                v = g < 2 ? (base >> 4) : (base & 15);
+            }
+            const uint64_t code = (uint64_t)(v < 0 ? (0x20 | -v) : v);
+            const int bit = 6 * j;
+            if (bit < 64) lo |= code << bit;
+            if (bit >= 64)
+                hi |= code << (bit - 64);
+            else if (bit + 6 > 64)
+                hi |= code >> (64 - bit);  // the code straddling bit 64
         }
-        wdev[k] = (uint8_t)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
+        wdev[k] = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, 0u);
+    }
+}
+
+// Offset terms per (channel, beam): corr[f][b] = (8 sum_i (w_re - w_im),
+// 8 sum_i (w_re + w_im)), zero for padding beams b >= B.  One block per
+// (channel, padded beam).
+__global__ void beam_corr_kernel(const int8_t *__restrict__ w_re, const int8_t *__restrict__ w_im, int32_t B,
+                                 int32_t N, int32_t bp, int2 *__restrict__ corr)
+{
+    const int64_t fb = blockIdx.x;
+    const int b = (int)(fb % bp);
+    const int64_t f = fb / bp;
+    int sre = 0, sim = 0;
+    if (b < B) {
+        const int64_t src = (f * B + b) * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int wr = w_re[src + i], wi = w_im[src + i];
+            sre += wr - wi;
+            sim += wr + wi;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sre += __shfl_xor_sync(0xffffffffu, sre, o);
+        sim += __shfl_xor_sync(0xffffffffu, sim, o);
+    }
+    __shared__ int red[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = sre;
+        red[1][threadIdx.x >> 5] = sim;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int r0 = 0, r1 = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+            r0 += red[0][k];
+            r1 += red[1][k];
+        }
+        corr[fb] = make_int2(8 * r0, 8 * r1);
     }
 }
 
@@ -439,20 +505,26 @@ int beam_padded(int32_t n_beams)
 }
 
 cudaError_t launch_beam_weights(const int8_t *w_re, const int8_t *w_im, int32_t F, int32_t B, int32_t N,
-                                uint8_t *wdev, cudaStream_t s)
+                                uint8_t *wdev, int32_t *corr, cudaStream_t s)
 {
     const int bp = beam_padded(B);
     const int n_pad = (int)round_up(N, 128);
-    const int64_t total = (int64_t)F * 8 * bp * n_pad;  // F x 4 Bp rows x 2 n_pad K positions
+    const int64_t total = (int64_t)F * 8 * bp * n_pad / 16;  // 16-position chunks of F x 4 Bp rows x 2 n_pad
     int64_t blocks = (total + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    beam_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(w_re, w_im, F, B, N, bp, n_pad, wdev);
+    beam_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(w_re, w_im, F, B, N, bp, n_pad,
+                                                         reinterpret_cast<uint4 *>(wdev));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    beam_corr_kernel<<<(unsigned)((int64_t)F * bp), 128, 0, s>>>(w_re, w_im, B, N, bp, reinterpret_cast<int2 *>(corr));
     return cudaGetLastError();
 }
 
-cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a, int num_sms, cudaStream_t s)
+cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, const int32_t *corr, BfArgs a, int num_sms,
+                            cudaStream_t s)
 {
     if (a.T <= 0) return cudaSuccess;
+    a.corr = corr;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     const int bp = beam_padded(a.B);
@@ -504,8 +576,9 @@ cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a,
 struct xbeam_s {
     int32_t N = 0, F = 0, B = 0;
     int device = 0, num_sms = 0;
-    uint8_t *wdev = nullptr;    // [F][4 Bp][2 n_pad] E4M3 weight operand
+    uint8_t *wdev = nullptr;    // [F][4 Bp][2 n_pad] E2M3 weight operand
     int64_t wdev_bytes = 0;
+    int32_t *corr = nullptr;    // [F][Bp][2] offset terms of the beams
     int8_t *wstage = nullptr;   // device copy of host weights
     int *d_err = nullptr;       // device status word of the kernels
     int *h_err = nullptr;       // pinned mirror, refreshed after each run
@@ -565,7 +638,10 @@ int xbeam_create(int32_t n_inputs, int32_t n_freq, int32_t n_beams, xbeam_t *out
     b->num_sms = prop.multiProcessorCount;
     b->wdev_bytes = (int64_t)n_freq * 8 * xeng::beam_padded(n_beams) * xeng::round_up(n_inputs, 128);
     cudaError_t e = cudaMalloc(&b->wdev, (size_t)b->wdev_bytes);
-    if (e == cudaSuccess) e = cudaMemset(b->wdev, 0, (size_t)b->wdev_bytes);  // E4M3 +0: all weights zero
+    if (e == cudaSuccess) e = cudaMemset(b->wdev, 0, (size_t)b->wdev_bytes);  // E2M3 +0: all weights zero
+    const size_t corr_bytes = (size_t)n_freq * xeng::beam_padded(n_beams) * 2 * sizeof(int32_t);
+    if (e == cudaSuccess) e = cudaMalloc(&b->corr, corr_bytes);
+    if (e == cudaSuccess) e = cudaMemset(b->corr, 0, corr_bytes);  // and so are their offset terms
     if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(int));
@@ -601,7 +677,8 @@ int xbeam_set_weights(xbeam_t b, const int8_t *w_re, const int8_t *w_im, void *s
         if (e == cudaSuccess && !dim) e = cudaMemcpyAsync(b->wstage + n, w_im, (size_t)n, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return (b->sticky = bf_status(e));
     }
-    e = xeng::launch_beam_weights(dre ? w_re : b->wstage, dim ? w_im : b->wstage + n, b->F, b->B, b->N, b->wdev, s);
+    e = xeng::launch_beam_weights(dre ? w_re : b->wstage, dim ? w_im : b->wstage + n, b->F, b->B, b->N, b->wdev,
+                                  b->corr, s);
     // host weights may be reused by the caller at once
     if (e == cudaSuccess && (!dre || !dim)) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return (b->sticky = bf_status(e));
@@ -626,7 +703,7 @@ int xbeam_run(xbeam_t b, const uint8_t *block, int64_t n_samples, int32_t *out, 
     a.B = b->B;
     a.out = out;
     a.err = b->d_err;
-    cudaError_t e = xeng::launch_beamform(block, b->wdev, a, b->num_sms, s);
+    cudaError_t e = xeng::launch_beamform(block, b->wdev, b->corr, a, b->num_sms, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return (b->sticky = bf_status(e));
     return XENG_OK;
@@ -637,6 +714,7 @@ void xbeam_destroy(xbeam_t b)
     if (!b) return;
     cudaDeviceSynchronize();
     cudaFree(b->wdev);
+    cudaFree(b->corr);
     cudaFree(b->wstage);
     cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);

@@ -65,6 +65,22 @@ __device__ __forceinline__ uint32_t nib4_to_e4m3(uint32_t x)
     return (pos & ~m) | (neg & m) | ((m << 1) & 0x80808080u);
 }
 
+// Raw offset nibbles as FP6 E2M3 codes, without decoding: in E2M3 (sign, two
+// exponent bits with bias 1, three mantissa bits) the subnormal binade and the
+// first normal binade share the spacing 1/8, so the code whose low four bits
+// are a nibble u (0..15) and whose top two bits are clear has the value u / 8
+// exactly.  A product of two such operands is u u' / 64 and the offset
+// (value = u - 8) is applied afterwards in integer arithmetic.  One word of
+// four raw bytes (inputs 0..3 of one sample; high nibble Re, low nibble Im)
+// gives the interleaved (Im, Re) codes of inputs 0, 1 and of inputs 2, 3.
+__device__ __forceinline__ void raw4_to_e2m3_pairs(uint32_t w, uint32_t &c01, uint32_t &c23)
+{
+    const uint32_t lo = w & 0x0F0F0F0Fu;         // Im nibbles of inputs 0..3
+    const uint32_t hi = (w >> 4) & 0x0F0F0F0Fu;  // Re nibbles of inputs 0..3
+    c01 = __byte_perm(lo, hi, 0x5140);           // Im0 Re0 Im1 Re1
+    c23 = __byte_perm(lo, hi, 0x7362);           // Im2 Re2 Im3 Re3
+}
+
 // Word of 4 samples (bytes = times t..t+3 of one input) -> (real codes, imag codes).
 __device__ __forceinline__ void decode_word(uint32_t c, uint32_t &re, uint32_t &im)
 {

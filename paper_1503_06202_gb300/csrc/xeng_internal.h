@@ -118,12 +118,14 @@ struct BfArgs {
     int32_t vec16 = 0;      // B even and out 16-byte aligned: two beams per store
     const uint8_t *block = nullptr;  // [T][F][N]
     int32_t *out = nullptr; // [T][F][B][2]
+    const int32_t *corr = nullptr;  // [F][Bp][2] offset terms (8 sum(w_re - w_im), 8 sum(w_re + w_im))
     int *err = nullptr;
 };
 int beam_padded(int32_t n_beams);  // 4, 8, 16, 32 or 64
 cudaError_t launch_beam_weights(const int8_t *w_re, const int8_t *w_im, int32_t F, int32_t B, int32_t N,
-                                uint8_t *wdev, cudaStream_t s);
-cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, BfArgs a, int num_sms, cudaStream_t s);
+                                uint8_t *wdev, int32_t *corr, cudaStream_t s);
+cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, const int32_t *corr, BfArgs a, int num_sms,
+                            cudaStream_t s);
 
 cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s);
 
