@@ -22,8 +22,8 @@
 // weights (-w_im, w_re interleaved), of the Im-y weights (w_re, w_im), then
 // the lo parts of both (4 Bp rows, Bp = beams rounded up), and one 128 x 4Bp
 // f32 accumulator collects the hi and lo parts of Re y and Im y side by side;
-// the epilogue scales them by 64 and forms y = 16 hi + lo - correction in
-// int32.  Products are u v / 64 with u v an integer of magnitude <= 15 * 15
+// the epilogue forms y = 64 (16 hi + lo) - correction in int32 (reading the
+// scaled integers out of the float bits, see the epilogue).  Products are u v / 64 with u v an integer of magnitude <= 15 * 15
 // and partial sums stay below 450 N / 64 (N <= 4096: 450 N < 2^24), so the
 // f32 accumulation is exact.
 //
@@ -68,9 +68,15 @@ constexpr int kEpiWarp0 = 2 + kConvWarps;            // 4 epilogue warps (one pe
 constexpr int kRawProdWarp = kEpiWarp0 + 4;          // TMA producer of the raw tiles
 constexpr int kBfThreads = 32 * (kRawProdWarp + 1);
 constexpr int kRawBytes = 128 * 128;                 // 128 samples x 128 inputs of one channel
-constexpr int kR = 2 * kGroups;                      // raw ring: a multiple of the groups, so each slot has one user
+// Raw-tile ring slots asked for (a build parameter); each configuration takes
+// the largest multiple of the groups up to this that leaves two weight stages.
+#ifndef XENG_BF_RAW_SLOTS
+#define XENG_BF_RAW_SLOTS 6
+#endif
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kXCols = 64;                      // one K chunk of 128 inputs: 256 codes, 4 to a column
+constexpr float kMagic = 196608.0f;                  // 1.5 * 2^17: its binade has the spacing 2^-6
+constexpr uint32_t kMagicBits = 0x48400000u;         // bit pattern of kMagic
 
 template <int kBp>
 struct BfCfg {
@@ -83,12 +89,19 @@ struct BfCfg {
     // step while the MMAs of the previous one run), else one
     static constexpr int kSlots = (kTmemCols - kXCol0) / (kGroups * kXCols) >= 2 ? 2 : 1;
     static_assert(kXCol0 + kGroups * kSlots * kXCols <= kTmemCols, "TMEM: accumulators + X slots");
-    static constexpr int kSWFit = (232448 - 1024 - 512 - kR * kRawBytes) / kWStageBytes;
+    // raw ring: a multiple of the groups, so each slot has one user
+    static constexpr int kRFit = (232448 - 1024 - 512 - 2 * kBp * 8 - 2 * kWStageBytes) / kRawBytes / kGroups * kGroups;
+    static constexpr int kRWant = XENG_BF_RAW_SLOTS / kGroups * kGroups;
+    static constexpr int kR = kRWant < kRFit ? kRWant : kRFit;
+    static_assert(kR >= kGroups, "raw ring needs a slot per converter group");
+    static constexpr int kCorrBytes = 2 * kBp * 8;                // offset terms of two items, staged for the epilogue
+    static constexpr int kSWFit = (232448 - 1024 - 512 - kCorrBytes - kR * kRawBytes) / kWStageBytes;
     static constexpr int kSW = kSWFit > 8 ? 8 : kSWFit;          // weight ring stages (L2 latency off the path)
     static_assert(kSW >= 2, "weight ring needs two stages");
     static constexpr int kXS = kGroups * kSlots;                 // X slots in all
     static constexpr int kBars = 2 * kR + 2 * kXS + 2 * kSW + 2 * kAcc + 1;
-    static constexpr size_t kSmem = 1024 + (size_t)kR * kRawBytes + (size_t)kSW * kWStageBytes + kBars * 8 + 16;
+    static constexpr size_t kSmem =
+        1024 + (size_t)kR * kRawBytes + (size_t)kSW * kWStageBytes + kBars * 8 + 16 + 8 + kCorrBytes;
     // kind::f8f6f4, D f32, A and B E2M3 (type 3) K-major, N and M = 128
     static constexpr uint32_t kIdesc = (1u << 4) | (3u << 7) | (3u << 10) | ((uint32_t)(kN >> 3) << 17) |
                                        ((uint32_t)(128 >> 4) << 24);
@@ -138,7 +151,7 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t rbase = (raw + 1023u) & ~1023u;                  // raw ring
     const uint8_t *rgen = smem_raw + (rbase - raw);                 // generic view of it
-    const uint32_t wbase = rbase + kR * kRawBytes;                  // weight ring
+    const uint32_t wbase = rbase + C::kR * kRawBytes;                  // weight ring
     const uint32_t bars = wbase + C::kSW * C::kWStageBytes;
     auto xf = [&](int x) { return bars + 8u * x; };                           // X slot x written
     auto xe = [&](int x) { return bars + 8u * (C::kXS + x); };                // X slot x consumed
@@ -148,7 +161,7 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
     auto acce = [&](int b) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + C::kAcc + b); };
     const uint32_t drain_bar = bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc);
     auto rawf = [&](int r) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc + 1 + r); };       // tile landed
-    auto rawe = [&](int r) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc + 1 + kR + r); };  // tile read
+    auto rawe = [&](int r) { return bars + 8u * (2 * C::kXS + 2 * C::kSW + 2 * C::kAcc + 1 + C::kR + r); };  // tile read
     // step n of this CTA belongs to group n % kGroups, which uses its slots in
     // turn: slot (n / kGroups) % kSlots of the group, phase (n / kGroups / kSlots) & 1
     auto xslot = [&](int64_t n) { return (int)(n % kGroups) * C::kSlots + (int)((n / kGroups) % C::kSlots); };
@@ -173,7 +186,7 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             mbar_init(acce(b), 128);
         }
         mbar_init(drain_bar, 1);
-        for (int r = 0; r < kR; r++) {
+        for (int r = 0; r < C::kR; r++) {
             mbar_init(rawf(r), 1);
             mbar_init(rawe(r), 128);
         }
@@ -234,12 +247,13 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
             // kept to a few integer operations since each step carries little
             // tensor work (N = 4 Bp).
             int sw = 0, local = 0, c = 0;  // c = step index modulo the X slots
-            uint32_t pw = 0, pxs = 0, uses[2] = {0, 0};
+            uint32_t pw = 0, pxs = 0;
             bool ok = true;
             for (int64_t it = blockIdx.x; ok && it < a.n_items; it += gridDim.x, ++local) {
                 const int ab = C::kAcc == 2 ? (local & 1) : 0;
-                if (!mbar_wait_backoff(acce(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma, 0)) break;
-                ++uses[ab];
+                // the accumulator's earlier uses: local / kAcc (a counter array indexed by ab would live in local memory)
+                const uint32_t used = (uint32_t)(C::kAcc == 2 ? (local >> 1) : local);
+                if (!mbar_wait_backoff(acce(ab), (used & 1u) ^ 1u, err, kDevTimeoutMma, 0)) break;
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(ab * C::kN);
                 for (int k = 0; k < a.n_kc; k++) {
@@ -286,8 +300,8 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
         const int row = q * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + C::kXCol0;
         for (int64_t n = g; n < n_seq; n += kGroups) {
-            const int r = (int)(n % kR);
-            const uint32_t pr = (uint32_t)((n / kR) & 1);
+            const int r = (int)(n % C::kR);
+            const uint32_t pr = (uint32_t)((n / C::kR) & 1);
             const int x = xslot(n);
             const bool ok = mbar_wait_backoff(rawf(r), pr, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS) &&
                             mbar_wait_backoff(xe(x), xphase(n) ^ 1u, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
@@ -315,23 +329,56 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
         }
     } else if (warp < kRawProdWarp) {
         // ---------------- epilogue (warps 14..17) ----------------
+        // The offset terms of an item's channel are loaded by the first
+        // epilogue warp while the MMAs run and staged in shared memory (two
+        // items' worth, alternating), where the four warps read them as
+        // broadcasts; a barrier over the four warps publishes them and also
+        // ORs the warps' wait results, so that all four leave together.
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
         const int row = q * 32 + lane;
+        const bool stager = warp == kEpiWarp0;
+        // [2][kBp], 16-byte aligned for the paired loads (the barrier area ends 8 bytes off a 16-byte boundary
+        // when the barrier count is odd)
+        int2 *corr_s = reinterpret_cast<int2 *>(smem_raw + (((bars + 8u * C::kBars + 16 + 15) & ~15u) - raw));
         constexpr int G = kBp < 16 ? kBp : 16;
-        uint32_t uses[2] = {0, 0};
+        constexpr int kPer = (kBp + 31) / 32;  // offset terms per lane of the staging warp
         int local = 0;
         for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x, ++local) {
             int f, tt;
             bf_item(a, it, f, tt);
             const int ab = C::kAcc == 2 ? (local & 1) : 0;
-            const bool ok = mbar_wait_backoff(accf(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue, 256);
-            if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
-            ++uses[ab];
+            int2 cv[kPer];
+            if (stager) {
+                const int2 *corr = reinterpret_cast<const int2 *>(a.corr) + (int64_t)f * kBp;
+                #pragma unroll
+                for (int k = 0; k < kPer; k++)
+                    if (lane + 32 * k < kBp) {
+                        const int2 c = __ldg(corr + lane + 32 * k);
+                        // with the conversion offsets of the hi (x 16) and lo parts folded in
+                        cv[k] = make_int2((int)((uint32_t)c.x + 17u * kMagicBits), (int)((uint32_t)c.y + 17u * kMagicBits));
+                    }
+            }
+            const uint32_t used = (uint32_t)(C::kAcc == 2 ? (local >> 1) : local);  // the accumulator's earlier uses
+            const bool ok = mbar_wait_backoff(accf(ab), used & 1u, err, kDevTimeoutEpilogue, 256);
+            int2 *cs = corr_s + (local & 1) * kBp;
+            if (stager) {
+                // the slot was last read two items ago, before the previous item's barrier
+                #pragma unroll
+                for (int k = 0; k < kPer; k++)
+                    if (lane + 32 * k < kBp) cs[lane + 32 * k] = cv[k];
+            }
+            uint32_t any_fail;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                "bar.red.or.pred p, 1, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(any_fail)
+                : "r"(ok ? 0u : 1u)
+                : "memory");
+            if (any_fail) break;  // all four warps, converged for tcgen05.ld
             fence_after();
             const int64_t t = (int64_t)tt * 128 + row;
             int2 *o = reinterpret_cast<int2 *>(a.out) + (t * a.F + f) * a.B;
             int4 *o4 = reinterpret_cast<int4 *>(o);  // two beams per store when B is even
-            const int2 *corr = reinterpret_cast<const int2 *>(a.corr) + (int64_t)f * kBp;  // offset terms of the beams
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::kN);
             #pragma unroll
             for (int b0 = 0; b0 < kBp; b0 += G) {
@@ -345,15 +392,24 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
                 }
                 tmem_ld_wait();
                 if (t < a.T) {
-                    // accumulators hold sums of u v / 64: x 64 is exact
+                    // An accumulator holds S / 64 for an integer |S| < 2^22; adding 1.5 * 2^17
+                    // (ulp 2^-6) is exact and leaves S + kMagicBits in the sum's bit pattern,
+                    // so y = 16 S_hi + S_lo - offset needs no float-to-int conversion.
                     int2 y[G];
                     #pragma unroll
                     for (int e = 0; e < G; e++) {
-                        const int2 c = __ldg(corr + b0 + e);
-                        y[e] = make_int2(16 * __float2int_rn(64.0f * __uint_as_float(hre[e])) +
-                                             __float2int_rn(64.0f * __uint_as_float(lre[e])) - c.x,
-                                         16 * __float2int_rn(64.0f * __uint_as_float(him[e])) +
-                                             __float2int_rn(64.0f * __uint_as_float(lim[e])) - c.y);
+                        int2 c;
+                        if (G >= 2) {  // two beams' offset terms per shared-memory load
+                            const int4 c2 = *reinterpret_cast<const int4 *>(cs + b0 + (e & ~1));
+                            c = (e & 1) ? make_int2(c2.z, c2.w) : make_int2(c2.x, c2.y);
+                        } else {
+                            c = cs[b0 + e];
+                        }
+                        const uint32_t bhr = __float_as_uint(__uint_as_float(hre[e]) + kMagic);
+                        const uint32_t blr = __float_as_uint(__uint_as_float(lre[e]) + kMagic);
+                        const uint32_t bhi = __float_as_uint(__uint_as_float(him[e]) + kMagic);
+                        const uint32_t bli = __float_as_uint(__uint_as_float(lim[e]) + kMagic);
+                        y[e] = make_int2((int)(16u * bhr + blr - (uint32_t)c.x), (int)(16u * bhi + bli - (uint32_t)c.y));
                     }
                     if (a.vec16) {
                         #pragma unroll
@@ -374,8 +430,8 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
         int issued = 0;
         bool ok = true;
         for (int64_t n = 0; n < n_seq; n++) {
-            const int r = (int)(n % kR);
-            if (!mbar_wait(rawe(r), (uint32_t)((n / kR) & 1) ^ 1u, err, kDevTimeoutProducer)) {
+            const int r = (int)(n % C::kR);
+            if (!mbar_wait(rawe(r), (uint32_t)((n / C::kR) & 1) ^ 1u, err, kDevTimeoutProducer)) {
                 ok = false;
                 break;
             }
@@ -388,8 +444,8 @@ beamform_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_consta
         }
         if (!ok) {
             // Let the copies already issued land before the CTA can exit.
-            for (int64_t n = issued - 1; n >= 0 && n >= issued - kR; n--)
-                (void)mbar_wait(rawf((int)(n % kR)), (uint32_t)((n / kR) & 1), err, kDevTimeoutProducer);
+            for (int64_t n = issued - 1; n >= 0 && n >= issued - C::kR; n--)
+                (void)mbar_wait(rawf((int)(n % C::kR)), (uint32_t)((n / C::kR) & 1), err, kDevTimeoutProducer);
         }
     }
 
