@@ -14,13 +14,27 @@
 // Each CTA supplies its 128 rows of A and its half of B, so both CTAs decode
 // only their own inputs.  The 256 x 256 complex accumulator fills all 512 TMEM
 // columns of both CTAs; the epilogue (tcgen05.ld -> int32 triangle) follows
-// each channel.  Exactness as in the two-pass path: products <= 64, partial
-// sums <= 128 * 65536 = 2^23 per launch.
+// each channel.
+//
+// The planes hold the raw nibbles, not the decoded values: a byte whose low
+// four bits are u (0..15) and whose high four bits are clear is the FP8 E4M3
+// code of u / 512 (the subnormal binade and the first normal one share the
+// spacing 2^-9), so the converters only split bytes.  With p, q the Re and Im
+// nibbles and x = (p - 8) + i (q - 8), per channel and launch of n samples
+//     Re V_ij = sum(p_i p_j + q_i q_j) - 8 (S_i + S_j) + 128 n,
+//     Im V_ij = sum(q_i p_j - p_i q_j) + 8 (D_i - D_j),
+// with S_i = P_i + Q_i, D_i = P_i - Q_i and P_i, Q_i the sums of input i's
+// nibbles.  The converters form P and Q as they go; at the end of a channel
+// each CTA reduces its inputs' sums and writes them into both CTAs' shared
+// memory (the epilogue of a row needs the sums of every column).  The MMA sums
+// are integers / 2^18 below 450 n / 2^18; with n <= 32768 per launch they stay
+// below 2^24 / 2^18 and the f32 accumulation is exact.
 //
 // Roles per CTA (704 threads):
 //   warp 0       TMA producer: raw tiles (128 inputs x 128 samples of one channel)
 //   warp 1       TMEM allocation (collective for the pair); MMA issuer (leader)
-//   warps 2..17  converters: raw tile -> transposed E4M3 planes A_a (Re), A_b (Im)
+//   warps 2..17  converters: raw tile -> transposed raw-nibble planes A_a (Re), A_b (Im)
+//                and the inputs' nibble sums
 //   warps 18..21 epilogue: TMEM -> packed int32 triangle
 // Converter mapping: a unit is 4 inputs (4q .. 4q + 3) x 16 samples (block b);
 // converter warp w (0..15) takes, for lane q, block b = (w + q) mod 8 and half
@@ -43,8 +57,12 @@ constexpr int kFPlane = 128 * 128;               // one plane tile (128 inputs x
 constexpr int kFStageBytes = kFRaw + 2 * kFPlane;
 constexpr int kFStages = 4;
 constexpr uint32_t kFTmemCols = 512;
-constexpr int kFBars = 3 * kFStages + 3;         // raw full, full, empty per stage; acc full, acc empty, drain
-constexpr size_t kFSmem = 1024 + (size_t)kFStages * kFStageBytes + kFBars * 8 + 16;
+constexpr int kFBars = 3 * kFStages + 7;         // raw full, full, empty per stage; acc full, acc empty, drain;
+                                                 // sums full and sums empty per parity
+constexpr int kFScratch = kFConvWarps * 128 * 8; // per-converter-warp partial sums (P, Q) of the CTA's 128 inputs
+constexpr int kFSums = 2 * 256 * 8;              // per channel parity: (S, D) of all 256 inputs of the pair
+constexpr size_t kFSmem = 1024 + (size_t)kFStages * kFStageBytes + kFScratch + kFSums + kFBars * 8 + 16;
+static_assert(kFSmem <= 232448, "shared memory over the per-CTA limit");
 
 __host__ __device__ constexpr uint32_t fused_idesc(bool neg_a)
 {
@@ -59,8 +77,58 @@ __device__ __forceinline__ uint64_t fdesc(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Bounded wait with cluster-scope acquire: the barrier's arrivals include a
+// peer CTA's, whose shared-memory writes (into this CTA) must be visible after.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int *err, int code)
+{
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        __nanosleep(64);
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int *)err != 0) return false;
+            if (globaltimer() - t0 > kWaitLimitNs) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, int x, int y)
+{
+    asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(x), "r"(y) : "memory");
+}
+
+// OR of a flag over the threads of named barrier `id` (count threads), which all must reach it.
+__device__ __forceinline__ bool bar_any(int id, int count, bool flag)
+{
+    uint32_t any;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(any)
+        : "r"(flag ? 1u : 0u), "r"(id), "r"(count)
+        : "memory");
+    return any != 0;
+}
+
 struct FusedArgs {
-    int64_t t0, nt;        // samples t0 .. t0 + nt - 1 of the block, nt <= 65536
+    int64_t t0, nt;        // samples t0 .. t0 + nt - 1 of the block, nt <= kFusedMaxSamples
     int32_t F, N, f0, nf;  // channels f0 .. f0 + nf - 1
     int32_t *acc;          // [nf][N(N+1)/2][2], channel f0 + fl at fl
     int accumulate;        // 0: store, 1: add
@@ -74,14 +142,20 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
     uint8_t *sgen = smem_raw + (sbase - raw);
-    const uint32_t bars = sbase + kFStages * kFStageBytes;
+    const uint32_t bars = sbase + kFStages * kFStageBytes + kFScratch + kFSums;
     auto rawf = [&](int s) { return bars + 8u * s; };
     auto full = [&](int s) { return bars + 8u * (kFStages + s); };
     auto empty = [&](int s) { return bars + 8u * (2 * kFStages + s); };
     const uint32_t accf = bars + 8u * (3 * kFStages);
     const uint32_t acce = bars + 8u * (3 * kFStages + 1);
     const uint32_t drain = bars + 8u * (3 * kFStages + 2);
+    auto sums_full = [&](int par) { return bars + 8u * (3 * kFStages + 3 + par); };
+    auto sums_empty = [&](int par) { return bars + 8u * (3 * kFStages + 5 + par); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * kFBars - raw));
+    // partial sums [converter warp][input] and the pair's sums [parity][input of 256], after the stage ring
+    int2 *scratch = reinterpret_cast<int2 *>(sgen + kFStages * kFStageBytes);
+    int2 *sums = reinterpret_cast<int2 *>(sgen + kFStages * kFStageBytes + kFScratch);
+    const uint32_t sums_u32 = sbase + kFStages * kFStageBytes + kFScratch;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
@@ -100,6 +174,10 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
         mbar_init(accf, 1);
         mbar_init(acce, 2 * kFEpiWarps);          // one arrival per epilogue warp of both CTAs
         mbar_init(drain, 1);
+        for (int par = 0; par < 2; par++) {
+            mbar_init(sums_full(par), 2 * 4);           // one arrival per reducing warp of both CTAs
+            mbar_init(sums_empty(par), 2 * kFEpiWarps); // one arrival per epilogue warp of both CTAs
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
     }
@@ -194,10 +272,12 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
         const int h = ((lane >> 3) & 1) ^ (cw >> 3);     // which 8 samples of the block
         const int q = lane;                              // inputs 4q .. 4q + 3
         const uint32_t full_leader = mapa_rank(full(0), 0) - full(0);  // offset into the leader's window
-        int stage = 0;
+        const uint32_t peer = rank ^ 1u;
+        int stage = 0, local = 0;
         uint32_t phase = 0;
-        for (int it = it_begin; it < a.nf; it += it_step) {
+        for (int it = it_begin; it < a.nf; it += it_step, ++local) {
             bool ok = true;
+            uint32_t sp[4] = {0, 0, 0, 0}, sq[4] = {0, 0, 0, 0};  // nibble sums of inputs 4q + m over this lane's samples
             for (int kc = 0; kc < n_k; kc++) {
                 ok = mbar_wait_backoff(rawf(stage), phase, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -215,13 +295,19 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
                     #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         const int t = b * 16 + h * 8 + g * 4 + k;
-                        r[k] = (tb + g * 4 + k < a.nt) ? rt[t * 32 + q] : 0x88888888u;  // past the end: value 0
+                        r[k] = (tb + g * 4 + k < a.nt) ? rt[t * 32 + q] : 0u;  // past the end: nibbles 0, no term
                     }
-                    // transpose + decode: r[k] byte m = (sample k, input m) -> input m's codes of samples 0..3
-                    decode_input4(r, 0, re[0][g], im[0][g]);
-                    decode_input4(r, 1, re[1][g], im[1][g]);
-                    decode_input4(r, 2, re[2][g], im[2][g]);
-                    decode_input4(r, 3, re[3][g], im[3][g]);
+                    // transpose: r[k] byte m = (sample k, input m) -> input m's bytes of samples 0..3,
+                    // then split into the Re (high) and Im (low) nibble codes
+                    #pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const uint32_t sel = (uint32_t)m | ((uint32_t)(4 + m) << 4);
+                        const uint32_t w = __byte_perm(__byte_perm(r[0], r[1], sel), __byte_perm(r[2], r[3], sel), 0x5410);
+                        re[m][g] = (w >> 4) & 0x0F0F0F0Fu;
+                        im[m][g] = w & 0x0F0F0F0Fu;
+                        sp[m] = __dp4a(re[m][g], 0x01010101u, sp[m]);
+                        sq[m] = __dp4a(im[m][g], 0x01010101u, sq[m]);
+                    }
                 }
                 #pragma unroll
                 for (int m = 0; m < 4; m++) {
@@ -238,24 +324,67 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
                     phase ^= 1u;
                 }
             }
-            if (!ok) break;
+            // End of the channel: every converter warp reaches both barriers below, failed or not,
+            // and they OR the failures, so the warps leave together.
+            if (ok) {
+                int4 *sc = reinterpret_cast<int4 *>(scratch + cw * 128 + 4 * q);
+                sc[0] = make_int4((int)sp[0], (int)sq[0], (int)sp[1], (int)sq[1]);
+                sc[1] = make_int4((int)sp[2], (int)sq[2], (int)sp[3], (int)sq[3]);
+            }
+            bool fail = bar_any(1, kFConvWarps * 32, !ok);
+            if (!fail && cw < 4) {
+                // warps 0..3: thread k sums input k's partials and publishes (S, D) to both CTAs
+                const int k = cw * 32 + lane;
+                int P = 0, Q = 0;
+                #pragma unroll
+                for (int w = 0; w < kFConvWarps; w++) {
+                    const int2 v = scratch[w * 128 + k];
+                    P += v.x;
+                    Q += v.y;
+                }
+                const int par = local & 1;
+                // the buffer was last read by both CTAs' epilogues two channels ago
+                ok = mbar_wait_cluster(sums_empty(par), (uint32_t)((local >> 1) & 1) ^ 1u, err, kDevTimeoutProducer);
+                if (__all_sync(0xffffffffu, ok)) {
+                    const uint32_t slot = sums_u32 + (uint32_t)((par * 256 + (int)rank * 128 + k) * 8);
+                    sums[par * 256 + (int)rank * 128 + k] = make_int2(P + Q, P - Q);
+                    st_cluster_v2(mapa_rank(slot, peer), P + Q, P - Q);
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive_cluster(mapa_rank(sums_full(par), rank));
+                        mbar_arrive_cluster(mapa_rank(sums_full(par), peer));
+                    }
+                } else {
+                    ok = false;
+                }
+            }
+            // the scratch may be rewritten (next channel) once every reducing thread has read it
+            fail = bar_any(1, kFConvWarps * 32, !ok) || fail;
+            if (fail) break;
         }
     } else {
         // ---------------- epilogue (warps 18..21 of both CTAs) ----------------
         const int q = warp & 3;                       // TMEM lane quadrant this warp may access
         const int row = q * 32 + lane;
         const uint32_t acce_leader = mapa_rank(acce, 0);
+        const uint32_t peer = rank ^ 1u;
         uint32_t uses = 0;
+        int local = 0;
         const int64_t N = a.N;
         const int64_t i = (int64_t)rank * 128 + row;
         const bool row_ok = i < N;
         const int64_t row_base = i * N - i * (i - 1) / 2 - i;
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
-        for (int it = it_begin; it < a.nf; it += it_step) {
-            const bool ok = mbar_wait_backoff(accf, uses & 1u, err, kDevTimeoutEpilogue, 128);
+        const int base_re = 128 * (int)a.nt;          // 64 n from each of the two products
+        for (int it = it_begin; it < a.nf; it += it_step, ++local) {
+            bool ok = mbar_wait_backoff(accf, uses & 1u, err, kDevTimeoutEpilogue, 128);
+            const int par = local & 1;
+            ok = ok && mbar_wait_cluster(sums_full(par), (uint32_t)((local >> 1) & 1), err, kDevTimeoutEpilogue);
             if (!__all_sync(0xffffffffu, ok)) break;
             ++uses;
             fence_after();
+            const int2 *sm = sums + par * 256;
+            const int2 si = sm[i];                    // (S_i, D_i)
             int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)it * (N * (N + 1) / 2);
             for (int c = 0; c < 256; c += 16) {
                 uint32_t vre[16], vim[16];
@@ -265,28 +394,41 @@ correlate_fused256_kernel(const __grid_constant__ CUtensorMap raw_map, const Fus
                 if (row_ok) {
                     int2 *p = out + row_base + c;  // pairs j = c + e, e = 0..15
                     const int64_t e_lo = i - c, e_hi = N - c;
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {  // corrected values in place of the accumulator words
+                        const int2 sj = sm[c + e];
+                        // accumulators hold integer sums / 2^18: x 2^18 is exact
+                        vre[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vre[e])) - 8 * (si.x + sj.x) +
+                                            base_re);
+                        vim[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vim[e])) + 8 * (si.y - sj.y));
+                    }
                     if (a.accumulate) {
-                        int2 old[16];
                         #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi) old[e] = p[e];
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi)
-                                p[e] = make_int2(old[e].x + __float2int_rn(__uint_as_float(vre[e])),
-                                                 old[e].y + __float2int_rn(__uint_as_float(vim[e])));
+                        for (int e0 = 0; e0 < 16; e0 += 8) {  // in halves: fewer registers live
+                            int2 old[8];
+                            #pragma unroll
+                            for (int e = 0; e < 8; e++)
+                                if (e0 + e >= e_lo && e0 + e < e_hi) old[e] = p[e0 + e];
+                            #pragma unroll
+                            for (int e = 0; e < 8; e++)
+                                if (e0 + e >= e_lo && e0 + e < e_hi)
+                                    p[e0 + e] = make_int2(old[e].x + (int)vre[e0 + e], old[e].y + (int)vim[e0 + e]);
+                        }
                     } else {
                         #pragma unroll
                         for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi)
-                                p[e] = make_int2(__float2int_rn(__uint_as_float(vre[e])),
-                                                 __float2int_rn(__uint_as_float(vim[e])));
+                            if (e >= e_lo && e < e_hi) p[e] = make_int2((int)vre[e], (int)vim[e]);
                     }
                 }
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(acce_leader);
+            if (lane == 0) {
+                mbar_arrive_cluster(acce_leader);
+                // this CTA's reads of the sums buffer are done: both CTAs' reducers may refill it
+                mbar_arrive_cluster(mapa_rank(sums_empty(par), rank));
+                mbar_arrive_cluster(mapa_rank(sums_empty(par), peer));
+            }
         }
     }
 
@@ -312,12 +454,13 @@ cudaError_t launch_correlate_fused256(const uint8_t *block, int64_t T_block, int
                                       int num_sms, cudaStream_t s)
 {
     if (nf <= 0 || nt <= 0) return cudaSuccess;
-    if (!fused256_ok(block, N) || nt > kMaxChunkSamples || t0 + nt > T_block) return cudaErrorInvalidValue;
+    if (!fused256_ok(block, N) || nt > kFusedMaxSamples || t0 + nt > T_block) return cudaErrorInvalidValue;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x 128 samples;
-    // inputs past N and samples past the block read as zero bytes (the converters
-    // zero the samples past the launch; the inputs past N are never written)
+    // inputs past N and samples past the block read as zero bytes, nibbles 0 that
+    // add nothing (the converters zero the samples past the launch; the inputs
+    // past N are never written)
     CUtensorMap map;
     cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T_block};
     cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};

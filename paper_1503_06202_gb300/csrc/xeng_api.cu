@@ -469,8 +469,9 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
     }
     cudaError_t e = cudaSuccess;
     if (XENG_FUSED_SMALL && !apply_shift && fused256_ok(dblock, (int32_t)N)) {
-        for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += h->chunk_t) {
-            const int64_t nt = (n_samples - t0) < h->chunk_t ? (n_samples - t0) : h->chunk_t;
+        const int64_t fc = h->chunk_t < kFusedMaxSamples ? h->chunk_t : kFusedMaxSamples;
+        for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += fc) {
+            const int64_t nt = (n_samples - t0) < fc ? (n_samples - t0) : fc;
             const int accumulate = (fresh && t0 == 0) ? 0 : 1;
             e = timed_launch(h, 1, s, [&] {
                 return launch_correlate_fused256(dblock, n_samples, t0, nt, (int32_t)F, (int32_t)N, 0, (int32_t)F,
@@ -646,10 +647,13 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
             bf0 = 0;
         }
         if (XENG_FUSED_SMALL && fused256_ok(blk, (int32_t)N)) {
-            e = timed_launch(h, 1, s, [&] {
-                return launch_correlate_fused256(blk, n, 0, n, bf, (int32_t)N, bf0, nf, target + f0 * nb2,
-                                                 fresh ? 0 : 1, h->d_err, h->num_sms, s);
-            });
+            for (int64_t t0 = 0; t0 < n && e == cudaSuccess; t0 += kFusedMaxSamples) {
+                const int64_t nt = (n - t0) < kFusedMaxSamples ? (n - t0) : kFusedMaxSamples;
+                e = timed_launch(h, 1, s, [&] {
+                    return launch_correlate_fused256(blk, n, t0, nt, bf, (int32_t)N, bf0, nf, target + f0 * nb2,
+                                                     (fresh && t0 == 0) ? 0 : 1, h->d_err, h->num_sms, s);
+                });
+            }
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
             if (e == cudaSuccess && host_out) {
                 e = cudaStreamWaitEvent(h->d2h, h->ev_cmp[buf], 0);

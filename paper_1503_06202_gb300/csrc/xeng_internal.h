@@ -9,6 +9,7 @@ namespace xeng {
 
 constexpr int kTile = 128;          // inputs per tensor-engine tile, samples per K chunk
 constexpr int kMaxChunkSamples = 65536;  // f32 sums stay <= 128 * 65536 = 2^23 (exact)
+constexpr int kFusedMaxSamples = 32768;  // raw-nibble sums of the fused kernel stay <= 450 * 32768 < 2^24
 
 // Device-side status codes written to the handle's error word.
 enum DevStatus : int {
