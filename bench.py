@@ -209,10 +209,10 @@ def run_batched(args, rank, world, local_rank):
             jobs.append((r.device(stream), out))
     stream.synchronize()
     ops = sum(useful_ops(r.T, r.F, r.N) for r in recipes)
-    cache = os.path.join(tempfile.gettempdir(), "xeng_batch_tune.txt")
+    cache = os.path.join(tempfile.gettempdir(), "xeng_batch_tune.jsonl")
     t0 = time.perf_counter()
     if args.batch_max_chunks > 0:  # a fixed plan (profiling runs), no tuning
-        rc, opts, tuned_ms = 2, xe.xeng._opts(args.batch_max_chunks, args.batch_policy, True), None
+        rc, opts, tuned_ms = 2, xe.xeng._opts(args.batch_max_chunks, args.batch_policy, True, args.batch_tile_order), None
     else:
         rc, opts, tuned_ms = xe.xeng_batch_autotune(jobs, cache, reps=3)
     tune_s = time.perf_counter() - t0
@@ -418,6 +418,7 @@ def main():
     ap.add_argument("--serve-compute-budget", type=float, default=0.0, help="TOPS; > 0 admits streams by compute too")
     ap.add_argument("--batch-max-chunks", type=int, default=0, help="fixed batch plan instead of autotuning")
     ap.add_argument("--batch-policy", type=int, default=1)
+    ap.add_argument("--batch-tile-order", type=int, default=0, help="with --batch-max-chunks: 0 row-major, 1 diagonal, 2 Morton")
     ap.add_argument("--no-per-job-dp4a", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

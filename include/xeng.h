@@ -268,11 +268,16 @@ typedef struct {
 #define XENG_SCHED_ORDERED     2  /* items in job order, each to the CTA expected to be
                                      free first: CTAs stay on neighbouring tiles       */
 
+#define XENG_TILES_ROW_MAJOR 0  /* a channel's tile pairs (I <= J) row by row              */
+#define XENG_TILES_DIAGONAL  1  /* by diagonal J - I, the main diagonal first              */
+#define XENG_TILES_MORTON    2  /* in Z order of (I, J): neighbouring tiles share operands */
+
 typedef struct {
     int32_t max_chunks_per_item; /* split a tile's integration into items of at most this many
                                     128-sample chunks (1..512; <= 0 means 512)            */
     int32_t policy;              /* XENG_SCHED_LPT, _ROUND_ROBIN or _ORDERED               */
     int32_t use_graph;           /* != 0: capture the run in a CUDA graph once, replay it */
+    int32_t tile_order;          /* XENG_TILES_ROW_MAJOR, _DIAGONAL or _MORTON            */
 } xeng_batch_opts_t;
 
 typedef struct {
@@ -284,6 +289,7 @@ typedef struct {
     int32_t max_chunks_per_item;
     int32_t policy;
     double  load_imbalance;      /* planned max / mean CTA load                          */
+    int32_t tile_order;
 } xeng_batch_info_t;
 
 typedef struct xeng_batch_s *xeng_batch_t;
@@ -293,8 +299,9 @@ typedef struct xeng_batch_s *xeng_batch_t;
  *   device: allocates the decode scratch (about twice the jobs' input bytes),
  *   per-job TMA descriptors and the work list, and (use_graph) captures the
  *   run in a CUDA graph.  The block and out pointers are bound now and used by
- *   every run.  opts may be NULL (LPT, 512 chunks, graph).  Synchronous.
- *   XENG_ERR_ARG for NULL or host pointers, XENG_ERR_RANGE for bad sizes.
+ *   every run.  opts may be NULL (LPT, 512 chunks, graph, row-major tiles).
+ *   Synchronous.  XENG_ERR_ARG for NULL or host pointers or an unknown policy
+ *   or tile order, XENG_ERR_RANGE for bad sizes.
  */
 XENG_API int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_opts_t *opts,
                                xeng_batch_t *out_batch);
@@ -313,12 +320,14 @@ XENG_API void xeng_batch_destroy(xeng_batch_t b);
 /*
  * xeng_batch_autotune -- pick xeng_batch_opts_t for these jobs by timing every
  *   (max_chunks_per_item in {16, 32, 64, 128, 256, 512}) x (policy) candidate
- *   for `reps` runs each, in two passes (forward, then reverse order; each
- *   candidate keeps its better time), overwriting the jobs' outputs.  With a cache_path,
- *   a text file of "signature max_chunks policy ms" lines keyed by the jobs'
- *   (N, F, T) list and the SM count is read first (hit: returns 1 without
- *   timing) and the winner appended after tuning (returns 0).  *best_ms (may
- *   be NULL) receives the winner's time per run.  Negative XENG_ERR_* on error.
+ *   with row-major tiles for `reps` runs each, in two passes (forward, then
+ *   reverse order; each candidate keeps its better time), then the winner with
+ *   the diagonal and Morton tile orders, overwriting the jobs' outputs.  With
+ *   a cache_path, a JSON-lines file of {"sig", "max_chunks", "policy",
+ *   "tile_order", "ms"} records keyed by the jobs' (N, F, T) list and the SM
+ *   count is read first (hit: returns 1 without timing) and the winner
+ *   appended after tuning (returns 0).  *best_ms (may be NULL) receives the
+ *   winner's time per run.  Negative XENG_ERR_* on error.
  */
 XENG_API int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cache_path, int32_t reps,
                                  xeng_batch_opts_t *best, double *best_ms);

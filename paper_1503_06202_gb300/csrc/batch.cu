@@ -14,7 +14,8 @@
 // assigned to one persistent CTA per SM longest-first onto the least-loaded
 // CTA (LPT), round-robin in job order, or in job order onto the CTA expected
 // to be free first (ORDERED: the CTAs move through the list together and share
-// each channel's operands in L2); each CTA runs its items in job/channel order.
+// each channel's operands in L2); each CTA runs its items in job/channel order,
+// a channel's tiles row by row, by diagonal or in Z (Morton) order.
 #include <algorithm>
 #include <cinttypes>
 #include <cstdio>
@@ -127,6 +128,28 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
     return e;
 }
 
+// A channel's upper-triangle tile pairs (I <= J) in the requested order.
+std::vector<std::pair<int, int>> tile_order(int nt, int order)
+{
+    std::vector<std::pair<int, int>> v;
+    for (int I = 0; I < nt; I++)
+        for (int J = I; J < nt; J++) v.push_back({I, J});
+    auto morton = [](int I, int J) {
+        uint32_t z = 0;
+        for (int k = 0; k < 16; k++) z |= (uint32_t)((I >> k) & 1) << (2 * k + 1) | (uint32_t)((J >> k) & 1) << (2 * k);
+        return z;
+    };
+    if (order == XENG_TILES_DIAGONAL)
+        std::stable_sort(v.begin(), v.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+            return x.second - x.first < y.second - y.first;
+        });
+    else if (order == XENG_TILES_MORTON)
+        std::stable_sort(v.begin(), v.end(), [&](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+            return morton(x.first, x.second) < morton(y.first, y.second);
+        });
+    return v;
+}
+
 int plan(xeng_batch_s *b)
 {
     const int n = (int)b->jobs.size();
@@ -199,22 +222,23 @@ int plan(xeng_batch_s *b)
         }
         if (ns > 1) b->zero_outs.push_back({jb.out, (size_t)jb.n_freq * n_baselines(jb.n_inputs) * 8});
         const int nt = (int)(n_pad[j] / kTile);
+        const std::vector<std::pair<int, int>> order = tile_order(nt, b->opts.tile_order);
         for (int f = 0; f < jb.n_freq; f++)
-            for (int I = 0; I < nt; I++)
-                for (int J = I; J < nt; J++)
-                    for (int sp = 0; sp < ns; sp++) {
-                        Cand c;
-                        c.w.job = j;
-                        c.w.fl = f;
-                        c.w.I = (int16_t)I;
-                        c.w.J = (int16_t)J;
-                        c.w.kc0 = sp * maxc;
-                        c.w.kc1 = std::min(n_k, (sp + 1) * maxc);
-                        // MMA time per chunk, plus a fixed cost for the epilogue and pipeline fill
-                        c.cost = (double)(c.w.kc1 - c.w.kc0) + 2.0;
-                        c.order = (int64_t)cand.size();
-                        cand.push_back(c);
-                    }
+            for (const auto &IJ : order)
+                for (int sp = 0; sp < ns; sp++) {
+                    const int I = IJ.first, J = IJ.second;
+                    Cand c;
+                    c.w.job = j;
+                    c.w.fl = f;
+                    c.w.I = (int16_t)I;
+                    c.w.J = (int16_t)J;
+                    c.w.kc0 = sp * maxc;
+                    c.w.kc1 = std::min(n_k, (sp + 1) * maxc);
+                    // MMA time per chunk, plus a fixed cost for the epilogue and pipeline fill
+                    c.cost = (double)(c.w.kc1 - c.w.kc0) + 2.0;
+                    c.order = (int64_t)cand.size();
+                    cand.push_back(c);
+                }
     }
     b->dec_ctas = cta0;
     b->n_dec = (int)dj.size();
@@ -327,11 +351,15 @@ int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_o
     o.max_chunks_per_item = kMaxChunkSamples / kTile;
     o.policy = XENG_SCHED_LPT;
     o.use_graph = 1;
+    o.tile_order = XENG_TILES_ROW_MAJOR;
     if (opts) {
         o = *opts;
         if (o.max_chunks_per_item <= 0 || o.max_chunks_per_item > kMaxChunkSamples / kTile)
             o.max_chunks_per_item = kMaxChunkSamples / kTile;
         if (o.policy != XENG_SCHED_LPT && o.policy != XENG_SCHED_ROUND_ROBIN && o.policy != XENG_SCHED_ORDERED)
+            return XENG_ERR_ARG;
+        if (o.tile_order != XENG_TILES_ROW_MAJOR && o.tile_order != XENG_TILES_DIAGONAL &&
+            o.tile_order != XENG_TILES_MORTON)
             return XENG_ERR_ARG;
     }
     for (int j = 0; j < n_jobs; j++) {
@@ -395,6 +423,7 @@ int xeng_batch_info(xeng_batch_t b, xeng_batch_info_t *info)
     info->planes_bytes = b->planes_bytes;
     info->max_chunks_per_item = b->opts.max_chunks_per_item;
     info->policy = b->opts.policy;
+    info->tile_order = b->opts.tile_order;
     info->load_imbalance = b->mean_load > 0 ? b->max_load / b->mean_load : 1.0;
     return XENG_OK;
 }
@@ -422,12 +451,15 @@ int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cach
             char line[256];
             while (fgets(line, sizeof(line), fp)) {
                 unsigned long long s = 0;
-                int mc = 0, pol = 0;
+                int mc = 0, pol = 0, ord = 0;
                 double ms = 0;
-                if (sscanf(line, "%llx %d %d %lf", &s, &mc, &pol, &ms) == 4 && (uint64_t)s == sig) {
+                if (sscanf(line, "{\"sig\": \"%llx\", \"max_chunks\": %d, \"policy\": %d, \"tile_order\": %d, \"ms\": %lf}",
+                           &s, &mc, &pol, &ord, &ms) == 5 &&
+                    (uint64_t)s == sig) {
                     best->max_chunks_per_item = mc;
                     best->policy = pol;
                     best->use_graph = 1;
+                    best->tile_order = ord;
                     if (best_ms) *best_ms = ms;
                     fclose(fp);
                     return 1;  // from the cache
@@ -455,34 +487,59 @@ int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cach
             o.max_chunks_per_item = mc;
             o.policy = pol;
             o.use_graph = 1;
+            o.tile_order = XENG_TILES_ROW_MAJOR;
             cands.push_back(o);
         }
+    // time cands[from, to) in two passes; each keeps its better time (< 0: failed)
     std::vector<double> t_best(cands.size(), -1.0);
-    for (int pass = 0; pass < 2; pass++)
-        for (size_t c = 0; c < cands.size(); c++) {
-            const size_t k = pass == 0 ? c : cands.size() - 1 - c;
-            xeng_batch_t b = nullptr;
-            if (xeng_batch_create(jobs, n_jobs, &cands[k], &b) != XENG_OK) continue;
-            int st = xeng_batch_run(b, s);
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && st == XENG_OK; r++) st = xeng_batch_run(b, s);
-            cudaEventRecord(e1, s);
-            float ms = 0;
-            if (st == XENG_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-                *(volatile int *)b->h_err == 0) {
-                const double t = ms / reps;
-                if (t_best[k] < 0 || t < t_best[k]) t_best[k] = t;
+    auto time_range = [&](size_t from, size_t to) {
+        for (int pass = 0; pass < 2; pass++)
+            for (size_t c = from; c < to; c++) {
+                const size_t k = pass == 0 ? c : to - 1 - (c - from);
+                xeng_batch_t b = nullptr;
+                if (xeng_batch_create(jobs, n_jobs, &cands[k], &b) != XENG_OK) continue;
+                int st = xeng_batch_run(b, s);
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && st == XENG_OK; r++) st = xeng_batch_run(b, s);
+                cudaEventRecord(e1, s);
+                float ms = 0;
+                if (st == XENG_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && *(volatile int *)b->h_err == 0) {
+                    const double t = ms / reps;
+                    if (t_best[k] < 0 || t < t_best[k]) t_best[k] = t;
+                }
+                xeng_batch_destroy(b);
             }
-            xeng_batch_destroy(b);
-        }
+    };
+    auto pick = [&](double &best_t) {
+        int at = -1;
+        for (size_t k = 0; k < cands.size(); k++)
+            if (t_best[k] >= 0 && (at < 0 || t_best[k] < best_t)) {
+                best_t = t_best[k];
+                at = (int)k;
+            }
+        return at;
+    };
+    time_range(0, cands.size());
     double best_t = -1;
-    int st_all = XENG_ERR_CUDA;
-    for (size_t k = 0; k < cands.size(); k++)
-        if (t_best[k] >= 0 && (best_t < 0 || t_best[k] < best_t)) {
-            best_t = t_best[k];
-            *best = cands[k];
-            st_all = XENG_OK;
+    int at = pick(best_t);
+    if (at >= 0) {
+        // the winner's schedule with the other tile orders
+        const size_t n0 = cands.size();
+        for (int ord : {XENG_TILES_DIAGONAL, XENG_TILES_MORTON}) {
+            xeng_batch_opts_t o = cands[at];
+            o.tile_order = ord;
+            cands.push_back(o);
+            t_best.push_back(-1.0);
         }
+        time_range(n0, cands.size());
+        at = pick(best_t);
+    }
+    int st_all = XENG_ERR_CUDA;
+    if (at >= 0) {
+        *best = cands[at];
+        st_all = XENG_OK;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
@@ -491,7 +548,8 @@ int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const char *cach
     if (cache_path) {
         FILE *fp = fopen(cache_path, "a");
         if (fp) {
-            fprintf(fp, "%016llx %d %d %.6f\n", (unsigned long long)sig, best->max_chunks_per_item, best->policy, best_t);
+            fprintf(fp, "{\"sig\": \"%016llx\", \"max_chunks\": %d, \"policy\": %d, \"tile_order\": %d, \"ms\": %.6f}\n",
+                    (unsigned long long)sig, best->max_chunks_per_item, best->policy, best->tile_order, best_t);
             fclose(fp);
         }
     }

@@ -339,6 +339,9 @@ def xeng_peak_probe(kind: int, iters: int):
 XENG_SCHED_LPT = 0
 XENG_SCHED_ROUND_ROBIN = 1
 XENG_SCHED_ORDERED = 2
+XENG_TILES_ROW_MAJOR = 0
+XENG_TILES_DIAGONAL = 1
+XENG_TILES_MORTON = 2
 
 
 class XengJob(ctypes.Structure):
@@ -347,7 +350,8 @@ class XengJob(ctypes.Structure):
 
 
 class XengBatchOpts(ctypes.Structure):
-    _fields_ = [("max_chunks_per_item", ctypes.c_int32), ("policy", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+    _fields_ = [("max_chunks_per_item", ctypes.c_int32), ("policy", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("tile_order", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -357,7 +361,7 @@ class XengBatchInfo(ctypes.Structure):
     _fields_ = [("n_jobs", ctypes.c_int32), ("n_items", ctypes.c_int64), ("grid", ctypes.c_int32),
                 ("decode_ctas", ctypes.c_int64), ("planes_bytes", ctypes.c_int64),
                 ("max_chunks_per_item", ctypes.c_int32), ("policy", ctypes.c_int32),
-                ("load_imbalance", ctypes.c_double)]
+                ("load_imbalance", ctypes.c_double), ("tile_order", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -395,8 +399,8 @@ def _jobs_array(jobs):
     return arr
 
 
-def _opts(max_chunks_per_item=0, policy=XENG_SCHED_LPT, use_graph=True):
-    return XengBatchOpts(max_chunks_per_item, policy, 1 if use_graph else 0)
+def _opts(max_chunks_per_item=0, policy=XENG_SCHED_LPT, use_graph=True, tile_order=XENG_TILES_ROW_MAJOR):
+    return XengBatchOpts(max_chunks_per_item, policy, 1 if use_graph else 0, tile_order)
 
 
 def xeng_batch_create(jobs, opts=None):

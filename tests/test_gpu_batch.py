@@ -1,6 +1,8 @@
 """Batches of uneven jobs (xeng_batch_*) against the oracle and against each
 job correlated alone: bit-exact, whatever the plan (split-K with atomics,
-LPT or round-robin assignment, graph or direct launches)."""
+LPT, round-robin or ordered assignment, row-major, diagonal or Morton tile
+order, graph or direct launches)."""
+import json
 import os
 import tempfile
 
@@ -61,9 +63,11 @@ def test_batch_matches_oracle_and_alone():
                                                       (512, xe.XENG_SCHED_LPT, False),
                                                       (2, xe.XENG_SCHED_ORDERED, True),
                                                       (512, xe.XENG_SCHED_ORDERED, True)])
-def test_batch_plans_agree(max_chunks, policy, graph):
+@pytest.mark.parametrize("tile_order", [xe.XENG_TILES_ROW_MAJOR, xe.XENG_TILES_DIAGONAL, xe.XENG_TILES_MORTON])
+def test_batch_plans_agree(max_chunks, policy, graph, tile_order):
     host, jobs = make_jobs(SMALL_MIX[:7], seed=41)
-    b = xe.XBatch(jobs, xe.xeng._opts(max_chunks, policy, graph))
+    b = xe.XBatch(jobs, xe.xeng._opts(max_chunks, policy, graph, tile_order))
+    assert b.info()["tile_order"] == tile_order
     for _ in range(2):  # a second run overwrites (split outputs are cleared first)
         b.run()
     torch.cuda.synchronize()
@@ -84,15 +88,20 @@ def test_batch_rejects_bad_jobs():
     assert rc == xe.XENG_ERR_ARG
     rc, _ = xe.xeng_batch_create([])
     assert rc == xe.XENG_ERR_ARG
+    rc, _ = xe.xeng_batch_create([(8, 1, 4, blk, out)], xe.xeng._opts(0, xe.XENG_SCHED_LPT, True, 3))
+    assert rc == xe.XENG_ERR_ARG  # unknown tile order
 
 
 def test_autotune_and_cache():
     _, jobs = make_jobs([(2048, 4, 256), (512, 2, 600), (9000, 1, 130)], seed=42)
     with tempfile.TemporaryDirectory() as d:
-        path = os.path.join(d, "tune.txt")
+        path = os.path.join(d, "tune.jsonl")
         rc, best, ms = xe.xeng_batch_autotune(jobs, path, reps=2)
         assert rc == 0 and ms > 0
         assert best.max_chunks_per_item in (16, 32, 64, 128, 256, 512)
+        assert best.tile_order in (xe.XENG_TILES_ROW_MAJOR, xe.XENG_TILES_DIAGONAL, xe.XENG_TILES_MORTON)
+        rec = json.loads(open(path).read().splitlines()[-1])  # the cache is JSON lines
+        assert rec["max_chunks"] == best.max_chunks_per_item and rec["tile_order"] == best.tile_order
         rc2, best2, ms2 = xe.xeng_batch_autotune(jobs, path, reps=2)
         assert rc2 == 1 and best2.as_dict() == best.as_dict() and abs(ms2 - ms) < 1e-3
     b = xe.XBatch(jobs, best)
