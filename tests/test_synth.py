@@ -48,3 +48,23 @@ def test_device_matches_host(recipe):
     d = recipe.device()
     torch.cuda.synchronize()
     assert np.array_equal(d.cpu().numpy(), recipe.host())
+
+
+def test_batched_workload_recipes():
+    """The 64-job batched workload: sizes drawn from the stated sets, T
+    log-uniform on [1024, 32768] in steps of 256, deterministic, and every job a
+    different sub-stream of the seed."""
+    jobs = synth.batched_jobs()
+    again = synth.batched_jobs()
+    assert len(jobs) == 64
+    assert [(r.N, r.F, r.T) for r in jobs] == [(r.N, r.F, r.T) for r in again]
+    for r in jobs:
+        assert r.N in synth.BATCH_N and r.F in synth.BATCH_F
+        assert 1024 <= r.T <= 32768 and r.T % 256 == 0
+    assert len({r.N for r in jobs}) >= 6 and len({r.F for r in jobs}) == 3
+    # log-uniform T: about as many jobs below the geometric middle (~5800) as above it
+    below = sum(r.T < 5793 for r in jobs)
+    assert 20 <= below <= 44
+    assert len({r.stream for r in jobs}) == 64
+    total = sum(r.T * r.F * r.N for r in jobs)
+    assert total < 120 << 30  # fits the HBM budget with its planes and outputs
