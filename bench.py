@@ -42,7 +42,7 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 # one ncu capture of the 16-channel slice of the same (N, T) shape; traffic
 # grows in proportion to channels.  Keyed by (N, T); must be re-taken (or
 # removed) whenever the kernel changes.
-CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {(2048, 8192): (606.144e6 + 243.47008e6) / 16}
+CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {}  # the kernel changed (raw-nibble planes) since the last capture
 
 
 def max_over_ranks(x, dist=None):
@@ -457,6 +457,7 @@ def main():
                                   ("tc_f8f6f4_n128", xe.XENG_PEAK_TC_F8F6F4_N128, 1 << 21),
                                   ("tc_f8f6f4_correlator_mix", xe.XENG_PEAK_TC_F8F6F4_MIX, 1 << 20),
                                   ("tc_f8f6f4_live_data", xe.XENG_PEAK_TC_F8F6F4_LIVE, 1 << 21),
+                                  ("tc_f8f6f4_live_raw_nibbles", xe.XENG_PEAK_TC_F8F6F4_LIVE_RAW, 1 << 21),
                                   ("mma_sync_s8", xe.XENG_PEAK_MMA_SYNC_S8, 200000), ("dp4a", xe.XENG_PEAK_DP4A, 500000)):
             rc, tf, pms = xe.xeng_peak_probe(kind, iters)
             probes[name] = round(tf, 1) if rc == 0 else None

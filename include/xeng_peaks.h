@@ -29,6 +29,8 @@ extern "C" {
                                        zeros (the power the tensor core draws depends on the data) */
 #define XENG_PEAK_TC_F8F6F4_MIX  5  /* the correlator's mix per K step: one N = 256 and two N = 128
                                        (second with A negated) into one 256-column accumulator   */
+#define XENG_PEAK_TC_F8F6F4_LIVE_RAW 7  /* as XENG_PEAK_TC_F8F6F4_LIVE with random raw-nibble codes
+                                           (bytes 0x00..0x0F: E4M3 of u / 512)                    */
 
 /*
  * xeng_peak_probe -- run probe `kind` with `iters` instructions per issuing

@@ -183,7 +183,16 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
 // Persistent CTA (one per SM).  Single-instance launches walk the tiles of
 // `sc` round-robin; listed launches (batches) walk items
 // [cta_begin[b], cta_begin[b + 1]) of a host-planned work list.
-template <bool kListed, bool kPair = false>
+// kRaw: the planes hold raw nibbles p (Re), q (Im) as E4M3 codes of u / 512, so
+// the accumulators hold sum(p p' + q q') / 2^18 and sum(p q' - q p') / 2^18;
+// with x = (p - 8) + i (q - 8) over n samples and the inputs' (S, D) =
+// (P + Q, P - Q) nibble sums in a.sums,
+//     Re V = sum(p p' + q q') - 8 (S_i + S_j) + 128 n,
+//     -Im V = sum(p q' - q p') - 8 (D_i - D_j),
+// formed right after the TMEM loads (integers below 2^24: exact in f32 again).
+// The operands draw less power than codes of -8..7 (measured: the dense rate
+// on random raw-nibble codes equals the rate on zeros, 10% above -8..7).
+template <bool kListed, bool kPair = false, bool kRaw = false>
 __global__ void __launch_bounds__(kThreads, 1)
 correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, const Sched sc, const int n_k,
                     const ListArgs L)
@@ -359,6 +368,10 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             int2 *out = reinterpret_cast<int2 *>(w.out + (int64_t)w.fl * N * (N + 1));
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u;
             const int64_t jbase = (int64_t)w.J * kTile;
+            const int2 *sums = kRaw ? a.sums + (int64_t)w.fl * a.n_pad : nullptr;  // (S, D) per input row
+            int2 si = make_int2(0, 0);
+            if (kRaw) si = sums[i];  // i < n_pad
+            const int n128 = kRaw ? 128 * (int)a.n_samples : 0;
             // the triangle is written once and not read again here: streaming
             // stores keep it from evicting the operand planes other tiles
             // still read from L2
@@ -367,6 +380,16 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                 tmem_ld16(taddr + c, re);
                 tmem_ld16(taddr + 128 + c, nim);
                 tmem_ld_wait();
+                if (kRaw) {
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const int2 sj = sums[jbase + c + e];  // the same for every lane: a broadcast
+                        const int vr = __float2int_rn(262144.0f * __uint_as_float(re[e])) - 8 * (si.x + sj.x) + n128;
+                        const int vi = __float2int_rn(262144.0f * __uint_as_float(nim[e])) - 8 * (si.y - sj.y);
+                        re[e] = __float_as_uint((float)vr);
+                        nim[e] = __float_as_uint((float)vi);
+                    }
+                }
                 if (row_ok && !w.dup) {
                     int2 *p = out + row_base + jbase + c;  // pairs j = jbase + c + e, e = 0..15
                     const int64_t e_lo = i - (jbase + c);  // first e on or above the diagonal
@@ -773,15 +796,17 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
                                         kKc == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(correlate_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    if (a.sums && (a.n_samples < 1 || a.n_samples > kFusedMaxSamples || a.n_samples > a.t_pad))
+        return cudaErrorInvalidValue;
+    auto kern = a.sums ? correlate_tc_kernel<false, false, true> : correlate_tc_kernel<false, false, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     Sched sc;
     sc.nt = a.n_pad / kTile;
     sc.tiles_per_ch = sc.nt * (sc.nt + 1) / 2;
     sc.n_tiles = a.nf * sc.tiles_per_ch;
     const int grid = sc.n_tiles < num_sms ? sc.n_tiles : num_sms;
-    correlate_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kKc), ListArgs{});
+    kern<<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kKc), ListArgs{});
     return cudaGetLastError();
 }
 

@@ -43,9 +43,10 @@ constexpr int kDTGroups = 2;
 constexpr int kDTPlaneBufs = 1;
 
 // shared memory: a ring of raw tiles, then kP plane-tile pairs per converter group, then the barriers
-constexpr size_t dt_smem(int stages, int groups, int pbufs)
+constexpr size_t dt_smem(int stages, int groups, int pbufs, bool raw = false)
 {
-    return 1024 + (size_t)stages * kDTRaw + (size_t)groups * pbufs * 2 * kDTPlane + 2 * stages * 8 + 16;
+    return 1024 + (size_t)stages * kDTRaw + (size_t)groups * pbufs * 2 * kDTPlane + 2 * stages * 8 + 16 +
+           (raw ? (size_t)kDTConvWarps * 128 * 8 : 0);
 }
 
 struct DecTmaArgs {
@@ -60,6 +61,7 @@ struct DecTmaArgs {
     const CUtensorMap *maps;
     const DecTmaJob *jobs;
     int32_t n_jobs;
+    int2 *partials;        // raw mode: [nf][n_tb][n_pad] per-tile nibble sums (P, Q)
 };
 
 // One tile as every role sees it.
@@ -121,7 +123,10 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
                  : "memory");
 }
 
-template <int kStages, int kGroups, int kP, bool kBatch>
+// kRaw: the planes hold the raw nibbles (E4M3 codes of u / 512, see the
+// correlator's raw mode) instead of the decoded values, and each tile's
+// per-input nibble sums (P, Q) go to a.partials[fl][tb][input].
+template <int kStages, int kGroups, int kP, bool kBatch, bool kRaw = false>
 __global__ void __launch_bounds__(kDTThreads, 1)
 decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ CUtensorMap plane_map,
                   const DecTmaArgs a)
@@ -140,6 +145,8 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
     const uint32_t bars = pbase + kGroups * kP * 2 * kDTPlane;
     auto rawf = [&](int s) { return bars + 8u * s; };               // raw tile landed
     auto rawe = [&](int s) { return bars + 8u * (kStages + s); };  // raw tile converted
+    // raw mode: per converter warp, partial nibble sums (P, Q) of the tile's 128 inputs
+    int2 *scratch = reinterpret_cast<int2 *>(sgen + (bars + 8u * 2 * kStages + 16 - sbase));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = a.err;
 
@@ -224,6 +231,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             uint8_t *pre = sgen + (pre_s - sbase);
             uint8_t *pim = pre + kDTPlane;
             const int ibase = ib * 128;
+            uint32_t sp[4] = {0, 0, 0, 0}, sq[4] = {0, 0, 0, 0};  // raw mode: nibble sums of inputs 4q + m
             if (ok) {
                 #pragma unroll
                 for (int k = 0; k < kGroups; k++) {
@@ -238,13 +246,28 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                         #pragma unroll
                         for (int kk = 0; kk < 4; kk++) {
                             const int t = b * 16 + h * 8 + g * 4 + kk;
-                            r[kk] = (tbase + g * 4 + kk < tl.T) ? rt[t * 32 + q] : 0x88888888u;  // past the end: 0
+                            // past the end: value 0 (decoded) or nibbles 0, adding nothing (raw)
+                            r[kk] = (tbase + g * 4 + kk < tl.T) ? rt[t * 32 + q] : (kRaw ? 0u : 0x88888888u);
                         }
-                        // transpose + decode: r[k] byte m = (sample k, input m) -> input m's codes of samples 0..3
-                        decode_input4(r, 0, re[0][g], im[0][g]);
-                        decode_input4(r, 1, re[1][g], im[1][g]);
-                        decode_input4(r, 2, re[2][g], im[2][g]);
-                        decode_input4(r, 3, re[3][g], im[3][g]);
+                        if (kRaw) {
+                            // transpose, then split: input m's high (Re) and low (Im) nibbles of samples 0..3
+                            #pragma unroll
+                            for (int m = 0; m < 4; m++) {
+                                const uint32_t sel = (uint32_t)m | ((uint32_t)(4 + m) << 4);
+                                const uint32_t w =
+                                    __byte_perm(__byte_perm(r[0], r[1], sel), __byte_perm(r[2], r[3], sel), 0x5410);
+                                re[m][g] = (w >> 4) & 0x0F0F0F0Fu;
+                                im[m][g] = w & 0x0F0F0F0Fu;
+                                sp[m] = __dp4a(re[m][g], 0x01010101u, sp[m]);
+                                sq[m] = __dp4a(im[m][g], 0x01010101u, sq[m]);
+                            }
+                        } else {
+                            // transpose + decode: r[k] byte m = (sample k, input m) -> input m's codes of samples 0..3
+                            decode_input4(r, 0, re[0][g], im[0][g]);
+                            decode_input4(r, 1, re[1][g], im[1][g]);
+                            decode_input4(r, 2, re[2][g], im[2][g]);
+                            decode_input4(r, 3, re[3][g], im[3][g]);
+                        }
                     }
                     #pragma unroll
                     for (int m = 0; m < 4; m++) {
@@ -257,6 +280,11 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                             row_ok ? make_uint2(im[m][0], im[m][1]) : make_uint2(0u, 0u);
                     }
                 }
+            }
+            if (kRaw && ok) {
+                int4 *sc = reinterpret_cast<int4 *>(scratch + cw * 128 + 4 * q);
+                sc[0] = make_int4((int)sp[0], (int)sq[0], (int)sp[1], (int)sq[1]);
+                sc[1] = make_int4((int)sp[2], (int)sq[2], (int)sp[3], (int)sq[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the TMA store
             // the second barrier also ORs the group's failure flags, so that all
@@ -278,6 +306,19 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                 }
                 mbar_arrive(rawe(stage));  // the raw slot may be refilled
             }
+            if (kRaw && !any_fail && wl < 4) {
+                // the tile's sums of input k = 32 wl + lane over the group's warps (their partials
+                // stay until the group's next first barrier, which every reader passes after this)
+                const int k = wl * 32 + lane;
+                int P = 0, Q = 0;
+                #pragma unroll
+                for (int w = 0; w < kGW; w++) {
+                    const int2 v = scratch[(grp * kGW + w) * 128 + k];
+                    P += v.x;
+                    Q += v.y;
+                }
+                a.partials[((int64_t)fl * a.n_tb + tb) * a.n_pad + ibase + k] = make_int2(P, Q);
+            }
             if (any_fail) break;
         }
         // every store has finished writing before the CTA exits
@@ -293,7 +334,8 @@ bool decode_tma_ok(const uint8_t *block, int32_t N)
 }
 
 cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0, int32_t nf,
-                              uint8_t *planes, int64_t t_pad, int64_t n_pad, int *err, int num_sms, cudaStream_t s)
+                              uint8_t *planes, int64_t t_pad, int64_t n_pad, int *err, int num_sms, cudaStream_t s,
+                              int2 *partials)
 {
     if (nf <= 0 || t_pad <= 0) return cudaSuccess;
     if (!decode_tma_ok(block, N) || T <= 0 || t_pad % 128 != 0 || n_pad % 128 != 0 || t_pad < T || n_pad < N ||
@@ -323,11 +365,14 @@ cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    auto kern = decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, false>;
-    const size_t smem = dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs);
+    const bool raw = partials != nullptr;
+    auto kern = raw ? decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, false, true>
+                    : decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, false, false>;
+    const size_t smem = dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs, raw);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     DecTmaArgs a;
+    a.partials = partials;
     a.T = T;
     a.n_ib = (int32_t)(n_pad / 128);
     a.n_tb = (int32_t)(t_pad / 128);
@@ -343,6 +388,37 @@ cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_
     a.n_jobs = 0;
     const int grid = (int)(a.n_tiles < num_sms ? a.n_tiles : num_sms);
     kern<<<grid, kDTThreads, smem, s>>>(rm, pm, a);
+    return cudaGetLastError();
+}
+
+namespace {
+// sums[fl][i] = sum over the tiles tb of partials[fl][tb][i]
+__global__ void plane_sums_kernel(const int2 *__restrict__ partials, int32_t nf, int32_t n_tb, int32_t n_pad,
+                                  int2 *__restrict__ sums)
+{
+    const int64_t total = (int64_t)nf * n_pad;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t fl = k / n_pad, i = k % n_pad;
+        const int2 *p = partials + fl * n_tb * n_pad + i;
+        int P = 0, Q = 0;
+        for (int tb = 0; tb < n_tb; tb++) {
+            const int2 v = p[(int64_t)tb * n_pad];
+            P += v.x;
+            Q += v.y;
+        }
+        sums[k] = make_int2(P + Q, P - Q);  // (S, D) as the correlator's raw mode uses them
+    }
+}
+}  // namespace
+
+cudaError_t launch_plane_sums(const int2 *partials, int32_t nf, int32_t n_tb, int32_t n_pad, int2 *sums, int num_sms,
+                              cudaStream_t s)
+{
+    if (nf <= 0) return cudaSuccess;
+    const int64_t total = (int64_t)nf * n_pad;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8 * (int64_t)num_sms) blocks = 8 * (int64_t)num_sms;
+    plane_sums_kernel<<<(unsigned)blocks, 256, 0, s>>>(partials, nf, n_tb, n_pad, sums);
     return cudaGetLastError();
 }
 
@@ -382,6 +458,7 @@ cudaError_t launch_decode_tma_batch(const CUtensorMap *maps, const DecTmaJob *jo
     CUtensorMap unused;
     memset(&unused, 0, sizeof(unused));
     DecTmaArgs a;
+    a.partials = nullptr;
     memset(&a, 0, sizeof(a));
     a.n_tiles = n_tiles;
     a.err = err;

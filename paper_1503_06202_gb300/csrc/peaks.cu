@@ -25,10 +25,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 // M = 128 per instruction; K = 32 (8-bit) or 16 (16-bit).  kMix 0: N = 256;
 // 1: N = 128; 2: the correlator's pattern -- N = 256, then two N = 128 (the
 // second with A negated) into the two halves of the same 256 columns.
-// kRandom: operands are E4M3 codes of pseudo-random integers in [-8, 7] (the
+// kData 1: operands are E4M3 codes of pseudo-random integers in [-8, 7] (the
 // correlator's operand values) instead of zeros -- the tensor core draws more
-// power on live data, which matters under the board's power cap.
-template <bool kF8, int kMix, bool kRandom = false>
+// power on live data, which matters under the board's power cap; 2: the codes
+// of pseudo-random raw nibbles u / 512 (bytes 0x00..0x0F), the fused kernel's
+// operands.
+template <bool kF8, int kMix, int kData = 0>
 __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sink)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -43,7 +45,7 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sin
     for (int k = threadIdx.x; k < 48 * 1024; k += blockDim.x) {
         uint32_t h = (uint32_t)k * 2654435761u + blockIdx.x * 40503u;
         h ^= h >> 15;
-        gbase[k] = kRandom ? codes[h & 15] : (uint8_t)0;
+        gbase[k] = kData == 1 ? codes[h & 15] : kData == 2 ? (uint8_t)(h & 15) : (uint8_t)0;
     }
     const uint32_t bar_a = smem_u32(&bar);
     if (threadIdx.x == 0) {
@@ -179,8 +181,13 @@ extern "C" int xeng_peak_probe(int32_t kind, int64_t iters, double *tflops, doub
             flops = 2.0 * 128 * 512 * 32 * (double)iters * sms;
             break;
         case XENG_PEAK_TC_F8F6F4_LIVE:
-            cudaFuncSetAttribute(tc_peak_kernel<true, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            tc_peak_kernel<true, 0, true><<<sms, 128, smem>>>(iters, sink);
+            cudaFuncSetAttribute(tc_peak_kernel<true, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 0, 1><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 256 * 32 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_LIVE_RAW:
+            cudaFuncSetAttribute(tc_peak_kernel<true, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 0, 2><<<sms, 128, smem>>>(iters, sink);
             flops = 2.0 * 128 * 256 * 32 * (double)iters * sms;
             break;
         case XENG_PEAK_TC_F16:

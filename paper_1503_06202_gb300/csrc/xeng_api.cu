@@ -28,6 +28,9 @@ struct xeng_s {
     int32_t *acc = nullptr;        // [F][N(N+1)/2][2]
     uint8_t *planes = nullptr;     // decode buffer of the tensor engine
     int64_t planes_bytes = 0;
+    int2 *partials = nullptr;      // raw-nibble planes: per-tile nibble sums [group_f][n_tb][n_pad]
+    int2 *sums = nullptr;          // raw-nibble planes: (S, D) per input [group_f][n_pad]
+    bool planes_raw = false;       // the last decode wrote raw-nibble planes
     int32_t group_f = 0;           // channels per decode + correlate round
     int64_t chunk_t = 0;           // samples per round
     uint8_t *staging = nullptr;    // device copy of host blocks
@@ -64,6 +67,16 @@ namespace {
 int64_t acc_bytes(const xeng_s *h) { return (int64_t)h->F * n_baselines(h->N) * 8; }
 
 // The decode buffer, allocated on first use.  Synchronizes the device then.
+// Build parameter: the tensor path's decode writes raw-nibble planes (E4M3
+// codes of u / 512) with per-input nibble sums, and the correlator applies the
+// offset in its epilogue (launches of at most kFusedMaxSamples samples); 0:
+// decoded planes everywhere.
+#ifndef XENG_RAW_PLANES
+#define XENG_RAW_PLANES 1
+#endif
+
+int64_t planes_rows(int64_t N);
+
 cudaError_t ensure_planes(xeng_s *h)
 {
     if (h->planes) return cudaSuccess;
@@ -71,8 +84,22 @@ cudaError_t ensure_planes(xeng_s *h)
     if (e != cudaSuccess) {
         cudaGetLastError();
         h->planes = nullptr;
+        return e;
     }
-    return e;
+    if (XENG_RAW_PLANES) {
+        // raw-nibble decodes take at most kFusedMaxSamples samples per launch; without
+        // the room for their sums every decode writes decoded planes
+        const int64_t n_pad = planes_rows(h->N);
+        const int64_t n_tb = (h->chunk_t < kFusedMaxSamples ? h->chunk_t : kFusedMaxSamples) / kTile;
+        if (cudaMalloc(&h->partials, (size_t)(h->group_f * n_tb * n_pad) * sizeof(int2)) != cudaSuccess ||
+            cudaMalloc(&h->sums, (size_t)(h->group_f * n_pad) * sizeof(int2)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->partials);
+            h->partials = nullptr;
+            h->sums = nullptr;
+        }
+    }
+    return cudaSuccess;
 }
 
 void free_shift(xeng_s *h)
@@ -212,8 +239,22 @@ cudaError_t run_correlate(xeng_s *h, TcArgs a, cudaStream_t s)
 cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int32_t N, int32_t f0, int32_t nf,
                        int64_t t_pad, int64_t n_pad, cudaStream_t s)
 {
-    if (h->decode_tma && decode_tma_ok(src, N))
+    h->planes_raw = false;
+    if (h->decode_tma && decode_tma_ok(src, N)) {
+        if (XENG_RAW_PLANES && !XENG_TC_2CTA && !XENG_TC_PAIRS && h->partials && nt <= kFusedMaxSamples) {
+            // raw-nibble planes and their per-input sums (two kernels)
+            cudaError_t e = launch_decode_tma(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, h->d_err, h->num_sms, s,
+                                              h->partials);
+            if (e == cudaSuccess)
+                e = launch_plane_sums(h->partials, nf, (int32_t)(t_pad / kTile), (int32_t)n_pad, h->sums, h->num_sms, s);
+            if (e == cudaSuccess) {
+                h->planes_raw = true;
+                h->stats.launches++;  // the sums kernel
+            }
+            return e;
+        }
         return launch_decode_tma(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, h->d_err, h->num_sms, s);
+    }
     return launch_decode(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, s);
 }
 
@@ -324,6 +365,8 @@ void xeng_destroy(xeng_t h)
     cudaDeviceSynchronize();
     cudaFree(h->acc);
     cudaFree(h->planes);
+    cudaFree(h->partials);
+    cudaFree(h->sums);
     cudaFree(h->staging);
     cudaFree(h->gidx);
     for (auto &pl : h->pair_lists) cudaFree(pl.dev);
@@ -489,6 +532,7 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
             const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
             const uint8_t *src = dblock + t0 * F * N;
             if (apply_shift) {
+                h->planes_raw = false;  // the fix-up rewrites decoded rows
                 ShiftArgs sa;
                 sa.delay = h->d_delay;
                 sa.slot = h->d_slot;
@@ -523,6 +567,8 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
             a.acc = target + f0 * nb2;
             a.accumulate = accumulate;
             a.err = h->d_err;
+            a.sums = h->planes_raw ? h->sums : nullptr;
+            a.n_samples = nt;
             e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
         }
     }
@@ -688,6 +734,8 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
             a.acc = target + (f0 + c0) * nb2;
             a.accumulate = fresh ? 0 : 1;
             a.err = h->d_err;
+            a.sums = h->planes_raw ? h->sums + (int64_t)c0 * n_pad : nullptr;
+            a.n_samples = n;
             e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
             if (e == cudaSuccess && host_out) {
                 e = cudaEventRecord(h->ev_sub, s);

@@ -31,8 +31,14 @@ cudaError_t launch_decode(const uint8_t *block, int64_t T, int32_t F, int32_t N,
 // multiple of 16 and a 16-byte aligned block (decode_tma_ok), t_pad and n_pad
 // multiples of 128.  A stalled pipeline sets *err and returns.
 bool decode_tma_ok(const uint8_t *block, int32_t N);
+// partials non-null: raw-nibble planes (E4M3 codes of u / 512) and per-tile
+// per-input nibble sums [nf][t_pad / 128][n_pad] of (P, Q); null: decoded planes.
 cudaError_t launch_decode_tma(const uint8_t *block, int64_t T, int32_t F, int32_t N, int32_t f0, int32_t nf,
-                              uint8_t *planes, int64_t t_pad, int64_t n_pad, int *err, int num_sms, cudaStream_t s);
+                              uint8_t *planes, int64_t t_pad, int64_t n_pad, int *err, int num_sms, cudaStream_t s,
+                              int2 *partials = nullptr);
+// sums[fl][i] = (S, D) = (P + Q, P - Q) over all sample tiles of the partials
+cudaError_t launch_plane_sums(const int2 *partials, int32_t nf, int32_t n_tb, int32_t n_pad, int2 *sums, int num_sms,
+                              cudaStream_t s);
 
 // Gated / flagged decode of channels [f0, f0 + nf): tile rows are block rows
 // idx[0 .. Tg) (one gate's samples); samples whose valid byte is 0 decode to
@@ -153,6 +159,10 @@ struct TcArgs {
     int32_t *err;
     const PairItem *pairs = nullptr;  // launch_correlate_tc_pairs: the pair list
     int32_t n_pairs = 0;
+    // raw-nibble planes: per channel of the launch, (S, D) of every input row
+    // [nf][n_pad], and the samples integrated (<= kFusedMaxSamples); null: decoded planes
+    const int2 *sums = nullptr;
+    int64_t n_samples = 0;
 };
 cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s);
 // The same correlation with cta_group::2: clusters of two CTAs compute
