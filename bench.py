@@ -660,7 +660,9 @@ def main():
     if args.engine == "tensor":
         peak = 2.0 * peaks["bf16_tflops_sustained"]
         peak_note = ("fp8 dense = 2 x %s sustained bf16 %.1f TFLOP/s (nominal fp8:bf16 = 4.5:2.25); "
-                     "sm_103a has no tcgen05 kind::i8" % (peak_src, peaks["bf16_tflops_sustained"]))
+                     "sm_103a has no tcgen05 kind::i8; the bf16 figure was sustained at a power-capped clock, "
+                     "so frac can exceed 1 -- the fp8 probes measured in this run (peak_probe_*) are the "
+                     "ceilings at this kernel's clock" % (peak_src, peaks["bf16_tflops_sustained"]))
         per_ch = CORRELATE_TC_DRAM_BYTES_PER_CHANNEL.get((N, T))
         traffic = per_ch * F / launches_per_step if per_ch else None
         roof = {"bound": "tensor", "kernel": "correlate_tc_kernel", "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12,
@@ -678,6 +680,11 @@ def main():
             roof["peak_probe_fp8_live_data"] = probes["tc_f8f6f4_live_data"]
             roof["frac_executed_of_probe_fp8_live_data"] = (roof["achieved"] * roof.get("executed_over_useful", 1.0)
                                                            / probes["tc_f8f6f4_live_data"])
+        if probes and probes.get("tc_f8f6f4_live_raw_nibbles"):
+            # the operands the tensor path feeds: codes of raw nibbles (u / 512)
+            roof["peak_probe_fp8_live_raw_nibbles"] = probes["tc_f8f6f4_live_raw_nibbles"]
+            roof["frac_executed_of_probe_fp8_live_raw_nibbles"] = (
+                roof["achieved"] * roof.get("executed_over_useful", 1.0) / probes["tc_f8f6f4_live_raw_nibbles"])
         if probes and probes.get("mma_sync_s8"):
             roof["frac_of_probe_int8_mma_sync"] = roof["achieved"] / probes["mma_sync_s8"]
     else:
