@@ -7,7 +7,8 @@ the floating-point formats' definitions and the oracle (no CUDA code runs):
 * with p, q the Re and Im nibbles (x = (p - 8) + i (q - 8)), the visibilities
   follow from sums over the raw nibbles and per-input nibble sums
   (Re V = sum(pp' + qq') - 8 (S_i + S_j) + 128 T, Im V = sum(qp' - pq') +
-  8 (D_i - D_j)), which is what the fused N <= 256 kernel's epilogue applies;
+  8 (D_i - D_j)), which is what the epilogues of the fused N <= 256 kernel
+  and of the tensor path's correlator on raw-nibble planes apply;
 * the beams follow from the raw nibbles and per-(channel, beam) offset terms
   (8 sum(w_re - w_im), 8 sum(w_re + w_im)), as the beamformer applies them;
 * the beamformer reads an integer S out of the float S / 64 + 1.5 * 2^17
