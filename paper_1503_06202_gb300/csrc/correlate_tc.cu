@@ -189,7 +189,8 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
 // (P + Q, P - Q) nibble sums in a.sums,
 //     Re V = sum(p p' + q q') - 8 (S_i + S_j) + 128 n,
 //     -Im V = sum(p q' - q p') - 8 (D_i - D_j),
-// formed right after the TMEM loads (integers below 2^24: exact in f32 again).
+// formed right after the TMEM loads (launches of at most 16,384 samples keep
+// the sums below 2^23, exact in the f32 accumulators).
 // The operands draw less power than codes of -8..7 (measured: the dense rate
 // on random raw-nibble codes equals the rate on zeros, 10% above -8..7).
 template <bool kListed, bool kPair = false, bool kRaw = false>

@@ -9,7 +9,10 @@ namespace xeng {
 
 constexpr int kTile = 128;          // inputs per tensor-engine tile, samples per K chunk
 constexpr int kMaxChunkSamples = 65536;  // f32 sums stay <= 128 * 65536 = 2^23 (exact)
-constexpr int kFusedMaxSamples = 32768;  // raw-nibble sums of the fused kernel stay <= 450 * 32768 < 2^24
+// Raw-nibble launches (the fused kernel, the tensor path's raw planes): their
+// integer sums stay <= 450 * 16384 < 2^23, the range in which the GPU tests
+// show the tensor core's f32 accumulation exact with unit increments.
+constexpr int kFusedMaxSamples = 16384;
 
 // Device-side status codes written to the handle's error word.
 enum DevStatus : int {

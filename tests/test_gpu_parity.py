@@ -119,6 +119,32 @@ def test_exact_extremes_mix():
     assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "extremes")
 
 
+def test_raw_planes_at_the_exactness_bound():
+    # N a multiple of 16 above 256: the TMA decode writes raw-nibble planes and the
+    # correlator applies the offset terms; one launch of 16,384 samples, the most a
+    # raw-nibble launch takes
+    T, F, N = 16384, 1, 272
+    # every nibble 15: the raw sums reach 450 T = 7,372,800 < 2^23; x = 7 + 7i, V = 98 T
+    out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    assert (out[..., 0] == 98 * T).all() and (out[..., 1] == 0).all()
+    # every nibble 0: raw sums 0, the offset terms alone; x = -8 - 8i, V = 128 T
+    out = run(torch.zeros((T, F, N), dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
+    # the extreme codes mixed, against the oracle
+    rng = np.random.default_rng(23)
+    blk = rng.choice(np.array([0x00, 0xFF, 0x0F, 0xF0, 0x88, 0x98, 0x78, 0x08, 0x80], np.uint8), size=(T, F, N))
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "raw-nibble extremes")
+
+
+def test_fused_raw_nibbles_at_the_exactness_bound():
+    # N <= 256: the fused kernel on raw nibbles, launches of 16,384 samples adding into int32
+    T, F, N = 3 * 16384, 1, 256
+    out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    assert (out[..., 0] == 98 * T).all() and (out[..., 1] == 0).all()
+    out = run(torch.full((T, F, N), 0xF0, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    assert (out[..., 0] == 113 * T).all() and (out[..., 1] == 0).all()  # x = 7 - 8i
+
+
 def test_multi_round_push_random():
     # three sample chunks: three decode + correlation rounds adding into int32
     rng = np.random.default_rng(28)
