@@ -424,7 +424,8 @@ XENG_API int xserve_stats(xserve_t sv, xserve_stats_t *out);
 /* xserve_destroy -- stop the worker (queued blocks are dropped) and free everything. */
 XENG_API void xserve_destroy(xserve_t sv);
 
-/* Size of the fixed device array xeng_correlate_noalloc works in (64 MiB). */
+/* Size of the decode area of the fixed device array xeng_correlate_noalloc
+ * works in (64 MiB; the array holds 256 bytes more for a status word). */
 #define XENG_NOALLOC_SCRATCH_BYTES 67108864LL
 
 /*
@@ -440,17 +441,20 @@ XENG_API void xserve_destroy(xserve_t sv);
  *   out:   [n_freq][N(N+1)/2][2] int32, device memory (caller-owned),
  *          8-byte aligned; overwritten (n_samples == 0 writes zeros).
  *   Working memory is one library-owned __device__ array of
- *   XENG_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until
- *   the process exits.  Sizes beyond what it holds are rejected with
- *   XENG_ERR_RANGE: n_samples <= 65536 and
- *   2 * round_up(N, 128) * round_up(n_samples, 128) <= XENG_NOALLOC_SCRATCH_BYTES - 256
- *   (e.g. N = 2048 with 8192 samples, or N = 256 with 65536 samples).
+ *   XENG_NOALLOC_SCRATCH_BYTES + 256 bytes that each GPU loading the library
+ *   holds until the process exits.  Sizes beyond what it holds are rejected
+ *   with XENG_ERR_RANGE: n_samples <= 65536 and
+ *   2 * round_up(N, 128) * round_up(n_samples, 128) <= XENG_NOALLOC_SCRATCH_BYTES
+ *   (e.g. N = 2048 with 16384 samples, or N = 256 with 65536 samples).
  *   Host pointers give XENG_ERR_ARG.  The call enqueues its work on `stream`
  *   and returns once it is done (it synchronizes `stream`); a device-side
  *   wait time-out gives XENG_ERR_TIMEOUT.  It calls no cudaMalloc, cudaFree
  *   or other allocating routine.
  *   The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.  All
+ *   device current; make that first call before any stream capture.  That
+ *   address is kept for the life of the process and does not survive
+ *   cudaDeviceReset: do not call this entry point on a device after
+ *   resetting it.  All
  *   calls on a device share the array: calls that overlap on the GPU (from
  *   several threads or streams) race and give wrong results.
  */

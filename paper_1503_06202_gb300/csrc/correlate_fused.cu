@@ -27,8 +27,8 @@
 // nibbles.  The converters form P and Q as they go; at the end of a channel
 // each CTA reduces its inputs' sums and writes them into both CTAs' shared
 // memory (the epilogue of a row needs the sums of every column).  The MMA sums
-// are integers / 2^18 below 450 n / 2^18; with n <= 16384 per launch they stay
-// below 2^23 / 2^18, where the f32 accumulation is exact.
+// are integers / 2^18 below 450 n / 2^18; with n <= 32768 per launch they stay
+// below 2^24 / 2^18, where the f32 accumulation is exact.
 //
 // Roles per CTA (704 threads):
 //   warp 0       TMA producer: raw tiles (128 inputs x 128 samples of one channel)

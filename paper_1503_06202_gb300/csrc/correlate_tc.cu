@@ -107,54 +107,16 @@ struct Work {
     int fl, I, J;
     int kc0, kc1;    // 128-sample chunks [kc0, kc1)
     int mode;
-    bool shared;     // pair launch: the peer works on the same A operand
-    bool dup;        // pair launch: this CTA repeats the peer's tile, writes nothing
 };
 
 
 
-// TMA load whose box lands at the same offset in the shared memory of every
-// CTA of the cluster in `mask`, completing bytes on each one's barrier there.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
-                 : "memory");
-}
-
-template <bool kListed, bool kPair>
+template <bool kListed>
 __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, const TcArgs &a, const Sched &sc, int n_k,
                                            const ListArgs &L)
 {
     Work w;
-    w.shared = false;
-    w.dup = false;
-    if (kPair) {
-        const PairItem pi = a.pairs[it];
-        const uint32_t r = cluster_rank();
-        w.map = tmap;
-        w.out = a.acc;
-        w.n_pad = a.n_pad;
-        w.N = a.N;
-        w.fl = pi.fl[r];
-        w.I = pi.I[r];
-        w.J = pi.J[r];
-        w.kc0 = 0;
-        w.kc1 = n_k;
-        w.mode = a.accumulate ? kAdd : kStore;
-        w.shared = (pi.flags & 1) != 0;
-        w.dup = (pi.flags & 2) != 0 && r == 1;
-    } else if (kListed) {
+    if (kListed) {
         const WorkItem wi = L.items[it];
         const JobDesc &jd = L.jobs[wi.job];
         w.map = &L.maps[wi.job];
@@ -189,11 +151,11 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
 // (P + Q, P - Q) nibble sums in a.sums,
 //     Re V = sum(p p' + q q') - 8 (S_i + S_j) + 128 n,
 //     -Im V = sum(p q' - q p') - 8 (D_i - D_j),
-// formed right after the TMEM loads (launches of at most 16,384 samples keep
-// the sums below 2^23, exact in the f32 accumulators).
+// formed right after the TMEM loads (launches of at most 32,768 samples keep
+// the sums below 2^24, exact in the f32 accumulators).
 // The operands draw less power than codes of -8..7 (measured: the dense rate
 // on random raw-nibble codes equals the rate on zeros, 10% above -8..7).
-template <bool kListed, bool kPair = false, bool kRaw = false>
+template <bool kListed, bool kRaw = false>
 __global__ void __launch_bounds__(kThreads, 1)
 correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, const Sched sc, const int n_k,
                     const ListArgs L)
@@ -215,17 +177,11 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
     int it_begin = strided ? (int)blockIdx.x : L.cta_begin[blockIdx.x];
     int it_end = !kListed ? sc.n_tiles : (strided ? (int)L.n_items : L.cta_begin[blockIdx.x + 1]);
     int it_step = strided ? (int)gridDim.x : 1;
-    if (kPair) {  // cluster c runs pair items c, c + clusters, ...
-        it_begin = (int)(blockIdx.x >> 1);
-        it_end = a.n_pairs;
-        it_step = (int)(gridDim.x >> 1);
-    }
-    const uint16_t kBoth = 0x3;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), kPair ? 2 : 1);  // pairs: both CTAs' MMAs release a stage
+            mbar_init(empty_bar(s), 1);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(accf_bar(b), 1);
@@ -243,7 +199,6 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
     fence_before();
     __syncthreads();
     fence_after();
-    if (kPair) cluster_sync();  // the peer's barriers exist before anything targets them
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
@@ -254,7 +209,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             int issued = 0;
             bool ok = true;
             for (int it = it_begin; ok && it < it_end; it += it_step) {
-                const Work w = fetch_work<kListed, kPair>(it, &tmap, a, sc, n_k, L);
+                const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
                 const bool diag = (w.I == w.J);
                 const int rowA = w.fl * 2 * w.n_pad + w.I * kTile;
                 const int rowB = w.fl * 2 * w.n_pad + w.J * kTile;
@@ -266,15 +221,8 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                     }
                     const uint32_t st = sbase + stage * kStageBytes;
                     mbar_expect_tx(full_bar(stage), diag ? 2 * kPlaneTile : 4 * kPlaneTile);
-                    if (kPair && w.shared) {
-                        // plane r of the shared A comes from CTA r into both CTAs
-                        const uint32_t r = cluster_rank();
-                        tma_load_2d_mc(st + r * kPlaneTile, w.map, kc * kKc, rowA + (int)r * w.n_pad, full_bar(stage),
-                                       kBoth);
-                    } else {
-                        tma_load_2d(st, w.map, kc * kKc, rowA, full_bar(stage));
-                        tma_load_2d(st + kPlaneTile, w.map, kc * kKc, rowA + w.n_pad, full_bar(stage));
-                    }
+                    tma_load_2d(st, w.map, kc * kKc, rowA, full_bar(stage));
+                    tma_load_2d(st + kPlaneTile, w.map, kc * kKc, rowA + w.n_pad, full_bar(stage));
                     if (!diag) {
                         tma_load_2d(st + 2 * kPlaneTile, w.map, kc * kKc, rowB, full_bar(stage));
                         tma_load_2d(st + 3 * kPlaneTile, w.map, kc * kKc, rowB + w.n_pad, full_bar(stage));
@@ -304,7 +252,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             bool ok = true;
             int local = 0;
             for (int it = it_begin; ok && it < it_end; it += it_step, ++local) {
-                const Work w = fetch_work<kListed, kPair>(it, &tmap, a, sc, n_k, L);
+                const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
                 const bool diag = (w.I == w.J);
                 const int ab = local & 1;
                 if (!mbar_wait(acce_bar(ab), (uses[ab] & 1u) ^ 1u, err, kDevTimeoutMma)) break;
@@ -334,8 +282,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                         mma_f8(d, dai + k2, dbi + k2, kIdescN128, 1u);
                         mma_f8(d + 128u, dai + k2, dbr + k2, kIdescN128Neg, 1u);
                     }
-                    if (kPair) mma_commit_mc(empty_bar(stage), kBoth);
-                    else mma_commit(empty_bar(stage));
+                    mma_commit(empty_bar(stage));
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -355,7 +302,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
         uint32_t uses[2] = {0, 0};
         int local = 0;
         for (int it = it_begin; it < it_end; it += it_step, ++local) {
-            const Work w = fetch_work<kListed, kPair>(it, &tmap, a, sc, n_k, L);
+            const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
             const int ab = local & 1;
             const bool ok = mbar_wait(accf_bar(ab), uses[ab] & 1u, err, kDevTimeoutEpilogue);
             if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
@@ -391,7 +338,7 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                         nim[e] = __float_as_uint((float)vi);
                     }
                 }
-                if (row_ok && !w.dup) {
+                if (row_ok) {
                     int2 *p = out + row_base + jbase + c;  // pairs j = jbase + c + e, e = 0..15
                     const int64_t e_lo = i - (jbase + c);  // first e on or above the diagonal
                     const int64_t e_hi = N - (jbase + c);  // first e past the last input
@@ -526,7 +473,6 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
     __syncwarp();
     fence_before();
     __syncthreads();
-    if (kPair) cluster_sync();  // no copy or commit from the peer may still target this CTA
     fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -799,7 +745,7 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     if (a.sums && (a.n_samples < 1 || a.n_samples > kFusedMaxSamples || a.n_samples > a.t_pad))
         return cudaErrorInvalidValue;
-    auto kern = a.sums ? correlate_tc_kernel<false, false, true> : correlate_tc_kernel<false, false, false>;
+    auto kern = a.sums ? correlate_tc_kernel<false, true> : correlate_tc_kernel<false, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     Sched sc;
@@ -809,77 +755,6 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s)
     const int grid = sc.n_tiles < num_sms ? sc.n_tiles : num_sms;
     kern<<<grid, kThreads, kSmemBytes, s>>>(map, a, sc, (int)(a.t_pad / kKc), ListArgs{});
     return cudaGetLastError();
-}
-
-void build_pair_list(int nt, int nf, std::vector<PairItem> &out)
-{
-    out.clear();
-    bool have = false;
-    PairItem pend{};
-    auto solo = [&](int fl, int I, int J) {
-        if (!have) {
-            pend.fl[0] = fl;
-            pend.I[0] = (int16_t)I;
-            pend.J[0] = (int16_t)J;
-            have = true;
-            return;
-        }
-        pend.fl[1] = fl;
-        pend.I[1] = (int16_t)I;
-        pend.J[1] = (int16_t)J;
-        pend.flags = (pend.fl[0] == fl && pend.I[0] == I) ? 1 : 0;
-        out.push_back(pend);
-        have = false;
-    };
-    for (int fl = 0; fl < nf; fl++)
-        for (int I = 0; I < nt; I++) {
-            int J = I;
-            for (; J + 1 < nt; J += 2) {  // neighbours in a tile row share A
-                PairItem p;
-                p.fl[0] = p.fl[1] = fl;
-                p.I[0] = p.I[1] = (int16_t)I;
-                p.J[0] = (int16_t)J;
-                p.J[1] = (int16_t)(J + 1);
-                p.flags = 1;
-                out.push_back(p);
-            }
-            if (J < nt) solo(fl, I, J);  // an odd row leaves one tile for the next solo
-        }
-    if (have) {  // an odd total: CTA 1 repeats the last tile and writes nothing
-        pend.fl[1] = pend.fl[0];
-        pend.I[1] = pend.I[0];
-        pend.J[1] = pend.J[0];
-        pend.flags = 1 | 2;
-        out.push_back(pend);
-    }
-}
-
-cudaError_t launch_correlate_tc_pairs(const TcArgs &a, int num_sms, cudaStream_t s)
-{
-    if (a.nf <= 0) return cudaSuccess;
-    if (!a.pairs || a.n_pairs <= 0) return cudaErrorInvalidValue;
-    if (a.t_pad % kTile != 0 || a.n_pad % kTile != 0 || a.t_pad > kMaxChunkSamples) return cudaErrorInvalidValue;
-    CUtensorMap map;
-    cudaError_t e = encode_planes_map(&map, a.planes, a.t_pad, (int64_t)a.nf * 2 * a.n_pad);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(correlate_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
-    const int clusters = a.n_pairs < num_sms / 2 ? a.n_pairs : num_sms / 2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * clusters, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = kSmemBytes;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    Sched sc{};
-    return cudaLaunchKernelEx(&cfg, correlate_tc_kernel<false, true>, map, a, sc, (int)(a.t_pad / kKc), ListArgs{});
 }
 
 cudaError_t launch_correlate_tc2(const TcArgs &a, int num_sms, cudaStream_t s)

@@ -20,7 +20,9 @@
 // name is a host-side stand-in, not a device address.  The device address is
 // looked up once per device with cudaGetSymbolAddress, with that device
 // current, on the first call made on it; make that first call before any
-// stream capture.
+// stream capture.  The address is kept for the life of the process: it does
+// not survive cudaDeviceReset, after which this entry point must not be
+// called on that device again.
 #include <mutex>
 
 #include "../../include/xeng.h"
@@ -30,11 +32,13 @@ namespace {
 
 using namespace xeng;
 
-constexpr int64_t kStatusBytes = 256;  // status word, padded to keep the planes 256-byte aligned
-constexpr int64_t kPlaneBytes = (int64_t)XENG_NOALLOC_SCRATCH_BYTES - kStatusBytes;
+// The planes take all of XENG_NOALLOC_SCRATCH_BYTES; the status word sits in
+// 256 bytes after them (kept apart so the planes stay 256-byte aligned).
+constexpr int64_t kPlaneBytes = (int64_t)XENG_NOALLOC_SCRATCH_BYTES;
+constexpr int64_t kStatusBytes = 256;
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) uint8_t xeng_noalloc_scratch[XENG_NOALLOC_SCRATCH_BYTES];
+static __device__ __align__(256) uint8_t xeng_noalloc_scratch[XENG_NOALLOC_SCRATCH_BYTES + kStatusBytes];
 
 std::mutex g_setup_mutex;
 uint8_t *g_scratch_addr[kMaxDevices];  // device address of the array, per device
@@ -98,8 +102,8 @@ extern "C" int xeng_correlate_noalloc(const uint8_t *block, int64_t n_samples, i
     uint8_t *scratch = nullptr;
     int st = scratch_on(dev, &scratch);
     if (st != XENG_OK) return st;
-    int *status = reinterpret_cast<int *>(scratch);
-    uint8_t *planes = scratch + kStatusBytes;
+    uint8_t *planes = scratch;
+    int *status = reinterpret_cast<int *>(scratch + kPlaneBytes);
 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = n_inputs, F = n_freq;

@@ -50,8 +50,6 @@ struct xeng_s {
     int64_t pstage_bytes = 0;
     int32_t *gidx = nullptr;       // sample indices of the gates of a gated call
     int64_t gidx_cap = 0;
-    struct PairList { int nt, nf, n; PairItem *dev; };
-    std::vector<PairList> pair_lists;  // device pair lists of the 2-CTA launches, by (nt, nf)
     // time shifting: delays, history of the delayed inputs (ping-pong), their list
     bool shifted = false;
     int32_t *d_delay = nullptr, *d_slot = nullptr, *d_chunk_delay = nullptr, *d_shift_inputs = nullptr;
@@ -167,14 +165,9 @@ cudaEvent_t take_event(xeng_s *h)
 
 // Correlation launches of a handle: one CTA per 128 x 128 tile (default), or
 // (build parameter XENG_TC_2CTA=1) cta_group::2 clusters computing 256 x 256
-// tiles, or (XENG_TC_PAIRS=1) 2-CTA clusters in which neighbouring 128 x 128
-// tiles of a tile row share their A operand through TMA multicast.  All give
-// the same bits; the alternatives measured no faster on GB300.
+// tiles.  Both give the same bits; the alternative measured no faster on GB300.
 #ifndef XENG_TC_2CTA
 #define XENG_TC_2CTA 0
-#endif
-#ifndef XENG_TC_PAIRS
-#define XENG_TC_PAIRS 0
 #endif
 // Up to 256 inputs: decode fused into the correlation (no planes in HBM).
 #ifndef XENG_FUSED_SMALL
@@ -205,27 +198,7 @@ int64_t planes_rows(int64_t N) { return round_up(N, XENG_TC_2CTA ? 256 : kTile);
 cudaError_t run_correlate(xeng_s *h, TcArgs a, cudaStream_t s)
 {
     if (XENG_TC_2CTA) return launch_correlate_tc2(a, h->num_sms, s);
-    if (!XENG_TC_PAIRS) return launch_correlate_tc(a, h->num_sms, s);
-    const int nt = a.n_pad / kTile;
-    const xeng_s::PairList *pl = nullptr;
-    for (auto &p : h->pair_lists)
-        if (p.nt == nt && p.nf == a.nf) pl = &p;
-    if (!pl) {
-        std::vector<PairItem> v;
-        build_pair_list(nt, a.nf, v);
-        PairItem *d = nullptr;
-        cudaError_t e = cudaMalloc(&d, v.size() * sizeof(PairItem));
-        if (e == cudaSuccess) e = cudaMemcpy(d, v.data(), v.size() * sizeof(PairItem), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cudaFree(d);
-            return e;
-        }
-        h->pair_lists.push_back({nt, a.nf, (int)v.size(), d});
-        pl = &h->pair_lists.back();
-    }
-    a.pairs = pl->dev;
-    a.n_pairs = pl->n;
-    return launch_correlate_tc_pairs(a, h->num_sms, s);
+    return launch_correlate_tc(a, h->num_sms, s);
 }
 
 // Decode launches of a handle: the persistent TMA pipeline where TMA can
@@ -241,7 +214,7 @@ cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int
 {
     h->planes_raw = false;
     if (h->decode_tma && decode_tma_ok(src, N)) {
-        if (XENG_RAW_PLANES && !XENG_TC_2CTA && !XENG_TC_PAIRS && h->partials && nt <= kFusedMaxSamples) {
+        if (XENG_RAW_PLANES && !XENG_TC_2CTA && h->partials && nt <= kFusedMaxSamples) {
             // raw-nibble planes and their per-input sums (two kernels)
             cudaError_t e = launch_decode_tma(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, h->d_err, h->num_sms, s,
                                               h->partials);
@@ -369,7 +342,6 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->sums);
     cudaFree(h->staging);
     cudaFree(h->gidx);
-    for (auto &pl : h->pair_lists) cudaFree(pl.dev);
     cudaFree(h->pstage[0]);
     cudaFree(h->pstage[1]);
     if (h->h2d) cudaStreamDestroy(h->h2d);
@@ -465,20 +437,8 @@ const uint8_t *device_block(xeng_s *h, const uint8_t *block, int64_t bytes, cuda
     *status = XENG_OK;
     if (is_device_pointer(block)) return block;
     if (h->staging_bytes < bytes) {
+        cudaStreamSynchronize(s);  // queued work may still read the old staging
         cudaFree(h->staging);
-    cudaFree(h->gidx);
-    for (auto &pl : h->pair_lists) cudaFree(pl.dev);
-    cudaFree(h->pstage[0]);
-    cudaFree(h->pstage[1]);
-    if (h->h2d) cudaStreamDestroy(h->h2d);
-    if (h->d2h) cudaStreamDestroy(h->d2h);
-    for (int k = 0; k < 2; k++) {
-        if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
-        if (h->ev_cmp[k]) cudaEventDestroy(h->ev_cmp[k]);
-    }
-    if (h->ev_start) cudaEventDestroy(h->ev_start);
-    if (h->ev_fin) cudaEventDestroy(h->ev_fin);
-    if (h->ev_sub) cudaEventDestroy(h->ev_sub);
         h->staging = nullptr;
         h->staging_bytes = 0;
         if (cudaMalloc(&h->staging, (size_t)bytes) != cudaSuccess) {

@@ -10,9 +10,10 @@ namespace xeng {
 constexpr int kTile = 128;          // inputs per tensor-engine tile, samples per K chunk
 constexpr int kMaxChunkSamples = 65536;  // f32 sums stay <= 128 * 65536 = 2^23 (exact)
 // Raw-nibble launches (the fused kernel, the tensor path's raw planes): their
-// integer sums stay <= 450 * 16384 < 2^23, the range in which the GPU tests
+// integer sums stay <= 450 * 32768 = 14,745,600 < 2^24, the range in which the
+// GPU tests (test_raw_nibble_sums_up_to_2_24, test_raw_nibble_unit_terms_above_2_23)
 // show the tensor core's f32 accumulation exact with unit increments.
-constexpr int kFusedMaxSamples = 16384;
+constexpr int kFusedMaxSamples = 32768;
 
 // Device-side status codes written to the handle's error word.
 enum DevStatus : int {
@@ -139,16 +140,6 @@ cudaError_t launch_beamform(const uint8_t *block, const uint8_t *wdev, const int
 
 cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total_ctas, cudaStream_t s);
 
-// Two tiles run together by the two CTAs of a cluster (CTA r takes tile r).
-// flags bit 0: same (channel, I) -- the CTAs share the A operand, each loading
-// one of its two planes into both CTAs' shared memory (TMA multicast);
-// bit 1: tile 1 repeats tile 0 to keep the pair in step (CTA 1 writes nothing).
-struct PairItem {
-    int32_t fl[2];
-    int16_t I[2], J[2];
-    int32_t flags;
-};
-
 // Tensor-core correlation of decoded planes (tcgen05, FP8 E4M3, f32 in TMEM).
 // acc: int32 [nf][N(N+1)/2][2] of the channel group; accumulate = add to it.
 struct TcArgs {
@@ -160,8 +151,6 @@ struct TcArgs {
     int32_t *acc;
     int32_t accumulate;
     int32_t *err;
-    const PairItem *pairs = nullptr;  // launch_correlate_tc_pairs: the pair list
-    int32_t n_pairs = 0;
     // raw-nibble planes: per channel of the launch, (S, D) of every input row
     // [nf][n_pad], and the samples integrated (<= kFusedMaxSamples); null: decoded planes
     const int2 *sums = nullptr;
@@ -171,10 +160,6 @@ cudaError_t launch_correlate_tc(const TcArgs &a, int num_sms, cudaStream_t s);
 // The same correlation with cta_group::2: clusters of two CTAs compute
 // 256 x 256 tiles (a.n_pad must be a multiple of 256).
 cudaError_t launch_correlate_tc2(const TcArgs &a, int num_sms, cudaStream_t s);
-// The same correlation by 2-CTA clusters over a pair list (see PairItem).
-cudaError_t launch_correlate_tc_pairs(const TcArgs &a, int num_sms, cudaStream_t s);
-// Pair list of nf channels of nt x nt tile grids, channel-major.
-void build_pair_list(int nt, int nf, std::vector<PairItem> &out);
 
 // Batched (listed) launches: a job table, per-job tensor maps and a work list
 // partitioned by CTA, all in device memory.

@@ -119,26 +119,53 @@ def test_exact_extremes_mix():
     assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "extremes")
 
 
-def test_raw_planes_at_the_exactness_bound():
-    # N a multiple of 16 above 256: the TMA decode writes raw-nibble planes and the
-    # correlator applies the offset terms; one launch of 16,384 samples, the most a
-    # raw-nibble launch takes
-    T, F, N = 16384, 1, 272
-    # every nibble 15: the raw sums reach 450 T = 7,372,800 < 2^23; x = 7 + 7i, V = 98 T
+# Raw-nibble launches (the fused kernel for N <= 256, the raw planes of the
+# TMA decode + tensor correlator above) hold sum(p p' + q q') over the launch's
+# samples in f32, up to 450 n: at 32,768 samples that is 14,745,600, between
+# 2^23 and 2^24, where an f32 sum has no bit to spare.  These cases put the
+# accumulators there and then add small terms, against closed forms and the
+# oracle.
+RAW_LAUNCH = 32768
+
+
+@pytest.mark.parametrize("N", [256, 272])  # the fused kernel; the TMA decode + tensor correlator
+def test_raw_nibble_sums_up_to_2_24(N):
+    T, F = RAW_LAUNCH, 1
+    # every nibble 15: raw sums 450 T; x = 7 + 7i, V = 98 T
     out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
     assert (out[..., 0] == 98 * T).all() and (out[..., 1] == 0).all()
     # every nibble 0: raw sums 0, the offset terms alone; x = -8 - 8i, V = 128 T
     out = run(torch.zeros((T, F, N), dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
     assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
-    # the extreme codes mixed, against the oracle
-    rng = np.random.default_rng(23)
+    # Re nibbles 15, Im nibbles 0: x = 7 - 8i, V = 113 T (raw sums 225 T)
+    out = run(torch.full((T, F, N), 0xF0, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    assert (out[..., 0] == 113 * T).all() and (out[..., 1] == 0).all()
+
+
+@pytest.mark.parametrize("N", [256, 272])
+def test_raw_nibble_unit_terms_above_2_23(N):
+    # 18,700 samples of nibbles 15 take every raw sum to 450 * 18,700 = 8,415,000 > 2^23;
+    # then each remaining sample adds 0 or 1 to a pair's raw sums (bytes 0x00, 0x10, 0x01),
+    # so every 32-sample MMA step adds a small integer that a sum keeping fewer than
+    # 24 bits would lose
+    rng = np.random.default_rng(41)
+    T, F = RAW_LAUNCH, 1
+    blk = np.full((T, F, N), 0xFF, np.uint8)
+    blk[18700:] = rng.choice(np.array([0x00, 0x00, 0x00, 0x10, 0x01], np.uint8), size=(T - 18700, F, N))
+    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "large raw sums, unit tail")
+
+
+@pytest.mark.parametrize("N", [256, 272])
+def test_raw_nibble_extremes_one_launch(N):
+    rng = np.random.default_rng(23 + N)
+    T, F = RAW_LAUNCH, 2
     blk = rng.choice(np.array([0x00, 0xFF, 0x0F, 0xF0, 0x88, 0x98, 0x78, 0x08, 0x80], np.uint8), size=(T, F, N))
     assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "raw-nibble extremes")
 
 
-def test_fused_raw_nibbles_at_the_exactness_bound():
-    # N <= 256: the fused kernel on raw nibbles, launches of 16,384 samples adding into int32
-    T, F, N = 3 * 16384, 1, 256
+def test_fused_raw_nibbles_over_several_launches():
+    # N <= 256: launches of 32,768 samples adding into int32 (raw sums of a launch < 2^24)
+    T, F, N = 3 * RAW_LAUNCH + 100, 1, 256
     out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
     assert (out[..., 0] == 98 * T).all() and (out[..., 1] == 0).all()
     out = run(torch.full((T, F, N), 0xF0, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)

@@ -13,8 +13,9 @@ the floating-point formats' definitions and the oracle (no CUDA code runs):
   (8 sum(w_re - w_im), 8 sum(w_re + w_im)), as the beamformer applies them;
 * the beamformer reads an integer S out of the float S / 64 + 1.5 * 2^17
   through its bit pattern;
-* the largest raw-nibble sums a launch of 16,384 samples can reach stay below
-  2^23, where the GPU tests show the f32 accumulation exact."""
+* the largest raw-nibble sums a launch of 32,768 samples can reach stay below
+  2^24, where every integer is exact in f32 and the GPU tests show the tensor
+  core's accumulation exact with unit increments."""
 import numpy as np
 import pytest
 
@@ -98,8 +99,11 @@ def test_integer_read_from_float_bits():
 
 
 def test_raw_nibble_sums_stay_exact_in_f32():
-    n = 16384
-    assert 450 * n < 2 ** 23          # sum over samples of p p' + q q' with p, q <= 15
-    assert 225 * n < 2 ** 23          # |q p' - p q'| per sample <= 225
+    n = 32768
+    assert 2 ** 23 < 450 * n < 2 ** 24  # sum over samples of p p' + q q' with p, q <= 15
+    assert 225 * n < 2 ** 23            # |q p' - p q'| per sample <= 225
+    # every integer below 2^24 is an f32, so the accumulators can hold the exact sums
+    k = np.arange(450 * n - 5000, 450 * n + 1, dtype=np.int64)
+    assert np.array_equal(k.astype(np.float32).astype(np.int64), k)
     N = 4096                          # beamformer: 2N K positions of u (<= 15) times a part (<= 15)
     assert 2 * N * 15 * 15 < 2 ** 22  # also inside the float-bit read-out's range

@@ -4,14 +4,16 @@ memory once at start-up, or one that cannot risk the device-wide pause a
 cudaMalloc / cudaFree may cause).  It works in a fixed array inside the
 library instead of allocating.
 
-Checked through the C ABI against the allocating path (xeng_push + xeng_dump
-on a handle), bit for bit, on calls made back to back -- the second call runs
-on whatever the first one left in the shared array.  This file is collected
-last on purpose; it needs nothing from the other tests.
+Checked through the C ABI, bit for bit, against the allocating path
+(xeng_push + xeng_dump on a handle) and against the integer oracle, on calls
+made back to back -- the second call runs on whatever the first one left in
+the shared array.  This file is collected last on purpose; it needs nothing
+from the other tests.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -40,12 +42,14 @@ def without_alloc(block):
 
 
 def test_noalloc_matches_allocating_path_on_consecutive_calls():
-    cases = [synth.Recipe("uniform", T=1000, F=3, N=200, seed=31),
-             synth.Recipe("sky", T=4096, F=4, N=256, seed=32),
-             # 32 MiB of planes per channel: two channels per round, three rounds
-             synth.Recipe("sky", T=8192, F=5, N=2048, seed=33),
-             synth.Recipe("uniform", T=129, F=2, N=130, seed=34)]
-    for rec in cases:
+    # (recipe, channels checked against the oracle)
+    cases = [(synth.Recipe("uniform", T=1000, F=3, N=200, seed=31), 3),
+             (synth.Recipe("sky", T=4096, F=4, N=256, seed=32), 4),
+             # 32 MiB of planes per channel: two channels per round, three rounds;
+             # the oracle checks the first channel and the last (the third round's)
+             (synth.Recipe("sky", T=8192, F=5, N=2048, seed=33), None),
+             (synth.Recipe("uniform", T=129, F=2, N=130, seed=34), 2)]
+    for rec, n_oracle in cases:
         block = rec.device()
         torch.cuda.synchronize()
         first = without_alloc(block)
@@ -53,13 +57,15 @@ def test_noalloc_matches_allocating_path_on_consecutive_calls():
         want = with_handle(block)
         assert np.array_equal(first, want), rec
         assert np.array_equal(second, want), rec
+        for f in (range(n_oracle) if n_oracle else (0, rec.F - 1)):
+            assert np.array_equal(second[f].astype(np.int64), oracle.correlate(rec.host(f0=f, nf=1))[0]), (rec, f)
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
     block = torch.zeros(16, dtype=torch.uint8, device="cuda")
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
-    # 2 * 4096 * 8192 bytes of planes per channel exceed the 64 MiB array
-    assert xe.xeng_correlate_noalloc(block, 8192, 1, 4096, out) == xe.XENG_ERR_RANGE
+    # 2 * 4096 * 8320 bytes of planes per channel exceed the 64 MiB array
+    assert xe.xeng_correlate_noalloc(block, 8193, 1, 4096, out) == xe.XENG_ERR_RANGE
     # more than 65536 samples in one call
     assert xe.xeng_correlate_noalloc(block, 65537, 1, 8, out) == xe.XENG_ERR_RANGE
     assert xe.xeng_correlate_noalloc(block, 10, 1, 0, out) == xe.XENG_ERR_RANGE
