@@ -191,15 +191,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, rank, world, local_rank):
-    """The batched workload: one planned, graph-captured batch run per step,
-    against one xeng_correlate call per job (tensor engine) and one dp4a
-    launch per job on the same GPU."""
+def batched_record(args, steps, warmup, local_rank):
+    """The batched workload (64 uneven jobs): one planned, graph-captured batch
+    run per step, against one xeng_correlate call per job (tensor engine) and
+    one dp4a launch per job on the same GPU.  Returns the record's fields."""
     import torch
     import synth
     import paper_1503_06202_gb300 as xe
 
-    torch.cuda.set_device(local_rank)
     recipes = synth.batched_jobs()
     stream = torch.cuda.Stream()
     jobs = []
@@ -219,18 +218,18 @@ def run_batched(args, rank, world, local_rank):
     if rc < 0:
         raise RuntimeError("autotune failed: %s" % xe.xeng_strerror(rc))
     b = xe.XBatch(jobs, opts)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run(stream)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(gpu_index_for(local_rank)) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.run(stream)
         ev1.record(stream)
         ev1.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     clocks = clk.summary()
     info = b.info()
 
@@ -252,44 +251,56 @@ def run_batched(args, rank, world, local_rank):
     per_tc_ms = per_job(xe.XENG_ENGINE_TENSOR, 3)
     per_dp4a_ms = per_job(xe.XENG_ENGINE_DP4A, 1) if not args.no_per_job_dp4a else float("nan")
     b.close()
+    del jobs
+    torch.cuda.synchronize()
     peaks, peak_src = load_peaks()
     value = ops / (ms * 1e-3) / 1e12
-    line = {"metric": METRIC, "value": value, "unit": "TOPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)", "data": "synthetic (seeded on-device generator)",
+    return {"value": value, "unit": "TOPS", "ms_per_step": ms, "steps": steps, "warmup": warmup,
             "config": {"workload": "batched", "description": WORKLOADS["batched"][1], "n_jobs": len(recipes),
                        "input_gb": sum(r.nbytes for r in recipes) / 1e9, "useful_ops": ops,
                        "l2": "inputs (%.1f GB) larger than L2; no flush" % (sum(r.nbytes for r in recipes) / 1e9)},
             "step_call": "xeng_batch_run (CUDA graph: TMA decode (+ thread-per-row decode for N % 16 != 0 jobs) "
                          "+ 1 persistent tensor-core launch)",
-            "gpu_launches": (2 + (1 if any(r.N % 16 for r in recipes) else 0)) * args.steps,
+            "gpu_launches": (2 + (1 if any(r.N % 16 for r in recipes) else 0)) * steps,
             "autotune": {"opts": opts.as_dict(), "tuned_ms": tuned_ms, "from_cache": rc == 1, "fixed": rc == 2,
                          "tune_s": tune_s},
             "plan": info,
-            "per_job_tensor": {"ms": per_tc_ms, "tops": ops / (per_tc_ms * 1e-3) / 1e12, "launches": 2 * len(recipes)},
+            "per_job_tensor": {"ms": per_tc_ms, "tops": ops / (per_tc_ms * 1e-3) / 1e12},
             "per_job_dp4a": {"ms": per_dp4a_ms, "tops": ops / (per_dp4a_ms * 1e-3) / 1e12, "launches": len(recipes)},
             "speedup_vs_per_job_tensor": per_tc_ms / ms, "speedup_vs_per_job_dp4a": per_dp4a_ms / ms,
             "roofline": {"bound": "tensor", "kernel": "decode + correlate_tc_kernel (listed)",
                          "achieved": value, "peak": 2.0 * peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
                          "frac": value / (2.0 * peaks["bf16_tflops_sustained"]), "traffic": None,
                          "note": "whole batched run, useful ops; peak = 2 x %s sustained bf16" % peak_src},
-            "clocks": clocks, "e2e": None, "cpu_baseline": None}
+            "clocks": clocks}
+
+
+def run_batched(args, rank, world, local_rank):
+    """--workload batched: the batched record as the contract's JSON line."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    r = batched_record(args, args.steps, args.warmup, local_rank)
+    line = {"metric": METRIC, "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)", "data": "synthetic (seeded on-device generator)",
+            "config": r.pop("config"), "gpu_launches": r.pop("gpu_launches"), "clocks": r.pop("clocks"),
+            "e2e": None, "cpu_baseline": None}
+    line.update(r)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serving(args, rank, world, local_rank):
+def serving_record(args, rates, seconds):
     """The streaming workload through the xserve_* service: Poisson block
     arrivals at r x the real-time rate per stream, continuous batching, dumps
     every 65536 samples; sustained TOPS and latency percentiles per rate,
-    against one plain xeng_push per block."""
+    against one plain xeng_push per block.  Returns the record's fields."""
     import threading
     import numpy as np
     import torch
     import synth
     import paper_1503_06202_gb300 as xe
 
-    torch.cuda.set_device(local_rank)
     BS, DUMP, POOL = 256, 65536, 16
     real_rate = 1.0 / (BS * 2.56e-6)  # blocks per second per stream at the 2.56 us sample period
     shapes = [(256, 256)] * 3 + [(512, 256)] * 3 + [(2048, 256)] * 2
@@ -300,7 +311,7 @@ def run_serving(args, rank, world, local_rank):
     demand = [8.0 * BS * F * N * (N + 1) / 2 * real_rate / 1e12 for N, F in shapes]
     results = []
     rng = np.random.default_rng(5)
-    for rate in args.serve_rates:
+    for rate in rates:
         rc, sv = xe.xserve_create(hbm_budget_bytes=120 << 30, max_blocks=args.serve_max_blocks, max_streams=16,
                                   compute_budget_tops=args.serve_compute_budget)
         if rc != xe.XENG_OK:
@@ -318,7 +329,7 @@ def run_serving(args, rank, world, local_rank):
         events = []
         for k in admitted:
             t = rng.exponential(1.0 / (rate * real_rate))
-            while t < args.serve_seconds:
+            while t < seconds:
                 events.append((t, k))
                 t += rng.exponential(1.0 / (rate * real_rate))
         events.sort()
@@ -379,18 +390,30 @@ def run_serving(args, rank, world, local_rank):
     plain_tops = nblk * sum(8.0 * BS * F * N * (N + 1) / 2 for N, F in shapes) / plain_s / 1e12
     for e_ in engs:
         e_.close()
+    del pools
+    torch.cuda.synchronize()
     head = results[0]
-    line = {"metric": METRIC, "value": head["sustained_tops"], "unit": "TOPS", "n_gpus": world, "steps": len(results),
-            "warmup": 0, "ms_per_step": head["busy_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)", "data": "synthetic (seeded on-device block pools)",
+    return {"value": head["sustained_tops"], "unit": "TOPS", "ms_per_step": head["busy_s"] * 1e3,
             "config": {"workload": "serving", "description": WORKLOADS["serving"][1],
                        "streams": ["N=%d F=%d" % sh for sh in shapes], "block_samples": BS, "dump_samples": DUMP,
-                       "max_blocks_per_round": args.serve_max_blocks, "arrival_seconds": args.serve_seconds,
+                       "max_blocks_per_round": args.serve_max_blocks, "arrival_seconds": seconds,
                        "compute_budget_tops": args.serve_compute_budget,
                        "real_time_blocks_per_s": real_rate, "real_time_demand_tops": sum(demand)},
             "per_rate": results, "plain_per_block_push_tops": plain_tops,
-            "speedup_vs_plain_per_block": head["sustained_tops"] / plain_tops,
+            "speedup_vs_plain_per_block": head["sustained_tops"] / plain_tops}
+
+
+def run_serving(args, rank, world, local_rank):
+    """--workload serving: the serving record as the contract's JSON line."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    r = serving_record(args, args.serve_rates, args.serve_seconds)
+    line = {"metric": METRIC, "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": world,
+            "steps": len(r["per_rate"]), "warmup": 0, "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)",
+            "data": "synthetic (seeded on-device block pools)", "config": r.pop("config"),
             "e2e": None, "cpu_baseline": None}
+    line.update(r)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -420,6 +443,10 @@ def main():
     ap.add_argument("--batch-policy", type=int, default=1)
     ap.add_argument("--batch-tile-order", type=int, default=0, help="with --batch-max-chunks: 0 row-major, 1 diagonal, 2 Morton")
     ap.add_argument("--no-per-job-dp4a", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="skip the batched and served records of the default run")
+    ap.add_argument("--systems-serve-seconds", type=float, default=0.75,
+                    help="arrival window of the default run's serving record (one rate, 1.0x)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -726,6 +753,20 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, exact = cpu_oracle_sample(rec, T, F, N, out)
 
+    # the batched and served workloads (configs of 64 uneven jobs and of 8
+    # concurrent streams) beside the plain per-instance kernels, in the same
+    # run, after the default workload's buffers are freed
+    batched = serving = None
+    if args.workload == "chime_full" and args.engine == "tensor" and not args.no_systems:
+        eng.close()
+        eng = None
+        del block, out
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        batched = batched_record(args, 5, 3, local_rank)
+        torch.cuda.empty_cache()
+        serving = serving_record(args, [1.0], args.systems_serve_seconds)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TOPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -737,12 +778,13 @@ def main():
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
                 "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "gating": gating, "beamform": beam,
-                "pathfinder_rate": secondary, "plain_dp4a": plain_dp4a,
+                "pathfinder_rate": secondary, "plain_dp4a": plain_dp4a, "batched": batched, "serving": serving,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "decode_roofline": decode_roof,
                 "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "bit_exact_on_cpu_sample": exact}
         print(json.dumps(line), flush=True)
-    eng.close()
+    if eng is not None:
+        eng.close()
     if dist:
         dist.destroy_process_group()
 

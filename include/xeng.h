@@ -55,6 +55,7 @@ extern "C" {
 #define XENG_ERR_CUDA        -5  /* a CUDA call or kernel failed              */
 #define XENG_ERR_TIMEOUT     -6  /* a device-side wait gave up (kernel status) */
 #define XENG_ERR_UNSUPPORTED -7  /* no usable sm_103 device                    */
+#define XENG_ERR_LATE        -8  /* serving: block of an integration already closed */
 
 /* Limits.  t_integ <= 2^24 - 1 keeps every |Re|, |Im| <= 128 * t_integ below
  * 2^31, so the int32 result of an integration cannot overflow (per sample
@@ -130,6 +131,47 @@ XENG_API int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, i
  */
 XENG_API int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int32_t *gate,
                                   int32_t n_gates, const uint8_t *valid, int32_t *out, int32_t *counts, void *stream);
+
+/*
+ * Gate accumulator sets (Sec. IV-C-4 gating, Sec. IV-A flagged data) kept on
+ * the handle across pushes, so that one integration (e.g. 2^23 samples, Sec.
+ * IV-C-1) is split into on/off sub-buffers by pulsar phase, each with the
+ * number of usable samples per (gate, channel, input) for renormalising.
+ *
+ * xeng_set_gates -- give the handle n_gates accumulator sets (1 <=
+ *   n_gates <= XENG_MAX_GATES, else XENG_ERR_RANGE) and their usable-sample
+ *   counts, n_gates * F * N(N+1)/2 * 8 + n_gates * F * N * 4 bytes of device
+ *   memory (XENG_ERR_NOMEM: the handle keeps one set).  Only with no
+ *   integration in progress (else XENG_ERR_ARG).  Synchronizes the device.
+ *   With one set (the default) xeng_push and xeng_dump work as always and
+ *   plain pushes count every sample as usable; with more, xeng_push and
+ *   xeng_dump return XENG_ERR_ARG and xeng_push_gated / xeng_dump_gated are
+ *   the calls.
+ *
+ * xeng_push_gated -- integrate n_samples more samples of device block
+ *   [n_samples][F][N] into the sets:
+ *     V^g_ij(f) += sum over t with gate[t] == g, valid_i(t), valid_j(t) of x_i conj(x_j),
+ *     counts[g][f][i] += #{t : gate[t] == g, valid_i(t)}.
+ *   gate: host int32 [n_samples], a set per sample (values outside
+ *   [0, n_gates) drop the sample), or NULL for set 0; valid: device uint8
+ *   [n_samples][F][N] (0 = missing or saturated), or NULL for all usable.
+ *   Any length (rounds of at most 65,536 samples per set); every sample
+ *   counts against t_integ (XENG_ERR_OVERFLOW, nothing done).  Tensor engine
+ *   only (else XENG_ERR_ARG), not while delays are set (XENG_ERR_UNSUPPORTED).
+ *   Reads `gate` before returning and synchronizes `stream` (it uploads the
+ *   per-set sample lists); the launches are asynchronous on `stream`.
+ *
+ * xeng_dump_gated -- write every set to out ([n_gates][F][N(N+1)/2][2]
+ *   int32) and, if counts is not NULL, the usable-sample counts to counts
+ *   ([n_gates][F][N] int32), device or host memory, then start a new
+ *   integration.  Returns the samples pushed (>= 0) or an XENG_ERR_* code;
+ *   returns once host buffers are written, else asynchronous on `stream`.
+ */
+#define XENG_MAX_GATES 64
+XENG_API int xeng_set_gates(xeng_t h, int32_t n_gates);
+XENG_API int xeng_push_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int32_t *gate,
+                             const uint8_t *valid, void *stream);
+XENG_API int64_t xeng_dump_gated(xeng_t h, int32_t *out, int32_t *counts, void *stream);
 
 /*
  * xeng_set_delays -- time shifting (Sec. IV-C-5).  The signal of an outlying
@@ -343,6 +385,16 @@ XENG_API int xeng_batch_autotune(const xeng_job_t *jobs, int32_t n_jobs, const c
  * decode slices each) and, optionally, a compute budget; closing a stream
  * frees its share for later admissions.  Results are bit-identical to
  * integrating each stream alone.
+ *
+ * Lost and late blocks (Sec. IV-A: momentary faults must not stop the data
+ * gathering).  Block number b of a stream (0, 1, 2, ... in the order the
+ * stream produced them) belongs to integration b / (dump_samples /
+ * block_samples).  An integration closes when all of its blocks are
+ * integrated, when a block of a later integration reaches the head of the
+ * stream's queue, or after xserve_flush; it is then dumped with the blocks it
+ * has (xserve_dump_info_t.blocks, .missing_blocks; integrations that received
+ * no block at all produce no dump).  A block of an integration that a later
+ * block has already closed is refused with XENG_ERR_LATE and counted.
  */
 typedef struct xserve_s *xserve_t;
 
@@ -356,9 +408,11 @@ typedef struct {
 
 typedef struct {
     int64_t seq;                 /* integration number of the stream (0, 1, ...)                  */
-    int64_t samples;             /* samples integrated (= dump_samples)                           */
+    int64_t samples;             /* samples integrated (dump_samples unless blocks were lost)     */
     double  last_arrival_s;      /* arrival time of the integration's last block (xserve_now clock) */
     double  ready_s;             /* time the dump was seen complete                               */
+    int64_t blocks;              /* blocks integrated                                             */
+    int64_t missing_blocks;      /* blocks of the integration never integrated (lost or late)     */
 } xserve_dump_info_t;
 
 typedef struct {
@@ -370,6 +424,8 @@ typedef struct {
     double  dump_p50_s, dump_p99_s;    /* last block of an integration -> dump available          */
     double  gpu_decode_ms, gpu_correlate_ms;  /* summed device time of the rounds' two launches   */
     double  host_plan_ms;                     /* summed host time spent building rounds           */
+    int64_t late_blocks;                      /* blocks refused with XENG_ERR_LATE                */
+    int64_t short_dumps;                      /* dumps of integrations closed with blocks missing */
 } xserve_stats_t;
 
 /* xserve_now -- the server's clock (seconds, monotonic) for arrival stamps. */
@@ -393,11 +449,27 @@ XENG_API int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, i
 
 /*
  * xserve_submit -- queue one block ([block_samples][F][N] bytes, device
- *   memory) that arrived at arrival_s (xserve_now clock; <= 0 = now).  Never
- *   waits for the GPU.  The caller keeps the block unchanged until
- *   xserve_consumed reports it (blocks of a stream are consumed in order).
+ *   memory) that arrived at arrival_s (xserve_now clock; <= 0 = now), as the
+ *   block after the highest-numbered one submitted so far.  Never waits for
+ *   the GPU.  The caller keeps the block unchanged until xserve_consumed
+ *   reports it (blocks of a stream are consumed in queue order).
  */
 XENG_API int xserve_submit(xserve_t sv, int32_t stream_id, const uint8_t *block, double arrival_s);
+
+/*
+ * xserve_submit_seq -- as xserve_submit, for block number seq (>= 0) of the
+ *   stream, so that lost blocks leave gaps.  Returns XENG_ERR_LATE (block not
+ *   queued) if a block of a later integration was submitted before it, and
+ *   XENG_ERR_ARG if block number seq was already submitted.
+ */
+XENG_API int xserve_submit_seq(xserve_t sv, int32_t stream_id, const uint8_t *block, int64_t seq, double arrival_s);
+
+/*
+ * xserve_flush -- close the stream's newest integration once the blocks
+ *   queued before this call are integrated, even if blocks are missing (for
+ *   example at the end of an observation); later blocks start the next one.
+ */
+XENG_API int xserve_flush(xserve_t sv, int32_t stream_id);
 
 /* xserve_consumed -- blocks of the stream whose round has completed. */
 XENG_API int64_t xserve_consumed(xserve_t sv, int32_t stream_id);

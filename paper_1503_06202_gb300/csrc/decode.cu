@@ -361,6 +361,26 @@ cudaError_t launch_decode_batch(const DecodeJob *jobs, int n_jobs, int64_t total
 
 namespace xeng {
 
+namespace {
+__global__ void counts_finish_kernel(int32_t *__restrict__ counts, int dirty, const GateBase base, int32_t G,
+                                     int64_t per_gate)
+{
+    const int64_t total = (int64_t)G * per_gate;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x)
+        counts[k] = (dirty ? counts[k] : 0) + (int32_t)base.v[k / per_gate];
+}
+}  // namespace
+
+cudaError_t launch_counts_finish(int32_t *counts, int dirty, const GateBase &base, int32_t G, int64_t per_gate,
+                                 cudaStream_t s)
+{
+    if (G <= 0 || G > kMaxGates || per_gate <= 0) return cudaErrorInvalidValue;
+    int64_t blocks = ((int64_t)G * per_gate + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    counts_finish_kernel<<<(unsigned)blocks, 256, 0, s>>>(counts, dirty, base, G, per_gate);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decode_gather(const uint8_t *block, int32_t F, int32_t N, int32_t f0, int32_t nf, const int32_t *idx,
                                  int64_t Tg, const uint8_t *valid, uint8_t *planes, int64_t t_pad, int64_t n_pad,
                                  int32_t *counts, cudaStream_t s)

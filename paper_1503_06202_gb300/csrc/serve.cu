@@ -22,6 +22,15 @@
 // worker polls their events, marks blocks consumed, publishes dumps and
 // records latencies: block arrival -> block integrated, and last block of an
 // integration -> its dump available.
+//
+// Lost and late blocks (Sec. IV-A: momentary faults must not stop the data
+// gathering).  Block number b of a stream belongs to integration
+// b / (dump_samples / block_samples).  Blocks may arrive with gaps; an
+// integration closes when all its blocks are in, when a block of a later
+// integration reaches the head of the stream's queue, or on xserve_flush --
+// then it is dumped with the samples it has, and the dump reports how many
+// blocks it holds and how many are missing.  A block of an integration that a
+// later block has already closed is refused (XENG_ERR_LATE) and counted.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -46,8 +55,9 @@ double now_s()
 }
 
 struct QBlock {
-    const uint8_t *ptr;
+    const uint8_t *ptr;  // nullptr: a flush marker (close the integration here)
     double arrival;
+    int64_t integ;       // integration the block belongs to
 };
 
 struct DumpSlot {
@@ -57,6 +67,7 @@ struct DumpSlot {
     int64_t samples = 0;
     double last_arrival = 0, ready_time = 0;
     int64_t seq = 0;         // integration number of the stream
+    int64_t blocks = 0;      // blocks integrated
 };
 
 struct SStream {
@@ -73,10 +84,15 @@ struct SStream {
     bool fresh = true;
     int64_t integrated = 0;          // samples in the current integration (launched)
     double last_arrival = 0;         // of the current integration's latest launched block
-    int64_t next_seq = 0;            // integrations finished so far
+    int64_t cur_integ = 0;           // integration the worker is filling
     std::deque<QBlock> queue;
     int64_t submitted = 0, consumed = 0;
     int64_t inflight = 0;            // blocks in rounds not yet complete
+    // submission side: the newest integration a block was submitted for, and
+    // which of its blocks have come (a block number may be submitted once)
+    int64_t top_integ = 0, next_block = 0;
+    std::vector<uint8_t> seen;
+    int64_t blocks_per_dump() const { return dump_samples / block_samples; }
 };
 
 struct Round {
@@ -117,7 +133,7 @@ struct xserve_s {
     // statistics
     std::vector<double> block_lat, dump_lat;
     double first_submit = -1, last_done = 0, ops_done = 0;
-    int64_t rounds = 0, refused = 0, blocks_done = 0, dumps_done = 0;
+    int64_t rounds = 0, refused = 0, blocks_done = 0, dumps_done = 0, late_blocks = 0, short_dumps = 0;
     double gpu_decode_ms = 0, gpu_correlate_ms = 0, host_plan_ms = 0;
     std::vector<cudaEvent_t> free_timers;
     int sticky = XENG_OK;
@@ -189,6 +205,7 @@ void reap(xserve_s *sv, std::unique_lock<std::mutex> &lk, bool wait_oldest)
                 d.ready_time = t;
                 sv->dump_lat.push_back(t - d.last_arrival);
                 sv->dumps_done++;
+                if (d.samples < st.dump_samples) sv->short_dumps++;
             }
         }
         sv->ops_done += r.useful_ops;
@@ -230,12 +247,32 @@ bool launch_round(xserve_s *sv)
     const double host_t0 = now_s();
     const int slot = sv->next_slot;
     const int K = sv->opts.max_blocks;
+    // nblocks == 0: the round only closes the stream's current integration
+    // (its next queued block belongs to a later one, or a flush asked for it)
     struct Pick { int stream; int nblocks; };
     std::vector<Pick> picks;
     for (auto &st : sv->streams) {
         if (!st.open || st.queue.empty()) continue;
+        const QBlock &head = st.queue.front();
+        if (!head.ptr || head.integ > st.cur_integ) {
+            if (st.integrated == 0) {
+                // nothing of the current integration was integrated: move on without a dump
+                st.cur_integ = head.ptr ? head.integ : std::max(st.cur_integ, head.integ + 1);
+                if (!head.ptr) st.queue.pop_front();
+                if (st.queue.empty() || !st.queue.front().ptr || st.queue.front().integ != st.cur_integ) continue;
+            } else {
+                if (st.dump[0].busy && st.dump[1].busy) continue;  // the close needs a free dump buffer
+                picks.push_back({st.id, 0});
+                continue;
+            }
+        }
+        int nb = 0;
+        for (const QBlock &qb : st.queue) {
+            if (nb == K || !qb.ptr || qb.integ != st.cur_integ) break;
+            ++nb;
+        }
         const int64_t to_dump = (st.dump_samples - st.integrated) / st.block_samples;
-        int nb = (int)std::min<int64_t>({(int64_t)K, (int64_t)st.queue.size(), to_dump});
+        nb = (int)std::min<int64_t>(nb, to_dump);
         if (nb <= 0) continue;
         // the round that completes an integration needs a free dump buffer
         if (st.integrated + nb * st.block_samples == st.dump_samples && st.dump[0].busy && st.dump[1].busy) continue;
@@ -249,6 +286,30 @@ bool launch_round(xserve_s *sv)
     int jobi = 0;
     for (auto &pk : picks) {
         SStream &st = sv->streams[pk.stream];
+        if (pk.nblocks == 0) {
+            // close the integration short: its accumulators are final once the
+            // rounds before this one complete, and this round does not touch them
+            Round::Part part;
+            part.stream = pk.stream;
+            part.nblocks = 0;
+            const int ds = st.dump[0].busy ? 1 : 0;
+            DumpSlot &d = st.dump[ds];
+            d.busy = true;
+            d.ready = false;
+            d.samples = st.integrated;
+            d.blocks = st.integrated / st.block_samples;
+            d.last_arrival = st.last_arrival;
+            d.seq = st.cur_integ;
+            part.dump_slot = ds;
+            const QBlock &head = st.queue.front();
+            st.cur_integ = head.ptr ? head.integ : std::max(st.cur_integ + 1, head.integ + 1);
+            if (!head.ptr) st.queue.pop_front();
+            st.integrated = 0;
+            st.fresh = true;
+            st.last_arrival = 0;
+            r.parts.push_back(std::move(part));
+            continue;
+        }
         const int64_t pitch = st.bs_pad * pk.nblocks;
         uint8_t *pl = st.planes[slot];
         Round::Part part;
@@ -323,8 +384,9 @@ bool launch_round(xserve_s *sv)
             d.busy = true;
             d.ready = false;
             d.samples = st.integrated;
+            d.blocks = st.integrated / st.block_samples;
             d.last_arrival = st.last_arrival;
-            d.seq = st.next_seq++;
+            d.seq = st.cur_integ++;
             part.dump_slot = ds;
             st.integrated = 0;
             st.fresh = true;
@@ -345,15 +407,18 @@ bool launch_round(xserve_s *sv)
                             s);
     if (e == cudaSuccess && n_djobs > 0)
         e = cudaMemcpyAsync(sv->d_djobs[slot], sv->h_djobs[slot], n_djobs * sizeof(DecTmaJob), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_maps[slot], sv->h_maps[slot], jobi * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_jobs[slot], sv->h_jobs[slot], jobi * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_items[slot], sv->h_items[slot], n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && jobi > 0)
+        e = cudaMemcpyAsync(sv->d_maps[slot], sv->h_maps[slot], jobi * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && jobi > 0)
+        e = cudaMemcpyAsync(sv->d_jobs[slot], sv->h_jobs[slot], jobi * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_items > 0)
+        e = cudaMemcpyAsync(sv->d_items[slot], sv->h_items[slot], n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && r.t0) e = cudaEventRecord(r.t0, s);
     if (e == cudaSuccess)
         e = launch_decode_tma_batch(sv->d_dmaps[slot], sv->d_djobs[slot], (int)n_djobs, dtiles, sv->d_err, sv->num_sms, s);
     if (e == cudaSuccess && n_dec > 0) e = launch_decode_batch(sv->d_dec[slot], (int)n_dec, dec_ctas, s);
     if (e == cudaSuccess && r.t1) e = cudaEventRecord(r.t1, s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && n_items > 0) {
         ListArgs L;
         L.maps = sv->d_maps[slot];
         L.jobs = sv->d_jobs[slot];
@@ -535,6 +600,7 @@ int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t bl
     st.n_pad = n_pad;
     st.demand_tops = demand;
     st.bytes = bytes;
+    st.seen.assign((size_t)(dump_samples / block_samples), 0);
     const size_t acc = (size_t)n_freq * n_baselines(n_inputs) * 8;
     const size_t planes = (size_t)n_freq * 2 * n_pad * bs_pad * sv->opts.max_blocks;
     cudaError_t e = cudaMalloc(&st.acc, acc);
@@ -555,6 +621,34 @@ int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t bl
     return XENG_OK;
 }
 
+namespace {
+
+// Queue block number `seq` of the stream (caller holds the lock).
+int submit_locked(xserve_s *sv, SStream &st, const uint8_t *block, int64_t seq, double t)
+{
+    const int64_t bpd = st.blocks_per_dump();
+    const int64_t integ = seq / bpd;
+    if (integ < st.top_integ) {  // a later integration's block has closed this one
+        sv->late_blocks++;
+        return XENG_ERR_LATE;
+    }
+    if (integ > st.top_integ) {
+        st.top_integ = integ;
+        std::fill(st.seen.begin(), st.seen.end(), 0);
+    }
+    uint8_t &seen = st.seen[(size_t)(seq - integ * bpd)];
+    if (seen) return XENG_ERR_ARG;  // this block number was submitted already
+    seen = 1;
+    st.queue.push_back({block, t, integ});
+    st.submitted++;
+    st.next_block = std::max(st.next_block, seq + 1);
+    if (sv->first_submit < 0 || t < sv->first_submit) sv->first_submit = t;
+    sv->cv.notify_all();
+    return XENG_OK;
+}
+
+}  // namespace
+
 int xserve_submit(xserve_t sv, int32_t stream_id, const uint8_t *block, double arrival_s)
 {
     if (!sv || !block) return XENG_ERR_ARG;
@@ -563,9 +657,31 @@ int xserve_submit(xserve_t sv, int32_t stream_id, const uint8_t *block, double a
     if (stream_id < 0 || stream_id >= (int)sv->streams.size() || !sv->streams[stream_id].open) return XENG_ERR_ARG;
     if (sv->sticky != XENG_OK) return sv->sticky;
     SStream &st = sv->streams[stream_id];
-    st.queue.push_back({block, t});
-    st.submitted++;
-    if (sv->first_submit < 0 || t < sv->first_submit) sv->first_submit = t;
+    return submit_locked(sv, st, block, st.next_block, t);
+}
+
+int xserve_submit_seq(xserve_t sv, int32_t stream_id, const uint8_t *block, int64_t seq, double arrival_s)
+{
+    if (!sv || !block || seq < 0) return XENG_ERR_ARG;
+    const double t = arrival_s > 0 ? arrival_s : now_s();
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (stream_id < 0 || stream_id >= (int)sv->streams.size() || !sv->streams[stream_id].open) return XENG_ERR_ARG;
+    if (sv->sticky != XENG_OK) return sv->sticky;
+    return submit_locked(sv, sv->streams[stream_id], block, seq, t);
+}
+
+int xserve_flush(xserve_t sv, int32_t stream_id)
+{
+    if (!sv) return XENG_ERR_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (stream_id < 0 || stream_id >= (int)sv->streams.size() || !sv->streams[stream_id].open) return XENG_ERR_ARG;
+    if (sv->sticky != XENG_OK) return sv->sticky;
+    SStream &st = sv->streams[stream_id];
+    // later blocks belong to the next integration
+    st.queue.push_back({nullptr, 0.0, st.top_integ});
+    st.top_integ++;
+    std::fill(st.seen.begin(), st.seen.end(), 0);
+    st.next_block = std::max(st.next_block, st.top_integ * st.blocks_per_dump());
     sv->cv.notify_all();
     return XENG_OK;
 }
@@ -602,6 +718,8 @@ int xserve_poll_dump(xserve_t sv, int32_t stream_id, int32_t *out, xserve_dump_i
         info->samples = d.samples;
         info->last_arrival_s = d.last_arrival;
         info->ready_s = d.ready_time;
+        info->blocks = d.blocks;
+        info->missing_blocks = st.blocks_per_dump() - d.blocks;
     }
     d.busy = false;
     d.ready = false;
@@ -619,8 +737,12 @@ int xserve_drain(xserve_t sv, double timeout_s)
         for (auto &st : sv->streams) {
             if (!st.open || st.queue.empty()) continue;
             // a stream whose next round waits for the client to take a dump does not count
+            const QBlock &head = st.queue.front();
+            const bool closes = !head.ptr || head.integ > st.cur_integ;
             const bool blocked = st.dump[0].busy && st.dump[1].busy &&
-                                 st.integrated + st.block_samples * std::min<int64_t>(sv->opts.max_blocks, st.queue.size()) >= st.dump_samples;
+                                 ((closes && st.integrated > 0) ||
+                                  st.integrated + st.block_samples * std::min<int64_t>(sv->opts.max_blocks, st.queue.size()) >=
+                                      st.dump_samples);
             busy = busy || !blocked;
         }
         if (!busy || sv->sticky != XENG_OK) break;
@@ -659,7 +781,7 @@ int xserve_stats(xserve_t sv, xserve_stats_t *out)
     for (auto &st : sv->streams) {
         if (!st.open) continue;
         ++open;
-        backlog += (int64_t)st.queue.size();
+        for (const QBlock &qb : st.queue) backlog += qb.ptr ? 1 : 0;
     }
     out->open_streams = open;
     out->backlog_blocks = backlog;
@@ -673,6 +795,8 @@ int xserve_stats(xserve_t sv, xserve_stats_t *out)
     out->gpu_decode_ms = sv->gpu_decode_ms;
     out->gpu_correlate_ms = sv->gpu_correlate_ms;
     out->host_plan_ms = sv->host_plan_ms;
+    out->late_blocks = sv->late_blocks;
+    out->short_dumps = sv->short_dumps;
     return sv->sticky;
 }
 

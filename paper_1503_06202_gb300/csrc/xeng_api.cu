@@ -12,6 +12,8 @@
 
 using namespace xeng;
 
+static_assert(XENG_MAX_GATES == kMaxGates, "gate set limit of the header and of the kernels");
+
 struct TimedLaunch {
     int kind;  // 0 = decode, 1 = correlate
     cudaEvent_t start, stop;
@@ -58,6 +60,13 @@ struct xeng_s {
     int64_t hist_H = 0;
     int32_t hist_S = 0;
     bool decode_tma = false;       // decode through the TMA pipeline where the block allows it
+    // gate accumulator sets (xeng_set_gates): acc holds n_gates sets of [F][B][2];
+    // set 0's "nothing integrated yet" flag is `fresh`, the others' gate_fresh[g]
+    int32_t n_gates = 1;
+    std::vector<char> gate_fresh;
+    std::vector<int64_t> gate_base;  // per set: samples pushed without a validity mask
+    int32_t *counts = nullptr;       // [n_gates][F][N] usable samples of flagged pushes
+    bool counts_dirty = false;       // counts hold something since the last dump
 };
 
 namespace {
@@ -268,6 +277,7 @@ const char *xeng_strerror(int code)
     case XENG_ERR_CUDA: return "CUDA call or kernel failed";
     case XENG_ERR_TIMEOUT: return "device-side wait timed out";
     case XENG_ERR_UNSUPPORTED: return "no usable sm_103 device";
+    case XENG_ERR_LATE: return "block of an integration that is already closed";
     default: return "unknown status";
     }
 }
@@ -328,6 +338,8 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
         return e == cudaErrorMemoryAllocation ? XENG_ERR_NOMEM : XENG_ERR_CUDA;
     }
     *h->h_err = 0;
+    h->gate_fresh.assign(1, 1);
+    h->gate_base.assign(1, 0);
     *out_handle = h;
     return XENG_OK;
 }
@@ -342,6 +354,7 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->sums);
     cudaFree(h->staging);
     cudaFree(h->gidx);
+    cudaFree(h->counts);
     cudaFree(h->pstage[0]);
     cudaFree(h->pstage[1]);
     if (h->h2d) cudaStreamDestroy(h->h2d);
@@ -722,6 +735,7 @@ int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
     if (n_samples > 0 && !block) return XENG_ERR_ARG;
     int st = check_sticky(h);
     if (st != XENG_OK) return st;
+    if (h->n_gates > 1) return XENG_ERR_ARG;  // several gate sets: xeng_push_gated names the set
     if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples == 0) return XENG_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -737,6 +751,7 @@ int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
     cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     h->samples += n_samples;
     h->fresh = false;
+    h->gate_base[0] += n_samples;  // every input of every sample usable
     return XENG_OK;
 }
 
@@ -858,11 +873,35 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
     return XENG_OK;
 }
 
+namespace {
+// Gate set g holds nothing of the current integration (its next launch stores).
+bool set_fresh(const xeng_s *h, int g) { return g == 0 ? h->fresh : h->gate_fresh[g] != 0; }
+void mark_set_used(xeng_s *h, int g)
+{
+    if (g == 0) h->fresh = false;
+    else h->gate_fresh[g] = 0;
+}
+
+// Start a new integration on every gate set.
+cudaError_t reset_integration(xeng_s *h, cudaStream_t s)
+{
+    h->samples = 0;
+    h->fresh = true;
+    std::fill(h->gate_fresh.begin(), h->gate_fresh.end(), 1);
+    std::fill(h->gate_base.begin(), h->gate_base.end(), 0);
+    cudaError_t e = cudaSuccess;
+    if (h->counts_dirty) e = cudaMemsetAsync(h->counts, 0, (size_t)h->n_gates * h->F * h->N * 4, s);
+    h->counts_dirty = false;
+    return e;
+}
+}  // namespace
+
 int64_t xeng_dump(xeng_t h, int32_t *out, void *stream)
 {
     if (!h || !out) return XENG_ERR_ARG;
     int st = check_sticky(h);
     if (st != XENG_OK) return st;
+    if (h->n_gates > 1) return XENG_ERR_ARG;  // several gate sets: xeng_dump_gated
     cudaStream_t s = (cudaStream_t)stream;
     const bool dev_out = is_device_pointer(out);
     const int64_t bytes = acc_bytes(h);
@@ -884,8 +923,206 @@ int64_t xeng_dump(xeng_t h, int32_t *out, void *stream)
         if (st != XENG_OK) return st;
     }
     const int64_t n = h->samples;
-    h->samples = 0;
+    e = reset_integration(h, s);
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    return n;
+}
+
+int xeng_set_gates(xeng_t h, int32_t n_gates)
+{
+    if (!h) return XENG_ERR_ARG;
+    if (n_gates < 1 || n_gates > XENG_MAX_GATES) return XENG_ERR_RANGE;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    if (h->samples > 0 || !h->fresh) return XENG_ERR_ARG;  // an integration is in progress
+    cudaError_t e = cudaDeviceSynchronize();  // queued work may still use the old sets
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    const size_t counts_bytes = (size_t)n_gates * h->F * h->N * 4;
+    if (n_gates != h->n_gates) {
+        cudaFree(h->acc);
+        h->acc = nullptr;
+        e = cudaMalloc(&h->acc, (size_t)n_gates * acc_bytes(h));
+        if (e != cudaSuccess) {
+            // keep the handle usable with one set
+            cudaGetLastError();
+            h->n_gates = 1;
+            if (cudaMalloc(&h->acc, (size_t)acc_bytes(h)) != cudaSuccess) {
+                cudaGetLastError();
+                h->acc = nullptr;
+                h->sticky = XENG_ERR_NOMEM;
+            }
+            cudaFree(h->counts);
+            h->counts = nullptr;
+            h->gate_fresh.assign(1, 1);
+            h->gate_base.assign(1, 0);
+            return XENG_ERR_NOMEM;
+        }
+        cudaFree(h->counts);
+        h->counts = nullptr;
+    }
+    if (!h->counts) {
+        e = cudaMalloc(&h->counts, counts_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->counts = nullptr;
+            return XENG_ERR_NOMEM;
+        }
+    }
+    e = cudaMemset(h->counts, 0, counts_bytes);
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    h->n_gates = n_gates;
+    h->gate_fresh.assign(n_gates, 1);
+    h->gate_base.assign(n_gates, 0);
+    h->counts_dirty = false;
     h->fresh = true;
+    return XENG_OK;
+}
+
+int xeng_push_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int32_t *gate, const uint8_t *valid,
+                    void *stream)
+{
+    if (!h || n_samples < 0 || (n_samples > 0 && !block)) return XENG_ERR_ARG;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
+    if (h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_ARG;
+    if (h->shifted) return XENG_ERR_UNSUPPORTED;
+    if (n_samples == 0) return XENG_OK;
+    if (!is_device_pointer(block) || (valid && !is_device_pointer(valid))) return XENG_ERR_ARG;
+    if (valid && !h->counts) {
+        cudaError_t e = cudaMalloc(&h->counts, (size_t)h->n_gates * h->F * h->N * 4);
+        if (e == cudaSuccess) e = cudaMemset(h->counts, 0, (size_t)h->n_gates * h->F * h->N * 4);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->counts);
+            h->counts = nullptr;
+            return XENG_ERR_NOMEM;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t G = h->n_gates;
+    const int64_t N = h->N, F = h->F;
+    const int64_t n_pad = planes_rows(N), nb2 = N * (N + 1);
+    // the samples of each set, in time order (rows of the block)
+    std::vector<int64_t> cnt(G + 1, 0);
+    for (int64_t t = 0; t < n_samples; t++) {
+        const int32_t g = gate ? gate[t] : 0;
+        if (g >= 0 && g < G) cnt[g + 1]++;
+    }
+    for (int g = 0; g < G; g++) cnt[g + 1] += cnt[g];
+    std::vector<int32_t> idx((size_t)std::max<int64_t>(cnt[G], 1));
+    {
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t t = 0; t < n_samples; t++) {
+            const int32_t g = gate ? gate[t] : 0;
+            if (g >= 0 && g < G) idx[fill[g]++] = (int32_t)t;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if ((int64_t)idx.size() > h->gidx_cap) {
+        e = cudaStreamSynchronize(s);  // an earlier gated call may still read the old list
+        cudaFree(h->gidx);
+        h->gidx = nullptr;
+        h->gidx_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&h->gidx, idx.size() * sizeof(int32_t));
+        if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+        h->gidx_cap = (int64_t)idx.size();
+    }
+    e = ensure_planes(h);
+    // the list is rewritten by the next gated call: this call's launches read it first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->gidx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // idx is pageable and goes out of scope
+    for (int g = 0; g < G && e == cudaSuccess; g++) {
+        const int64_t Tg = cnt[g + 1] - cnt[g];
+        if (Tg == 0) continue;
+        int32_t *set = h->acc + (int64_t)g * F * nb2;
+        // rounds of at most chunk_t samples of the set: exact f32 sums per launch
+        for (int64_t k0 = 0; k0 < Tg && e == cudaSuccess; k0 += h->chunk_t) {
+            const int64_t nk = std::min<int64_t>(h->chunk_t, Tg - k0);
+            const int64_t t_pad = round_up(nk, kTile);
+            for (int64_t f0 = 0; f0 < F && e == cudaSuccess; f0 += h->group_f) {
+                const int32_t nf = (int32_t)((F - f0) < h->group_f ? (F - f0) : h->group_f);
+                e = timed_launch(h, 0, s, [&] {
+                    return launch_decode_gather(block, (int32_t)F, (int32_t)N, (int32_t)f0, nf, h->gidx + cnt[g] + k0,
+                                                nk, valid, h->planes, t_pad, n_pad,
+                                                valid ? h->counts + ((int64_t)g * F + f0) * N : nullptr, s);
+                });
+                if (e != cudaSuccess) break;
+                TcArgs a;
+                a.planes = h->planes;
+                a.t_pad = t_pad;
+                a.n_pad = (int32_t)n_pad;
+                a.N = (int32_t)N;
+                a.nf = nf;
+                a.acc = set + f0 * nb2;
+                a.accumulate = set_fresh(h, g) ? 0 : 1;
+                a.err = h->d_err;
+                e = timed_launch(h, 1, s, [&] { return run_correlate(h, a, s); });
+            }
+            mark_set_used(h, g);
+        }
+        if (valid) h->counts_dirty = true;
+        else h->gate_base[g] += Tg;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    h->samples += n_samples;
+    return XENG_OK;
+}
+
+int64_t xeng_dump_gated(xeng_t h, int32_t *out, int32_t *counts, void *stream)
+{
+    if (!h || !out) return XENG_ERR_ARG;
+    int st = check_sticky(h);
+    if (st != XENG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev_out = is_device_pointer(out);
+    const bool dev_counts = counts && is_device_pointer(counts);
+    if (dev_out && (reinterpret_cast<uintptr_t>(out) & 3) != 0) return XENG_ERR_ARG;
+    const int32_t G = h->n_gates;
+    const int64_t set_bytes = acc_bytes(h);
+    const int64_t counts_bytes = (int64_t)G * h->F * h->N * 4;
+    cudaError_t e = cudaSuccess;
+    if (!dev_out || (counts && !dev_counts)) e = cudaStreamSynchronize(s);  // host memory is written below
+    for (int g = 0; g < G && e == cudaSuccess; g++) {
+        const bool fresh = set_fresh(h, g);
+        int32_t *dst = out + (int64_t)g * (set_bytes / 4);
+        if (fresh) {
+            if (dev_out) e = cudaMemsetAsync(dst, 0, (size_t)set_bytes, s);
+            else memset(dst, 0, (size_t)set_bytes);
+        } else {
+            e = cudaMemcpyAsync(dst, h->acc + (int64_t)g * (set_bytes / 4), (size_t)set_bytes,
+                                dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e == cudaSuccess && counts) {
+        if (!h->counts) {
+            e = cudaMalloc(&h->counts, (size_t)counts_bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->counts = nullptr;
+                return XENG_ERR_NOMEM;
+            }
+            h->counts_dirty = false;
+        }
+        GateBase base;
+        for (int g = 0; g < kMaxGates; g++) base.v[g] = g < G ? h->gate_base[g] : 0;
+        e = launch_counts_finish(h->counts, h->counts_dirty ? 1 : 0, base, G, (int64_t)h->F * h->N, s);
+        h->counts_dirty = true;  // the buffer now holds this integration's counts: cleared below
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(counts, h->counts, (size_t)counts_bytes,
+                                dev_counts ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    }
+    const int64_t n = h->samples;
+    if (e == cudaSuccess) e = reset_integration(h, s);
+    if (e == cudaSuccess && (!dev_out || (counts && !dev_counts))) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return (h->sticky = cuda_status(e));
+    if (!dev_out || (counts && !dev_counts)) {
+        st = check_sticky(h);
+        if (st != XENG_OK) return st;
+    }
     return n;
 }
 

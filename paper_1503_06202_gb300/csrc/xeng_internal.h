@@ -51,6 +51,16 @@ cudaError_t launch_decode_gather(const uint8_t *block, int32_t F, int32_t N, int
                                  int64_t Tg, const uint8_t *valid, uint8_t *planes, int64_t t_pad, int64_t n_pad,
                                  int32_t *counts, cudaStream_t s);
 
+// Gate accumulator sets of a handle (Sec. IV-C-4) and their usable-sample
+// counts: counts[g][k] = (dirty ? counts[g][k] : 0) + base[g] for k < per_gate
+// (base: samples of the set pushed without a validity mask).
+constexpr int kMaxGates = 64;
+struct GateBase {
+    int64_t v[kMaxGates];
+};
+cudaError_t launch_counts_finish(int32_t *counts, int dirty, const GateBase &base, int32_t G, int64_t per_gate,
+                                 cudaStream_t s);
+
 // Batched decode: one launch over the tiles of several blocks.
 struct DecodeJob {
     const uint8_t *block;  // [T][F][N]

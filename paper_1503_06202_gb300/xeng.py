@@ -21,11 +21,13 @@ XENG_ERR_NOMEM = -4
 XENG_ERR_CUDA = -5
 XENG_ERR_TIMEOUT = -6
 XENG_ERR_UNSUPPORTED = -7
+XENG_ERR_LATE = -8
 XENG_MAX_INPUTS = 4096
 XENG_MAX_T_INTEG = 16777215
 XENG_ENGINE_TENSOR = 0
 XENG_ENGINE_DP4A = 1
 XENG_MAX_DELAY = 131072
+XENG_MAX_GATES = 64
 XBEAM_MAX_BEAMS = 64
 
 
@@ -66,6 +68,12 @@ def lib():
         L.xeng_correlate.restype = ctypes.c_int
         L.xeng_correlate_gated.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, vp]
         L.xeng_correlate_gated.restype = ctypes.c_int
+        L.xeng_set_gates.argtypes = [vp, i32]
+        L.xeng_set_gates.restype = ctypes.c_int
+        L.xeng_push_gated.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.xeng_push_gated.restype = ctypes.c_int
+        L.xeng_dump_gated.argtypes = [vp, vp, vp, vp]
+        L.xeng_dump_gated.restype = i64
         L.xeng_destroy.argtypes = [vp]
         L.xeng_destroy.restype = None
         L.xeng_strerror.argtypes = [ctypes.c_int]
@@ -140,6 +148,19 @@ def xeng_correlate_gated(h, block, n_samples, gate, n_gates, valid, out, counts,
     """gate: host int32 array [n_samples] (numpy); valid/counts may be None."""
     return lib().xeng_correlate_gated(h, _ptr(block), n_samples, _ptr(gate), n_gates, _ptr(valid), _ptr(out),
                                       _ptr(counts), _stream(stream))
+
+
+def xeng_set_gates(h, n_gates: int) -> int:
+    return lib().xeng_set_gates(h, n_gates)
+
+
+def xeng_push_gated(h, block, n_samples, gate=None, valid=None, stream=None) -> int:
+    """gate: host int32 array [n_samples] (numpy) or None (set 0); valid: device uint8 [n][F][N] or None."""
+    return lib().xeng_push_gated(h, _ptr(block), n_samples, _ptr(gate), _ptr(valid), _stream(stream))
+
+
+def xeng_dump_gated(h, out, counts=None, stream=None) -> int:
+    return lib().xeng_dump_gated(h, _ptr(out), _ptr(counts), _stream(stream))
 
 
 def xeng_destroy(h) -> None:
@@ -477,7 +498,7 @@ class XserveOpts(ctypes.Structure):
 
 class XserveDumpInfo(ctypes.Structure):
     _fields_ = [("seq", ctypes.c_int64), ("samples", ctypes.c_int64), ("last_arrival_s", ctypes.c_double),
-                ("ready_s", ctypes.c_double)]
+                ("ready_s", ctypes.c_double), ("blocks", ctypes.c_int64), ("missing_blocks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -490,7 +511,7 @@ class XserveStats(ctypes.Structure):
                 ("busy_s", ctypes.c_double), ("block_p50_s", ctypes.c_double), ("block_p99_s", ctypes.c_double),
                 ("dump_p50_s", ctypes.c_double), ("dump_p99_s", ctypes.c_double),
                 ("gpu_decode_ms", ctypes.c_double), ("gpu_correlate_ms", ctypes.c_double),
-                ("host_plan_ms", ctypes.c_double)]
+                ("host_plan_ms", ctypes.c_double), ("late_blocks", ctypes.c_int64), ("short_dumps", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
@@ -508,6 +529,10 @@ def _serve_lib():
         L.xserve_open_stream.restype = ctypes.c_int
         L.xserve_submit.argtypes = [vp, i32, vp, dbl]
         L.xserve_submit.restype = ctypes.c_int
+        L.xserve_submit_seq.argtypes = [vp, i32, vp, i64, dbl]
+        L.xserve_submit_seq.restype = ctypes.c_int
+        L.xserve_flush.argtypes = [vp, i32]
+        L.xserve_flush.restype = ctypes.c_int
         L.xserve_consumed.argtypes = [vp, i32]
         L.xserve_consumed.restype = i64
         L.xserve_poll_dump.argtypes = [vp, i32, vp, ctypes.POINTER(XserveDumpInfo)]
@@ -545,6 +570,14 @@ def xserve_open_stream(sv, n_inputs, n_freq, block_samples, dump_samples, rate_b
 
 def xserve_submit(sv, stream_id, block, arrival_s=0.0) -> int:
     return _serve_lib().xserve_submit(sv, stream_id, _ptr(block), arrival_s)
+
+
+def xserve_submit_seq(sv, stream_id, block, seq, arrival_s=0.0) -> int:
+    return _serve_lib().xserve_submit_seq(sv, stream_id, _ptr(block), seq, arrival_s)
+
+
+def xserve_flush(sv, stream_id) -> int:
+    return _serve_lib().xserve_flush(sv, stream_id)
 
 
 def xserve_consumed(sv, stream_id) -> int:

@@ -8,12 +8,14 @@ import pytest
 
 import paper_1503_06202_gb300 as xe
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "xeng.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADER = os.path.join(INCLUDE, "xeng.h")
 
 
 def declared_symbols():
-    text = open(HEADER).read()
-    return sorted(set(re.findall(r"XENG_API\s+[^;(]*?\b(xeng_\w+)\s*\(", text)))
+    """Every entry point any header under include/ declares."""
+    text = "".join(open(os.path.join(INCLUDE, f)).read() for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h"))
+    return sorted(set(re.findall(r"XENG_API\s+[^;(]*?\b(x(?:eng|serve|beam)_\w+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
@@ -31,7 +33,8 @@ def test_library_exports_every_declared_symbol():
 def test_header_constants_match_binding():
     text = open(HEADER).read()
     for name in ("XENG_OK", "XENG_ERR_ARG", "XENG_ERR_RANGE", "XENG_ERR_OVERFLOW", "XENG_ERR_NOMEM",
-                 "XENG_ERR_CUDA", "XENG_ERR_TIMEOUT", "XENG_ERR_UNSUPPORTED", "XENG_MAX_INPUTS",
+                 "XENG_ERR_CUDA", "XENG_ERR_TIMEOUT", "XENG_ERR_UNSUPPORTED", "XENG_ERR_LATE", "XENG_MAX_INPUTS",
+                 "XENG_MAX_GATES", "XENG_MAX_DELAY",
                  "XENG_ENGINE_TENSOR", "XENG_ENGINE_DP4A", "XENG_SCHED_LPT", "XENG_SCHED_ROUND_ROBIN",
                  "XENG_SCHED_ORDERED", "XENG_TILES_ROW_MAJOR", "XENG_TILES_DIAGONAL", "XENG_TILES_MORTON"):
         m = re.search(r"#define\s+%s\s+(-?\d+)" % name, text)

@@ -168,3 +168,132 @@ def test_serve_dump_backpressure():
     for i in range(3):
         assert np.array_equal(got[i], oracle.correlate(np.concatenate(host[i * PER_DUMP:(i + 1) * PER_DUMP], axis=0)))
     xe.xserve_destroy(sv)
+
+
+def run_server_seq(streams, events, max_blocks=4):
+    """streams: list of (N, F, device blocks); events: (stream, kind, block number)
+    in submission order, kind "seq" (submit block b by number), "late" (submit
+    block b, expecting XENG_ERR_LATE) or "flush".  Returns, per stream, the
+    (info, dump) pairs in integration order, and the final stats."""
+    rc, sv = xe.xserve_create(hbm_budget_bytes=8 << 30, max_blocks=max_blocks, max_streams=8)
+    assert rc == xe.XENG_OK
+    ids = []
+    for N, F, _ in streams:
+        rc, sid = xe.xserve_open_stream(sv, N, F, BS, BS * PER_DUMP)
+        assert rc == xe.XENG_OK
+        ids.append(sid)
+    dumps = [[] for _ in streams]
+    outs = [torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda") for N, F, _ in streams]
+
+    def poll(s):
+        rc, info = xe.xserve_poll_dump(sv, ids[s], outs[s])
+        assert rc >= 0
+        if rc == 1:
+            dumps[s].append((info, outs[s].cpu().numpy().astype(np.int64)))
+        return rc == 1
+
+    rng = random.Random(17)
+    for k, kind, b in events:
+        if kind == "flush":
+            assert xe.xserve_flush(sv, ids[k]) == xe.XENG_OK
+        else:
+            rc = xe.xserve_submit_seq(sv, ids[k], streams[k][2][b], b)
+            assert rc == (xe.XENG_ERR_LATE if kind == "late" else xe.XENG_OK), (k, kind, b, rc)
+        if rng.random() < 0.3:
+            time.sleep(rng.random() * 2e-3)
+        for s in range(len(streams)):
+            poll(s)
+    assert xe.xserve_drain(sv, 60.0) == xe.XENG_OK
+    for s in range(len(streams)):
+        while poll(s):
+            pass
+    rc, st = xe.xserve_stats(sv)
+    assert rc == xe.XENG_OK
+    xe.xserve_destroy(sv)
+    return [sorted(ds, key=lambda x: x[0]["seq"]) for ds in dumps], st
+
+
+def interleave(per_stream, seed):
+    """Merge per-stream event lists at random, keeping each stream's order."""
+    rng = random.Random(seed)
+    pos = [0] * len(per_stream)
+    out = []
+    while any(p < len(ev) for p, ev in zip(pos, per_stream)):
+        k = rng.choice([i for i, ev in enumerate(per_stream) if pos[i] < len(ev)])
+        out.append(per_stream[k][pos[k]])
+        pos[k] += 1
+    return out
+
+
+def test_serve_lost_and_late_blocks_in_a_mix():
+    # Sec. IV-A: lost data must not stop the integration of the rest.  Stream A
+    # loses blocks 2 and 11 (one in each integration; the last integration is
+    # closed by a flush); stream B's block 5 arrives after block 6 has opened its
+    # next integration and is refused as late; stream C is clean and must give
+    # exactly its alone result.
+    n = 2 * PER_DUMP
+    data = []
+    for k, (N, F) in enumerate(STREAMS):
+        host, dev = make_blocks(N, F, n, seed=300 + k)
+        data.append((N, F, host, dev))
+    ev_a = [(0, "seq", b) for b in range(n) if b not in (2, 11)] + [(0, "flush", None)]
+    ev_b = [(1, "seq", b) for b in range(5)] + [(1, "seq", 6), (1, "late", 5)] + [(1, "seq", b) for b in range(7, n)]
+    ev_c = [(2, "seq", b) for b in range(n)]
+    streams = [(N, F, dev) for (N, F, _, dev) in data]
+    mixed, st = run_server_seq(streams, interleave([ev_a, ev_b, ev_c], seed=5))
+    alone_c, _ = run_server_seq([streams[2]], [(0, "seq", b) for b in range(n)])
+
+    def want(k, blocks):
+        return oracle.correlate(np.concatenate([data[k][2][b] for b in blocks], axis=0))
+
+    # stream A: integration 0 without block 2, integration 1 without block 11
+    (i0, d0), (i1, d1) = mixed[0]
+    assert (i0["seq"], i0["blocks"], i0["missing_blocks"], i0["samples"]) == (0, 5, 1, 5 * BS)
+    assert (i1["seq"], i1["blocks"], i1["missing_blocks"], i1["samples"]) == (1, 5, 1, 5 * BS)
+    assert np.array_equal(d0, want(0, [0, 1, 3, 4, 5]))
+    assert np.array_equal(d1, want(0, [6, 7, 8, 9, 10]))
+    # stream B: block 5 refused as late, so integration 0 holds blocks 0..4
+    (i0, d0), (i1, d1) = mixed[1]
+    assert (i0["seq"], i0["blocks"], i0["missing_blocks"]) == (0, 5, 1)
+    assert (i1["seq"], i1["blocks"], i1["missing_blocks"]) == (1, 6, 0)
+    assert np.array_equal(d0, want(1, range(5)))
+    assert np.array_equal(d1, want(1, range(6, 12)))
+    # stream C: unaffected, bit-identical to its alone run and to the oracle
+    assert len(mixed[2]) == len(alone_c[0]) == 2
+    for (im, dm), (ia, da), i in zip(mixed[2], alone_c[0], range(2)):
+        assert im["blocks"] == ia["blocks"] == PER_DUMP and im["missing_blocks"] == 0
+        assert np.array_equal(dm, da)
+        assert np.array_equal(dm, want(2, range(i * PER_DUMP, (i + 1) * PER_DUMP)))
+    assert st["late_blocks"] == 1 and st["short_dumps"] == 3
+    assert st["blocks_done"] == 3 * n - 3  # two lost, one refused
+
+
+def test_serve_duplicates_gaps_and_empty_flushes():
+    N, F = 64, 1
+    host, dev = make_blocks(N, F, 3 * PER_DUMP, seed=13)
+    rc, sv = xe.xserve_create(max_blocks=4, max_streams=2)
+    assert rc == xe.XENG_OK
+    rc, s = xe.xserve_open_stream(sv, N, F, BS, BS * PER_DUMP)
+    assert xe.xserve_flush(sv, s) == xe.XENG_OK        # nothing integrated: no dump, integration 0 skipped
+    assert xe.xserve_submit_seq(sv, s, dev[0], 0) == xe.XENG_ERR_LATE  # integration 0 was closed
+    assert xe.xserve_submit_seq(sv, s, dev[7], 7) == xe.XENG_OK
+    assert xe.xserve_submit_seq(sv, s, dev[7], 7) == xe.XENG_ERR_ARG   # the same block number twice
+    assert xe.xserve_submit_seq(sv, s, dev[7], -1) == xe.XENG_ERR_ARG
+    # integration 2 entirely lost; integration 3 gets its first and last blocks
+    assert xe.xserve_submit_seq(sv, s, dev[0], 18) == xe.XENG_OK
+    assert xe.xserve_submit(sv, s, dev[1]) == xe.XENG_OK  # plain submit: block 19, the next number
+    assert xe.xserve_flush(sv, s) == xe.XENG_OK
+    assert xe.xserve_drain(sv, 60.0) == xe.XENG_OK
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    got = []
+    while True:
+        rc, info = xe.xserve_poll_dump(sv, s, out)
+        if rc != 1:
+            break
+        got.append((info, out.cpu().numpy().astype(np.int64)))
+    assert [(i["seq"], i["blocks"], i["missing_blocks"]) for i, _ in got] == [(1, 1, 5), (3, 2, 4)]
+    assert np.array_equal(got[0][1], oracle.correlate(host[7]))
+    assert np.array_equal(got[1][1], oracle.correlate(np.concatenate([host[0], host[1]], axis=0)))
+    rc, st = xe.xserve_stats(sv)
+    assert st["late_blocks"] == 1 and st["short_dumps"] == 2 and st["backlog_blocks"] == 0
+    xe.xserve_destroy(sv)
