@@ -45,6 +45,17 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {}  # the kernel changed (raw-nibble planes) since the last capture
 
 
+def correlate_kernel(engine, N):
+    """(name, tile) of the correlation kernel an engine runs for N inputs (tile:
+    the square of inputs one work item computes, lower halves of diagonal
+    items included)."""
+    if engine in ("tensor", "fused") and N % 16 == 0 and N <= 256:
+        return "correlate_fused256_kernel (decode fused; the full 256 x 256 square)", 256
+    if engine == "fused" and N % 16 == 0:
+        return "correlate_raw_kernel (raw bytes split in shared memory; 256-input block pairs)", 256
+    return "correlate_tc_kernel (decoded planes; 128-input tile pairs)", 128
+
+
 def max_over_ranks(x, dist=None):
     """Largest value of x over all ranks (x itself without a process group).
     Works on the gloo (CPU tensors) and nccl (CUDA tensors) backends."""
@@ -425,7 +436,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xeng", choices=["xeng", "reference"])
     ap.add_argument("--workload", default="chime_full", choices=sorted(WORKLOADS))
-    ap.add_argument("--engine", default="tensor", choices=["tensor", "dp4a"])
+    ap.add_argument("--engine", default="tensor", choices=["tensor", "dp4a", "planes", "fused"],
+                    help="tensor: the default engine; planes: always decode to HBM planes, then correlate; "
+                         "fused: single pass (raw bytes split in shared memory) wherever N is a multiple of 16")
+    ap.add_argument("--no-fused-compare", action="store_true",
+                    help="skip timing the single-pass (fused) engine beside the default one")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -488,7 +503,9 @@ def main():
                                   ("mma_sync_s8", xe.XENG_PEAK_MMA_SYNC_S8, 200000), ("dp4a", xe.XENG_PEAK_DP4A, 500000)):
             rc, tf, pms = xe.xeng_peak_probe(kind, iters)
             probes[name] = round(tf, 1) if rc == 0 else None
-    engine = xe.XENG_ENGINE_TENSOR if args.engine == "tensor" else xe.XENG_ENGINE_DP4A
+    engine = {"tensor": xe.XENG_ENGINE_TENSOR, "dp4a": xe.XENG_ENGINE_DP4A,
+              "planes": xe.XENG_ENGINE_TENSOR_PLANES, "fused": xe.XENG_ENGINE_TENSOR_FUSED}[args.engine]
+    tensor_engine = args.engine != "dp4a"
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         block = rec.device(stream)
@@ -537,11 +554,37 @@ def main():
         return ev0.elapsed_time(ev1) / reps, s2["decode_ms"] / reps
 
     push_dump_ms, push_dump_decode_ms = push_dump()
+    # the single-pass engine on the same block (raw bytes split in shared memory,
+    # no planes in HBM), measured in the same run beside the default engine
+    fused_cmp = None
+    if args.engine == "tensor" and N > 256 and N % 16 == 0 and not args.no_fused_compare:
+        eng_p = xe.XEngine(N, F, T, xe.XENG_ENGINE_TENSOR_FUSED)
+        out_p = torch.empty_like(out)
+        for _ in range(2):
+            eng_p.correlate(block, out_p, T, stream)
+        eng_p.set_profiling(True)
+        eng_p.stats(reset=True)
+        reps_p = 3
+        ev0.record(stream)
+        for _ in range(reps_p):
+            eng_p.correlate(block, out_p, T, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        sp = eng_p.stats(reset=True)
+        p_ms = ev0.elapsed_time(ev1) / reps_p
+        fused_cmp = {"engine": "tensor_fused", "ms_per_step": p_ms, "value": useful_ops(T, F, N) / (p_ms * 1e-3) / 1e12,
+                     "unit": "TOPS", "correlate_ms_per_step": sp["correlate_ms"] / reps_p,
+                     "equals_default_engine_output": bool(torch.equal(out_p, out)),
+                     "kernels": "raw_sums_kernel + correlate_raw_kernel (256-input block pairs, MN-major raw-nibble "
+                                "operands split in shared memory)"}
+        eng_p.close()
+        del out_p
+        torch.cuda.synchronize()
     # time shifting (Sec. IV-C-5): two inputs of an outlying station delayed by
     # 168 ms (65,625 samples), the rest undelayed; the stream history carries
     # across the pushes
     shift = None
-    if args.engine == "tensor" and not args.no_shift:
+    if tensor_engine and not args.no_shift:
         import numpy as np
         d = np.zeros(N, np.int32)
         d[N - 2:] = 65625
@@ -560,7 +603,7 @@ def main():
     # gates (on / off, alternating every 64 samples) and 1% of the (sample,
     # channel, input) bytes flagged; the counts of usable samples come back too
     gating = None
-    if args.engine == "tensor" and not args.no_gate:
+    if tensor_engine and not args.no_gate:
         import numpy as np
         G = 2
         gate = ((np.arange(T) // 64) % G).astype(np.int32)
@@ -598,7 +641,7 @@ def main():
     # beamforming (Sec. IV-C-3): 16 beams over the same block, int8 weights;
     # HBM-bound: reads the block once, writes T x F x 16 complex int32
     beam = None
-    if args.engine == "tensor" and not args.no_beam:
+    if tensor_engine and not args.no_beam:
         nb = 16
         bf = xe.XBeam(N, F, nb)
         g = torch.Generator(device="cuda").manual_seed(5)
@@ -652,7 +695,7 @@ def main():
     # a channel sample of the same block (its full step takes seconds): its
     # rate, and whether its output equals the tensor path's for those channels
     plain_dp4a = None
-    if args.engine == "tensor" and not args.no_dp4a:
+    if tensor_engine and not args.no_dp4a:
         fs = min(F, 16)
         with torch.cuda.stream(stream):
             blk_s = block[:, :fs, :].contiguous()
@@ -684,7 +727,7 @@ def main():
     corr_ms = st["correlate_ms"] / max(1, st["timed_correlate"])
     launches_per_step = st["correlate_launches"] / args.steps
     flops_per_launch = ops / launches_per_step
-    if args.engine == "tensor":
+    if tensor_engine:
         peak = 2.0 * peaks["bf16_tflops_sustained"]
         peak_note = ("fp8 dense = 2 x %s sustained bf16 %.1f TFLOP/s (nominal fp8:bf16 = 4.5:2.25); "
                      "sm_103a has no tcgen05 kind::i8; the bf16 figure was sustained at a power-capped clock, "
@@ -692,15 +735,16 @@ def main():
                      "ceilings at this kernel's clock" % (peak_src, peaks["bf16_tflops_sustained"]))
         per_ch = CORRELATE_TC_DRAM_BYTES_PER_CHANNEL.get((N, T))
         traffic = per_ch * F / launches_per_step if per_ch else None
-        roof = {"bound": "tensor", "kernel": "correlate_tc_kernel", "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12,
+        kernel, tile = correlate_kernel(args.engine, N)
+        roof = {"bound": "tensor", "kernel": kernel, "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "traffic": traffic, "peak_note": peak_note}
         roof["frac"] = roof["achieved"] / peak
         if probes and probes.get("tc_f8f6f4"):
             roof["peak_probe_fp8"] = probes["tc_f8f6f4"]
             roof["frac_of_probe_fp8"] = roof["achieved"] / probes["tc_f8f6f4"]
             # useful ops exclude the lower halves of diagonal tiles the MMAs also compute
-            nt = -(-N // 128)
-            executed = nt * (nt + 1) // 2 * 128 * 128 / (N * (N + 1) / 2)
+            nt = -(-N // tile)
+            executed = (nt * (nt + 1) // 2 * tile * tile if tile < 256 or N > 256 else 256 * 256) / (N * (N + 1) / 2)
             roof["executed_over_useful"] = executed
             roof["frac_executed_of_probe_fp8"] = roof["achieved"] * executed / probes["tc_f8f6f4"]
         if probes and probes.get("tc_f8f6f4_live_data"):
@@ -722,7 +766,7 @@ def main():
     roof["decode_ms_per_step"] = st["decode_ms"] / args.steps
     # the decode stage (HBM-bound): 1 byte read + 2 plane bytes written per (input, sample, channel)
     decode_roof = None
-    if args.engine == "tensor" and st["decode_ms"] > 0:
+    if tensor_engine and st["decode_ms"] > 0:
         dec_ms = st["decode_ms"] / args.steps
         dec_bytes = 3 * T * F * N
         decode_roof = {"kernel": "decode_tma_kernel" if N % 16 == 0 else "decode_kernel", "bound": "hbm",
@@ -770,14 +814,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TOPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)" if args.engine == "tensor" else "int8->int32",
+                "vs_baseline": None, "dtype": "fp8e4m3->f32 (exact integers)" if tensor_engine else "int8->int32",
                 "data": "synthetic (seeded on-device generator)",
                 "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
                            "n_inputs": N, "n_freq": F, "t_integ": T, "engine": args.engine,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
-                "push_dump_ms_per_step": push_dump_ms, "time_shift": shift, "gating": gating, "beamform": beam,
+                "push_dump_ms_per_step": push_dump_ms, "fused_engine": fused_cmp, "time_shift": shift, "gating": gating, "beamform": beam,
                 "pathfinder_rate": secondary, "plain_dp4a": plain_dp4a, "batched": batched, "serving": serving,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "decode_roofline": decode_roof,
                 "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,

@@ -63,9 +63,15 @@ extern "C" {
 #define XENG_MAX_INPUTS   4096
 #define XENG_MAX_T_INTEG  16777215LL
 
-/* Correlation engines (both give identical bits). */
-#define XENG_ENGINE_TENSOR 0  /* decode to FP8 planes + tcgen05 tensor-core GEMM (default) */
-#define XENG_ENGINE_DP4A   1  /* plain CUDA-core kernel: int8 dp4a straight from the bytes  */
+/* Correlation engines (all give identical bits). */
+#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 256 (a multiple of 16, block
+                                        16-byte aligned) one kernel splits the raw bytes in shared memory and
+                                        correlates them; otherwise as XENG_ENGINE_TENSOR_PLANES              */
+#define XENG_ENGINE_DP4A          1  /* plain CUDA-core kernel: int8 dp4a straight from the bytes            */
+#define XENG_ENGINE_TENSOR_PLANES 2  /* two passes: decode to FP8 planes in HBM, then the tensor-core GEMM   */
+#define XENG_ENGINE_TENSOR_FUSED  3  /* single pass for every N that is a multiple of 16 (block 16-byte
+                                        aligned): no decode planes, F * N * 8 bytes of scratch instead of up
+                                        to 16 GiB; slower than two passes above 256 inputs on GB300        */
 
 typedef struct xeng_s *xeng_t;
 
@@ -233,9 +239,10 @@ XENG_API void xeng_destroy(xeng_t h);
 XENG_API const char *xeng_strerror(int code);
 
 /*
- * xeng_set_engine -- choose XENG_ENGINE_TENSOR or XENG_ENGINE_DP4A for the
- *   following pushes (XENG_ERR_ARG for other values).  Both engines add into
- *   the same int32 accumulators, so an integration may mix them.
+ * xeng_set_engine -- choose XENG_ENGINE_TENSOR, XENG_ENGINE_DP4A,
+ *   XENG_ENGINE_TENSOR_PLANES or XENG_ENGINE_TENSOR_FUSED for the following
+ *   pushes (XENG_ERR_ARG for other values).  All engines add into the same
+ *   int32 accumulators, so an integration may mix them.
  */
 XENG_API int xeng_set_engine(xeng_t h, int32_t engine);
 

@@ -77,56 +77,6 @@ __device__ __forceinline__ uint64_t fdesc(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Bounded wait with cluster-scope acquire: the barrier's arrivals include a
-// peer CTA's, whose shared-memory writes (into this CTA) must be visible after.
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int *err, int code)
-{
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        __nanosleep(64);
-        if (mbar_try_wait_cluster(bar, parity)) return true;
-        if ((it & 15) == 0) {
-            if (*(volatile int *)err != 0) return false;
-            if (globaltimer() - t0 > kWaitLimitNs) {
-                atomicCAS(err, 0, code);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void st_cluster_v2(uint32_t addr, int x, int y)
-{
-    asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(x), "r"(y) : "memory");
-}
-
-// OR of a flag over the threads of named barrier `id` (count threads), which all must reach it.
-__device__ __forceinline__ bool bar_any(int id, int count, bool flag)
-{
-    uint32_t any;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(any)
-        : "r"(flag ? 1u : 0u), "r"(id), "r"(count)
-        : "memory");
-    return any != 0;
-}
-
 struct FusedArgs {
     int64_t t0, nt;        // samples t0 .. t0 + nt - 1 of the block, nt <= kFusedMaxSamples
     int32_t F, N, f0, nf;  // channels f0 .. f0 + nf - 1

@@ -32,6 +32,7 @@ struct xeng_s {
     int64_t planes_bytes = 0;
     int2 *partials = nullptr;      // raw-nibble planes: per-tile nibble sums [group_f][n_tb][n_pad]
     int2 *sums = nullptr;          // raw-nibble planes: (S, D) per input [group_f][n_pad]
+    int2 *raw_sums = nullptr;      // single-pass kernel above 256 inputs: (S, D) per input [F][N]
     bool planes_raw = false;       // the last decode wrote raw-nibble planes
     int32_t group_f = 0;           // channels per decode + correlate round
     int64_t chunk_t = 0;           // samples per round
@@ -183,6 +184,7 @@ cudaEvent_t take_event(xeng_s *h)
 #define XENG_FUSED_SMALL 1
 #endif
 
+
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
 // either end (the first group's upload and the last group's download overlap
 // nothing), but each group's pitched upload copies T rows of (channels x N)
@@ -238,6 +240,38 @@ cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int
         return launch_decode_tma(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, h->d_err, h->num_sms, s);
     }
     return launch_decode(src, nt, F, N, f0, nf, h->planes, t_pad, n_pad, s);
+}
+
+// The tensor engines' single-pass kernels (decode fused into the correlation)
+// apply to this block: launches of at most kFusedMaxSamples samples over all
+// channels, no planes in HBM.  Up to 256 inputs both engines take them; above,
+// only XENG_ENGINE_TENSOR_FUSED (measured on GB300: full CHIME 50.8 ms single
+// pass against 44.8 ms for decode + correlation, so the two passes are the
+// default there).
+bool fused_ok(const xeng_s *h, const uint8_t *block)
+{
+    if (h->engine == XENG_ENGINE_TENSOR) return XENG_FUSED_SMALL && fused256_ok(block, h->N);
+    if (h->engine == XENG_ENGINE_TENSOR_FUSED)
+        return (XENG_FUSED_SMALL && fused256_ok(block, h->N)) || correlate_raw_ok(block, h->N);
+    return false;
+}
+
+cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
+                         int32_t f0, int32_t nf, int32_t *acc, int accumulate, cudaStream_t s)
+{
+    if (h->N <= 256)
+        return launch_correlate_fused256(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
+                                         s);
+    if (!h->raw_sums) {  // the per-input sums of the largest launch: every channel of the handle
+        cudaError_t e = cudaMalloc(&h->raw_sums, (size_t)h->F * h->N * sizeof(int2));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->raw_sums = nullptr;
+            return e;
+        }
+    }
+    return launch_correlate_raw(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->raw_sums, h->d_err,
+                                h->num_sms, s);
 }
 
 // Run one kernel launch, bracketed by events when profiling.
@@ -352,6 +386,7 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->planes);
     cudaFree(h->partials);
     cudaFree(h->sums);
+    cudaFree(h->raw_sums);
     cudaFree(h->staging);
     cudaFree(h->gidx);
     cudaFree(h->counts);
@@ -381,7 +416,9 @@ void xeng_destroy(xeng_t h)
 int xeng_set_engine(xeng_t h, int32_t engine)
 {
     if (!h) return XENG_ERR_ARG;
-    if (engine != XENG_ENGINE_TENSOR && engine != XENG_ENGINE_DP4A) return XENG_ERR_ARG;
+    if (engine != XENG_ENGINE_TENSOR && engine != XENG_ENGINE_DP4A && engine != XENG_ENGINE_TENSOR_PLANES &&
+        engine != XENG_ENGINE_TENSOR_FUSED)
+        return XENG_ERR_ARG;
     if (engine == XENG_ENGINE_DP4A && h->shifted) return XENG_ERR_UNSUPPORTED;
     h->engine = engine;
     return XENG_OK;
@@ -397,7 +434,7 @@ int xeng_set_delays(xeng_t h, const int32_t *delays)
             if (delays[i] < 0 || delays[i] > XENG_MAX_DELAY) return XENG_ERR_RANGE;
             if (delays[i] > H) H = delays[i];
         }
-    if (H > 0 && h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_UNSUPPORTED;
+    if (H > 0 && h->engine == XENG_ENGINE_DP4A) return XENG_ERR_UNSUPPORTED;
     cudaDeviceSynchronize();  // queued pushes may still read the old delays and history
     free_shift(h);
     if (H == 0) return cuda_status(cudaGetLastError());
@@ -484,14 +521,13 @@ cudaError_t integrate(xeng_s *h, const uint8_t *dblock, int64_t n_samples, int32
         });
     }
     cudaError_t e = cudaSuccess;
-    if (XENG_FUSED_SMALL && !apply_shift && fused256_ok(dblock, (int32_t)N)) {
-        const int64_t fc = h->chunk_t < kFusedMaxSamples ? h->chunk_t : kFusedMaxSamples;
+    if (!apply_shift && fused_ok(h, dblock)) {
+        const int64_t fc = kFusedMaxSamples;
         for (int64_t t0 = 0; t0 < n_samples && e == cudaSuccess; t0 += fc) {
             const int64_t nt = (n_samples - t0) < fc ? (n_samples - t0) : fc;
             const int accumulate = (fresh && t0 == 0) ? 0 : 1;
             e = timed_launch(h, 1, s, [&] {
-                return launch_correlate_fused256(dblock, n_samples, t0, nt, (int32_t)F, (int32_t)N, 0, (int32_t)F,
-                                                 target, accumulate, h->d_err, h->num_sms, s);
+                return launch_fused(h, dblock, n_samples, t0, nt, (int32_t)F, 0, (int32_t)F, target, accumulate, s);
             });
         }
         return e;
@@ -665,12 +701,12 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
             bf = nf;
             bf0 = 0;
         }
-        if (XENG_FUSED_SMALL && fused256_ok(blk, (int32_t)N)) {
+        if (fused_ok(h, blk)) {
             for (int64_t t0 = 0; t0 < n && e == cudaSuccess; t0 += kFusedMaxSamples) {
                 const int64_t nt = (n - t0) < kFusedMaxSamples ? (n - t0) : kFusedMaxSamples;
                 e = timed_launch(h, 1, s, [&] {
-                    return launch_correlate_fused256(blk, n, t0, nt, bf, (int32_t)N, bf0, nf, target + f0 * nb2,
-                                                     (fresh && t0 == 0) ? 0 : 1, h->d_err, h->num_sms, s);
+                    return launch_fused(h, blk, n, t0, nt, bf, bf0, nf, target + f0 * nb2, (fresh && t0 == 0) ? 0 : 1,
+                                        s);
                 });
             }
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
@@ -739,7 +775,7 @@ int xeng_push(xeng_t h, const uint8_t *block, int64_t n_samples, void *stream)
     if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples == 0) return XENG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->engine == XENG_ENGINE_TENSOR && n_samples <= h->chunk_t && !is_device_pointer(block) && !h->shifted) {
+    if (h->engine != XENG_ENGINE_DP4A && n_samples <= h->chunk_t && !is_device_pointer(block) && !h->shifted) {
         st = integrate_pipelined(h, block, true, n_samples, h->acc, nullptr, h->fresh, s);
         if (st != XENG_OK) return (h->sticky = st);
     } else {
@@ -776,7 +812,7 @@ int xeng_correlate(xeng_t h, const uint8_t *block, int64_t n_samples, int32_t *o
         return cuda_status(e);
     }
     const bool dev_in = is_device_pointer(block);
-    if (h->engine == XENG_ENGINE_TENSOR && n_samples <= h->chunk_t && (!dev_in || !dev_out)) {
+    if (h->engine != XENG_ENGINE_DP4A && n_samples <= h->chunk_t && (!dev_in || !dev_out)) {
         // host buffers: copies overlap the compute, group by group
         st = integrate_pipelined(h, block, !dev_in, n_samples, dev_out ? out : h->acc, dev_out ? nullptr : out, true, s);
         if (st == XENG_OK) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -806,7 +842,7 @@ int xeng_correlate_gated(xeng_t h, const uint8_t *block, int64_t n_samples, cons
     if (st != XENG_OK) return st;
     if (n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
     if (n_samples > h->chunk_t) return XENG_ERR_RANGE;
-    if (h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_ARG;
+    if (h->engine == XENG_ENGINE_DP4A) return XENG_ERR_ARG;
     if (h->shifted) return XENG_ERR_UNSUPPORTED;
     if (!is_device_pointer(out) || (counts && !is_device_pointer(counts)) || (valid && !is_device_pointer(valid)) ||
         (n_samples > 0 && !is_device_pointer(block)) || (reinterpret_cast<uintptr_t>(out) & 7) != 0)
@@ -985,7 +1021,7 @@ int xeng_push_gated(xeng_t h, const uint8_t *block, int64_t n_samples, const int
     int st = check_sticky(h);
     if (st != XENG_OK) return st;
     if (h->samples + n_samples > h->t_integ) return XENG_ERR_OVERFLOW;
-    if (h->engine != XENG_ENGINE_TENSOR) return XENG_ERR_ARG;
+    if (h->engine == XENG_ENGINE_DP4A) return XENG_ERR_ARG;
     if (h->shifted) return XENG_ERR_UNSUPPORTED;
     if (n_samples == 0) return XENG_OK;
     if (!is_device_pointer(block) || (valid && !is_device_pointer(valid))) return XENG_ERR_ARG;

@@ -127,6 +127,16 @@ cudaError_t launch_correlate_fused256(const uint8_t *block, int64_t T_block, int
                                       int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
                                       int num_sms, cudaStream_t s);
 
+// Decode fused into the correlation for 256 < N <= 4096 (N % 16 == 0, block
+// 16-byte aligned), as launch_correlate_fused256: a pass forming every input's
+// nibble sums into `sums` (scratch of nf * N int2), then 2-CTA clusters over
+// every channel's upper-triangle pairs of 256-input blocks; nt <=
+// kFusedMaxSamples, acc 8-byte aligned.
+bool correlate_raw_ok(const uint8_t *block, int32_t N);
+cudaError_t launch_correlate_raw(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
+                                 int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *sums, int *err,
+                                 int num_sms, cudaStream_t s);
+
 // Beamforming (Sec. IV-C-3).  The host fills T, F, N, B, out and err; the
 // launcher fills the rest.
 struct BfArgs {

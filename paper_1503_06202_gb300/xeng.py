@@ -26,6 +26,8 @@ XENG_MAX_INPUTS = 4096
 XENG_MAX_T_INTEG = 16777215
 XENG_ENGINE_TENSOR = 0
 XENG_ENGINE_DP4A = 1
+XENG_ENGINE_TENSOR_PLANES = 2
+XENG_ENGINE_TENSOR_FUSED = 3
 XENG_MAX_DELAY = 131072
 XENG_MAX_GATES = 64
 XBEAM_MAX_BEAMS = 64

@@ -35,7 +35,7 @@ def test_header_constants_match_binding():
     for name in ("XENG_OK", "XENG_ERR_ARG", "XENG_ERR_RANGE", "XENG_ERR_OVERFLOW", "XENG_ERR_NOMEM",
                  "XENG_ERR_CUDA", "XENG_ERR_TIMEOUT", "XENG_ERR_UNSUPPORTED", "XENG_ERR_LATE", "XENG_MAX_INPUTS",
                  "XENG_MAX_GATES", "XENG_MAX_DELAY",
-                 "XENG_ENGINE_TENSOR", "XENG_ENGINE_DP4A", "XENG_SCHED_LPT", "XENG_SCHED_ROUND_ROBIN",
+                 "XENG_ENGINE_TENSOR", "XENG_ENGINE_DP4A", "XENG_ENGINE_TENSOR_PLANES", "XENG_ENGINE_TENSOR_FUSED", "XENG_SCHED_LPT", "XENG_SCHED_ROUND_ROBIN",
                  "XENG_SCHED_ORDERED", "XENG_TILES_ROW_MAJOR", "XENG_TILES_DIAGONAL", "XENG_TILES_MORTON"):
         m = re.search(r"#define\s+%s\s+(-?\d+)" % name, text)
         assert m and int(m.group(1)) == getattr(xe.xeng, name), name

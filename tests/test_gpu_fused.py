@@ -14,9 +14,9 @@ torch = pytest.importorskip("torch")
 import paper_1503_06202_gb300 as xe  # noqa: E402
 
 
-def correlate(blk, pieces=None, host=False, t_integ=None):
+def correlate(blk, pieces=None, host=False, t_integ=None, engine=xe.XENG_ENGINE_TENSOR):
     T, F, N = blk.shape
-    eng = xe.XEngine(N, F, t_integ or max(T, 1))
+    eng = xe.XEngine(N, F, t_integ or max(T, 1), engine)
     out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
     src = blk if host else torch.from_numpy(blk).cuda()
     if pieces:
@@ -65,3 +65,53 @@ def test_fused_host_buffers_and_many_channels():
     want = oracle.correlate(blk)
     assert np.array_equal(correlate(blk), want)
     assert np.array_equal(correlate(blk, host=True), want)
+
+
+# ---- more than 256 inputs (fused engine): the raw bytes correlated by 2-CTA clusters
+# ---- over pairs of 256-input blocks (diagonal pairs, ragged last blocks, both CTAs' halves)
+
+FUSED = xe.XENG_ENGINE_TENSOR_FUSED
+
+@pytest.mark.parametrize("T,F,N", [(1, 1, 272), (127, 2, 288), (129, 2, 512), (1000, 3, 528), (300, 2, 784),
+                                   (257, 1, 1024), (200, 2, 2048), (130, 1, 4096)])
+def test_fused_raw_shapes(T, F, N):
+    rng = np.random.default_rng(T * 37 + F * 5 + N)
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    assert np.array_equal(correlate(blk, engine=FUSED), oracle.correlate(blk)), (T, F, N)
+
+
+def test_fused_raw_several_launches_pieces_and_host_buffers():
+    # 70,000 samples = three launches of <= 32,768 adding into int32; pushes in pieces;
+    # host buffers through the channel-group pipeline
+    rng = np.random.default_rng(15)
+    T, F, N = 70000, 2, 400
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    assert np.array_equal(correlate(blk, engine=FUSED), want)
+    assert np.array_equal(correlate(blk, pieces=[100, 32768, 3], engine=FUSED), want)
+    T2, F2 = 3000, 40
+    blk2 = rng.integers(0, 256, size=(T2, F2, N), dtype=np.uint8)
+    assert np.array_equal(correlate(blk2, host=True, engine=FUSED), oracle.correlate(blk2))
+
+
+def test_fused_raw_many_channels_per_cluster_and_plane_engine_agree():
+    # 90 channels x 3 block pairs over the 76 clusters; the two-pass engine gives the same bits
+    rng = np.random.default_rng(16)
+    T, F, N = 384, 90, 512
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    got = correlate(blk, engine=FUSED)
+    d = torch.from_numpy(blk).cuda()
+    eng = xe.XEngine(N, F, T, xe.XENG_ENGINE_TENSOR_PLANES)
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    eng.correlate(d, out, T)
+    torch.cuda.synchronize()
+    eng.close()
+    assert np.array_equal(got, out.cpu().numpy().astype(np.int64))
+    assert np.array_equal(got[[0, 45, 89]], oracle.correlate(blk, f0=0, nf=F)[[0, 45, 89]])
+
+
+def test_fused_raw_int32_beyond_f32_range():
+    # every sample -8-8i over 70,000 samples (three launches): Re = 8,960,000 > 2^23
+    T, F, N = 70000, 1, 272
+    out = correlate(np.zeros((T, F, N), np.uint8), engine=FUSED)
+    assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()

@@ -17,7 +17,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 import paper_1503_06202_gb300 as xe  # noqa: E402
 
-ENGINES = {"tensor": xe.XENG_ENGINE_TENSOR, "dp4a": xe.XENG_ENGINE_DP4A}
+# tensor: the default (single pass up to 256 inputs, two passes above); planes:
+# always the two passes; fused: single pass wherever N is a multiple of 16
+ENGINES = {"tensor": xe.XENG_ENGINE_TENSOR, "dp4a": xe.XENG_ENGINE_DP4A, "planes": xe.XENG_ENGINE_TENSOR_PLANES,
+           "fused": xe.XENG_ENGINE_TENSOR_FUSED}
 
 
 def to_dev(block: np.ndarray):
@@ -128,22 +131,28 @@ def test_exact_extremes_mix():
 RAW_LAUNCH = 32768
 
 
-@pytest.mark.parametrize("N", [256, 272])  # the fused kernel; the TMA decode + tensor correlator
-def test_raw_nibble_sums_up_to_2_24(N):
+# N = 256: the single-pass kernel of up to 256 inputs; N = 272: the TMA decode's
+# raw planes + tensor correlator (default engine) and the single-pass kernel of
+# 256-input block pairs (fused engine)
+RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR_FUSED)]
+
+
+@pytest.mark.parametrize("N,engine", RAW_CASES)
+def test_raw_nibble_sums_up_to_2_24(N, engine):
     T, F = RAW_LAUNCH, 1
     # every nibble 15: raw sums 450 T; x = 7 + 7i, V = 98 T
-    out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), engine)
     assert (out[..., 0] == 98 * T).all() and (out[..., 1] == 0).all()
     # every nibble 0: raw sums 0, the offset terms alone; x = -8 - 8i, V = 128 T
-    out = run(torch.zeros((T, F, N), dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    out = run(torch.zeros((T, F, N), dtype=torch.uint8, device="cuda"), engine)
     assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
     # Re nibbles 15, Im nibbles 0: x = 7 - 8i, V = 113 T (raw sums 225 T)
-    out = run(torch.full((T, F, N), 0xF0, dtype=torch.uint8, device="cuda"), xe.XENG_ENGINE_TENSOR)
+    out = run(torch.full((T, F, N), 0xF0, dtype=torch.uint8, device="cuda"), engine)
     assert (out[..., 0] == 113 * T).all() and (out[..., 1] == 0).all()
 
 
-@pytest.mark.parametrize("N", [256, 272])
-def test_raw_nibble_unit_terms_above_2_23(N):
+@pytest.mark.parametrize("N,engine", RAW_CASES)
+def test_raw_nibble_unit_terms_above_2_23(N, engine):
     # 18,700 samples of nibbles 15 take every raw sum to 450 * 18,700 = 8,415,000 > 2^23;
     # then each remaining sample adds 0 or 1 to a pair's raw sums (bytes 0x00, 0x10, 0x01),
     # so every 32-sample MMA step adds a small integer that a sum keeping fewer than
@@ -152,15 +161,15 @@ def test_raw_nibble_unit_terms_above_2_23(N):
     T, F = RAW_LAUNCH, 1
     blk = np.full((T, F, N), 0xFF, np.uint8)
     blk[18700:] = rng.choice(np.array([0x00, 0x00, 0x00, 0x10, 0x01], np.uint8), size=(T - 18700, F, N))
-    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "large raw sums, unit tail")
+    assert_same(run(to_dev(blk), engine), oracle.correlate(blk), "large raw sums, unit tail")
 
 
-@pytest.mark.parametrize("N", [256, 272])
-def test_raw_nibble_extremes_one_launch(N):
+@pytest.mark.parametrize("N,engine", RAW_CASES)
+def test_raw_nibble_extremes_one_launch(N, engine):
     rng = np.random.default_rng(23 + N)
     T, F = RAW_LAUNCH, 2
     blk = rng.choice(np.array([0x00, 0xFF, 0x0F, 0xF0, 0x88, 0x98, 0x78, 0x08, 0x80], np.uint8), size=(T, F, N))
-    assert_same(run(to_dev(blk), xe.XENG_ENGINE_TENSOR), oracle.correlate(blk), "raw-nibble extremes")
+    assert_same(run(to_dev(blk), engine), oracle.correlate(blk), "raw-nibble extremes")
 
 
 def test_fused_raw_nibbles_over_several_launches():
