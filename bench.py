@@ -38,11 +38,15 @@ WORKLOADS = {
 }
 METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)"
 
-# DRAM bytes (read + write) per channel of one correlate_tc_kernel launch, from
-# one ncu capture of the 16-channel slice of the same (N, T) shape; traffic
-# grows in proportion to channels.  Keyed by (N, T); must be re-taken (or
-# removed) whenever the kernel changes.
-CORRELATE_TC_DRAM_BYTES_PER_CHANNEL = {}  # the kernel changed (raw-nibble planes) since the last capture
+# DRAM bytes (read + write) per channel of one launch of a correlation kernel,
+# from one ncu capture of the 16-channel slice of the same (N, T) shape
+# (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows in proportion to
+# channels.  Keyed by (kernel, N, T); re-take (or remove) an entry whenever its
+# kernel changes.
+DRAM_BYTES_PER_CHANNEL = {
+    ("correlate_tc", 2048, 8192): (658.302976e6 + 244.678912e6) / 16,   # raw-nibble planes, 16-channel slice
+    ("correlate_raw", 2048, 8192): (307.412224e6 + 223.055104e6) / 16,  # fused engine, 16-channel slice
+}
 
 
 def correlate_kernel(engine, N):
@@ -729,15 +733,22 @@ def main():
     flops_per_launch = ops / launches_per_step
     if tensor_engine:
         peak = 2.0 * peaks["bf16_tflops_sustained"]
+        kernel, tile = correlate_kernel(args.engine, N)
         peak_note = ("fp8 dense = 2 x %s sustained bf16 %.1f TFLOP/s (nominal fp8:bf16 = 4.5:2.25); "
                      "sm_103a has no tcgen05 kind::i8; the bf16 figure was sustained at a power-capped clock, "
                      "so frac can exceed 1 -- the fp8 probes measured in this run (peak_probe_*) are the "
                      "ceilings at this kernel's clock" % (peak_src, peaks["bf16_tflops_sustained"]))
-        per_ch = CORRELATE_TC_DRAM_BYTES_PER_CHANNEL.get((N, T))
+        per_ch = DRAM_BYTES_PER_CHANNEL.get((kernel.split()[0].replace("_kernel", ""), N, T))
         traffic = per_ch * F / launches_per_step if per_ch else None
-        kernel, tile = correlate_kernel(args.engine, N)
         roof = {"bound": "tensor", "kernel": kernel, "achieved": flops_per_launch / (corr_ms * 1e-3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "traffic": traffic, "peak_note": peak_note}
+        if traffic:
+            # algorithmic bytes of one launch: the operands read once (planes: 2 bytes per
+            # input and sample; raw: 1 byte) and the triangle written once
+            op_bytes = (2 if kernel.startswith("correlate_tc") else 1) * T * N * F / launches_per_step
+            roof["algorithmic_bytes"] = op_bytes + 8.0 * B * F / launches_per_step
+            roof["traffic_over_algorithmic"] = traffic / roof["algorithmic_bytes"]
+            roof["traffic_source"] = "ncu capture of the 16-channel slice, scaled by channels"
         roof["frac"] = roof["achieved"] / peak
         if probes and probes.get("tc_f8f6f4"):
             roof["peak_probe_fp8"] = probes["tc_f8f6f4"]
