@@ -7,7 +7,11 @@
 // job alone.
 //
 // Planning: every job gets its own region of one decode buffer and its own
-// TMA descriptor.  Its upper-triangle 128x128 tile pairs (per channel) become
+// TMA descriptor.  Jobs the TMA decode can address get raw-nibble planes (E4M3
+// codes of u / 512, as the single-instance path): the decode also writes each
+// tile's per-input nibble sums, one small launch totals them per job, and the
+// correlation's epilogue applies the offset terms (their items then span at
+// most 32,768 samples, keeping every f32 sum below 2^24).  Its upper-triangle 128x128 tile pairs (per channel) become
 // work items; a tile whose integration is longer than `max_chunks` 128-sample
 // chunks is split along time into several items whose int32 results are added
 // with atomics (exact: integer addition is order-independent).  Items are
@@ -47,6 +51,11 @@ struct xeng_batch_s {
     DecTmaJob *d_djobs = nullptr;
     int n_djobs = 0;
     int64_t dtiles = 0;
+    int2 *partials = nullptr;        // raw-nibble jobs: per-tile nibble sums, then their totals
+    int2 *sums = nullptr;
+    SumJob *d_sjobs = nullptr;
+    int n_sjobs = 0;
+    int64_t sum_entries = 0;
     int grid = 0;
     int64_t n_items = 0;
     double max_load = 0, mean_load = 0;
@@ -99,6 +108,9 @@ void free_batch(xeng_batch_s *b)
     cudaFree(b->d_dec);
     cudaFree(b->d_dmaps);
     cudaFree(b->d_djobs);
+    cudaFree(b->partials);
+    cudaFree(b->sums);
+    cudaFree(b->d_sjobs);
     cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     cudaGetLastError();
@@ -114,6 +126,8 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
     if (e == cudaSuccess) e = launch_decode_tma_batch(b->d_dmaps, b->d_djobs, b->n_djobs, b->dtiles, b->d_err,
                                                       b->num_sms, s);
     if (e == cudaSuccess && b->n_dec > 0) e = launch_decode_batch(b->d_dec, b->n_dec, b->dec_ctas, s);
+    if (e == cudaSuccess && b->n_sjobs > 0)
+        e = launch_plane_sums_batch(b->d_sjobs, b->n_sjobs, b->sum_entries, b->num_sms, s);
     if (e == cudaSuccess) {
         ListArgs L;
         L.maps = b->d_maps;
@@ -153,18 +167,27 @@ std::vector<std::pair<int, int>> tile_order(int nt, int order)
 int plan(xeng_batch_s *b)
 {
     const int n = (int)b->jobs.size();
-    std::vector<int64_t> off(n), n_pad(n), t_pad(n);
-    int64_t total = 0;
+    std::vector<int64_t> off(n), n_pad(n), t_pad(n), poff(n, -1), soff(n, -1);
+    int64_t total = 0, ptotal = 0, stotal = 0;
     for (int j = 0; j < n; j++) {
         const xeng_job_t &jb = b->jobs[j];
         n_pad[j] = round_up(jb.n_inputs, kTile);
         t_pad[j] = round_up(jb.n_samples, kTile);
         off[j] = total;
         total += round_up((int64_t)jb.n_freq * 2 * n_pad[j] * t_pad[j], 1024);
+        if (decode_tma_ok(jb.block, jb.n_inputs)) {  // raw-nibble planes: room for the nibble sums
+            poff[j] = ptotal;
+            soff[j] = stotal;
+            ptotal += (int64_t)jb.n_freq * (t_pad[j] / kTile) * n_pad[j];
+            stotal += (int64_t)jb.n_freq * n_pad[j];
+        }
     }
     b->planes_bytes = total;
     cudaError_t e = cudaMalloc(&b->planes, (size_t)std::max<int64_t>(total, 1));
+    if (e == cudaSuccess && ptotal > 0) e = cudaMalloc(&b->partials, (size_t)ptotal * sizeof(int2));
+    if (e == cudaSuccess && stotal > 0) e = cudaMalloc(&b->sums, (size_t)stotal * sizeof(int2));
     if (e != cudaSuccess) return status_of(e);
+    std::vector<SumJob> sjobs;
 
     std::vector<CUtensorMap> maps(n);
     std::vector<JobDesc> jd(n);
@@ -182,15 +205,32 @@ int plan(xeng_batch_s *b)
         e = encode_planes_map(&maps[j], pl, t_pad[j], (int64_t)jb.n_freq * 2 * n_pad[j]);
         if (e != cudaSuccess) return status_of(e);
         const int n_k = (int)(t_pad[j] / kTile);
-        const int ns = (n_k + maxc - 1) / maxc;
+        CUtensorMap rmap, pmap;
+        const bool tma = encode_decode_tma_maps(jb.block, jb.n_samples, jb.n_freq, jb.n_inputs, pl, t_pad[j],
+                                                n_pad[j], &rmap, &pmap);
+        const bool raw = tma && poff[j] >= 0;
+        // raw-nibble items span at most kFusedMaxSamples samples (exact f32 sums)
+        const int maxc_j = raw ? std::min(maxc, kFusedMaxSamples / kTile) : maxc;
+        const int ns = (n_k + maxc_j - 1) / maxc_j;
         jd[j].out = jb.out;
         jd[j].n_pad = (int32_t)n_pad[j];
         jd[j].N = jb.n_inputs;
         jd[j].mode = ns > 1 ? 2 : 0;  // split tiles add atomically into zeroed outputs
-        jd[j].pad_ = 0;
-        CUtensorMap rmap, pmap;
-        if (encode_decode_tma_maps(jb.block, jb.n_samples, jb.n_freq, jb.n_inputs, pl, t_pad[j], n_pad[j], &rmap,
-                                   &pmap)) {
+        jd[j].n_samples = (int32_t)jb.n_samples;
+        jd[j].sums = raw ? b->sums + soff[j] : nullptr;
+        if (raw) {
+            SumJob sj;
+            sj.partials = b->partials + poff[j];
+            sj.sums = b->sums + soff[j];
+            sj.first = b->sum_entries;
+            sj.n_tb = n_k;
+            sj.part_n_tb = n_k;
+            sj.n_pad = (int32_t)n_pad[j];
+            sj.pad_ = 0;
+            sjobs.push_back(sj);
+            b->sum_entries += (int64_t)jb.n_freq * n_pad[j];
+        }
+        if (tma) {
             DecTmaJob dt;
             dt.tile0 = dtiles;
             dt.T = jb.n_samples;
@@ -200,6 +240,9 @@ int plan(xeng_batch_s *b)
             dt.N = jb.n_inputs;
             dt.n_pad = (int32_t)n_pad[j];
             dt.x0 = 0;
+            dt.partials = raw ? b->partials + poff[j] : nullptr;
+            dt.part_n_tb = dt.n_tb;
+            dt.pad_ = 0;
             dtiles += (int64_t)dt.n_ib * dt.F * dt.n_tb;
             djobs.push_back(dt);
             dmaps.push_back(rmap);
@@ -232,8 +275,8 @@ int plan(xeng_batch_s *b)
                     c.w.fl = f;
                     c.w.I = (int16_t)I;
                     c.w.J = (int16_t)J;
-                    c.w.kc0 = sp * maxc;
-                    c.w.kc1 = std::min(n_k, (sp + 1) * maxc);
+                    c.w.kc0 = sp * maxc_j;
+                    c.w.kc1 = std::min(n_k, (sp + 1) * maxc_j);
                     // MMA time per chunk, plus a fixed cost for the epilogue and pipeline fill
                     c.cost = (double)(c.w.kc1 - c.w.kc0) + 2.0;
                     c.order = (int64_t)cand.size();
@@ -241,6 +284,7 @@ int plan(xeng_batch_s *b)
                 }
     }
     b->dec_ctas = cta0;
+    b->n_sjobs = (int)sjobs.size();
     b->n_dec = (int)dj.size();
     b->n_djobs = (int)djobs.size();
     b->dtiles = dtiles;
@@ -310,6 +354,7 @@ int plan(xeng_batch_s *b)
     if (e == cudaSuccess) e = upload(&b->d_dec, dj);
     if (e == cudaSuccess) e = upload(&b->d_dmaps, dmaps);
     if (e == cudaSuccess) e = upload(&b->d_djobs, djobs);
+    if (e == cudaSuccess) e = upload(&b->d_sjobs, sjobs);
     return status_of(e);
 }
 

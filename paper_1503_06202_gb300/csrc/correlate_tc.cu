@@ -107,6 +107,12 @@ struct Work {
     int fl, I, J;
     int kc0, kc1;    // 128-sample chunks [kc0, kc1)
     int mode;
+    // raw-nibble planes: (S, D) of the channel's inputs (null: decoded planes),
+    // 128 x samples of the integration, and whether this item adds the offset
+    // terms (items split along time add them once, in the first part)
+    const int2 *sums;
+    int n128;
+    bool offset;
 };
 
 
@@ -129,6 +135,9 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
         w.kc0 = wi.kc0 * kChunksPer128;
         w.kc1 = wi.kc1 * kChunksPer128;
         w.mode = jd.mode;
+        w.sums = jd.sums ? jd.sums + (int64_t)wi.fl * jd.n_pad : nullptr;
+        w.n128 = 128 * jd.n_samples;
+        w.offset = wi.kc0 == 0;
     } else {
         w.map = tmap;
         w.out = a.acc;
@@ -138,6 +147,9 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
         w.kc0 = 0;
         w.kc1 = n_k;
         w.mode = a.accumulate ? kAdd : kStore;
+        w.sums = a.sums ? a.sums + (int64_t)w.fl * a.n_pad : nullptr;
+        w.n128 = 128 * (int)a.n_samples;
+        w.offset = true;
     }
     return w;
 }
@@ -152,7 +164,8 @@ __device__ __forceinline__ Work fetch_work(int it, const CUtensorMap *tmap, cons
 //     Re V = sum(p p' + q q') - 8 (S_i + S_j) + 128 n,
 //     -Im V = sum(p q' - q p') - 8 (D_i - D_j),
 // formed right after the TMEM loads (launches of at most 32,768 samples keep
-// the sums below 2^24, exact in the f32 accumulators).
+// the sums below 2^24, exact in the f32 accumulators).  Listed launches take
+// raw-nibble or decoded planes per job (JobDesc::sums).
 // The operands draw less power than codes of -8..7 (measured: the dense rate
 // on random raw-nibble codes equals the rate on zeros, 10% above -8..7).
 template <bool kListed, bool kRaw = false>
@@ -316,10 +329,11 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             int2 *out = reinterpret_cast<int2 *>(w.out + (int64_t)w.fl * N * (N + 1));
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u;
             const int64_t jbase = (int64_t)w.J * kTile;
-            const int2 *sums = kRaw ? a.sums + (int64_t)w.fl * a.n_pad : nullptr;  // (S, D) per input row
+            const bool raw = kRaw || (kListed && w.sums != nullptr);  // uniform over the item
+            const int2 *sums = w.sums;                                // (S, D) per input row
             int2 si = make_int2(0, 0);
-            if (kRaw) si = sums[i];  // i < n_pad
-            const int n128 = kRaw ? 128 * (int)a.n_samples : 0;
+            if (raw && w.offset) si = sums[i];  // i < n_pad
+            const int n128 = raw && w.offset ? w.n128 : 0;
             // the triangle is written once and not read again here: streaming
             // stores keep it from evicting the operand planes other tiles
             // still read from L2
@@ -328,10 +342,11 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
                 tmem_ld16(taddr + c, re);
                 tmem_ld16(taddr + 128 + c, nim);
                 tmem_ld_wait();
-                if (kRaw) {
+                if (raw) {
                     #pragma unroll
                     for (int e = 0; e < 16; e++) {
-                        const int2 sj = sums[jbase + c + e];  // the same for every lane: a broadcast
+                        // the same for every lane: a broadcast
+                        const int2 sj = w.offset ? sums[jbase + c + e] : make_int2(0, 0);
                         const int vr = __float2int_rn(262144.0f * __uint_as_float(re[e])) - 8 * (si.x + sj.x) + n128;
                         const int vi = __float2int_rn(262144.0f * __uint_as_float(nim[e])) - 8 * (si.y - sj.y);
                         re[e] = __float_as_uint((float)vr);

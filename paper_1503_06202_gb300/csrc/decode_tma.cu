@@ -69,6 +69,8 @@ struct DtTile {
     const CUtensorMap *rm, *pm;
     int ib, fl, tb, f, N, n_pad, x0;
     int64_t T, t0;
+    int2 *part;      // raw-nibble planes: the (P, Q) partial sums of the tile's inputs go to
+    int part_row;    // part[part_row * n_pad + input] (null: decoded planes)
 };
 
 // Tile order within a block (job): input block fastest, then channel, then
@@ -92,6 +94,8 @@ __device__ __forceinline__ DtTile dt_tile(const DecTmaArgs &a, const CUtensorMap
         t.n_pad = a.n_pad;
         t.T = a.T;
         t.t0 = a.t0;
+        t.part = a.partials;
+        t.part_row = t.fl * a.n_tb + t.tb;
     } else {
         int lo = 0, hi = a.n_jobs - 1;
         while (lo < hi) {  // last job whose first tile is <= tile
@@ -112,6 +116,8 @@ __device__ __forceinline__ DtTile dt_tile(const DecTmaArgs &a, const CUtensorMap
         t.n_pad = j.n_pad;
         t.T = j.T;
         t.t0 = 0;
+        t.part = j.partials;
+        t.part_row = t.fl * j.part_n_tb + (j.x0 >> 7) + t.tb;
     }
     return t;
 }
@@ -125,7 +131,8 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
 
 // kRaw: the planes hold the raw nibbles (E4M3 codes of u / 512, see the
 // correlator's raw mode) instead of the decoded values, and each tile's
-// per-input nibble sums (P, Q) go to a.partials[fl][tb][input].
+// per-input nibble sums (P, Q) go to a.partials[fl][tb][input].  Batched
+// launches (kBatch) decide per job: raw where the job has a partial-sum buffer.
 template <int kStages, int kGroups, int kP, bool kBatch, bool kRaw = false>
 __global__ void __launch_bounds__(kDTThreads, 1)
 decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_constant__ CUtensorMap plane_map,
@@ -231,6 +238,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
             uint8_t *pre = sgen + (pre_s - sbase);
             uint8_t *pim = pre + kDTPlane;
             const int ibase = ib * 128;
+            const bool raw = kBatch ? tl.part != nullptr : kRaw;  // uniform over the tile
             uint32_t sp[4] = {0, 0, 0, 0}, sq[4] = {0, 0, 0, 0};  // raw mode: nibble sums of inputs 4q + m
             if (ok) {
                 #pragma unroll
@@ -247,9 +255,9 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                         for (int kk = 0; kk < 4; kk++) {
                             const int t = b * 16 + h * 8 + g * 4 + kk;
                             // past the end: value 0 (decoded) or nibbles 0, adding nothing (raw)
-                            r[kk] = (tbase + g * 4 + kk < tl.T) ? rt[t * 32 + q] : (kRaw ? 0u : 0x88888888u);
+                            r[kk] = (tbase + g * 4 + kk < tl.T) ? rt[t * 32 + q] : (raw ? 0u : 0x88888888u);
                         }
-                        if (kRaw) {
+                        if (raw) {
                             // transpose, then split: input m's high (Re) and low (Im) nibbles of samples 0..3
                             #pragma unroll
                             for (int m = 0; m < 4; m++) {
@@ -281,7 +289,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                     }
                 }
             }
-            if (kRaw && ok) {
+            if (raw && ok) {
                 int4 *sc = reinterpret_cast<int4 *>(scratch + cw * 128 + 4 * q);
                 sc[0] = make_int4((int)sp[0], (int)sq[0], (int)sp[1], (int)sq[1]);
                 sc[1] = make_int4((int)sp[2], (int)sq[2], (int)sp[3], (int)sq[3]);
@@ -306,7 +314,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                 }
                 mbar_arrive(rawe(stage));  // the raw slot may be refilled
             }
-            if (kRaw && !any_fail && wl < 4) {
+            if (raw && !any_fail && wl < 4) {
                 // the tile's sums of input k = 32 wl + lane over the group's warps (their partials
                 // stay until the group's next first barrier, which every reader passes after this)
                 const int k = wl * 32 + lane;
@@ -317,7 +325,7 @@ decode_tma_kernel(const __grid_constant__ CUtensorMap raw_map, const __grid_cons
                     P += v.x;
                     Q += v.y;
                 }
-                a.partials[((int64_t)fl * a.n_tb + tb) * a.n_pad + ibase + k] = make_int2(P, Q);
+                tl.part[(int64_t)tl.part_row * tl.n_pad + ibase + k] = make_int2(P, Q);
             }
             if (any_fail) break;
         }
@@ -422,6 +430,42 @@ cudaError_t launch_plane_sums(const int2 *partials, int32_t nf, int32_t n_tb, in
     return cudaGetLastError();
 }
 
+namespace {
+// Batched: sums of job j = (S, D) totals over its tile rows of the partials;
+// entry k of the launch is job j's (fl, i) with k - jobs[j].first = fl * n_pad + i.
+__global__ void plane_sums_batch_kernel(const SumJob *__restrict__ jobs, int32_t n_jobs, int64_t total)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {  // last job whose first entry is <= k
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].first <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        const SumJob &j = jobs[lo];
+        const int64_t local = k - j.first;
+        const int64_t fl = local / j.n_pad, i = local % j.n_pad;
+        const int2 *p = j.partials + fl * j.part_n_tb * j.n_pad + i;
+        int P = 0, Q = 0;
+        for (int tb = 0; tb < j.n_tb; tb++) {
+            const int2 v = p[(int64_t)tb * j.n_pad];
+            P += v.x;
+            Q += v.y;
+        }
+        j.sums[local] = make_int2(P + Q, P - Q);
+    }
+}
+}  // namespace
+
+cudaError_t launch_plane_sums_batch(const SumJob *jobs, int32_t n_jobs, int64_t total, int num_sms, cudaStream_t s)
+{
+    if (n_jobs <= 0 || total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8 * (int64_t)num_sms) blocks = 8 * (int64_t)num_sms;
+    plane_sums_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs, total);
+    return cudaGetLastError();
+}
+
 bool encode_decode_tma_maps(const uint8_t *block, int64_t T, int32_t F, int32_t N, uint8_t *planes, int64_t t_pad,
                             int64_t n_pad, CUtensorMap *raw_map, CUtensorMap *plane_map)
 {
@@ -444,11 +488,13 @@ bool encode_decode_tma_maps(const uint8_t *block, int64_t T, int32_t F, int32_t 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Batched launches decide raw or decoded planes per job, so their shared
+// memory always has room for the raw mode's partial sums.
 cudaError_t prepare_decode_tma_batch()
 {
     return cudaFuncSetAttribute(decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs));
+                                (int)dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs, true));
 }
 
 cudaError_t launch_decode_tma_batch(const CUtensorMap *maps, const DecTmaJob *jobs, int n_jobs, int64_t n_tiles,
@@ -467,7 +513,7 @@ cudaError_t launch_decode_tma_batch(const CUtensorMap *maps, const DecTmaJob *jo
     a.n_jobs = n_jobs;
     const int grid = (int)(n_tiles < num_sms ? n_tiles : num_sms);
     decode_tma_kernel<kDTSlots, kDTGroups, kDTPlaneBufs, true>
-        <<<grid, kDTThreads, dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs), s>>>(unused, unused, a);
+        <<<grid, kDTThreads, dt_smem(kDTSlots, kDTGroups, kDTPlaneBufs, true), s>>>(unused, unused, a);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,8 @@ struct SStream {
     int64_t bytes = 0;               // charged to the HBM budget
     int32_t *acc = nullptr;
     uint8_t *planes[2] = {nullptr, nullptr};
+    int2 *partials[2] = {nullptr, nullptr};  // raw-nibble rounds: per-tile nibble sums of the slice
+    int2 *sums[2] = {nullptr, nullptr};      // ... and their totals (S, D) per [F][n_pad]
     DumpSlot dump[2];
     bool fresh = true;
     int64_t integrated = 0;          // samples in the current integration (launched)
@@ -126,6 +128,7 @@ struct xserve_s {
     DecodeJob *d_dec[2] = {nullptr, nullptr}, *h_dec[2] = {nullptr, nullptr};  // blocks TMA cannot address
     CUtensorMap *d_dmaps[2] = {nullptr, nullptr}, *h_dmaps[2] = {nullptr, nullptr};  // TMA decode: 2 maps per block
     DecTmaJob *d_djobs[2] = {nullptr, nullptr}, *h_djobs[2] = {nullptr, nullptr};
+    SumJob *d_sjobs[2] = {nullptr, nullptr}, *h_sjobs[2] = {nullptr, nullptr};  // raw-nibble streams of a round
     int *d_err = nullptr, *h_err = nullptr;
     std::deque<Round> inflight;
     int next_slot = 0;
@@ -145,7 +148,10 @@ int64_t stream_bytes(const SStream &st, int max_blocks)
 {
     const int64_t acc = (int64_t)st.F * n_baselines(st.N) * 8;
     const int64_t planes = (int64_t)st.F * 2 * st.n_pad * (st.bs_pad * max_blocks);
-    return 3 * acc + 2 * planes;  // accumulators, two dump buffers, two plane slices
+    const int64_t part = (int64_t)st.F * (st.bs_pad * max_blocks / kTile) * st.n_pad * 8;
+    const int64_t sums = (int64_t)st.F * st.n_pad * 8;
+    // accumulators, two dump buffers, two plane slices with their nibble sums
+    return 3 * acc + 2 * (planes + part + sums);
 }
 
 void free_stream_memory(SStream &st)
@@ -155,6 +161,12 @@ void free_stream_memory(SStream &st)
     cudaFree(st.planes[1]);
     cudaFree(st.dump[0].buf);
     cudaFree(st.dump[1].buf);
+    for (int k = 0; k < 2; k++) {
+        cudaFree(st.partials[k]);
+        cudaFree(st.sums[k]);
+        st.partials[k] = nullptr;
+        st.sums[k] = nullptr;
+    }
     st.acc = nullptr;
     st.planes[0] = st.planes[1] = nullptr;
     st.dump[0].buf = st.dump[1].buf = nullptr;
@@ -282,7 +294,7 @@ bool launch_round(xserve_s *sv)
 
     Round r;
     r.slot = slot;
-    int64_t n_items = 0, n_dec = 0, dec_ctas = 0, n_djobs = 0, dtiles = 0;
+    int64_t n_items = 0, n_dec = 0, dec_ctas = 0, n_djobs = 0, dtiles = 0, n_sjobs = 0, sum_entries = 0;
     int jobi = 0;
     for (auto &pk : picks) {
         SStream &st = sv->streams[pk.stream];
@@ -312,6 +324,10 @@ bool launch_round(xserve_s *sv)
         }
         const int64_t pitch = st.bs_pad * pk.nblocks;
         uint8_t *pl = st.planes[slot];
+        // raw-nibble planes when every block of the round goes through the TMA
+        // decode and the round spans at most kFusedMaxSamples samples
+        bool raw = st.partials[slot] && pitch <= kFusedMaxSamples;
+        for (int b = 0; raw && b < pk.nblocks; b++) raw = decode_tma_ok(st.queue[b].ptr, st.N);
         Round::Part part;
         part.stream = pk.stream;
         part.nblocks = pk.nblocks;
@@ -324,7 +340,13 @@ bool launch_round(xserve_s *sv)
             // the TMA decode where the block's rows allow it: the block's raw
             // map and the slice's plane map, the block at column b * bs_pad
             CUtensorMap *mp = sv->h_dmaps[slot] + 2 * n_djobs;
-            if (encode_decode_tma_maps(qb.ptr, st.block_samples, st.F, st.N, pl, pitch, st.n_pad, mp, mp + 1)) {
+            const bool tma = encode_decode_tma_maps(qb.ptr, st.block_samples, st.F, st.N, pl, pitch, st.n_pad, mp,
+                                                    mp + 1);
+            if (raw && !tma) {
+                sv->sticky = XENG_ERR_CUDA;  // a block checked above could not be encoded
+                return false;
+            }
+            if (tma) {
                 DecTmaJob &dt = sv->h_djobs[slot][n_djobs++];
                 dt.tile0 = dtiles;
                 dt.T = st.block_samples;
@@ -334,6 +356,9 @@ bool launch_round(xserve_s *sv)
                 dt.N = st.N;
                 dt.n_pad = (int32_t)st.n_pad;
                 dt.x0 = (int32_t)(b * st.bs_pad);
+                dt.partials = raw ? st.partials[slot] : nullptr;
+                dt.part_n_tb = (int32_t)(pitch / kTile);
+                dt.pad_ = 0;
                 dtiles += (int64_t)dt.n_ib * dt.F * dt.n_tb;
             } else {
                 DecodeJob &dj = sv->h_dec[slot][n_dec++];
@@ -360,7 +385,19 @@ bool launch_round(xserve_s *sv)
         jd.n_pad = (int32_t)st.n_pad;
         jd.N = st.N;
         jd.mode = st.fresh ? 0 : 1;
-        jd.pad_ = 0;
+        jd.n_samples = (int32_t)(pk.nblocks * st.block_samples);
+        jd.sums = raw ? st.sums[slot] : nullptr;
+        if (raw) {
+            SumJob &sj = sv->h_sjobs[slot][n_sjobs++];
+            sj.partials = st.partials[slot];
+            sj.sums = st.sums[slot];
+            sj.first = sum_entries;
+            sj.n_tb = (int32_t)(pitch / kTile);
+            sj.part_n_tb = (int32_t)(pitch / kTile);
+            sj.n_pad = (int32_t)st.n_pad;
+            sj.pad_ = 0;
+            sum_entries += (int64_t)st.F * st.n_pad;
+        }
         const int nt = (int)(st.n_pad / kTile);
         const int n_k = (int)(pitch / kTile);
         for (int f = 0; f < st.F; f++)
@@ -407,6 +444,8 @@ bool launch_round(xserve_s *sv)
                             s);
     if (e == cudaSuccess && n_djobs > 0)
         e = cudaMemcpyAsync(sv->d_djobs[slot], sv->h_djobs[slot], n_djobs * sizeof(DecTmaJob), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_sjobs > 0)
+        e = cudaMemcpyAsync(sv->d_sjobs[slot], sv->h_sjobs[slot], n_sjobs * sizeof(SumJob), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && jobi > 0)
         e = cudaMemcpyAsync(sv->d_maps[slot], sv->h_maps[slot], jobi * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && jobi > 0)
@@ -417,6 +456,8 @@ bool launch_round(xserve_s *sv)
     if (e == cudaSuccess)
         e = launch_decode_tma_batch(sv->d_dmaps[slot], sv->d_djobs[slot], (int)n_djobs, dtiles, sv->d_err, sv->num_sms, s);
     if (e == cudaSuccess && n_dec > 0) e = launch_decode_batch(sv->d_dec[slot], (int)n_dec, dec_ctas, s);
+    if (e == cudaSuccess && n_sjobs > 0)
+        e = launch_plane_sums_batch(sv->d_sjobs[slot], (int32_t)n_sjobs, sum_entries, sv->num_sms, s);
     if (e == cudaSuccess && r.t1) e = cudaEventRecord(r.t1, s);
     if (e == cudaSuccess && n_items > 0) {
         ListArgs L;
@@ -540,6 +581,8 @@ int xserve_create(const xserve_opts_t *opts, xserve_t *out)
         if (e == cudaSuccess) e = cudaMalloc(&sv->d_djobs[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecTmaJob));
         if (e == cudaSuccess)
             e = cudaMallocHost(&sv->h_djobs[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecTmaJob));
+        if (e == cudaSuccess) e = cudaMalloc(&sv->d_sjobs[k], (size_t)o.max_streams * sizeof(SumJob));
+        if (e == cudaSuccess) e = cudaMallocHost(&sv->h_sjobs[k], (size_t)o.max_streams * sizeof(SumJob));
     }
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(sv->d_err, 0, sizeof(int));
@@ -608,6 +651,12 @@ int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t bl
     if (e == cudaSuccess) e = cudaMalloc(&st.dump[1].buf, acc);
     if (e == cudaSuccess) e = cudaMalloc(&st.planes[0], planes);
     if (e == cudaSuccess) e = cudaMalloc(&st.planes[1], planes);
+    const size_t part = (size_t)n_freq * (bs_pad * sv->opts.max_blocks / kTile) * n_pad * sizeof(int2);
+    const size_t sums = (size_t)n_freq * n_pad * sizeof(int2);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaMalloc(&st.partials[k], part);
+        if (e == cudaSuccess) e = cudaMalloc(&st.sums[k], sums);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_stream_memory(st);
@@ -825,6 +874,8 @@ void xserve_destroy(xserve_t sv)
         cudaFreeHost(sv->h_dmaps[k]);
         cudaFree(sv->d_djobs[k]);
         cudaFreeHost(sv->h_djobs[k]);
+        cudaFree(sv->d_sjobs[k]);
+        cudaFreeHost(sv->h_sjobs[k]);
     }
     cudaFree(sv->d_err);
     if (sv->h_err) cudaFreeHost(sv->h_err);

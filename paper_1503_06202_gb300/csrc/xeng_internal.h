@@ -99,8 +99,22 @@ struct DecTmaJob {
     int64_t tile0;
     int64_t T;
     int32_t n_ib, n_tb, F, N, n_pad;
-    int32_t x0;  // first plane column of the job in its plane map (a multiple of 128)
+    int32_t x0;          // first plane column of the job in its plane map (a multiple of 128)
+    int2 *partials;      // non-null: raw-nibble planes, the tiles' (P, Q) sums to
+                         // partials[fl][x0 / 128 + tb][n_pad] ...
+    int32_t part_n_tb;   // ... whose rows per channel are part_n_tb
+    int32_t pad_;
 };
+// Totals of raw-nibble partial sums for several jobs in one launch: job j's
+// sums[fl][i] = (S, D) over tile rows 0 .. n_tb - 1 of partials[fl][.][i]
+// (rows per channel part_n_tb); its entries are k = first .. first + F * n_pad - 1.
+struct SumJob {
+    const int2 *partials;
+    int2 *sums;
+    int64_t first;
+    int32_t n_tb, part_n_tb, n_pad, pad_;
+};
+cudaError_t launch_plane_sums_batch(const SumJob *jobs, int32_t n_jobs, int64_t total, int num_sms, cudaStream_t s);
 bool encode_decode_tma_maps(const uint8_t *block, int64_t T, int32_t F, int32_t N, uint8_t *planes, int64_t t_pad,
                             int64_t n_pad, CUtensorMap *raw_map, CUtensorMap *plane_map);
 cudaError_t prepare_decode_tma_batch();
@@ -188,7 +202,8 @@ struct JobDesc {
     int32_t n_pad;     // inputs rounded up to 128
     int32_t N;
     int32_t mode;      // epilogue: 0 store, 1 add (read-modify-write), 2 atomic add (items share tiles)
-    int32_t pad_;
+    int32_t n_samples; // raw-nibble planes: samples integrated (the offset terms' n)
+    const int2 *sums;  // raw-nibble planes: (S, D) per [F][n_pad]; null: decoded planes
 };
 struct WorkItem {
     int32_t job, fl;   // job index, channel within the job
