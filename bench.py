@@ -200,6 +200,10 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded generator)",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload][1],
                        "n_inputs": N, "n_freq": F, "t_integ": T, "step_sample": "channel 0, %d samples" % Ts},
+            "sample_ops_per_step": ops, "workload_ops_per_step": useful_ops(T, F, N),
+            "extrapolation": ("value = useful ops of the sample / its time; the oracle's work grows linearly with "
+                              "channels and samples, so the whole workload (%.3g ops) would take %.1f s per step "
+                              "on these cores" % (useful_ops(T, F, N), useful_ops(T, F, N) / (value * 1e12))),
             "cpu_baseline": {"value": value, "unit": "TOPS", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "channel 0, all %d inputs, %d samples per step" % (N, Ts)},
             "e2e": {"value": value, "unit": "TOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
