@@ -183,6 +183,11 @@ cudaEvent_t take_event(xeng_s *h)
 #ifndef XENG_FUSED_SMALL
 #define XENG_FUSED_SMALL 1
 #endif
+// Its kernel: 1 = single CTAs over upper-triangle blocks (correlate_small.cu),
+// 0 = 2-CTA clusters over the full 256 x 256 product (correlate_fused.cu).
+#ifndef XENG_SMALL_1CTA
+#define XENG_SMALL_1CTA 1
+#endif
 
 
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
@@ -259,6 +264,8 @@ bool fused_ok(const xeng_s *h, const uint8_t *block)
 cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                          int32_t f0, int32_t nf, int32_t *acc, int accumulate, cudaStream_t s)
 {
+    if (h->N <= 256 && XENG_SMALL_1CTA)
+        return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms, s);
     if (h->N <= 256)
         return launch_correlate_fused256(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
                                          s);

@@ -1,8 +1,10 @@
 """The fused decode + correlation used for up to 256 inputs (N a multiple of
-16): bit-exact against the oracle for tiny N (the second CTA of the cluster
-reads only padding), ragged sample counts, one sample, several launches
-adding into int32, pushes in pieces, host buffers, and many channels per
-cluster."""
+16): bit-exact against the oracle for tiny N (tiles mostly padding), up to and
+above 128 inputs (diagonal items of two channels; row items and diagonal items
+of the upper input halves), odd channel counts (a diagonal item of one
+channel), ragged sample counts, one sample, several launches adding into
+int32, pushes in pieces, host buffers, and many items per CTA (both parities of
+the item sums, store and add)."""
 import numpy as np
 import pytest
 
@@ -65,6 +67,18 @@ def test_fused_host_buffers_and_many_channels():
     want = oracle.correlate(blk)
     assert np.array_equal(correlate(blk), want)
     assert np.array_equal(correlate(blk, host=True), want)
+
+
+@pytest.mark.parametrize("N", [64, 192, 256])
+def test_fused_many_items_per_cta(N):
+    # 1001 channels: N > 128 gives 1502 items (about ten per CTA), N <= 128 501;
+    # pushed in two pieces, so the second launch adds into the first
+    rng = np.random.default_rng(N)
+    T, F = 96, 1001
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    assert np.array_equal(correlate(blk), want)
+    assert np.array_equal(correlate(blk, pieces=[33]), want)
 
 
 # ---- more than 256 inputs (fused engine): the raw bytes correlated by 2-CTA clusters
