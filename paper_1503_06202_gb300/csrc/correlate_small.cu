@@ -17,12 +17,23 @@
 // raw tiles of 128 inputs x 64 samples ("X" and "Y": the channel's two input
 // halves, or the two channels' upper halves).
 //
+// The launch's work -- its items in order, each of n_k stages of 64 samples --
+// is split evenly over the CTAs: CTA b takes stages [b T / G, (b + 1) T / G)
+// of that sequence (T stages in all, G CTAs), so every CTA does the same
+// number of MMAs whether or not the items divide evenly.  An item cut between
+// CTAs is finished by its owner, the CTA holding its first stages (which
+// reaches them last): the CTAs holding its later pieces (which start with
+// them) write their corrected partial blocks to a workspace and raise a flag
+// stamped with the launch's epoch; the owner waits for those flags (bounded),
+// adds the partials to its own and stores.  A cooperative launch keeps every
+// CTA resident, so the waits end.
+//
 // The TMA writes raw tiles with a 128-byte swizzle: rows are samples, each 128
 // input bytes -- the canonical MN-major layout of an 8-bit tcgen05 operand
 // (inputs along M or N, samples along K).  The converter warps split each byte
 // at its own offset into the Re plane (high nibble) and the Im plane (low
 // nibble) of a plane stage; the raw slots form their own ring, so the TMA runs
-// up to five tiles ahead of the conversion whatever the MMAs are doing.  The
+// up to five stages ahead of the conversion.  The
 // MMAs of a stage (both operands MN-major; B of a row item spans the X and Y
 // tiles, the leading byte offset stepping from one to the other):
 //     Re += A_re B_re^T + A_im B_im^T,   Im += A_im B_re^T + (-A_re) B_im^T.
@@ -65,6 +76,7 @@ constexpr int kSPlaneBytes = 4 * kSBox;     // plane stage: Re_X, Re_Y, Im_X, Im
 #define XENG_SMALL_RAW_SLOTS 5
 #endif
 constexpr int kSPlanes = XENG_SMALL_PLANE_STAGES, kSRaws = XENG_SMALL_RAW_SLOTS;
+
 constexpr int kSConvWarp0 = 2, kSConvWarps = 8;
 constexpr int kSEpiWarp0 = kSConvWarp0 + kSConvWarps, kSEpiWarps = 8;
 constexpr int kSThreads = 32 * (kSEpiWarp0 + kSEpiWarps);
@@ -76,6 +88,7 @@ constexpr int kSBars = 2 * kSRaws + 2 * kSPlanes + 3 + 4;
 constexpr size_t kSSmem =
     1024 + (size_t)kSPlanes * kSPlaneBytes + (size_t)kSRaws * kSRawBytes + kSSums + kSBars * 8 + 16;
 static_assert(kSSmem <= 232448, "shared memory over the per-CTA limit");
+constexpr int kSMinPiece = 32;  // stages per CTA at least (the grid shrinks for small launches)
 static_assert(kSConvWarps * 32 == 2 * kSBox / 16 / 4, "each converter thread splits four 16-byte chunks per stage");
 
 // Instruction descriptor, kind::f8f6f4: D f32, A and B E4M3, both MN-major
@@ -100,11 +113,42 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 struct SmallArgs {
     int64_t t0, nt;        // samples t0 .. t0 + nt - 1 of the block, nt <= kFusedMaxSamples
     int32_t F, N, f0, nf;  // channels f0 .. f0 + nf - 1
-    int32_t n_items;
+    int32_t n_items, n_k;  // items; stages (of kSKc samples) per item
+    int64_t total;         // n_items * n_k: the launch's (item, stage) sequence, split evenly over the CTAs
     int32_t *acc;          // [nf][N(N+1)/2][2], channel f0 + fl at fl
     int accumulate;        // 0: store, 1: add
+    int2 *ws;              // [grid][2][16][128][8] partial blocks of pieces that do not start their item
+    int *flags;            // [grid]: epoch once the CTA's partial is in ws
+    int epoch;             // this launch's flag value (distinct from every earlier launch's)
     int *err;
 };
+
+// A CTA's work: the stages [lo, hi) of the launch's sequence (item-major),
+// lo = b * total / grid, as pieces (item, stages k0 .. k1 - 1).  A piece with
+// k0 > 0 (only ever a CTA's first) adds its partial block through ws; the CTA
+// whose piece starts the item (its owner) adds them into its own and stores.
+struct Piece {
+    int it, k0, k1;
+};
+
+__device__ __forceinline__ int64_t range_lo(const SmallArgs &a, int b) { return (int64_t)b * a.total / gridDim.x; }
+
+// The CTA whose range holds stage x of the sequence.
+__device__ __forceinline__ int stage_cta(const SmallArgs &a, int64_t x)
+{
+    return (int)(((x + 1) * (int64_t)gridDim.x - 1) / a.total);
+}
+
+__device__ __forceinline__ bool next_piece(const SmallArgs &a, int64_t &x, int64_t hi, Piece &p)
+{
+    if (x >= hi) return false;
+    p.it = (int)(x / a.n_k);
+    const int64_t first = (int64_t)p.it * a.n_k;
+    p.k0 = (int)(x - first);
+    p.k1 = (int)(hi - first < a.n_k ? hi - first : a.n_k);
+    x = first + p.k1;
+    return true;
+}
 
 // Item `it`.  N > 128: per channel pair (2m, 2m + 1) the row item of 2m, the
 // diagonal item of both, the row item of 2m + 1 (an odd last channel: its row
@@ -166,8 +210,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = a.err;
-    const int it_begin = (int)blockIdx.x, it_step = (int)gridDim.x;
-    const int n_k = (int)((a.nt + kSKc - 1) / kSKc);
+    const int64_t lo = range_lo(a, (int)blockIdx.x), hi = range_lo(a, (int)blockIdx.x + 1);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSRaws; s++) {
@@ -205,11 +248,13 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
             int s = 0, issued = 0;
             uint32_t ph = 0;
             bool ok = true;
-            for (int it = it_begin; ok && it < a.n_items; it += it_step) {
-                const SmallItem w = small_item(a, it);
+            int64_t x = lo;
+            Piece pc;
+            while (ok && next_piece(a, x, hi, pc)) {
+                const SmallItem w = small_item(a, pc.it);
                 const int fX = a.f0 + w.fx, fY = a.f0 + (w.fy >= 0 ? w.fy : w.fx);
                 const int xX = w.base, xY = w.row ? 128 : w.base;
-                for (int kc = 0; kc < n_k; kc++) {
+                for (int kc = pc.k0; kc < pc.k1; kc++) {
                     if (!mbar_try_wait(rawe(s), ph ^ 1u) && !mbar_wait(rawe(s), ph ^ 1u, err, kDevTimeoutProducer)) {
                         ok = false;
                         break;
@@ -240,12 +285,14 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
             int s = 0;
             uint32_t ph = 0, uses = 0;
             bool ok = true;
-            for (int it = it_begin; ok && it < a.n_items; it += it_step) {
-                const SmallItem w = small_item(a, it);
+            int64_t x = lo;
+            Piece pc;
+            while (ok && next_piece(a, x, hi, pc)) {
+                const SmallItem w = small_item(a, pc.it);
                 if (!mbar_wait(acce, (uses & 1u) ^ 1u, err, kDevTimeoutMma)) break;
                 ++uses;
                 fence_after();
-                for (int kc = 0; kc < n_k; kc++) {
+                for (int kc = pc.k0; kc < pc.k1; kc++) {
                     if (!mbar_try_wait(full(s), ph) && !mbar_wait(full(s), ph, err, kDevTimeoutMma)) {
                         ok = false;
                         break;
@@ -257,7 +304,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                         const uint64_t dre = sdesc(st), dim = sdesc(st + 2 * kSBox);
                         #pragma unroll
                         for (int kk = 0; kk < kSKc / 32; kk++) {  // +32 samples = +4 KB = +256 in the address field
-                            const uint32_t acc = (kc != 0 || kk != 0) ? 1u : 0u;
+                            const uint32_t acc = (kc != pc.k0 || kk != 0) ? 1u : 0u;
                             const uint64_t k4 = 256u * kk;
                             mma_f8(tmem, dre + k4, dre + k4, small_idesc(256, false), acc);
                             mma_f8(tmem, dim + k4, dim + k4, small_idesc(256, false), 1u);
@@ -272,7 +319,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                             const uint32_t dr = tmem + 128u * h, di = tmem + 256u + 128u * h;
                             #pragma unroll
                             for (int kk = 0; kk < kSKc / 32; kk++) {
-                                const uint32_t acc = (kc != 0 || kk != 0) ? 1u : 0u;
+                                const uint32_t acc = (kc != pc.k0 || kk != 0) ? 1u : 0u;
                                 const uint64_t k4 = 256u * kk;
                                 mma_f8(dr, dre + k4, dre + k4, small_idesc(128, false), acc);
                                 mma_f8(dr, dim + k4, dim + k4, small_idesc(128, false), 1u);
@@ -310,7 +357,9 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
         int rs = 0, ps = 0, local = 0;
         uint32_t rph = 0, pph = 0;
         bool ok = true;
-        for (int it = it_begin; ok && it < a.n_items; it += it_step, ++local) {
+        int64_t x = lo;
+        Piece pc;
+        for (; ok && next_piece(a, x, hi, pc); ++local) {
             // nibble sums of the thread's 16 inputs: byte lanes over up to four
             // stages (16 samples, <= 240), then 16-bit lanes (<= 15 x 2048 samples)
             uint32_t pb[4] = {0, 0, 0, 0}, qb[4] = {0, 0, 0, 0};
@@ -325,7 +374,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     pb[w] = qb[w] = 0;
                 }
             };
-            for (int kc = 0; kc < n_k; kc++) {
+            for (int kc = pc.k0; kc < pc.k1; kc++) {
                 ok = mbar_wait_backoff(rawf(rs), rph, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
@@ -339,8 +388,14 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     x[k] = *reinterpret_cast<const uint4 *>(src + 2048 * k);
                     if (r0 + 16 * k >= rows_left) x[k] = make_uint4(0, 0, 0, 0);  // past the launch: adds nothing
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(rawe(rs));  // the slot's bytes are in registers
+                // The raw slot goes back to the producer with the plane stage below, once
+                // the plane stores (which consume the loaded words) are done.  An arrival
+                // right after the loads, with nothing waiting for their data, let the TMA
+                // refill the slot under loads still in flight (measured on GB300: whole
+                // items wrong in about one launch in two when the MMAs stalled behind a
+                // long epilogue); one whose address depended on the loaded words was
+                // exact but 1% slower than this.
+                const int rcur = rs;
                 if (++rs == kSRaws) {
                     rs = 0;
                     rph ^= 1u;
@@ -370,12 +425,15 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the MMAs
                 __syncwarp();
-                if (lane == 0) mbar_arrive(full(ps));
+                if (lane == 0) {
+                    mbar_arrive(full(ps));
+                    mbar_arrive(rawe(rcur));
+                }
                 if (++ps == kSPlanes) {
                     ps = 0;
                     pph ^= 1u;
                 }
-                if ((kc & 3) == 3) widen();
+                if (((kc - pc.k0) & 3) == 3) widen();
             }
             if (!ok) break;
             widen();
@@ -423,16 +481,29 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
         const int et = (warp - kSEpiWarp0) * 32 + lane;
         const int row = q * 32 + lane;              // TMEM lane: row within the block
         const int N = a.N;                          // <= 256
-        const int n128 = 128 * (int)a.nt;           // 64 n from each of the two products
+        const int nt = (int)a.nt;
         const int64_t nb = (int64_t)N * (N + 1) / 2;
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+        // partial blocks in ws: [CTA][block h][chunk c / 8][row][8 pairs]
+        constexpr int kWs = 2 * 16 * 128 * 8;
+        const int wsi = ((h * 16) * 128 + row) * 8;  // + (c / 8) * 1024
         uint32_t uses = 0;
         int local = 0;
-        for (int it = it_begin; it < a.n_items; it += it_step, ++local) {
-            const SmallItem w = small_item(a, it);
+        int64_t x = lo;
+        Piece pc;
+        while (next_piece(a, x, hi, pc)) {
+            const SmallItem w = small_item(a, pc.it);
             const int par = local & 1;
+            // the piece's samples inside the launch: 64 n from each of the two products
+            const int n128 = 128 * ((pc.k1 * kSKc < nt ? pc.k1 * kSKc : nt) - pc.k0 * kSKc);
+            const bool owner = pc.k0 == 0;
+            // an owner whose item runs on: the CTAs after it that hold the rest
+            const int c_lo = (int)blockIdx.x + 1;
+            const int c_hi = owner && pc.k1 < a.n_k ? stage_cta(a, (int64_t)(pc.it + 1) * a.n_k - 1) : 0;
             bool ok = mbar_wait_backoff(accf, uses & 1u, err, kDevTimeoutEpilogue, 128);
             ok = ok && mbar_wait_backoff(sums_full(par), (uint32_t)((local >> 1) & 1), err, kDevTimeoutEpilogue, 128);
+            if (et == 0)
+                for (int b = c_lo; ok && b <= c_hi; b++) ok = flag_wait(a.flags + b, a.epoch, err, kDevTimeoutEpilogue);
             // the barrier ORs the eight warps' failures, so they leave together
             if (bar_any(2, kSEpiWarps * 32, !ok)) break;
             ++uses;
@@ -461,24 +532,45 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     tmem_ld8(taddr + 128u * h + c, vre);
                     tmem_ld8(taddr + 256u + 128u * h + c, vim);
                     tmem_ld_wait();
-                    if (row_ok) {
-                        #pragma unroll
-                        for (int e = 0; e < 8; e++) {  // corrected values in place of the accumulator words
-                            const int2 pj = scol[c + e];  // the same for every lane: a broadcast
-                            // accumulators hold integer sums / 2^18: x 2^18 is exact
-                            vre[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vre[e])) -
-                                                8 * (si + pj.x + pj.y) + n128);
-                            vim[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vim[e])) +
-                                                8 * (di - (pj.x - pj.y)));
-                        }
-                        if (a.accumulate) put8<true>(out + row_base + j0, i - j0, N - j0, vre, vim);
-                        else put8<false>(out + row_base + j0, i - j0, N - j0, vre, vim);
+                    if (!row_ok) continue;
+                    #pragma unroll
+                    for (int e = 0; e < 8; e++) {  // corrected values in place of the accumulator words
+                        const int2 pj = scol[c + e];  // the same for every lane: a broadcast
+                        // accumulators hold integer sums / 2^18: x 2^18 is exact
+                        vre[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vre[e])) -
+                                            8 * (si + pj.x + pj.y) + n128);
+                        vim[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vim[e])) +
+                                            8 * (di - (pj.x - pj.y)));
                     }
+                    const int wo = wsi + (c >> 3) * 1024;
+                    if (!owner) {
+                        // a later piece of the item: the partial goes to this CTA's slot
+                        int4 *d = reinterpret_cast<int4 *>(a.ws + (int64_t)blockIdx.x * kWs + wo);
+                        #pragma unroll
+                        for (int e = 0; e < 8; e += 2)
+                            __stcg(d + e / 2, make_int4((int)vre[e], (int)vim[e], (int)vre[e + 1], (int)vim[e + 1]));
+                        continue;
+                    }
+                    for (int b = c_lo; b <= c_hi; b++) {  // the item's later pieces (none for a whole item)
+                        const int4 *src = reinterpret_cast<const int4 *>(a.ws + (int64_t)b * kWs + wo);
+                        #pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            const int4 v = __ldcg(src + e / 2);
+                            vre[e] += (uint32_t)v.x;
+                            vim[e] += (uint32_t)v.y;
+                            vre[e + 1] += (uint32_t)v.z;
+                            vim[e + 1] += (uint32_t)v.w;
+                        }
+                    }
+                    if (a.accumulate) put8<true>(out + row_base + j0, i - j0, N - j0, vre, vim);
+                    else put8<false>(out + row_base + j0, i - j0, N - j0, vre, vim);
                 }
             }
+            if (!owner) __threadfence();  // the partial is visible at GPU scope before the flag below
             // every epilogue thread is done with this parity's sums: clear them for
-            // the item after next, then hand TMEM and the buffer back
+            // the piece after next, then hand TMEM and the buffer back
             named_bar_sync(2, kSEpiWarps * 32);
+            if (!owner && et == 0) st_release_gpu(a.flags + blockIdx.x, a.epoch);
             sums[par * 256 + et] = make_int2(0, 0);
             fence_before();
             __syncwarp();
@@ -486,6 +578,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                 mbar_arrive(acce);
                 mbar_arrive(sums_empty(par));
             }
+            ++local;
         }
     }
 
@@ -500,15 +593,18 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
 
 }  // namespace
 
+size_t small_ws_bytes(int num_sms) { return (size_t)num_sms * 2 * 16 * 128 * 8 * sizeof(int2); }
+
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
-                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
-                                   cudaStream_t s)
+                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
+                                   int epoch, int *err, int num_sms, cudaStream_t s)
 {
     if (nf <= 0 || nt <= 0) return cudaSuccess;
     if (!fused256_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
-        f0 < 0 || f0 + nf > F || num_sms < 1 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0)
+        f0 < 0 || f0 + nf > F || num_sms < 1 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0 || !ws || !flags)
         return cudaErrorInvalidValue;
     const int64_t n_items = N > 128 ? (int64_t)nf + (nf + 1) / 2 : (int64_t)(nf + 1) / 2;
+    const int n_k = (int)((nt + kSKc - 1) / kSKc);
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x 64
@@ -535,12 +631,32 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
     a.f0 = f0;
     a.nf = nf;
     a.n_items = (int32_t)n_items;
+    a.n_k = n_k;
+    a.total = n_items * n_k;
     a.acc = acc;
     a.accumulate = accumulate;
+    a.ws = ws;
+    a.flags = flags;
+    a.epoch = epoch;
     a.err = err;
-    const int grid = n_items < num_sms ? (int)n_items : num_sms;
-    correlate_small_kernel<<<grid, kSThreads, kSSmem, s>>>(map, a);
-    return cudaGetLastError();
+    // every CTA gets at least kSMinPiece stages (a piece's epilogue and partial
+    // cost about as much as a few stages of MMAs), at most one CTA per SM
+    int64_t grid = a.total / kSMinPiece;
+    if (grid < 1) grid = 1;
+    if (grid > num_sms) grid = num_sms;
+    // the owner of a split item waits for the CTAs holding its later pieces:
+    // a cooperative launch has every CTA resident at once (or fails)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(kSThreads, 1, 1);
+    cfg.dynamicSmemBytes = kSSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, correlate_small_kernel, map, a);
 }
 
 }  // namespace xeng

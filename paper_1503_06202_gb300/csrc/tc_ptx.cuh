@@ -264,6 +264,39 @@ __device__ __forceinline__ bool bar_any(int id, int count, bool flag)
     return any != 0;
 }
 
+// Flags between CTAs of one launch: a release store after the data it
+// publishes, an acquire load before the data it guards.
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait for *flag == v (as mbar_wait: false once the error word is set
+// or the limit passes, then this thread sets it to `code`).
+__device__ __noinline__ bool flag_wait(const int *flag, int v, int *err, int code)
+{
+    if (ld_acquire_gpu(flag) == v) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        __nanosleep(128);
+        if (ld_acquire_gpu(flag) == v) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int *)err != 0) return false;
+            if (globaltimer() - t0 > kWaitLimitNs) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
 // Named barrier `id` over count threads (a multiple of 32), which all must reach it.
 __device__ __forceinline__ void named_bar_sync(int id, int count)
 {

@@ -33,6 +33,9 @@ struct xeng_s {
     int2 *partials = nullptr;      // raw-nibble planes: per-tile nibble sums [group_f][n_tb][n_pad]
     int2 *sums = nullptr;          // raw-nibble planes: (S, D) per input [group_f][n_pad]
     int2 *raw_sums = nullptr;      // single-pass kernel above 256 inputs: (S, D) per input [F][N]
+    int2 *small_ws = nullptr;      // single-pass kernel up to 256 inputs: partial blocks of split items
+    int *small_flags = nullptr;    // and the flags that publish them (num_sms ints)
+    int small_epoch = 0;           // its launches so far
     bool planes_raw = false;       // the last decode wrote raw-nibble planes
     int32_t group_f = 0;           // channels per decode + correlate round
     int64_t chunk_t = 0;           // samples per round
@@ -264,8 +267,24 @@ bool fused_ok(const xeng_s *h, const uint8_t *block)
 cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                          int32_t f0, int32_t nf, int32_t *acc, int accumulate, cudaStream_t s)
 {
-    if (h->N <= 256 && XENG_SMALL_1CTA)
-        return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms, s);
+    if (h->N <= 256 && XENG_SMALL_1CTA) {
+        if (!h->small_ws) {
+            cudaError_t e = cudaMalloc(&h->small_ws, small_ws_bytes(h->num_sms));
+            if (e == cudaSuccess) e = cudaMalloc(&h->small_flags, (size_t)h->num_sms * sizeof(int));
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->small_flags, 0, (size_t)h->num_sms * sizeof(int), s);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(h->small_ws);
+                cudaFree(h->small_flags);
+                h->small_ws = nullptr;
+                h->small_flags = nullptr;
+                return e;
+            }
+        }
+        if (++h->small_epoch <= 0) h->small_epoch = 1;  // flags start at 0: never an epoch
+        return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->small_ws,
+                                      h->small_flags, h->small_epoch, h->d_err, h->num_sms, s);
+    }
     if (h->N <= 256)
         return launch_correlate_fused256(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
                                          s);
@@ -394,6 +413,8 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->partials);
     cudaFree(h->sums);
     cudaFree(h->raw_sums);
+    cudaFree(h->small_ws);
+    cudaFree(h->small_flags);
     cudaFree(h->staging);
     cudaFree(h->gidx);
     cudaFree(h->counts);

@@ -142,11 +142,15 @@ cudaError_t launch_correlate_fused256(const uint8_t *block, int64_t T_block, int
                                       int num_sms, cudaStream_t s);
 
 // The same step with single CTAs over upper-triangle 128 x 128 blocks only
-// (three per channel of 129..256 inputs instead of the pair's four): same
-// arguments and conditions as launch_correlate_fused256.
+// (three per channel of 129..256 inputs instead of the pair's four), same
+// conditions as launch_correlate_fused256.  The launch's work is split evenly
+// over the CTAs; an item cut between CTAs is completed through ws (scratch of
+// small_ws_bytes(num_sms)) and flags (num_sms ints, zeroed once), with `epoch`
+// different from every earlier launch's on the same flags.
+size_t small_ws_bytes(int num_sms);
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
-                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
-                                   cudaStream_t s);
+                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
+                                   int epoch, int *err, int num_sms, cudaStream_t s);
 
 // Decode fused into the correlation for 256 < N <= 4096 (N % 16 == 0, block
 // 16-byte aligned), as launch_correlate_fused256: a pass forming every input's

@@ -81,6 +81,19 @@ def test_fused_many_items_per_cta(N):
     assert np.array_equal(correlate(blk, pieces=[33]), want)
 
 
+@pytest.mark.parametrize("N", [64, 192])
+def test_fused_items_split_over_many_ctas(N):
+    # a few channels over a whole 32,768-sample launch: each item's stages are
+    # split over many CTAs, whose partial blocks the item's first CTA adds up;
+    # stored, then added by a second push
+    rng = np.random.default_rng(N + 1)
+    T, F = 32768, 5
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    assert np.array_equal(correlate(blk), want)
+    assert np.array_equal(correlate(blk, pieces=[20000]), want)
+
+
 # ---- more than 256 inputs (fused engine): the raw bytes correlated by 2-CTA clusters
 # ---- over pairs of 256-input blocks (diagonal pairs, ragged last blocks, both CTAs' halves)
 
