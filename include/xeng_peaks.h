@@ -31,6 +31,15 @@ extern "C" {
                                        (second with A negated) into one 256-column accumulator   */
 #define XENG_PEAK_TC_F8F6F4_LIVE_RAW 7  /* as XENG_PEAK_TC_F8F6F4_LIVE with random raw-nibble codes
                                            (bytes 0x00..0x0F: E4M3 of u / 512)                    */
+#define XENG_PEAK_TC_F8F6F4_MN 8    /* as XENG_PEAK_TC_F8F6F4_LIVE_RAW with both operands MN-major
+                                       (128-byte swizzle; B two 128-element atoms along N)        */
+#define XENG_PEAK_TC_F8F6F4_MN_N128 9  /* as XENG_PEAK_TC_F8F6F4_MN with N = 128                 */
+#define XENG_PEAK_TC_F8F6F4_MN_RING 10 /* as XENG_PEAK_TC_F8F6F4_MN in the single-pass kernels'
+                                          issue pattern: per 64-sample stage eight N = 256 MMAs into
+                                          two accumulators (one with A negated), a commit to the
+                                          stage's mbarrier, and a wait for the stage four back      */
+#define XENG_PEAK_TC_F8F6F4_MN_PAIRS 11 /* the MMAs of XENG_PEAK_TC_F8F6F4_MN_RING without the ring:
+                                           one commit at the end                                    */
 
 /*
  * xeng_peak_probe -- run probe `kind` with `iters` instructions per issuing

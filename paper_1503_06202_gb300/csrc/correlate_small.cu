@@ -11,7 +11,8 @@
 // cost, each two 128 x 128 complex blocks, 512 TMEM columns:
 //   row item of channel c:        A = inputs 0..127, B = inputs 0..255 (one
 //                                 N = 256 MMA per product): blocks (0,0), (0,1)
-//   diagonal item of channels c, c':  block (1,1) of each (N = 128 MMAs)
+//   diagonal item of channels c, c':  block (1,1) of each (one N = 256 and
+//                                 two N = 128 MMAs per product pair)
 // Up to 128 inputs a channel is one diagonal block, and every item is a
 // diagonal item over two channels' inputs 0..127.  Per stage an item reads two
 // raw tiles of 128 inputs x 64 samples ("X" and "Y": the channel's two input
@@ -67,7 +68,7 @@ namespace {
 constexpr int kSKc = 64;                    // samples per stage
 constexpr int kSBox = kSKc * 128;           // one raw tile or plane tile: 64 samples x 128 inputs
 constexpr int kSRawBytes = 2 * kSBox;       // raw slot: tiles X and Y
-constexpr int kSPlaneBytes = 4 * kSBox;     // plane stage: Re_X, Re_Y, Im_X, Im_Y
+constexpr int kSPlaneBytes = 4 * kSBox;     // plane stage: Im_X, Im_Y, Re_X, Re_Y
 // Ring depths (build parameters; 4 x 32 KB + 5 x 16 KB fill the shared memory).
 #ifndef XENG_SMALL_PLANE_STAGES
 #define XENG_SMALL_PLANE_STAGES 4
@@ -101,12 +102,11 @@ __host__ __device__ constexpr uint32_t small_idesc(int n, bool neg_a)
 
 // MN-major operand with a 128-byte swizzle: rows of 128 elements along M/N,
 // 8-row groups along K 1 KB apart (stride byte offset), version 1.  The
-// leading byte offset is the step between 128-element atoms along M/N: an
-// N = 256 operand continues in the next plane tile, 8 KB on (one-atom operands
-// ignore it).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+// leading byte offset `lbo` is the step between 128-element atoms along M/N,
+// where an N = 256 operand continues (one-atom operands ignore it).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo)
 {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kSBox >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
@@ -300,8 +300,9 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     fence_after();
                     const uint32_t st = plane(s);
                     if (w.row) {
-                        // A = X rows, B = X and Y columns: Re in columns 0..255, Im in 256..511
-                        const uint64_t dre = sdesc(st), dim = sdesc(st + 2 * kSBox);
+                        // A = X rows, B = X and Y columns (the Y plane 8 KB after the X
+                        // plane): Re in columns 0..255, Im in 256..511
+                        const uint64_t dre = sdesc(st + 2 * kSBox, kSBox), dim = sdesc(st, kSBox);
                         #pragma unroll
                         for (int kk = 0; kk < kSKc / 32; kk++) {  // +32 samples = +4 KB = +256 in the address field
                             const uint32_t acc = (kc != pc.k0 || kk != 0) ? 1u : 0u;
@@ -312,19 +313,22 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                             mma_f8(tmem + 256u, dre + k4, dim + k4, small_idesc(256, true), 1u);
                         }
                     } else {
-                        // each tile against itself: Re of tile h in columns 128h.., Im in 256 + 128h..
+                        // each tile against itself, in columns 256h..: one N = 256 MMA of
+                        // A_im against [B_im | B_re] (Re_h 16 KB after Im_h) gives
+                        // [Im Im^T | Im Re^T]; A_re B_re^T completes Re, and (-A_re) B_im^T
+                        // makes the second half Im Re^T - Re Im^T = Im.  (Four N = 128 MMAs
+                        // per tile instead ran at about 72% of the tensor rate.)
                         #pragma unroll
                         for (int h = 0; h < 2; h++) {
-                            const uint64_t dre = sdesc(st + h * kSBox), dim = sdesc(st + (2 + h) * kSBox);
-                            const uint32_t dr = tmem + 128u * h, di = tmem + 256u + 128u * h;
+                            const uint64_t dim = sdesc(st + h * kSBox, 2 * kSBox), dre = sdesc(st + (2 + h) * kSBox, 2 * kSBox);
+                            const uint32_t d = tmem + 256u * h;
                             #pragma unroll
                             for (int kk = 0; kk < kSKc / 32; kk++) {
                                 const uint32_t acc = (kc != pc.k0 || kk != 0) ? 1u : 0u;
                                 const uint64_t k4 = 256u * kk;
-                                mma_f8(dr, dre + k4, dre + k4, small_idesc(128, false), acc);
-                                mma_f8(dr, dim + k4, dim + k4, small_idesc(128, false), 1u);
-                                mma_f8(di, dim + k4, dre + k4, small_idesc(128, false), acc);
-                                mma_f8(di, dre + k4, dim + k4, small_idesc(128, true), 1u);
+                                mma_f8(d, dim + k4, dim + k4, small_idesc(256, false), acc);
+                                mma_f8(d, dre + k4, dre + k4, small_idesc(128, false), 1u);
+                                mma_f8(d + 128u, dre + k4, dim + k4, small_idesc(128, true), 1u);
                             }
                         }
                     }
@@ -405,8 +409,8 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     ok = false;
                     break;
                 }
-                uint8_t *dre = sgen + (plane(ps) - sbase) + off0;  // Re_X / Re_Y
-                uint8_t *dim = dre + 2 * kSBox;                    // Im_X / Im_Y
+                uint8_t *dim = sgen + (plane(ps) - sbase) + off0;  // Im_X / Im_Y
+                uint8_t *dre = dim + 2 * kSBox;                    // Re_X / Re_Y
                 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     uint4 re, im;
@@ -523,14 +527,18 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                 const int si = pq.x + pq.y, di = pq.x - pq.y;
                 const int row_base = i * N - i * (i - 1) / 2 - i;  // pair (i, j) at row_base + j
                 int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)fl * nb;
+                // TMEM columns of the block: row items Re at 128h.., Im at 256 + 128h..;
+                // diagonal items Re at 256h.., Im at 256h + 128..
+                const uint32_t cre = w.row ? 128u * h : 256u * h;
+                const uint32_t cim = cre + (w.row ? 256u : 128u);
                 for (int c = 0; c < 128; c += 8) {
                     const int j0 = j0b + c;
                     // warp-uniform skips: chunks past the last input or below every row's diagonal
                     if (j0 >= N) break;
                     if (j0 + 7 < i_warp) continue;
                     uint32_t vre[8], vim[8];
-                    tmem_ld8(taddr + 128u * h + c, vre);
-                    tmem_ld8(taddr + 256u + 128u * h + c, vim);
+                    tmem_ld8(taddr + cre + c, vre);
+                    tmem_ld8(taddr + cim + c, vim);
                     tmem_ld_wait();
                     if (!row_ok) continue;
                     #pragma unroll

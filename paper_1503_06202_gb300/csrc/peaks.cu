@@ -29,8 +29,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 // correlator's operand values) instead of zeros -- the tensor core draws more
 // power on live data, which matters under the board's power cap; 2: the codes
 // of pseudo-random raw nibbles u / 512 (bytes 0x00..0x0F), the fused kernel's
-// operands.
-template <bool kF8, int kMix, int kData = 0>
+// operands.  kMN: both operands MN-major (128-byte swizzle, 8-row groups along K
+// 1 KB apart, 128-element atoms along M/N 8 KB apart), as the single-pass
+// kernels lay out raw tiles; a K step of 32 rows is 4 KB.
+template <bool kF8, int kMix, int kData = 0, bool kMN = false>
 __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sink)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -63,10 +65,21 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sin
     const uint32_t tmem = tmem_slot;
     if (threadIdx.x == 0) {
         const uint32_t a = base, b = base + 16384;
-        const uint32_t idesc = (1u << 4) | ((uint32_t)((kMix == 1 ? 128 : 256) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        const uint32_t mn = kMN ? (1u << 15) | (1u << 16) : 0u;
+        const uint32_t idesc =
+            (1u << 4) | mn | ((uint32_t)((kMix == 1 ? 128 : 256) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         const uint32_t idesc128 = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        // the MN-major descriptors: leading byte offset 8 KB (the next atom along N)
+        const uint64_t mn_lbo = kMN ? ((uint64_t)((8192 >> 4) - 1) << 16) : 0u;
         for (int64_t i = 0; i < iters; i++) {
-            const uint32_t off = (uint32_t)(i & 3) * 32;
+            const uint32_t off = kMN ? (uint32_t)(i & 1) * 4096 : (uint32_t)(i & 3) * 32;
+            if (kF8 && kMN) {
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem), "l"(desc_sw128(a + off) + mn_lbo), "l"(desc_sw128(b + off) + mn_lbo),
+                               "r"(idesc), "r"(1));
+                continue;
+            }
             if (kF8) {
                 asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                              "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
@@ -109,6 +122,111 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, int *sin
 }
 
 // 8 warps x 8 independent m16n8k32 s8 accumulators per warp.
+// The single-pass kernels' MMA issue pattern with the operands standing still:
+// per stage two K steps of four N = 256 MMAs (D0 += A B, D0 += A' B', D1 +=
+// A' B, D1 -= A B'), MN-major operands, a commit to the stage's mbarrier, and
+// before each stage a wait for the commit of the stage four back (a four-deep
+// ring whose producer is instant).  kRing false: the same MMAs, one commit at the end.
+template <bool kRing>
+__global__ void __launch_bounds__(128, 1) tc_ring_peak_kernel(int64_t iters, int *sink)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t bars[4];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    for (int k = threadIdx.x; k < 48 * 1024; k += blockDim.x) {
+        uint32_t h = (uint32_t)k * 2654435761u + blockIdx.x * 40503u;
+        h ^= h >> 15;
+        gbase[k] = (uint8_t)(h & 15);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 4; s++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        const uint64_t lbo = (uint64_t)((8192 >> 4) - 1) << 16;
+        const uint64_t da = desc_sw128(base) + lbo, db = desc_sw128(base + 16384) + lbo;
+        bool ok = true;
+        for (int64_t i = 0; ok && i < iters; i++) {
+            const int s = (int)(i & 3);
+            const uint32_t bar = smem_u32(&bars[s]);
+            if (kRing && i >= 4) {  // bounded wait (about 2 s) for the stage four back
+                const uint32_t par = (uint32_t)(((i >> 2) - 1) & 1);
+                uint64_t t0, t1;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+                for (;;) {
+                    uint32_t done;
+                    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(par) : "memory");
+                    if (done) break;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                    if (t1 - t0 > 2000000000ull) {
+                        atomicExch(sink, 1);
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) break;
+            }
+            #pragma unroll
+            for (int kk = 0; kk < 2; kk++) {
+                const uint64_t k4 = 256u * kk;
+                const uint32_t acc = 1u;
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem), "l"(da + k4), "l"(da + k4), "r"(idesc), "r"(acc));
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem), "l"(db + k4), "l"(db + k4), "r"(idesc), "r"(1u));
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem + 256), "l"(db + k4), "l"(da + k4), "r"(idesc), "r"(acc));
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                             ::"r"(tmem + 256), "l"(da + k4), "l"(db + k4), "r"(idesc | (1u << 13)), "r"(1u));
+            }
+            if (kRing || i == iters - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                             : "memory");
+        }
+        // drain: wait (bounded) for the last stages' commits
+        for (int64_t i = kRing ? (iters - 4 > 0 ? iters - 4 : 0) : iters - 1; ok && i < iters; i++) {
+            const uint32_t bar = smem_u32(&bars[i & 3]);
+            const uint32_t par = (uint32_t)((i >> 2) & 1);
+            uint64_t t0, t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (;;) {
+                uint32_t done;
+                asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                             "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(par) : "memory");
+                if (done) break;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                if (t1 - t0 > 2000000000ull) {
+                    atomicExch(sink, 1);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
 __global__ void __launch_bounds__(256) mma_s8_peak_kernel(int64_t iters, int seed, int *sink)
 {
     uint32_t a0 = seed * 0x01010101u, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, b0 = a0 ^ 5, b1 = a0 ^ 9;
@@ -189,6 +307,26 @@ extern "C" int xeng_peak_probe(int32_t kind, int64_t iters, double *tflops, doub
             cudaFuncSetAttribute(tc_peak_kernel<true, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             tc_peak_kernel<true, 0, 2><<<sms, 128, smem>>>(iters, sink);
             flops = 2.0 * 128 * 256 * 32 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_MN:
+            cudaFuncSetAttribute(tc_peak_kernel<true, 0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 0, 2, true><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 256 * 32 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_MN_N128:
+            cudaFuncSetAttribute(tc_peak_kernel<true, 1, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_peak_kernel<true, 1, 2, true><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 128 * 32 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_MN_RING:
+            cudaFuncSetAttribute(tc_ring_peak_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_ring_peak_kernel<true><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 256 * 32 * 8 * (double)iters * sms;
+            break;
+        case XENG_PEAK_TC_F8F6F4_MN_PAIRS:
+            cudaFuncSetAttribute(tc_ring_peak_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            tc_ring_peak_kernel<false><<<sms, 128, smem>>>(iters, sink);
+            flops = 2.0 * 128 * 256 * 32 * 8 * (double)iters * sms;
             break;
         case XENG_PEAK_TC_F16:
             cudaFuncSetAttribute(tc_peak_kernel<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

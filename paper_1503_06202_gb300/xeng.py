@@ -342,7 +342,8 @@ def xeng_correlate_noalloc(block, n_samples, n_freq, n_inputs, out, stream=None)
 
 XENG_PEAK_TC_F8F6F4, XENG_PEAK_TC_F16, XENG_PEAK_MMA_SYNC_S8, XENG_PEAK_DP4A = 0, 1, 2, 3
 XENG_PEAK_TC_F8F6F4_N128, XENG_PEAK_TC_F8F6F4_MIX, XENG_PEAK_TC_F8F6F4_LIVE = 4, 5, 6
-XENG_PEAK_TC_F8F6F4_LIVE_RAW = 7
+XENG_PEAK_TC_F8F6F4_LIVE_RAW, XENG_PEAK_TC_F8F6F4_MN, XENG_PEAK_TC_F8F6F4_MN_N128 = 7, 8, 9
+XENG_PEAK_TC_F8F6F4_MN_RING, XENG_PEAK_TC_F8F6F4_MN_PAIRS = 10, 11
 
 
 def xeng_peak_probe(kind: int, iters: int):
