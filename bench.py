@@ -54,7 +54,7 @@ def correlate_kernel(engine, N):
     the square of inputs one work item computes, lower halves of diagonal
     items included)."""
     if engine in ("tensor", "fused") and N % 16 == 0 and N <= 256:
-        return "correlate_fused256_kernel (decode fused; the full 256 x 256 square)", 256
+        return "correlate_small_kernel (decode fused; upper-triangle 128-input blocks, one CTA each)", 128
     if engine == "fused" and N % 16 == 0:
         return "correlate_raw_kernel (raw bytes split in shared memory; 256-input block pairs)", 256
     return "correlate_tc_kernel (decoded planes; 128-input tile pairs)", 128
@@ -696,7 +696,8 @@ def main():
         ms2 = ev0.elapsed_time(ev1) / reps2
         secondary = {"workload": "pathfinder_full", "description": WORKLOADS["pathfinder_full"][1],
                      "ms_per_step": ms2, "value": useful_ops(r2.T, r2.F, r2.N) / (ms2 * 1e-3) / 1e12, "unit": "TOPS",
-                     "steps": reps2, "kernel": "correlate_fused256_kernel (decode fused into the correlation)"}
+                     "steps": reps2, "kernel": "correlate_small_kernel (decode fused into the correlation; "
+                                               "upper-triangle 128-input blocks)"}
         eng2.close()
         del blk2, out2
     # the plain single-instance CUDA-core (dp4a) correlator on the same GPU, on
@@ -757,9 +758,10 @@ def main():
         if probes and probes.get("tc_f8f6f4"):
             roof["peak_probe_fp8"] = probes["tc_f8f6f4"]
             roof["frac_of_probe_fp8"] = roof["achieved"] / probes["tc_f8f6f4"]
-            # useful ops exclude the lower halves of diagonal tiles the MMAs also compute
+            # useful ops exclude the lower halves of diagonal tiles (and the padding past N)
+            # the MMAs also compute: nt (nt + 1) / 2 tiles of tile x tile per channel
             nt = -(-N // tile)
-            executed = (nt * (nt + 1) // 2 * tile * tile if tile < 256 or N > 256 else 256 * 256) / (N * (N + 1) / 2)
+            executed = (nt * (nt + 1) // 2 * tile * tile) / (N * (N + 1) / 2)
             roof["executed_over_useful"] = executed
             roof["frac_executed_of_probe_fp8"] = roof["achieved"] * executed / probes["tc_f8f6f4"]
         if probes and probes.get("tc_f8f6f4_live_data"):

@@ -601,6 +601,11 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
 
 }  // namespace
 
+bool small_ok(const uint8_t *block, int32_t N)
+{
+    return N >= 1 && N <= 256 && N % 16 == 0 && (reinterpret_cast<uintptr_t>(block) & 15) == 0;
+}
+
 size_t small_ws_bytes(int num_sms) { return (size_t)num_sms * 2 * 16 * 128 * 8 * sizeof(int2); }
 
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
@@ -608,7 +613,7 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
                                    int epoch, int *err, int num_sms, cudaStream_t s)
 {
     if (nf <= 0 || nt <= 0) return cudaSuccess;
-    if (!fused256_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
+    if (!small_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
         f0 < 0 || f0 + nf > F || num_sms < 1 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0 || !ws || !flags)
         return cudaErrorInvalidValue;
     const int64_t n_items = N > 128 ? (int64_t)nf + (nf + 1) / 2 : (int64_t)(nf + 1) / 2;

@@ -186,11 +186,6 @@ cudaEvent_t take_event(xeng_s *h)
 #ifndef XENG_FUSED_SMALL
 #define XENG_FUSED_SMALL 1
 #endif
-// Its kernel: 1 = single CTAs over upper-triangle blocks (correlate_small.cu),
-// 0 = 2-CTA clusters over the full 256 x 256 product (correlate_fused.cu).
-#ifndef XENG_SMALL_1CTA
-#define XENG_SMALL_1CTA 1
-#endif
 
 
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
@@ -258,16 +253,16 @@ cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int
 // default there).
 bool fused_ok(const xeng_s *h, const uint8_t *block)
 {
-    if (h->engine == XENG_ENGINE_TENSOR) return XENG_FUSED_SMALL && fused256_ok(block, h->N);
+    if (h->engine == XENG_ENGINE_TENSOR) return XENG_FUSED_SMALL && small_ok(block, h->N);
     if (h->engine == XENG_ENGINE_TENSOR_FUSED)
-        return (XENG_FUSED_SMALL && fused256_ok(block, h->N)) || correlate_raw_ok(block, h->N);
+        return (XENG_FUSED_SMALL && small_ok(block, h->N)) || correlate_raw_ok(block, h->N);
     return false;
 }
 
 cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                          int32_t f0, int32_t nf, int32_t *acc, int accumulate, cudaStream_t s)
 {
-    if (h->N <= 256 && XENG_SMALL_1CTA) {
+    if (h->N <= 256) {
         if (!h->small_ws) {
             cudaError_t e = cudaMalloc(&h->small_ws, small_ws_bytes(h->num_sms));
             if (e == cudaSuccess) e = cudaMalloc(&h->small_flags, (size_t)h->num_sms * sizeof(int));
@@ -285,9 +280,6 @@ cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64
         return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->small_ws,
                                       h->small_flags, h->small_epoch, h->d_err, h->num_sms, s);
     }
-    if (h->N <= 256)
-        return launch_correlate_fused256(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
-                                         s);
     if (!h->raw_sums) {  // the per-input sums of the largest launch: every channel of the handle
         cudaError_t e = cudaMalloc(&h->raw_sums, (size_t)h->F * h->N * sizeof(int2));
         if (e != cudaSuccess) {

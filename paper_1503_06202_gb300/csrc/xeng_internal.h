@@ -132,28 +132,23 @@ cudaError_t launch_shift_fixup(const uint8_t *block, int64_t t0, int64_t nt, int
 cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, int64_t n, int32_t F, int32_t N,
                                  const int32_t *inputs, int32_t S, int64_t H, uint8_t *hist_new, cudaStream_t s);
 
-// Decode fused into the correlation for N <= 256 (N % 16 == 0, block 16-byte
-// aligned): samples t0 .. t0 + nt - 1 (nt <= 65536) of the block (T_block
-// samples), channels f0 .. f0 + nf - 1, stored (accumulate = 0) or added into
-// acc [nf][N(N+1)/2][2]; no decoded planes.
-bool fused256_ok(const uint8_t *block, int32_t N);
-cudaError_t launch_correlate_fused256(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
-                                      int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
-                                      int num_sms, cudaStream_t s);
-
-// The same step with single CTAs over upper-triangle 128 x 128 blocks only
-// (three per channel of 129..256 inputs instead of the pair's four), same
-// conditions as launch_correlate_fused256.  The launch's work is split evenly
-// over the CTAs; an item cut between CTAs is completed through ws (scratch of
-// small_ws_bytes(num_sms)) and flags (num_sms ints, zeroed once), with `epoch`
-// different from every earlier launch's on the same flags.
+// Decode fused into the correlation for N <= 256 (small_ok: N % 16 == 0, block
+// 16-byte aligned): samples t0 .. t0 + nt - 1 (nt <= kFusedMaxSamples) of the
+// block (T_block samples), channels f0 .. f0 + nf - 1, stored (accumulate = 0)
+// or added into acc [nf][N(N+1)/2][2] (8-byte aligned); no decoded planes.
+// Single CTAs over upper-triangle 128 x 128 blocks only (three per channel of
+// 129..256 inputs).  The launch's work is split evenly over the CTAs; an item
+// cut between CTAs is completed through ws (scratch of small_ws_bytes(num_sms))
+// and flags (num_sms ints, zeroed once), with `epoch` different from every
+// earlier launch's on the same flags.
+bool small_ok(const uint8_t *block, int32_t N);
 size_t small_ws_bytes(int num_sms);
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
                                    int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
                                    int epoch, int *err, int num_sms, cudaStream_t s);
 
 // Decode fused into the correlation for 256 < N <= 4096 (N % 16 == 0, block
-// 16-byte aligned), as launch_correlate_fused256: a pass forming every input's
+// 16-byte aligned), as launch_correlate_small: a pass forming every input's
 // nibble sums into `sums` (scratch of nf * N int2), then 2-CTA clusters over
 // every channel's upper-triangle pairs of 256-input blocks; nt <=
 // kFusedMaxSamples, acc 8-byte aligned.

@@ -60,7 +60,7 @@ def test_fused_int32_beyond_f32_range():
 
 
 def test_fused_host_buffers_and_many_channels():
-    # 300 channels over the 76 clusters: several channels per cluster
+    # 300 channels, 450 items over the CTAs: several pieces per CTA, items cut between CTAs
     rng = np.random.default_rng(6)
     T, F, N = 640, 300, 256
     blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
