@@ -46,6 +46,7 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 DRAM_BYTES_PER_CHANNEL = {
     ("correlate_tc", 2048, 8192): (658.302976e6 + 244.678912e6) / 16,   # raw-nibble planes, 16-channel slice
     ("correlate_raw", 2048, 8192): (307.412224e6 + 223.055104e6) / 16,  # fused engine, 16-channel slice
+    ("correlate_small", 256, 32768): (822.840832e6 + 22.4192e6) / 64,   # N <= 256 kernel, 64-channel slice
 }
 
 
