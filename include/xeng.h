@@ -64,10 +64,10 @@ extern "C" {
 #define XENG_MAX_T_INTEG  16777215LL
 
 /* Correlation engines (all give identical bits). */
-#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 256 (a multiple of 16, block
+#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 768 (a multiple of 16, block
                                         16-byte aligned) one kernel splits the raw bytes in shared memory and
-                                        correlates them (scratch: 256 KB per SM, allocated at the first
-                                        such call); otherwise as XENG_ENGINE_TENSOR_PLANES                   */
+                                        correlates them (N <= 256: scratch of 256 KB per SM, allocated at
+                                        the first such call); otherwise as XENG_ENGINE_TENSOR_PLANES         */
 #define XENG_ENGINE_DP4A          1  /* plain CUDA-core kernel: int8 dp4a straight from the bytes            */
 #define XENG_ENGINE_TENSOR_PLANES 2  /* two passes: decode to FP8 planes in HBM, then the tensor-core GEMM   */
 #define XENG_ENGINE_TENSOR_FUSED  3  /* single pass for every N that is a multiple of 16 (block 16-byte

@@ -186,6 +186,19 @@ cudaEvent_t take_event(xeng_s *h)
 #ifndef XENG_FUSED_SMALL
 #define XENG_FUSED_SMALL 1
 #endif
+// Up to this many inputs (above 256) one pass with single CTAs over 128-input
+// block pairs (correlate_onepass.cu) is the tensor engines' path; above it the
+// default engine decodes to planes first and the fused engine runs 2-CTA
+// clusters over 256-input block pairs (correlate_raw.cu).  Measured on GB300,
+// F = 1024, T = 8192, ms (one pass / two passes / 2-CTA pass): N = 384 2.64 /
+// 3.50 / 4.56, 512 4.32 / 5.09 / 5.05, 768 9.21 / 9.14 / 9.03, 1024 15.9 /
+// 14.4 / 14.6, 1536 34.7 / 28.5 / 28.8, 2048 61.1 / 45.2 / 52: each 128 x 128
+// block pair converts two raw tiles per 512 MMA cycles, and above six blocks
+// that shared-memory traffic costs more than the decode pass (N = 704 takes
+// 9.09 ms in one pass, N = 720 9.99 ms in two).  0 disables it.
+#ifndef XENG_ONEPASS_MAX_N
+#define XENG_ONEPASS_MAX_N 768
+#endif
 
 
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
@@ -247,15 +260,16 @@ cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int
 
 // The tensor engines' single-pass kernels (decode fused into the correlation)
 // apply to this block: launches of at most kFusedMaxSamples samples over all
-// channels, no planes in HBM.  Up to 256 inputs both engines take them; above,
-// only XENG_ENGINE_TENSOR_FUSED (measured on GB300: full CHIME 50.8 ms single
-// pass against 44.8 ms for decode + correlation, so the two passes are the
-// default there).
+// channels, no planes in HBM.  Up to XENG_ONEPASS_MAX_N inputs both engines
+// take them; above, only XENG_ENGINE_TENSOR_FUSED (measured on GB300: full
+// CHIME 52 ms single pass against 44.3 ms for decode + correlation, so the two
+// passes are the default there).
 bool fused_ok(const xeng_s *h, const uint8_t *block)
 {
-    if (h->engine == XENG_ENGINE_TENSOR) return XENG_FUSED_SMALL && small_ok(block, h->N);
+    const bool onepass = h->N > 256 && h->N <= XENG_ONEPASS_MAX_N && onepass_ok(block, h->N);
+    if (h->engine == XENG_ENGINE_TENSOR) return (XENG_FUSED_SMALL && small_ok(block, h->N)) || onepass;
     if (h->engine == XENG_ENGINE_TENSOR_FUSED)
-        return (XENG_FUSED_SMALL && small_ok(block, h->N)) || correlate_raw_ok(block, h->N);
+        return (XENG_FUSED_SMALL && small_ok(block, h->N)) || onepass || correlate_raw_ok(block, h->N);
     return false;
 }
 
@@ -280,6 +294,9 @@ cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64
         return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->small_ws,
                                       h->small_flags, h->small_epoch, h->d_err, h->num_sms, s);
     }
+    if (h->N <= XENG_ONEPASS_MAX_N)
+        return launch_correlate_onepass(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err,
+                                        h->num_sms, s);
     if (!h->raw_sums) {  // the per-input sums of the largest launch: every channel of the handle
         cudaError_t e = cudaMalloc(&h->raw_sums, (size_t)h->F * h->N * sizeof(int2));
         if (e != cudaSuccess) {

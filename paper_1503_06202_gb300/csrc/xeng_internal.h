@@ -147,6 +147,15 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
                                    int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
                                    int epoch, int *err, int num_sms, cudaStream_t s);
 
+// One pass over the raw bytes for N a multiple of 16 up to 4096 (block 16-byte
+// aligned; used above 256 inputs): single CTAs over every channel's
+// upper-triangle pairs of 128-input blocks, the nibble split and each pair's
+// nibble sums in shared memory; nt <= kFusedMaxSamples, acc 8-byte aligned.
+bool onepass_ok(const uint8_t *block, int32_t N);
+cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
+                                     int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
+                                     int num_sms, cudaStream_t s);
+
 // Decode fused into the correlation for 256 < N <= 4096 (N % 16 == 0, block
 // 16-byte aligned), as launch_correlate_small: a pass forming every input's
 // nibble sums into `sums` (scratch of nf * N int2), then 2-CTA clusters over

@@ -94,8 +94,9 @@ def test_fused_items_split_over_many_ctas(N):
     assert np.array_equal(correlate(blk, pieces=[20000]), want)
 
 
-# ---- more than 256 inputs (fused engine): the raw bytes correlated by 2-CTA clusters
-# ---- over pairs of 256-input blocks (diagonal pairs, ragged last blocks, both CTAs' halves)
+# ---- more than 256 inputs: up to 768 (both tensor engines) single CTAs over pairs of
+# ---- 128-input blocks; above (fused engine) 2-CTA clusters over pairs of 256-input blocks
+# ---- (diagonal pairs, ragged last blocks, both CTAs' halves)
 
 FUSED = xe.XENG_ENGINE_TENSOR_FUSED
 
@@ -107,16 +108,17 @@ def test_fused_raw_shapes(T, F, N):
     assert np.array_equal(correlate(blk, engine=FUSED), oracle.correlate(blk)), (T, F, N)
 
 
-def test_fused_raw_several_launches_pieces_and_host_buffers():
-    # 70,000 samples = three launches of <= 32,768 adding into int32; pushes in pieces;
+@pytest.mark.parametrize("N,T", [(400, 70000), (784, 40000)])
+def test_fused_raw_several_launches_pieces_and_host_buffers(N, T):
+    # more than 32,768 samples = several launches adding into int32; pushes in pieces;
     # host buffers through the channel-group pipeline
-    rng = np.random.default_rng(15)
-    T, F, N = 70000, 2, 400
+    rng = np.random.default_rng(15 + N)
+    F = 2
     blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
     want = oracle.correlate(blk)
     assert np.array_equal(correlate(blk, engine=FUSED), want)
     assert np.array_equal(correlate(blk, pieces=[100, 32768, 3], engine=FUSED), want)
-    T2, F2 = 3000, 40
+    T2, F2 = 3000, 40 if N < 512 else 6
     blk2 = rng.integers(0, 256, size=(T2, F2, N), dtype=np.uint8)
     assert np.array_equal(correlate(blk2, host=True, engine=FUSED), oracle.correlate(blk2))
 
@@ -135,6 +137,27 @@ def test_fused_raw_many_channels_per_cluster_and_plane_engine_agree():
     eng.close()
     assert np.array_equal(got, out.cpu().numpy().astype(np.int64))
     assert np.array_equal(got[[0, 45, 89]], oracle.correlate(blk, f0=0, nf=F)[[0, 45, 89]])
+
+
+@pytest.mark.parametrize("N", [384, 704, 768])
+def test_onepass_many_items_per_cta_and_engines_agree(N):
+    # 300 channels of 6 or 21 block pairs: several items per CTA, both accumulators and
+    # both sums parities; the default engine (the same kernel) and the planes engine
+    # agree, and sampled channels match the oracle; stored, then added by a second push
+    rng = np.random.default_rng(N)
+    T, F = 160, 300
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    got = correlate(blk)
+    assert np.array_equal(correlate(blk, pieces=[70]), got)
+    d = torch.from_numpy(blk).cuda()
+    eng = xe.XEngine(N, F, T, xe.XENG_ENGINE_TENSOR_PLANES)
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    eng.correlate(d, out, T)
+    torch.cuda.synchronize()
+    eng.close()
+    assert np.array_equal(got, out.cpu().numpy().astype(np.int64))
+    pick = [0, 151, 299]
+    assert np.array_equal(got[pick], oracle.correlate(np.ascontiguousarray(blk[:, pick])))
 
 
 def test_fused_raw_int32_beyond_f32_range():

@@ -77,8 +77,11 @@ def test_decode_stage_codes(T, F, N, f0, nf):
 
 SHAPES = [(1, 1, 1), (5, 3, 2), (129, 2, 7), (300, 2, 127), (128, 1, 128), (257, 2, 129), (1000, 3, 200),
           (700, 2, 300), (1024, 1, 513), (64, 2, 1024),
-          # N > 256 and a multiple of 16: the TMA decode pipeline, ragged tiles
-          (1000, 3, 272), (129, 2, 400), (5, 2, 288)]
+          # N > 256 and a multiple of 16: the single pass over 128-input block pairs
+          # (default and fused engines) or the TMA decode pipeline (planes engine), ragged tiles
+          (1000, 3, 272), (129, 2, 400), (5, 2, 288),
+          # above 768 inputs: the TMA decode's raw planes (default engine), 256-input block pairs (fused)
+          (300, 2, 784)]
 
 
 @pytest.mark.parametrize("engine", sorted(ENGINES))
@@ -131,10 +134,12 @@ def test_exact_extremes_mix():
 RAW_LAUNCH = 32768
 
 
-# N = 256: the single-pass kernel of up to 256 inputs; N = 272: the TMA decode's
-# raw planes + tensor correlator (default engine) and the single-pass kernel of
-# 256-input block pairs (fused engine)
-RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR_FUSED)]
+# N = 256: the single-pass kernel of up to 256 inputs; N = 272: the single pass
+# over 128-input block pairs; N = 784: the TMA decode's raw planes + tensor
+# correlator (default engine) and the single pass over 256-input block pairs
+# (fused engine)
+RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR), (784, xe.XENG_ENGINE_TENSOR),
+             (784, xe.XENG_ENGINE_TENSOR_FUSED)]
 
 
 @pytest.mark.parametrize("N,engine", RAW_CASES)
