@@ -32,6 +32,8 @@ WORKLOADS = {
     "pathfinder_small": ("PATHFINDER_SMALL", "Pathfinder-shaped small: N=256, 8 channels, T=4096, uniform nibbles"),
     "chime_slice": ("CHIME_SLICE", "16 channels of the full-CHIME shape (N=2048, T=8192): profiling case"),
     "pathfinder_slice": ("PATHFINDER_SLICE", "64 channels of the Pathfinder shape (N=256, T=32768): profiling case"),
+    "mid_slice": ("MID_SLICE", "128 channels of N=512, T=8192, sky+noise: profiling case of the one pass over 128-input "
+                               "block pairs"),
     "batched": (None, "64 independent jobs, N in {64..2048}, F in {1,16,64}, T log-uniform 1024..32768, uniform nibbles"),
     "serving": (None, "8 concurrent streams (3 x N=256, 3 x N=512, 2 x N=2048), 256 channels each, 256-sample blocks, "
                       "Poisson arrivals at r x real time, dumps every 65536 samples"),
@@ -47,6 +49,7 @@ DRAM_BYTES_PER_CHANNEL = {
     ("correlate_tc", 2048, 8192): (658.302976e6 + 244.678912e6) / 16,   # raw-nibble planes, 16-channel slice
     ("correlate_raw", 2048, 8192): (307.412224e6 + 223.055104e6) / 16,  # fused engine, 16-channel slice
     ("correlate_small", 256, 32768): (822.840832e6 + 22.4192e6) / 64,   # N <= 256 kernel, 64-channel slice
+    ("correlate_onepass", 512, 8192): (543.91808e6 + 114.089728e6) / 128,  # one pass, 128-channel slice
 }
 
 
