@@ -118,8 +118,8 @@ struct SmallArgs {
     int32_t *acc;          // [nf][N(N+1)/2][2], channel f0 + fl at fl
     int accumulate;        // 0: store, 1: add
     int2 *ws;              // [grid][2][16][128][8] partial blocks of pieces that do not start their item
-    int *flags;            // [grid]: epoch once the CTA's partial is in ws
-    int epoch;             // this launch's flag value (distinct from every earlier launch's)
+    int *flags;            // [grid]: this launch's epoch once the CTA's partial is in ws
+    const int *epoch;      // launches so far on these flags: this launch's epoch is *epoch + 1
     int *err;
 };
 
@@ -211,6 +211,8 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = a.err;
     const int64_t lo = range_lo(a, (int)blockIdx.x), hi = range_lo(a, (int)blockIdx.x + 1);
+    // incremented by small_epoch_kernel after the launch, so every CTA reads the same value
+    const int epoch = *a.epoch + 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSRaws; s++) {
@@ -507,7 +509,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
             bool ok = mbar_wait_backoff(accf, uses & 1u, err, kDevTimeoutEpilogue, 128);
             ok = ok && mbar_wait_backoff(sums_full(par), (uint32_t)((local >> 1) & 1), err, kDevTimeoutEpilogue, 128);
             if (et == 0)
-                for (int b = c_lo; ok && b <= c_hi; b++) ok = flag_wait(a.flags + b, a.epoch, err, kDevTimeoutEpilogue);
+                for (int b = c_lo; ok && b <= c_hi; b++) ok = flag_wait(a.flags + b, epoch, err, kDevTimeoutEpilogue);
             // the barrier ORs the eight warps' failures, so they leave together
             if (bar_any(2, kSEpiWarps * 32, !ok)) break;
             ++uses;
@@ -578,7 +580,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
             // every epilogue thread is done with this parity's sums: clear them for
             // the piece after next, then hand TMEM and the buffer back
             named_bar_sync(2, kSEpiWarps * 32);
-            if (!owner && et == 0) st_release_gpu(a.flags + blockIdx.x, a.epoch);
+            if (!owner && et == 0) st_release_gpu(a.flags + blockIdx.x, epoch);
             sums[par * 256 + et] = make_int2(0, 0);
             fence_before();
             __syncwarp();
@@ -599,6 +601,14 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
     }
 }
 
+// One launch more on these flags (after each correlate_small_kernel, in stream
+// order, so a replayed graph gives every run a fresh epoch).
+__global__ void small_epoch_kernel(int *epoch)
+{
+    const int e = *epoch;
+    *epoch = e >= 0x7FFFFFFE ? 0 : e + 1;  // launch epochs e + 1 run 1 .. 2^31 - 1, never 0 (unset flags)
+}
+
 }  // namespace
 
 bool small_ok(const uint8_t *block, int32_t N)
@@ -607,10 +617,11 @@ bool small_ok(const uint8_t *block, int32_t N)
 }
 
 size_t small_ws_bytes(int num_sms) { return (size_t)num_sms * 2 * 16 * 128 * 8 * sizeof(int2); }
+size_t small_flags_bytes(int num_sms) { return (size_t)(num_sms + 1) * sizeof(int); }
 
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
                                    int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
-                                   int epoch, int *err, int num_sms, cudaStream_t s)
+                                   int *err, int num_sms, cudaStream_t s)
 {
     if (nf <= 0 || nt <= 0) return cudaSuccess;
     if (!small_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
@@ -650,7 +661,7 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
     a.accumulate = accumulate;
     a.ws = ws;
     a.flags = flags;
-    a.epoch = epoch;
+    a.epoch = flags + num_sms;
     a.err = err;
     // every CTA gets at least kSMinPiece stages (a piece's epilogue and partial
     // cost about as much as a few stages of MMAs), at most one CTA per SM
@@ -669,7 +680,10 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, correlate_small_kernel, map, a);
+    e = cudaLaunchKernelEx(&cfg, correlate_small_kernel, map, a);
+    if (e != cudaSuccess) return e;
+    small_epoch_kernel<<<1, 1, 0, s>>>(flags + num_sms);
+    return cudaGetLastError();
 }
 
 }  // namespace xeng

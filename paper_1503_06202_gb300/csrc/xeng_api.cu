@@ -34,8 +34,7 @@ struct xeng_s {
     int2 *sums = nullptr;          // raw-nibble planes: (S, D) per input [group_f][n_pad]
     int2 *raw_sums = nullptr;      // single-pass kernel above 256 inputs: (S, D) per input [F][N]
     int2 *small_ws = nullptr;      // single-pass kernel up to 256 inputs: partial blocks of split items
-    int *small_flags = nullptr;    // and the flags that publish them (num_sms ints)
-    int small_epoch = 0;           // its launches so far
+    int *small_flags = nullptr;    // and the flags that publish them, with the launch count
     bool planes_raw = false;       // the last decode wrote raw-nibble planes
     int32_t group_f = 0;           // channels per decode + correlate round
     int64_t chunk_t = 0;           // samples per round
@@ -279,8 +278,8 @@ cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64
     if (h->N <= 256) {
         if (!h->small_ws) {
             cudaError_t e = cudaMalloc(&h->small_ws, small_ws_bytes(h->num_sms));
-            if (e == cudaSuccess) e = cudaMalloc(&h->small_flags, (size_t)h->num_sms * sizeof(int));
-            if (e == cudaSuccess) e = cudaMemsetAsync(h->small_flags, 0, (size_t)h->num_sms * sizeof(int), s);
+            if (e == cudaSuccess) e = cudaMalloc(&h->small_flags, small_flags_bytes(h->num_sms));
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->small_flags, 0, small_flags_bytes(h->num_sms), s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 cudaFree(h->small_ws);
@@ -290,9 +289,8 @@ cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64
                 return e;
             }
         }
-        if (++h->small_epoch <= 0) h->small_epoch = 1;  // flags start at 0: never an epoch
         return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->small_ws,
-                                      h->small_flags, h->small_epoch, h->d_err, h->num_sms, s);
+                                      h->small_flags, h->d_err, h->num_sms, s);
     }
     if (h->N <= XENG_ONEPASS_MAX_N)
         return launch_correlate_onepass(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err,

@@ -139,13 +139,15 @@ cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, 
 // Single CTAs over upper-triangle 128 x 128 blocks only (three per channel of
 // 129..256 inputs).  The launch's work is split evenly over the CTAs; an item
 // cut between CTAs is completed through ws (scratch of small_ws_bytes(num_sms))
-// and flags (num_sms ints, zeroed once), with `epoch` different from every
-// earlier launch's on the same flags.
+// and flags (small_flags_bytes(num_sms), zeroed once: a flag per CTA and the
+// count of launches on them, which a one-thread kernel after each launch
+// advances, so replays of a captured launch stay apart).
 bool small_ok(const uint8_t *block, int32_t N);
 size_t small_ws_bytes(int num_sms);
+size_t small_flags_bytes(int num_sms);
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
                                    int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
-                                   int epoch, int *err, int num_sms, cudaStream_t s);
+                                   int *err, int num_sms, cudaStream_t s);
 
 // One pass over the raw bytes for N a multiple of 16 up to 4096 (block 16-byte
 // aligned; used above 256 inputs): single CTAs over every channel's

@@ -94,6 +94,31 @@ def test_fused_items_split_over_many_ctas(N):
     assert np.array_equal(correlate(blk, pieces=[20000]), want)
 
 
+def test_fused_graph_replays_stay_exact():
+    # one captured call replayed: the flags that publish split items' partial
+    # blocks carry a count the device advances after every launch, so no replay
+    # takes another's flags for its own
+    rng = np.random.default_rng(77)
+    T, F, N = 640, 300, 256  # 450 items over the CTAs, several cut between CTAs
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    want = oracle.correlate(blk)
+    d = torch.from_numpy(blk).cuda()
+    eng = xe.XEngine(N, F, T)
+    out = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    eng.correlate(d, out, T)  # the kernel's scratch is allocated here, outside the capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        eng.correlate(d, out, T, s)
+    for _ in range(4):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), want)
+    eng.close()
+
+
 # ---- more than 256 inputs: up to 768 (both tensor engines) single CTAs over pairs of
 # ---- 128-input blocks; above (fused engine) 2-CTA clusters over pairs of 256-input blocks
 # ---- (diagonal pairs, ragged last blocks, both CTAs' halves)
