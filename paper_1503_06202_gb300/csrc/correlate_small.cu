@@ -119,7 +119,8 @@ struct SmallArgs {
     int accumulate;        // 0: store, 1: add
     int2 *ws;              // [grid][2][16][128][8] partial blocks of pieces that do not start their item
     int *flags;            // [grid]: this launch's epoch once the CTA's partial is in ws
-    const int *epoch;      // launches so far on these flags: this launch's epoch is *epoch + 1
+    int *epoch;            // [0]: launches so far on these flags (this launch's epoch is [0] + 1);
+                           // [1]: CTAs of this launch finished
     int *err;
 };
 
@@ -183,6 +184,10 @@ __device__ __forceinline__ SmallItem small_item(const SmallArgs &a, int it)
     return w;
 }
 
+// kAdd: add into acc (a.accumulate != 0) instead of storing; a template so that
+// each launch carries only its own triangle-store path (the adding one needs
+// more registers).
+template <bool kAdd>
 __global__ void __launch_bounds__(kSThreads, 1)
 correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallArgs a)
 {
@@ -207,12 +212,13 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
     auto sums_full = [&](int par) { return accf + 24u + 8u * par; };
     auto sums_empty = [&](int par) { return accf + 40u + 8u * par; };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + (bars + 8u * kSBars - raw));
+    // this launch's flag value, read once at the start: the last CTA of the launch
+    // to finish advances the count (at the end), after every CTA has read it here
+    int *s_epoch = reinterpret_cast<int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = a.err;
     const int64_t lo = range_lo(a, (int)blockIdx.x), hi = range_lo(a, (int)blockIdx.x + 1);
-    // incremented by small_epoch_kernel after the launch, so every CTA reads the same value
-    const int epoch = *a.epoch + 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSRaws; s++) {
@@ -232,6 +238,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&raw_map) : "memory");
+        *s_epoch = *(volatile int *)a.epoch + 1;
     }
     for (int k = threadIdx.x; k < 2 * 256; k += kSThreads) sums[k] = make_int2(0, 0);
     if (warp == 1) {
@@ -509,7 +516,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
             bool ok = mbar_wait_backoff(accf, uses & 1u, err, kDevTimeoutEpilogue, 128);
             ok = ok && mbar_wait_backoff(sums_full(par), (uint32_t)((local >> 1) & 1), err, kDevTimeoutEpilogue, 128);
             if (et == 0)
-                for (int b = c_lo; ok && b <= c_hi; b++) ok = flag_wait(a.flags + b, epoch, err, kDevTimeoutEpilogue);
+                for (int b = c_lo; ok && b <= c_hi; b++) ok = flag_wait(a.flags + b, *s_epoch, err, kDevTimeoutEpilogue);
             // the barrier ORs the eight warps' failures, so they leave together
             if (bar_any(2, kSEpiWarps * 32, !ok)) break;
             ++uses;
@@ -572,15 +579,14 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                             vim[e + 1] += (uint32_t)v.w;
                         }
                     }
-                    if (a.accumulate) put8<true>(out + row_base + j0, i - j0, N - j0, vre, vim);
-                    else put8<false>(out + row_base + j0, i - j0, N - j0, vre, vim);
+                    put8<kAdd>(out + row_base + j0, i - j0, N - j0, vre, vim);
                 }
             }
             if (!owner) __threadfence();  // the partial is visible at GPU scope before the flag below
             // every epilogue thread is done with this parity's sums: clear them for
             // the piece after next, then hand TMEM and the buffer back
             named_bar_sync(2, kSEpiWarps * 32);
-            if (!owner && et == 0) st_release_gpu(a.flags + blockIdx.x, epoch);
+            if (!owner && et == 0) st_release_gpu(a.flags + blockIdx.x, *s_epoch);
             sums[par * 256 + et] = make_int2(0, 0);
             fence_before();
             __syncwarp();
@@ -599,14 +605,19 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSTmemCols));
     }
-}
-
-// One launch more on these flags (after each correlate_small_kernel, in stream
-// order, so a replayed graph gives every run a fresh epoch).
-__global__ void small_epoch_kernel(int *epoch)
-{
-    const int e = *epoch;
-    *epoch = e >= 0x7FFFFFFE ? 0 : e + 1;  // launch epochs e + 1 run 1 .. 2^31 - 1, never 0 (unset flags)
+    // One launch more on these flags: the last CTA to get here (every CTA read the
+    // epoch when it started, before getting here) advances the count and resets
+    // the arrivals, so the next launch -- or the next replay of a captured one --
+    // takes a fresh epoch.  Epochs run 1 .. 2^31 - 1, never 0 (an unset flag).
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.epoch + 1, 1) == (int)gridDim.x - 1) {
+            const int e = *(volatile int *)a.epoch;
+            a.epoch[1] = 0;
+            a.epoch[0] = e >= 0x7FFFFFFE ? 0 : e + 1;
+            __threadfence();
+        }
+    }
 }
 
 }  // namespace
@@ -617,7 +628,7 @@ bool small_ok(const uint8_t *block, int32_t N)
 }
 
 size_t small_ws_bytes(int num_sms) { return (size_t)num_sms * 2 * 16 * 128 * 8 * sizeof(int2); }
-size_t small_flags_bytes(int num_sms) { return (size_t)(num_sms + 1) * sizeof(int); }
+size_t small_flags_bytes(int num_sms) { return (size_t)(num_sms + 2) * sizeof(int); }
 
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
                                    int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
@@ -644,8 +655,8 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    cudaError_t e =
-        cudaFuncSetAttribute(correlate_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSSmem);
+    auto kern = accumulate ? correlate_small_kernel<true> : correlate_small_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSSmem);
     if (e != cudaSuccess) return e;
     SmallArgs a;
     a.t0 = t0;
@@ -680,10 +691,7 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, correlate_small_kernel, map, a);
-    if (e != cudaSuccess) return e;
-    small_epoch_kernel<<<1, 1, 0, s>>>(flags + num_sms);
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, kern, map, a);
 }
 
 }  // namespace xeng

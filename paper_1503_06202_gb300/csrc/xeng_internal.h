@@ -139,9 +139,9 @@ cudaError_t launch_shift_history(const uint8_t *hist_old, const uint8_t *block, 
 // Single CTAs over upper-triangle 128 x 128 blocks only (three per channel of
 // 129..256 inputs).  The launch's work is split evenly over the CTAs; an item
 // cut between CTAs is completed through ws (scratch of small_ws_bytes(num_sms))
-// and flags (small_flags_bytes(num_sms), zeroed once: a flag per CTA and the
-// count of launches on them, which a one-thread kernel after each launch
-// advances, so replays of a captured launch stay apart).
+// and flags (small_flags_bytes(num_sms), zeroed once: a flag per CTA, the
+// count of launches on them and an arrival counter, with which the last CTA of
+// each launch advances the count, so replays of a captured launch stay apart).
 bool small_ok(const uint8_t *block, int32_t N);
 size_t small_ws_bytes(int num_sms);
 size_t small_flags_bytes(int num_sms);
