@@ -34,10 +34,11 @@
 // (inputs along M or N, samples along K).  The converter warps split each byte
 // at its own offset into the Re plane (high nibble) and the Im plane (low
 // nibble) of a plane stage; the raw slots form their own ring, so the TMA runs
-// up to five stages ahead of the conversion.  The
-// MMAs of a stage (both operands MN-major; B of a row item spans the X and Y
-// tiles, the leading byte offset stepping from one to the other):
-//     Re += A_re B_re^T + A_im B_im^T,   Im += A_im B_re^T + (-A_re) B_im^T.
+// up to five stages ahead of the conversion.  The MMAs of a row item's stage
+// (both operands MN-major; B spans the X and Y tiles, the leading byte offset
+// stepping from one to the other):
+//     Re += A_re B_re^T + A_im B_im^T,   Im += A_im B_re^T + (-A_re) B_im^T;
+// a diagonal item's tile against itself: [B_im | B_re] as one N = 256 operand.
 //
 // The planes hold raw nibbles: a byte whose low four bits are u (0..15) and
 // whose high four bits are clear is the FP8 E4M3 code of u / 512 (the
@@ -48,9 +49,10 @@
 //     Im V_ij = sum(q_i p_j - p_i q_j) + 8 (D_i - D_j),
 // with S = P + Q, D = P - Q and P, Q the sums of an input's nibbles, which the
 // converters form as they split (byte lanes, widened to 16-bit lanes every
-// four stages, totalled per item in shared memory).  The MMA sums are integers
-// / 2^18 of at most 450 n; launches of at most 32,768 samples keep them below
-// 2^24, exact in f32.
+// four stages, totalled per piece in shared memory); a piece of an item is
+// corrected with its own n and sums, and the pieces' results add up to the
+// item's.  The MMA sums are integers / 2^18 of at most 450 n; launches of at
+// most 32,768 samples keep them below 2^24, exact in f32.
 //
 // Roles (576 threads):
 //   warp 0       TMA producer: raw tiles into the raw ring
