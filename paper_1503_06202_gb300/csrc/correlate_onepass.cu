@@ -1,9 +1,14 @@
-// correlate_onepass.cu -- the X-engine step for more than 256 inputs in one
-// pass over the raw bytes: the nibble split (paper Sec. II-A) fused into the
-// Hermitian correlation (Sec. IV-C-1, Eq. 1), with no decoded planes in HBM.
+// correlate_onepass.cu -- the X-engine step in one pass over the raw bytes
+// (used for 257..768 inputs): the nibble split (paper Sec. II-A) fused into
+// the Hermitian correlation (Sec. IV-C-1, Eq. 1), with no decoded planes in
+// HBM.
 //
 // A separate decode writes two plane bytes per input byte to HBM and the
-// correlation reads them back.  Here each CTA (one per SM, cta_group::1)
+// correlation reads them back.  Converting in shared memory instead costs
+// shared-memory bandwidth: each 128 x 128 block pair converts two raw tiles
+// per 512 MMA cycles, so this kernel runs at about half the MMA rate -- ahead
+// of the two passes while the decode is a large share of the step (up to 768
+// inputs), behind them above.  Here each CTA (one per SM, cta_group::1)
 // takes upper-triangle tile pairs (I <= J) of 128-input blocks of a channel,
 // channel-major and round-robin over the CTAs, so the CTAs at work at any time
 // share one or two channels' raw bytes in L2.  Per stage of 64 samples the
