@@ -4,11 +4,11 @@
 // HBM.
 //
 // A separate decode writes two plane bytes per input byte to HBM and the
-// correlation reads them back.  Converting in shared memory instead costs
-// shared-memory bandwidth: each 128 x 128 block pair converts two raw tiles
-// per 512 MMA cycles, so this kernel runs at about half the MMA rate -- ahead
-// of the two passes while the decode is a large share of the step (up to 768
-// inputs), behind them above.  Here each CTA (one per SM, cta_group::1)
+// correlation reads them back.  Converting in shared memory instead takes the
+// converter warps' time: each 128 x 128 block pair converts two raw tiles per
+// 512 MMA cycles, about what eight converter warps manage, so this kernel runs
+// at about half the MMA rate -- ahead of the two passes while the decode is a
+// large share of the step (up to 768 inputs), behind them above.  Here each CTA (one per SM, cta_group::1)
 // takes upper-triangle tile pairs (I <= J) of 128-input blocks of a channel,
 // channel-major and round-robin over the CTAs, so the CTAs at work at any time
 // share one or two channels' raw bytes in L2.  Per stage of 64 samples the
