@@ -59,7 +59,7 @@ def correlate_kernel(engine, N):
     items included)."""
     if engine in ("tensor", "fused") and N % 16 == 0 and N <= 256:
         return "correlate_small_kernel (decode fused; upper-triangle 128-input blocks, one CTA each)", 128
-    if engine in ("tensor", "fused") and N % 16 == 0 and N <= 768:
+    if engine in ("tensor", "fused") and N % 16 == 0 and N <= 1024:
         return "correlate_onepass_kernel (decode fused; 128-input block pairs, one CTA each)", 128
     if engine == "fused" and N % 16 == 0:
         return "correlate_raw_kernel (raw bytes split in shared memory; 256-input block pairs)", 256

@@ -64,7 +64,7 @@ extern "C" {
 #define XENG_MAX_T_INTEG  16777215LL
 
 /* Correlation engines (all give identical bits). */
-#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 768 (a multiple of 16, block
+#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 1024 (a multiple of 16, block
                                         16-byte aligned) one kernel splits the raw bytes in shared memory and
                                         correlates them (N <= 256: scratch of 256 KB per SM, allocated at
                                         the first such call); otherwise as XENG_ENGINE_TENSOR_PLANES         */

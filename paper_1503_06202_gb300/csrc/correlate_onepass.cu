@@ -46,21 +46,41 @@
 namespace xeng {
 namespace {
 
-constexpr int kOKc = 64;                    // samples per stage
+// Samples per stage (a build parameter: 32, 64 or 128); the rings hold 208 KB
+// (32, 64) or 192 KB (128) of stages.  Each stage carries a fixed cost in the
+// pipeline: measured on GB300 (N = 512 / 2048, F = 1024, T = 8192) 32 samples
+// 5.87 / 81.9 ms, 64 4.32 / 61.0, 128 3.66 / 58.8.
+#ifndef XENG_ONEPASS_KC
+#define XENG_ONEPASS_KC 128
+#endif
+constexpr int kOKc = XENG_ONEPASS_KC;       // samples per stage
+static_assert(kOKc == 32 || kOKc == 64 || kOKc == 128, "32, 64 or 128 samples per stage");
 constexpr int kOBox = kOKc * 128;           // one raw tile or plane tile: 64 samples x 128 inputs
 constexpr int kORawBytes = 2 * kOBox;       // raw slot: blocks I and J
 constexpr int kOPlaneBytes = 4 * kOBox;     // plane stage: A_im, A_re, B_im, B_re
 // Ring depths (build parameters; 4 x 32 KB + 5 x 16 KB fill the shared memory).
 #ifndef XENG_ONEPASS_PLANE_STAGES
-#define XENG_ONEPASS_PLANE_STAGES 4
+#define XENG_ONEPASS_PLANE_STAGES (4 * 64 / XENG_ONEPASS_KC)
 #endif
 #ifndef XENG_ONEPASS_RAW_SLOTS
-#define XENG_ONEPASS_RAW_SLOTS 5
+#define XENG_ONEPASS_RAW_SLOTS (XENG_ONEPASS_KC == 128 ? 2 : 5 * 64 / XENG_ONEPASS_KC)
 #endif
 constexpr int kOPlanes = XENG_ONEPASS_PLANE_STAGES, kORaws = XENG_ONEPASS_RAW_SLOTS;
-constexpr int kOConvWarp0 = 2, kOConvWarps = 8;
-constexpr int kOEpiWarp0 = kOConvWarp0 + kOConvWarps, kOEpiWarps = 8;
+// Converter and epilogue warps (build parameters): the converters' throughput
+// bounds the kernel, the epilogue overlaps the next pair's MMAs.
+#ifndef XENG_ONEPASS_CONV_WARPS
+#define XENG_ONEPASS_CONV_WARPS 8
+#endif
+#ifndef XENG_ONEPASS_EPI_WARPS
+#define XENG_ONEPASS_EPI_WARPS 8
+#endif
+constexpr int kOConvWarp0 = 2, kOConvWarps = XENG_ONEPASS_CONV_WARPS;
+constexpr int kOEpiWarp0 = kOConvWarp0 + kOConvWarps, kOEpiWarps = XENG_ONEPASS_EPI_WARPS;
 constexpr int kOThreads = 32 * (kOEpiWarp0 + kOEpiWarps);
+constexpr int kOCT = 16 * kOConvWarps;        // converter threads per tile
+constexpr int kOChunks = kOBox / 16 / kOCT;   // 16-byte chunks of a tile per converter thread and stage
+static_assert(kOConvWarps == 8 || kOConvWarps == 16, "8 or 16 converter warps");
+static_assert(kOEpiWarps == 4 || kOEpiWarps == 8, "4 or 8 epilogue warps");
 constexpr uint32_t kOTmemCols = 512;
 constexpr int kOSums = 2 * 256 * 8;  // per item parity: (P, Q) of block I's inputs, then block J's
 // barriers: raw full and empty per slot, plane full and empty per stage; acc full
@@ -69,7 +89,8 @@ constexpr int kOBars = 2 * kORaws + 2 * kOPlanes + 4 + 1 + 4;
 constexpr size_t kOSmem =
     1024 + (size_t)kOPlanes * kOPlaneBytes + (size_t)kORaws * kORawBytes + kOSums + kOBars * 8 + 16;
 static_assert(kOSmem <= 232448, "shared memory over the per-CTA limit");
-static_assert(kOConvWarps * 32 == 2 * kOBox / 16 / 4, "each converter thread splits four 16-byte chunks per stage");
+static_assert(kOChunks * kOCT * 16 == kOBox, "the converter threads cover a tile");
+constexpr int kOWiden = 16 / kOChunks;        // stages between widenings of the byte-lane sums (<= 240)
 
 // Instruction descriptor, kind::f8f6f4: D f32, A and B E4M3, both MN-major
 // (bits 15, 16), N = n, M = 128; bit 13 negates A.
@@ -266,17 +287,18 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
         }
     } else if (warp < kOEpiWarp0) {
         // ---------------- converters ----------------
-        // Thread u (0..255) takes tile g = u / 128 (block I, then J) and, in it,
-        // the 16-byte chunks v + 128 k (v = u % 128, k = 0..3): sample rows
-        // v / 8 + 16 k, physical chunk v % 8 -- a quarter-warp covers one whole
-        // 128-byte row, so the accesses are bank-conflict-free.  The rows'
-        // swizzle (chunk ^ row % 8) is the same for all four rows, so the thread
-        // always holds the same 16 inputs: logical chunk lc = (v % 8) ^ (v / 8 % 8).
+        // Thread u takes tile g = u / kOCT (block I, then J) and, in it, the
+        // 16-byte chunks v + kOCT k (v = u % kOCT, k < kOChunks): sample rows
+        // v / 8 + kOCT / 8 k, physical chunk v % 8 -- a quarter-warp covers one
+        // whole 128-byte row, so the accesses are bank-conflict-free.  The rows'
+        // swizzle (chunk ^ row % 8) is the same for all of them (kOCT / 8 is a
+        // multiple of 8), so the thread always holds the same 16 inputs: logical
+        // chunk lc = (v % 8) ^ (v / 8 % 8).
         const int u = (warp - kOConvWarp0) * 32 + lane;
-        const int g = u >> 7, v = u & 127;
+        const int g = u / kOCT, v = u % kOCT;
         const int r0 = v >> 3, lc = (v & 7) ^ (r0 & 7);
-        const uint32_t roff = (uint32_t)(g * kOBox + v * 16);      // in a raw slot (+ 2048 k)
-        const uint32_t poff = (uint32_t)(2 * g * kOBox + v * 16);  // Im plane of the tile (+ 2048 k; Re 8 KB on)
+        const uint32_t roff = (uint32_t)(g * kOBox + v * 16);      // in a raw slot (+ 16 kOCT k)
+        const uint32_t poff = (uint32_t)(2 * g * kOBox + v * 16);  // Im plane of the tile (+ 16 kOCT k; Re 8 KB on)
         const int nt = (int)a.nt;                                  // <= kFusedMaxSamples
         int rs = 0, ps = 0, local = 0;
         uint32_t rph = 0, pph = 0;
@@ -306,11 +328,11 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                 }
                 const int rows_left = nt - kc * kOKc;  // samples of this stage inside the launch (may exceed kOKc)
                 const uint8_t *src = sgen + (slot(rs) - sbase) + roff;
-                uint4 x[4];
+                uint4 x[kOChunks];
                 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    x[k] = active ? *reinterpret_cast<const uint4 *>(src + 2048 * k) : make_uint4(0, 0, 0, 0);
-                    if (r0 + 16 * k >= rows_left) x[k] = make_uint4(0, 0, 0, 0);  // past the launch: adds nothing
+                for (int k = 0; k < kOChunks; k++) {
+                    x[k] = active ? *reinterpret_cast<const uint4 *>(src + 16 * kOCT * k) : make_uint4(0, 0, 0, 0);
+                    if (r0 + kOCT / 8 * k >= rows_left) x[k] = make_uint4(0, 0, 0, 0);  // past the launch: adds nothing
                 }
                 // The raw slot goes back to the producer with the plane stage below,
                 // once the plane stores (which consume the loaded words) are done.
@@ -328,7 +350,7 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                     uint8_t *dim = sgen + (plane(ps) - sbase) + poff;  // Im plane of the tile
                     uint8_t *dre = dim + kOBox;                        // Re plane of the tile
                     #pragma unroll
-                    for (int k = 0; k < 4; k++) {
+                    for (int k = 0; k < kOChunks; k++) {
                         uint4 re, im;
                         re.x = (x[k].x >> 4) & 0x0F0F0F0Fu;
                         re.y = (x[k].y >> 4) & 0x0F0F0F0Fu;
@@ -338,8 +360,8 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                         im.y = x[k].y & 0x0F0F0F0Fu;
                         im.z = x[k].z & 0x0F0F0F0Fu;
                         im.w = x[k].w & 0x0F0F0F0Fu;
-                        *reinterpret_cast<uint4 *>(dre + 2048 * k) = re;
-                        *reinterpret_cast<uint4 *>(dim + 2048 * k) = im;
+                        *reinterpret_cast<uint4 *>(dre + 16 * kOCT * k) = re;
+                        *reinterpret_cast<uint4 *>(dim + 16 * kOCT * k) = im;
                         pb[0] += re.x; pb[1] += re.y; pb[2] += re.z; pb[3] += re.w;
                         qb[0] += im.x; qb[1] += im.y; qb[2] += im.z; qb[3] += im.w;
                     }
@@ -354,7 +376,7 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                     ps = 0;
                     pph ^= 1u;
                 }
-                if ((kc & 3) == 3) widen();
+                if ((kc + 1) % kOWiden == 0) widen();
             }
             if (!ok) break;
             widen();
@@ -398,7 +420,8 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
     } else {
         // ---------------- epilogue ----------------
         const int q = warp & 3;                          // TMEM lane quadrant this warp may access
-        const int half = (warp - kOEpiWarp0) >> 2;       // columns 64 half .. 64 half + 63 of the tile
+        constexpr int kCols = 128 / (kOEpiWarps / 4);     // columns per epilogue warp
+        const int half = (warp - kOEpiWarp0) >> 2;       // columns kCols half .. of the tile
         const int et = (warp - kOEpiWarp0) * 32 + lane;
         const int row = q * 32 + lane;                   // TMEM lane: row within the tile
         const int N = a.N;                               // <= 4096: triangle offsets within a channel fit in int
@@ -425,7 +448,7 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                 const int row_base = i * N - i * (i - 1) / 2 - i;  // pair (i, j) at row_base + j
                 int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)w.fl * nb2;
                 const uint32_t tb = taddr + 256u * ab;
-                for (int c = 64 * half; c < 64 * half + 64; c += 8) {
+                for (int c = kCols * half; c < kCols * half + kCols; c += 8) {
                     const int j0 = w.J * 128 + c;
                     // warp-uniform skips: chunks past the last input or below every row's diagonal
                     if (j0 >= N) break;
@@ -452,7 +475,7 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
             // with this parity's sums: clear them for the item after next
             fence_before();
             named_bar_sync(2, kOEpiWarps * 32);
-            sums[par * 256 + et] = make_int2(0, 0);
+            for (int k = et; k < 256; k += kOEpiWarps * 32) sums[par * 256 + k] = make_int2(0, 0);
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(acce(ab));

@@ -15,10 +15,10 @@
 //                                 two N = 128 MMAs per product pair)
 // Up to 128 inputs a channel is one diagonal block, and every item is a
 // diagonal item over two channels' inputs 0..127.  Per stage an item reads two
-// raw tiles of 128 inputs x 64 samples ("X" and "Y": the channel's two input
+// raw tiles of 128 inputs x 128 samples ("X" and "Y": the channel's two input
 // halves, or the two channels' upper halves).
 //
-// The launch's work -- its items in order, each of n_k stages of 64 samples --
+// The launch's work -- its items in order, each of n_k stages of 128 samples --
 // is split evenly over the CTAs: CTA b takes stages [b T / G, (b + 1) T / G)
 // of that sequence (T stages in all, G CTAs), so every CTA does the same
 // number of MMAs whether or not the items divide evenly.  An item cut between
@@ -34,7 +34,7 @@
 // (inputs along M or N, samples along K).  The converter warps split each byte
 // at its own offset into the Re plane (high nibble) and the Im plane (low
 // nibble) of a plane stage; the raw slots form their own ring, so the TMA runs
-// up to five stages ahead of the conversion.  The MMAs of a row item's stage
+// ahead of the conversion.  The MMAs of a row item's stage
 // (both operands MN-major; B spans the X and Y tiles, the leading byte offset
 // stepping from one to the other):
 //     Re += A_re B_re^T + A_im B_im^T,   Im += A_im B_re^T + (-A_re) B_im^T;
@@ -67,16 +67,25 @@
 namespace xeng {
 namespace {
 
-constexpr int kSKc = 64;                    // samples per stage
-constexpr int kSBox = kSKc * 128;           // one raw tile or plane tile: 64 samples x 128 inputs
+// Samples per stage (a build parameter, 64 or 128): every stage carries a fixed
+// cost in the pipeline (barrier round trips, a commit, the converters' fence),
+// so fewer, larger stages run faster although the rings then hold two plane
+// stages instead of four (measured on GB300, full Pathfinder rate: 64 samples
+// 3.17 ms, 128 samples 2.99 ms).  The rings hold 208 KB (64) or 192 KB (128).
+#ifndef XENG_SMALL_KC
+#define XENG_SMALL_KC 128
+#endif
+constexpr int kSKc = XENG_SMALL_KC;         // samples per stage
+static_assert(kSKc == 64 || kSKc == 128, "64 or 128 samples per stage");
+constexpr int kSBox = kSKc * 128;           // one raw tile or plane tile: kSKc samples x 128 inputs
 constexpr int kSRawBytes = 2 * kSBox;       // raw slot: tiles X and Y
 constexpr int kSPlaneBytes = 4 * kSBox;     // plane stage: Im_X, Im_Y, Re_X, Re_Y
 // Ring depths (build parameters; 4 x 32 KB + 5 x 16 KB fill the shared memory).
 #ifndef XENG_SMALL_PLANE_STAGES
-#define XENG_SMALL_PLANE_STAGES 4
+#define XENG_SMALL_PLANE_STAGES (4 * 64 / XENG_SMALL_KC)
 #endif
 #ifndef XENG_SMALL_RAW_SLOTS
-#define XENG_SMALL_RAW_SLOTS 5
+#define XENG_SMALL_RAW_SLOTS (XENG_SMALL_KC == 128 ? 2 : 5)
 #endif
 constexpr int kSPlanes = XENG_SMALL_PLANE_STAGES, kSRaws = XENG_SMALL_RAW_SLOTS;
 
@@ -92,7 +101,9 @@ constexpr size_t kSSmem =
     1024 + (size_t)kSPlanes * kSPlaneBytes + (size_t)kSRaws * kSRawBytes + kSSums + kSBars * 8 + 16;
 static_assert(kSSmem <= 232448, "shared memory over the per-CTA limit");
 constexpr int kSMinPiece = 32;  // stages per CTA at least (the grid shrinks for small launches)
-static_assert(kSConvWarps * 32 == 2 * kSBox / 16 / 4, "each converter thread splits four 16-byte chunks per stage");
+constexpr int kSChunks = 2 * kSBox / 16 / (32 * kSConvWarps);  // 16-byte chunks per converter thread and stage
+static_assert(kSChunks * 32 * kSConvWarps * 16 == 2 * kSBox, "the converter threads cover both tiles");
+constexpr int kSWiden = 16 / kSChunks;  // stages between widenings of the byte-lane sums (<= 240)
 
 // Instruction descriptor, kind::f8f6f4: D f32, A and B E4M3, both MN-major
 // (bits 15, 16), N = n, M = 128; bit 13 negates A.
@@ -359,10 +370,10 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
     } else if (warp < kSEpiWarp0) {
         // ---------------- converters ----------------
         // Thread u (0..255) takes tile g = u / 128 and, in it, the 16-byte chunks
-        // v + 128 k (v = u % 128, k = 0..3): sample rows v / 8 + 16 k, physical
-        // chunk v % 8 -- a quarter-warp covers one whole 128-byte row, so the
-        // accesses are bank-conflict-free.  The rows' swizzle (chunk ^ row % 8)
-        // is the same for all four rows, so the thread always holds the same 16
+        // v + 128 k (v = u % 128, k < kSChunks): sample rows v / 8 + 16 k,
+        // physical chunk v % 8 -- a quarter-warp covers one whole 128-byte row, so
+        // the accesses are bank-conflict-free.  The rows' swizzle (chunk ^ row % 8)
+        // is the same for all of them, so the thread always holds the same 16
         // inputs: logical chunk lc = (v % 8) ^ (v / 8 % 8).
         const int u = (warp - kSConvWarp0) * 32 + lane;
         const int g = u >> 7, v = u & 127;
@@ -375,8 +386,8 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
         int64_t x = lo;
         Piece pc;
         for (; ok && next_piece(a, x, hi, pc); ++local) {
-            // nibble sums of the thread's 16 inputs: byte lanes over up to four
-            // stages (16 samples, <= 240), then 16-bit lanes (<= 15 x 2048 samples)
+            // nibble sums of the thread's 16 inputs: byte lanes over up to 16
+            // samples (<= 240), then 16-bit lanes (<= 15 x 2048 samples)
             uint32_t pb[4] = {0, 0, 0, 0}, qb[4] = {0, 0, 0, 0};
             uint32_t P16[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Q16[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             auto widen = [&]() {
@@ -397,9 +408,9 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                 }
                 const int rows_left = nt - kc * kSKc;  // samples of this stage inside the launch (may exceed kSKc)
                 const uint8_t *src = sgen + (slot(rs) - sbase) + off0;
-                uint4 x[4];
+                uint4 x[kSChunks];
                 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < kSChunks; k++) {
                     x[k] = *reinterpret_cast<const uint4 *>(src + 2048 * k);
                     if (r0 + 16 * k >= rows_left) x[k] = make_uint4(0, 0, 0, 0);  // past the launch: adds nothing
                 }
@@ -423,7 +434,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                 uint8_t *dim = sgen + (plane(ps) - sbase) + off0;  // Im_X / Im_Y
                 uint8_t *dre = dim + 2 * kSBox;                    // Re_X / Re_Y
                 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < kSChunks; k++) {
                     uint4 re, im;
                     re.x = (x[k].x >> 4) & 0x0F0F0F0Fu;
                     re.y = (x[k].y >> 4) & 0x0F0F0F0Fu;
@@ -448,7 +459,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     ps = 0;
                     pph ^= 1u;
                 }
-                if (((kc - pc.k0) & 3) == 3) widen();
+                if ((kc - pc.k0 + 1) % kSWiden == 0) widen();
             }
             if (!ok) break;
             widen();

@@ -189,14 +189,13 @@ cudaEvent_t take_event(xeng_s *h)
 // block pairs (correlate_onepass.cu) is the tensor engines' path; above it the
 // default engine decodes to planes first and the fused engine runs 2-CTA
 // clusters over 256-input block pairs (correlate_raw.cu).  Measured on GB300,
-// F = 1024, T = 8192, ms (one pass / two passes / 2-CTA pass): N = 384 2.64 /
-// 3.50 / 4.56, 512 4.32 / 5.09 / 5.05, 768 9.21 / 9.14 / 9.03, 1024 15.9 /
-// 14.4 / 14.6, 1536 34.7 / 28.5 / 28.8, 2048 61.1 / 45.2 / 52: each 128 x 128
-// block pair converts two raw tiles per 512 MMA cycles, and above six blocks
-// that shared-memory traffic costs more than the decode pass (N = 704 takes
-// 9.09 ms in one pass, N = 720 9.99 ms in two).  0 disables it.
+// F = 1024, T = 8192, ms (one pass with 128-sample stages / two passes):
+// N = 512 3.66 / 5.09, 768 7.63 / 9.01, 1024 13.04 / 14.00, 1536 28.59 /
+// 27.27, 2048 58.8 / 45.2: each 128 x 128 block pair converts two raw tiles
+// per 1024 MMA cycles, which above about eight blocks costs more than the
+// decode pass.  0 disables it.
 #ifndef XENG_ONEPASS_MAX_N
-#define XENG_ONEPASS_MAX_N 768
+#define XENG_ONEPASS_MAX_N 1024
 #endif
 
 

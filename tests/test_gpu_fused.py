@@ -119,7 +119,7 @@ def test_fused_graph_replays_stay_exact():
     eng.close()
 
 
-# ---- more than 256 inputs: up to 768 (both tensor engines) single CTAs over pairs of
+# ---- more than 256 inputs: up to 1024 (both tensor engines) single CTAs over pairs of
 # ---- 128-input blocks; above (fused engine) 2-CTA clusters over pairs of 256-input blocks
 # ---- (diagonal pairs, ragged last blocks, both CTAs' halves)
 
@@ -133,7 +133,7 @@ def test_fused_raw_shapes(T, F, N):
     assert np.array_equal(correlate(blk, engine=FUSED), oracle.correlate(blk)), (T, F, N)
 
 
-@pytest.mark.parametrize("N,T", [(400, 70000), (784, 40000)])
+@pytest.mark.parametrize("N,T", [(400, 70000), (1040, 36000)])
 def test_fused_raw_several_launches_pieces_and_host_buffers(N, T):
     # more than 32,768 samples = several launches adding into int32; pushes in pieces;
     # host buffers through the channel-group pipeline
@@ -164,9 +164,9 @@ def test_fused_raw_many_channels_per_cluster_and_plane_engine_agree():
     assert np.array_equal(got[[0, 45, 89]], oracle.correlate(blk, f0=0, nf=F)[[0, 45, 89]])
 
 
-@pytest.mark.parametrize("N", [384, 704, 768])
+@pytest.mark.parametrize("N", [384, 704, 1024])
 def test_onepass_many_items_per_cta_and_engines_agree(N):
-    # 300 channels of 6 or 21 block pairs: several items per CTA, both accumulators and
+    # 300 channels of 6, 21 or 36 block pairs: several items per CTA, both accumulators and
     # both sums parities; the default engine (the same kernel) and the planes engine
     # agree, and sampled channels match the oracle; stored, then added by a second push
     rng = np.random.default_rng(N)

@@ -80,8 +80,8 @@ SHAPES = [(1, 1, 1), (5, 3, 2), (129, 2, 7), (300, 2, 127), (128, 1, 128), (257,
           # N > 256 and a multiple of 16: the single pass over 128-input block pairs
           # (default and fused engines) or the TMA decode pipeline (planes engine), ragged tiles
           (1000, 3, 272), (129, 2, 400), (5, 2, 288),
-          # above 768 inputs: the TMA decode's raw planes (default engine), 256-input block pairs (fused)
-          (300, 2, 784)]
+          # above 1024 inputs: the TMA decode's raw planes (default engine), 256-input block pairs (fused)
+          (200, 2, 1040)]
 
 
 @pytest.mark.parametrize("engine", sorted(ENGINES))
@@ -135,11 +135,11 @@ RAW_LAUNCH = 32768
 
 
 # N = 256: the single-pass kernel of up to 256 inputs; N = 272: the single pass
-# over 128-input block pairs; N = 784: the TMA decode's raw planes + tensor
+# over 128-input block pairs; N = 1040: the TMA decode's raw planes + tensor
 # correlator (default engine) and the single pass over 256-input block pairs
 # (fused engine)
-RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR), (784, xe.XENG_ENGINE_TENSOR),
-             (784, xe.XENG_ENGINE_TENSOR_FUSED)]
+RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR), (1040, xe.XENG_ENGINE_TENSOR),
+             (1040, xe.XENG_ENGINE_TENSOR_FUSED)]
 
 
 @pytest.mark.parametrize("N,engine", RAW_CASES)
