@@ -47,22 +47,33 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 # kernel changes.
 DRAM_BYTES_PER_CHANNEL = {
     ("correlate_tc", 2048, 8192): (658.302976e6 + 244.678912e6) / 16,   # raw-nibble planes, 16-channel slice
-    ("correlate_raw", 2048, 8192): (307.412224e6 + 223.055104e6) / 16,  # fused engine, 16-channel slice
     ("correlate_small", 256, 32768): (822.840832e6 + 22.4192e6) / 64,   # N <= 256 kernel, 64-channel slice
     ("correlate_onepass", 512, 8192): (543.91808e6 + 114.089728e6) / 128,  # one pass, 128-channel slice
 }
+
+
+# The library's choice between its two single-pass kernels above 256 inputs, at
+# its default build parameters: measured cost of one block pair (tens of us per
+# 1024 channels x 8192 samples) times the upper-triangle block pairs.
+PAIR_COST, ONEPASS_COST, FUSED_MAX_N = 116, 36, 4096
+
+
+def use_pair_kernel(N):
+    b2, b1 = -(-N // 256), -(-N // 128)
+    return PAIR_COST * (b2 * (b2 + 1) // 2) < ONEPASS_COST * (b1 * (b1 + 1) // 2)
 
 
 def correlate_kernel(engine, N):
     """(name, tile) of the correlation kernel an engine runs for N inputs (tile:
     the square of inputs one work item computes, lower halves of diagonal
     items included)."""
-    if engine in ("tensor", "fused") and N % 16 == 0 and N <= 256:
+    fused = N % 16 == 0 and (engine == "fused" or (engine == "tensor" and N <= FUSED_MAX_N))
+    if fused and N <= 256:
         return "correlate_small_kernel (decode fused; upper-triangle 128-input blocks, one CTA each)", 128
-    if engine in ("tensor", "fused") and N % 16 == 0 and N <= 1024:
+    if fused and use_pair_kernel(N):
+        return "correlate_pair_kernel (decode fused; 256-input block pairs, 2-CTA clusters)", 256
+    if fused:
         return "correlate_onepass_kernel (decode fused; 128-input block pairs, one CTA each)", 128
-    if engine == "fused" and N % 16 == 0:
-        return "correlate_raw_kernel (raw bytes split in shared memory; 256-input block pairs)", 256
     return "correlate_tc_kernel (decoded planes; 128-input tile pairs)", 128
 
 
@@ -453,8 +464,8 @@ def main():
     ap.add_argument("--engine", default="tensor", choices=["tensor", "dp4a", "planes", "fused"],
                     help="tensor: the default engine; planes: always decode to HBM planes, then correlate; "
                          "fused: single pass (raw bytes split in shared memory) wherever N is a multiple of 16")
-    ap.add_argument("--no-fused-compare", action="store_true",
-                    help="skip timing the single-pass (fused) engine beside the default one")
+    ap.add_argument("--no-engine-compare", "--no-fused-compare", dest="no_engine_compare", action="store_true",
+                    help="skip timing the two-pass (planes) engine beside the default one")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -568,11 +579,11 @@ def main():
         return ev0.elapsed_time(ev1) / reps, s2["decode_ms"] / reps
 
     push_dump_ms, push_dump_decode_ms = push_dump()
-    # the single-pass engine on the same block (raw bytes split in shared memory,
-    # no planes in HBM), measured in the same run beside the default engine
-    fused_cmp = None
-    if args.engine == "tensor" and N > 256 and N % 16 == 0 and not args.no_fused_compare:
-        eng_p = xe.XEngine(N, F, T, xe.XENG_ENGINE_TENSOR_FUSED)
+    # the two-pass engine on the same block (decode to FP8 planes in HBM, then the
+    # tensor-core GEMM), measured in the same run beside the default engine
+    planes_cmp = None
+    if args.engine == "tensor" and N > 256 and N % 16 == 0 and not args.no_engine_compare:
+        eng_p = xe.XEngine(N, F, T, xe.XENG_ENGINE_TENSOR_PLANES)
         out_p = torch.empty_like(out)
         for _ in range(2):
             eng_p.correlate(block, out_p, T, stream)
@@ -586,11 +597,13 @@ def main():
         ev1.synchronize()
         sp = eng_p.stats(reset=True)
         p_ms = ev0.elapsed_time(ev1) / reps_p
-        fused_cmp = {"engine": "tensor_fused", "ms_per_step": p_ms, "value": useful_ops(T, F, N) / (p_ms * 1e-3) / 1e12,
-                     "unit": "TOPS", "correlate_ms_per_step": sp["correlate_ms"] / reps_p,
-                     "equals_default_engine_output": bool(torch.equal(out_p, out)),
-                     "kernels": "raw_sums_kernel + correlate_raw_kernel (256-input block pairs, MN-major raw-nibble "
-                                "operands split in shared memory)"}
+        planes_cmp = {"engine": "tensor_planes", "ms_per_step": p_ms,
+                      "value": useful_ops(T, F, N) / (p_ms * 1e-3) / 1e12, "unit": "TOPS",
+                      "decode_ms_per_step": sp["decode_ms"] / reps_p,
+                      "correlate_ms_per_step": sp["correlate_ms"] / reps_p,
+                      "equals_default_engine_output": bool(torch.equal(out_p, out)),
+                      "kernels": "decode_tma_kernel + plane_sums_kernel + correlate_tc_kernel (raw-nibble FP8 "
+                                 "planes in HBM, 128-input tile pairs)"}
         eng_p.close()
         del out_p
         torch.cuda.synchronize()
@@ -844,7 +857,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs (%.1f GiB) larger than L2; no flush" % (T * F * N / 2 ** 30)},
                 "cmac_per_s": value / 8.0 * 1e12, "ops_per_cmac": 8, "step_call": "xeng_correlate",
-                "push_dump_ms_per_step": push_dump_ms, "fused_engine": fused_cmp, "time_shift": shift, "gating": gating, "beamform": beam,
+                "push_dump_ms_per_step": push_dump_ms, "two_pass_engine": planes_cmp, "time_shift": shift, "gating": gating, "beamform": beam,
                 "pathfinder_rate": secondary, "plain_dp4a": plain_dp4a, "batched": batched, "serving": serving,
                 "gpu_launches": int(st["launches"]), "roofline": roof, "decode_roofline": decode_roof,
                 "peak_probes_tflops": probes, "clocks": clocks, "e2e": e2e,

@@ -64,15 +64,22 @@ extern "C" {
 #define XENG_MAX_T_INTEG  16777215LL
 
 /* Correlation engines (all give identical bits). */
-#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 1024 (a multiple of 16, block
+#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 4096 a multiple of 16 (block
                                         16-byte aligned) one kernel splits the raw bytes in shared memory and
-                                        correlates them (N <= 256: scratch of 256 KB per SM, allocated at
-                                        the first such call); otherwise as XENG_ENGINE_TENSOR_PLANES         */
+                                        correlates them -- N <= 256: single CTAs over 128-input blocks
+                                        (scratch of 256 KB per SM, allocated at the first such call); above:
+                                        single CTAs over 128-input block pairs or 2-CTA clusters over
+                                        256-input block pairs, whichever does less padded work for N.  The
+                                        environment variable XENG_FUSED_KERNEL=onepass or =pair (read by
+                                        xeng_create) forces one of the two for every such N.  Otherwise as
+                                        XENG_ENGINE_TENSOR_PLANES                                            */
 #define XENG_ENGINE_DP4A          1  /* plain CUDA-core kernel: int8 dp4a straight from the bytes            */
-#define XENG_ENGINE_TENSOR_PLANES 2  /* two passes: decode to FP8 planes in HBM, then the tensor-core GEMM   */
-#define XENG_ENGINE_TENSOR_FUSED  3  /* single pass for every N that is a multiple of 16 (block 16-byte
-                                        aligned): no decode planes, F * N * 8 bytes of scratch instead of up
-                                        to 16 GiB; slower than two passes above 256 inputs on GB300        */
+#define XENG_ENGINE_TENSOR_PLANES 2  /* two passes: decode to FP8 planes in HBM, then the tensor-core GEMM
+                                        (decode buffer of up to 16 GiB, allocated at the first such call)    */
+#define XENG_ENGINE_TENSOR_FUSED  3  /* the default engine's single pass for every N that is a multiple of
+                                        16 (block 16-byte aligned), also above the build parameter
+                                        XENG_FUSED_MAX_N up to which the default engine takes it (4096 in the
+                                        default build, where the two engines are the same)                   */
 
 typedef struct xeng_s *xeng_t;
 

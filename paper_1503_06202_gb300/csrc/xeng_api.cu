@@ -32,7 +32,6 @@ struct xeng_s {
     int64_t planes_bytes = 0;
     int2 *partials = nullptr;      // raw-nibble planes: per-tile nibble sums [group_f][n_tb][n_pad]
     int2 *sums = nullptr;          // raw-nibble planes: (S, D) per input [group_f][n_pad]
-    int2 *raw_sums = nullptr;      // single-pass kernel above 256 inputs: (S, D) per input [F][N]
     int2 *small_ws = nullptr;      // single-pass kernel up to 256 inputs: partial blocks of split items
     int *small_flags = nullptr;    // and the flags that publish them, with the launch count
     bool planes_raw = false;       // the last decode wrote raw-nibble planes
@@ -63,6 +62,7 @@ struct xeng_s {
     int64_t hist_H = 0;
     int32_t hist_S = 0;
     bool decode_tma = false;       // decode through the TMA pipeline where the block allows it
+    int fused_force = 0;           // single-pass kernel forced for every N: 0 none, else a FusedKernel
     // gate accumulator sets (xeng_set_gates): acc holds n_gates sets of [F][B][2];
     // set 0's "nothing integrated yet" flag is `fresh`, the others' gate_fresh[g]
     int32_t n_gates = 1;
@@ -185,19 +185,46 @@ cudaEvent_t take_event(xeng_s *h)
 #ifndef XENG_FUSED_SMALL
 #define XENG_FUSED_SMALL 1
 #endif
-// Up to this many inputs (above 256) one pass with single CTAs over 128-input
-// block pairs (correlate_onepass.cu) is the tensor engines' path; above it the
-// default engine decodes to planes first and the fused engine runs 2-CTA
-// clusters over 256-input block pairs (correlate_raw.cu).  Measured on GB300,
-// F = 1024, T = 8192, ms (one pass with 128-sample stages / two passes):
-// N = 512 3.66 / 5.09, 768 7.63 / 9.01, 1024 13.04 / 14.00, 1536 28.59 /
-// 27.27, 2048 58.8 / 45.2: each 128 x 128 block pair converts two raw tiles
-// per 1024 MMA cycles, which above about eight blocks costs more than the
-// decode pass.  0 disables it.
-#ifndef XENG_ONEPASS_MAX_N
-#define XENG_ONEPASS_MAX_N 1024
+// Above 256 inputs the single pass runs either the 2-CTA pair kernel over
+// 256-input block pairs (correlate_pair.cu) or single CTAs over 128-input block
+// pairs (correlate_onepass.cu), whichever costs less by the measured time of
+// one block pair (GB300, 1024 channels x 8192 samples: 1.16 ms per 256 x 256
+// pair, 0.36 ms per 128 x 128 pair, in units of 10 us).  The pair kernel does
+// a quarter of the MMAs per block in a quarter of the items, but pads N to 256:
+// it wins unless ceil(N / 128) is odd (N = 384: 3.29 against 2.35 ms; 512:
+// 3.40 / 3.66; 768: 7.01 / 7.50; 1024: 11.55 / 13.04; 1536: 24.76 / 28.62).
+// A cost of 0 forces that kernel.
+#ifndef XENG_PAIR_COST
+#define XENG_PAIR_COST 116
+#endif
+#ifndef XENG_ONEPASS_COST
+#define XENG_ONEPASS_COST 36
+#endif
+// Above this many inputs the default engine decodes to planes first (two
+// passes) instead of the single pass (GB300, 8192 samples, ms single / two
+// passes: N = 2048 x 1024 channels 43.5 / 44.3, N = 4096 x 256 channels
+// 40.8 / 40.0).
+#ifndef XENG_FUSED_MAX_N
+#define XENG_FUSED_MAX_N 4096
 #endif
 
+bool use_pair_kernel(int32_t N)
+{
+    const int64_t b2 = (N + 255) / 256, b1 = (N + 127) / 128;
+    return (int64_t)XENG_PAIR_COST * (b2 * (b2 + 1) / 2) < (int64_t)XENG_ONEPASS_COST * (b1 * (b1 + 1) / 2);
+}
+
+// The single-pass kernel of a handle: by N, unless the environment variable
+// XENG_FUSED_KERNEL (read at handle creation) is "pair" or "onepass", which
+// takes that kernel for every N it covers (all three give the same bits).
+enum FusedKernel { kFusedSmall = 1, kFusedOnepass = 2, kFusedPair = 3 };
+
+int fused_kernel(const xeng_s *h)
+{
+    if (h->fused_force) return h->fused_force;
+    if (h->N <= 256) return kFusedSmall;
+    return use_pair_kernel(h->N) ? kFusedPair : kFusedOnepass;
+}
 
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
 // either end (the first group's upload and the last group's download overlap
@@ -258,23 +285,24 @@ cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int
 
 // The tensor engines' single-pass kernels (decode fused into the correlation)
 // apply to this block: launches of at most kFusedMaxSamples samples over all
-// channels, no planes in HBM.  Up to XENG_ONEPASS_MAX_N inputs both engines
-// take them; above, only XENG_ENGINE_TENSOR_FUSED (measured on GB300: full
-// CHIME 52 ms single pass against 44.3 ms for decode + correlation, so the two
-// passes are the default there).
+// channels, no planes in HBM.  The default engine takes them up to
+// XENG_FUSED_MAX_N inputs, XENG_ENGINE_TENSOR_FUSED for every N they cover.
 bool fused_ok(const xeng_s *h, const uint8_t *block)
 {
-    const bool onepass = h->N > 256 && h->N <= XENG_ONEPASS_MAX_N && onepass_ok(block, h->N);
-    if (h->engine == XENG_ENGINE_TENSOR) return (XENG_FUSED_SMALL && small_ok(block, h->N)) || onepass;
-    if (h->engine == XENG_ENGINE_TENSOR_FUSED)
-        return (XENG_FUSED_SMALL && small_ok(block, h->N)) || onepass || correlate_raw_ok(block, h->N);
-    return false;
+    if (h->engine != XENG_ENGINE_TENSOR && h->engine != XENG_ENGINE_TENSOR_FUSED) return false;
+    if (h->engine == XENG_ENGINE_TENSOR && h->N > XENG_FUSED_MAX_N) return false;
+    switch (fused_kernel(h)) {
+    case kFusedSmall: return XENG_FUSED_SMALL && small_ok(block, h->N);
+    case kFusedPair: return pair_ok(block, h->N);
+    default: return onepass_ok(block, h->N);
+    }
 }
 
 cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                          int32_t f0, int32_t nf, int32_t *acc, int accumulate, cudaStream_t s)
 {
-    if (h->N <= 256) {
+    const int kernel = fused_kernel(h);
+    if (kernel == kFusedSmall) {
         if (!h->small_ws) {
             cudaError_t e = cudaMalloc(&h->small_ws, small_ws_bytes(h->num_sms));
             if (e == cudaSuccess) e = cudaMalloc(&h->small_flags, small_flags_bytes(h->num_sms));
@@ -291,19 +319,11 @@ cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64
         return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->small_ws,
                                       h->small_flags, h->d_err, h->num_sms, s);
     }
-    if (h->N <= XENG_ONEPASS_MAX_N)
-        return launch_correlate_onepass(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err,
-                                        h->num_sms, s);
-    if (!h->raw_sums) {  // the per-input sums of the largest launch: every channel of the handle
-        cudaError_t e = cudaMalloc(&h->raw_sums, (size_t)h->F * h->N * sizeof(int2));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            h->raw_sums = nullptr;
-            return e;
-        }
-    }
-    return launch_correlate_raw(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->raw_sums, h->d_err,
-                                h->num_sms, s);
+    if (kernel == kFusedPair)
+        return launch_correlate_pair(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
+                                     s);
+    return launch_correlate_onepass(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
+                                    s);
 }
 
 // Run one kernel launch, bracketed by events when profiling.
@@ -375,6 +395,8 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
     {
         const char *env = getenv("XENG_DECODE_THREADS");
         h->decode_tma = XENG_DECODE_TMA && !(env && env[0] == '1');
+        env = getenv("XENG_FUSED_KERNEL");
+        h->fused_force = !env ? 0 : !strcmp(env, "pair") ? kFusedPair : !strcmp(env, "onepass") ? kFusedOnepass : 0;
     }
 
     // Decode buffer: rounds of (group_f channels x chunk_t samples); the
@@ -418,7 +440,6 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->planes);
     cudaFree(h->partials);
     cudaFree(h->sums);
-    cudaFree(h->raw_sums);
     cudaFree(h->small_ws);
     cudaFree(h->small_flags);
     cudaFree(h->staging);

@@ -158,15 +158,14 @@ cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int6
                                      int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
                                      int num_sms, cudaStream_t s);
 
-// Decode fused into the correlation for 256 < N <= 4096 (N % 16 == 0, block
-// 16-byte aligned), as launch_correlate_small: a pass forming every input's
-// nibble sums into `sums` (scratch of nf * N int2), then 2-CTA clusters over
-// every channel's upper-triangle pairs of 256-input blocks; nt <=
-// kFusedMaxSamples, acc 8-byte aligned.
-bool correlate_raw_ok(const uint8_t *block, int32_t N);
-cudaError_t launch_correlate_raw(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
-                                 int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *sums, int *err,
-                                 int num_sms, cudaStream_t s);
+// Decode fused into the correlation for 16 <= N <= 4096 (N % 16 == 0, block
+// 16-byte aligned), as launch_correlate_small: 2-CTA clusters over every
+// channel's upper-triangle pairs of 256-input blocks, nibble sums in shared
+// memory; nt <= kFusedMaxSamples, acc 8-byte aligned.
+bool pair_ok(const uint8_t *block, int32_t N);
+cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
+                                  int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
+                                  cudaStream_t s);
 
 // Beamforming (Sec. IV-C-3).  The host fills T, F, N, B, out and err; the
 // launcher fills the rest.

@@ -1,10 +1,11 @@
-"""The fused decode + correlation used for up to 256 inputs (N a multiple of
-16): bit-exact against the oracle for tiny N (tiles mostly padding), up to and
-above 128 inputs (diagonal items of two channels; row items and diagonal items
-of the upper input halves), odd channel counts (a diagonal item of one
-channel), ragged sample counts, one sample, several launches adding into
-int32, pushes in pieces, host buffers, and many items per CTA (both parities of
-the item sums, store and add)."""
+"""The fused decode + correlation (N a multiple of 16).  Up to 256 inputs, single
+CTAs over 128-input blocks: bit-exact against the oracle for tiny N (tiles
+mostly padding), up to and above 128 inputs (diagonal items of two channels;
+row items and diagonal items of the upper input halves), odd channel counts (a
+diagonal item of one channel), ragged sample counts, one sample, several
+launches adding into int32, pushes in pieces, host buffers, and many items per
+CTA (both parities of the item sums, store and add).  Then both single passes
+over block pairs, each forced for every case."""
 import numpy as np
 import pytest
 
@@ -119,22 +120,32 @@ def test_fused_graph_replays_stay_exact():
     eng.close()
 
 
-# ---- more than 256 inputs: up to 1024 (both tensor engines) single CTAs over pairs of
-# ---- 128-input blocks; above (fused engine) 2-CTA clusters over pairs of 256-input blocks
-# ---- (diagonal pairs, ragged last blocks, both CTAs' halves)
+# ---- the single passes over block pairs, for any N that is a multiple of 16: single
+# ---- CTAs over pairs of 128-input blocks (onepass) and 2-CTA clusters over pairs of
+# ---- 256-input blocks (pair).  Above 256 inputs the library picks one by N; the
+# ---- environment variable XENG_FUSED_KERNEL forces either, so both run every case
+# ---- (diagonal pairs, ragged last blocks, both CTAs' halves, inputs below 256)
 
 FUSED = xe.XENG_ENGINE_TENSOR_FUSED
 
-@pytest.mark.parametrize("T,F,N", [(1, 1, 272), (127, 2, 288), (129, 2, 512), (1000, 3, 528), (300, 2, 784),
-                                   (257, 1, 1024), (200, 2, 2048), (130, 1, 4096)])
-def test_fused_raw_shapes(T, F, N):
+
+@pytest.fixture(params=["onepass", "pair"])
+def fused_kernel(request, monkeypatch):
+    monkeypatch.setenv("XENG_FUSED_KERNEL", request.param)
+    return request.param
+
+
+@pytest.mark.parametrize("T,F,N", [(1, 1, 16), (129, 3, 32), (513, 2, 240), (1, 1, 272), (127, 2, 288),
+                                   (129, 2, 512), (1000, 3, 528), (300, 2, 784), (257, 1, 1024), (200, 2, 2048),
+                                   (130, 1, 4096)])
+def test_fused_raw_shapes(T, F, N, fused_kernel):
     rng = np.random.default_rng(T * 37 + F * 5 + N)
     blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
-    assert np.array_equal(correlate(blk, engine=FUSED), oracle.correlate(blk)), (T, F, N)
+    assert np.array_equal(correlate(blk, engine=FUSED), oracle.correlate(blk)), (T, F, N, fused_kernel)
 
 
 @pytest.mark.parametrize("N,T", [(400, 70000), (1040, 36000)])
-def test_fused_raw_several_launches_pieces_and_host_buffers(N, T):
+def test_fused_raw_several_launches_pieces_and_host_buffers(N, T, fused_kernel):
     # more than 32,768 samples = several launches adding into int32; pushes in pieces;
     # host buffers through the channel-group pipeline
     rng = np.random.default_rng(15 + N)
@@ -148,8 +159,9 @@ def test_fused_raw_several_launches_pieces_and_host_buffers(N, T):
     assert np.array_equal(correlate(blk2, host=True, engine=FUSED), oracle.correlate(blk2))
 
 
-def test_fused_raw_many_channels_per_cluster_and_plane_engine_agree():
-    # 90 channels x 3 block pairs over the 76 clusters; the two-pass engine gives the same bits
+def test_fused_raw_many_channels_per_cluster_and_plane_engine_agree(fused_kernel):
+    # 90 channels x 3 block pairs over the 76 clusters (or 10 over the CTAs); the
+    # two-pass engine gives the same bits
     rng = np.random.default_rng(16)
     T, F, N = 384, 90, 512
     blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
@@ -165,9 +177,10 @@ def test_fused_raw_many_channels_per_cluster_and_plane_engine_agree():
 
 
 @pytest.mark.parametrize("N", [384, 704, 1024])
-def test_onepass_many_items_per_cta_and_engines_agree(N):
-    # 300 channels of 6, 21 or 36 block pairs: several items per CTA, both accumulators and
-    # both sums parities; the default engine (the same kernel) and the planes engine
+def test_single_pass_many_items_per_cta_and_engines_agree(N, fused_kernel):
+    # 300 channels of 6, 21 or 36 pairs of 128-input blocks (3, 6 or 10 of 256-input
+    # blocks): several items per CTA or cluster, both accumulators and both sums
+    # parities; the default engine (forced to the same kernel) and the planes engine
     # agree, and sampled channels match the oracle; stored, then added by a second push
     rng = np.random.default_rng(N)
     T, F = 160, 300
@@ -185,7 +198,7 @@ def test_onepass_many_items_per_cta_and_engines_agree(N):
     assert np.array_equal(got[pick], oracle.correlate(np.ascontiguousarray(blk[:, pick])))
 
 
-def test_fused_raw_int32_beyond_f32_range():
+def test_fused_raw_int32_beyond_f32_range(fused_kernel):
     # every sample -8-8i over 70,000 samples (three launches): Re = 8,960,000 > 2^23
     T, F, N = 70000, 1, 272
     out = correlate(np.zeros((T, F, N), np.uint8), engine=FUSED)

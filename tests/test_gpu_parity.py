@@ -17,8 +17,11 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 import paper_1503_06202_gb300 as xe  # noqa: E402
 
-# tensor: the default (single pass up to 256 inputs, two passes above); planes:
-# always the two passes; fused: single pass wherever N is a multiple of 16
+# tensor: the default (single pass wherever N is a multiple of 16: up to 256
+# inputs single CTAs over 128-input blocks, above single CTAs over 128-input or
+# 2-CTA clusters over 256-input block pairs by N; two passes otherwise); planes:
+# always the two passes; fused: as the default (single pass for every N that is
+# a multiple of 16)
 ENGINES = {"tensor": xe.XENG_ENGINE_TENSOR, "dp4a": xe.XENG_ENGINE_DP4A, "planes": xe.XENG_ENGINE_TENSOR_PLANES,
            "fused": xe.XENG_ENGINE_TENSOR_FUSED}
 
@@ -78,10 +81,9 @@ def test_decode_stage_codes(T, F, N, f0, nf):
 SHAPES = [(1, 1, 1), (5, 3, 2), (129, 2, 7), (300, 2, 127), (128, 1, 128), (257, 2, 129), (1000, 3, 200),
           (700, 2, 300), (1024, 1, 513), (64, 2, 1024),
           # N > 256 and a multiple of 16: the single pass over 128-input block pairs
-          # (default and fused engines) or the TMA decode pipeline (planes engine), ragged tiles
-          (1000, 3, 272), (129, 2, 400), (5, 2, 288),
-          # above 1024 inputs: the TMA decode's raw planes (default engine), 256-input block pairs (fused)
-          (200, 2, 1040)]
+          # (272, 288, 1040) or 256-input block pairs (400, and 1024 above), default and
+          # fused engines; the TMA decode pipeline (planes engine); ragged tiles
+          (1000, 3, 272), (129, 2, 400), (5, 2, 288), (200, 2, 1040)]
 
 
 @pytest.mark.parametrize("engine", sorted(ENGINES))
@@ -135,15 +137,25 @@ RAW_LAUNCH = 32768
 
 
 # N = 256: the single-pass kernel of up to 256 inputs; N = 272: the single pass
-# over 128-input block pairs; N = 1040: the TMA decode's raw planes + tensor
-# correlator (default engine) and the single pass over 256-input block pairs
-# (fused engine)
-RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR), (272, xe.XENG_ENGINE_TENSOR), (1040, xe.XENG_ENGINE_TENSOR),
-             (1040, xe.XENG_ENGINE_TENSOR_FUSED)]
+# over 128-input block pairs; N = 1024: the single pass over 256-input block
+# pairs, and at N = 1040 (a ragged last block) forced by XENG_FUSED_KERNEL; the
+# TMA decode's raw planes + tensor correlator (planes engine)
+RAW_CASES = [(256, xe.XENG_ENGINE_TENSOR, None), (272, xe.XENG_ENGINE_TENSOR, None),
+             (1024, xe.XENG_ENGINE_TENSOR, None), (1040, xe.XENG_ENGINE_TENSOR, "pair"),
+             (1040, xe.XENG_ENGINE_TENSOR_PLANES, None)]
 
 
-@pytest.mark.parametrize("N,engine", RAW_CASES)
-def test_raw_nibble_sums_up_to_2_24(N, engine):
+@pytest.fixture
+def raw_case(request, monkeypatch):
+    N, engine, force = request.param
+    if force:
+        monkeypatch.setenv("XENG_FUSED_KERNEL", force)
+    return N, engine
+
+
+@pytest.mark.parametrize("raw_case", RAW_CASES, indirect=True)
+def test_raw_nibble_sums_up_to_2_24(raw_case):
+    N, engine = raw_case
     T, F = RAW_LAUNCH, 1
     # every nibble 15: raw sums 450 T; x = 7 + 7i, V = 98 T
     out = run(torch.full((T, F, N), 0xFF, dtype=torch.uint8, device="cuda"), engine)
@@ -156,8 +168,9 @@ def test_raw_nibble_sums_up_to_2_24(N, engine):
     assert (out[..., 0] == 113 * T).all() and (out[..., 1] == 0).all()
 
 
-@pytest.mark.parametrize("N,engine", RAW_CASES)
-def test_raw_nibble_unit_terms_above_2_23(N, engine):
+@pytest.mark.parametrize("raw_case", RAW_CASES, indirect=True)
+def test_raw_nibble_unit_terms_above_2_23(raw_case):
+    N, engine = raw_case
     # 18,700 samples of nibbles 15 take every raw sum to 450 * 18,700 = 8,415,000 > 2^23;
     # then each remaining sample adds 0 or 1 to a pair's raw sums (bytes 0x00, 0x10, 0x01),
     # so every 32-sample MMA step adds a small integer that a sum keeping fewer than
@@ -169,8 +182,9 @@ def test_raw_nibble_unit_terms_above_2_23(N, engine):
     assert_same(run(to_dev(blk), engine), oracle.correlate(blk), "large raw sums, unit tail")
 
 
-@pytest.mark.parametrize("N,engine", RAW_CASES)
-def test_raw_nibble_extremes_one_launch(N, engine):
+@pytest.mark.parametrize("raw_case", RAW_CASES, indirect=True)
+def test_raw_nibble_extremes_one_launch(raw_case):
+    N, engine = raw_case
     rng = np.random.default_rng(23 + N)
     T, F = RAW_LAUNCH, 2
     blk = rng.choice(np.array([0x00, 0xFF, 0x0F, 0xF0, 0x88, 0x98, 0x78, 0x08, 0x80], np.uint8), size=(T, F, N))
