@@ -32,7 +32,7 @@ WORKLOADS = {
     "pathfinder_small": ("PATHFINDER_SMALL", "Pathfinder-shaped small: N=256, 8 channels, T=4096, uniform nibbles"),
     "chime_slice": ("CHIME_SLICE", "16 channels of the full-CHIME shape (N=2048, T=8192): profiling case"),
     "pathfinder_slice": ("PATHFINDER_SLICE", "64 channels of the Pathfinder shape (N=256, T=32768): profiling case"),
-    "mid_slice": ("MID_SLICE", "128 channels of N=512, T=8192, sky+noise: profiling case of the one pass over 128-input "
+    "mid_slice": ("MID_SLICE", "128 channels of N=640, T=8192, sky+noise: profiling case of the one pass over 128-input "
                                "block pairs"),
     "batched": (None, "64 independent jobs, N in {64..2048}, F in {1,16,64}, T log-uniform 1024..32768, uniform nibbles"),
     "serving": (None, "8 concurrent streams (3 x N=256, 3 x N=512, 2 x N=2048), 256 channels each, 256-sample blocks, "
@@ -47,15 +47,16 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 # kernel changes.
 DRAM_BYTES_PER_CHANNEL = {
     ("correlate_tc", 2048, 8192): (658.302976e6 + 244.678912e6) / 16,   # raw-nibble planes, 16-channel slice
-    ("correlate_small", 256, 32768): (822.840832e6 + 22.4192e6) / 64,   # N <= 256 kernel, 64-channel slice
-    ("correlate_onepass", 512, 8192): (543.91808e6 + 114.089728e6) / 128,  # one pass, 128-channel slice
+    ("correlate_pair", 2048, 8192): (311.818752e6 + 222.252032e6) / 16,  # 256-input block pairs, 16-channel slice
+    ("correlate_small", 256, 32768): (821.271808e6 + 19.28704e6) / 64,  # N <= 256 kernel, 64-channel slice
+    ("correlate_onepass", 640, 8192): (676.602112e6 + 185.624576e6) / 128,  # one pass, 128-channel slice
 }
 
 
 # The library's choice between its two single-pass kernels above 256 inputs, at
 # its default build parameters: measured cost of one block pair (tens of us per
 # 1024 channels x 8192 samples) times the upper-triangle block pairs.
-PAIR_COST, ONEPASS_COST, FUSED_MAX_N = 116, 36, 4096
+PAIR_COST, ONEPASS_COST, FUSED_MAX_N = 116, 36, 3584
 
 
 def use_pair_kernel(N):

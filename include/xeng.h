@@ -64,7 +64,7 @@ extern "C" {
 #define XENG_MAX_T_INTEG  16777215LL
 
 /* Correlation engines (all give identical bits). */
-#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 4096 a multiple of 16 (block
+#define XENG_ENGINE_TENSOR        0  /* tcgen05 tensor cores (default): for N <= 3584 a multiple of 16 (block
                                         16-byte aligned) one kernel splits the raw bytes in shared memory and
                                         correlates them -- N <= 256: single CTAs over 128-input blocks
                                         (scratch of 256 KB per SM, allocated at the first such call); above:
@@ -77,9 +77,9 @@ extern "C" {
 #define XENG_ENGINE_TENSOR_PLANES 2  /* two passes: decode to FP8 planes in HBM, then the tensor-core GEMM
                                         (decode buffer of up to 16 GiB, allocated at the first such call)    */
 #define XENG_ENGINE_TENSOR_FUSED  3  /* the default engine's single pass for every N that is a multiple of
-                                        16 (block 16-byte aligned), also above the build parameter
-                                        XENG_FUSED_MAX_N up to which the default engine takes it (4096 in the
-                                        default build, where the two engines are the same)                   */
+                                        16 (block 16-byte aligned), also above the N up to which the default
+                                        engine takes it (the build parameter XENG_FUSED_MAX_N, 3584): no
+                                        decode buffer, about 2% slower than two passes at N = 4096           */
 
 typedef struct xeng_s *xeng_t;
 

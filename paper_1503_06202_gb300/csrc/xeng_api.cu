@@ -201,11 +201,13 @@ cudaEvent_t take_event(xeng_s *h)
 #define XENG_ONEPASS_COST 36
 #endif
 // Above this many inputs the default engine decodes to planes first (two
-// passes) instead of the single pass (GB300, 8192 samples, ms single / two
-// passes: N = 2048 x 1024 channels 43.5 / 44.3, N = 4096 x 256 channels
-// 40.8 / 40.0).
+// passes) instead of the single pass: the decode pass grows with N, the
+// correlation with N^2, and the plane GEMM does a block pair about 15% faster
+// than the pair kernel's converters feed it (GB300, 8192 samples, ms single /
+// two passes: N = 2048 x 1024 channels 43.5 / 45.1, N = 3072 x 512 46.8 / 47.7,
+// N = 4096 x 256 40.8 / 40.0; a fit of both puts the crossover near 3600).
 #ifndef XENG_FUSED_MAX_N
-#define XENG_FUSED_MAX_N 4096
+#define XENG_FUSED_MAX_N 3584
 #endif
 
 bool use_pair_kernel(int32_t N)

@@ -183,9 +183,10 @@ CHIME_FULL = Recipe("sky", T=8192, F=1024, N=2048, seed=2)
 CHIME_SLICE = Recipe("sky", T=8192, F=16, N=2048, seed=2)
 # 64 channels of the Pathfinder shape (512 MiB of input): its profiling case.
 PATHFINDER_SLICE = Recipe("sky", T=32768, F=64, N=256, seed=1)
-# 128 channels of N = 512 (512 MiB of input): the profiling case of the one pass
-# over 128-input block pairs.
-MID_SLICE = Recipe("sky", T=8192, F=128, N=512, seed=3)
+# 128 channels of N = 640 (640 MiB of input): the profiling case of the one pass
+# over 128-input block pairs (an odd number of 128-input blocks, where it pads
+# less than 256-input block pairs).
+MID_SLICE = Recipe("sky", T=8192, F=128, N=640, seed=3)
 
 
 BATCH_N = (64, 96, 128, 200, 256, 512, 1024, 2048)

@@ -17,11 +17,11 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 import paper_1503_06202_gb300 as xe  # noqa: E402
 
-# tensor: the default (single pass wherever N is a multiple of 16: up to 256
-# inputs single CTAs over 128-input blocks, above single CTAs over 128-input or
-# 2-CTA clusters over 256-input block pairs by N; two passes otherwise); planes:
-# always the two passes; fused: as the default (single pass for every N that is
-# a multiple of 16)
+# tensor: the default (single pass where N is a multiple of 16 up to 3584: up to
+# 256 inputs single CTAs over 128-input blocks, above single CTAs over 128-input
+# or 2-CTA clusters over 256-input block pairs by N; two passes otherwise);
+# planes: always the two passes; fused: the single pass for every N that is a
+# multiple of 16
 ENGINES = {"tensor": xe.XENG_ENGINE_TENSOR, "dp4a": xe.XENG_ENGINE_DP4A, "planes": xe.XENG_ENGINE_TENSOR_PLANES,
            "fused": xe.XENG_ENGINE_TENSOR_FUSED}
 
