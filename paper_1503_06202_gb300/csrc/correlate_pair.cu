@@ -5,19 +5,25 @@
 // A cluster of two CTAs owns one upper-triangle pair (I2 <= J2) of 256-input
 // blocks of one channel at a time, channel-major and round-robin over the
 // clusters (the clusters at work share one or two channels' raw bytes in L2).
-// CTA r takes A inputs I2*256 + r*128 + [0, 128) and B inputs J2*256 + r*128 +
-// [0, 128).  Per stage of kPKc (128) samples its producer TMA-loads those two
-// raw tiles (one on the diagonal, where A = B) with a 128-byte swizzle -- the
-// canonical MN-major layout of an 8-bit tcgen05 operand -- into a raw ring;
-// its converter warps split each byte at its own offset into the Im and Re
-// planes of a plane stage and sum each input's nibbles.  The leader issues
-// cta_group::2 MMAs of M = 256, N = 256 over the pair's planes:
-//     Re += A_re B_re^T + A_im B_im^T,   Im += A_im B_re^T + (-A_re) B_im^T
-// (each CTA supplies its 128 rows of A and its half of B, so per MMA a CTA
-// reads 8 KB of operands for 128 x 256 x 32 multiply-adds; per stage it
-// converts two 16 KB tiles for 16 MMAs, about 2048 tensor cycles).  The
-// 256 x 256 complex accumulator fills all 512 TMEM columns of both CTAs; the
-// epilogue (tcgen05.ld -> int32 triangle) follows each pair.
+// The A operand is the column block: CTA r takes A inputs j = J2*256 + r*128 +
+// [0, 128) and B inputs i = I2*256 + r*128 + [0, 128), so a CTA's TMEM lanes
+// are inputs j and its columns inputs i.  Per stage of kPKc (128) samples its
+// producer TMA-loads those two raw tiles (one on the diagonal, where A = B)
+// with a 128-byte swizzle -- the canonical MN-major layout of an 8-bit tcgen05
+// operand -- into a raw ring; its converter warps split each byte at its own
+// offset into the Im and Re planes of a plane stage and sum each input's
+// nibbles.  The leader issues cta_group::2 MMAs of M = 256, N = 256 over the
+// pair's planes:
+//     Re += A_re B_re^T + A_im B_im^T,   Im += A_re B_im^T + (-A_im) B_re^T
+// which with A = x_j, B = x_i is Im of x_i conj(x_j) (each CTA supplies its
+// 128 rows of A and its half of B, so per MMA a CTA reads 8 KB of operands for
+// 128 x 256 x 32 multiply-adds; per stage it converts two 16 KB tiles for 16
+// MMAs, about 2048 tensor cycles).  The 256 x 256 complex accumulator fills
+// all 512 TMEM columns of both CTAs; the epilogue (tcgen05.ld -> int32
+// triangle) follows each pair and cannot overlap the next pair's MMAs, so its
+// stores are laid out for the memory system: per column i, a warp's 32 lanes
+// hold 32 consecutive inputs j, one 256-byte run of the triangle's row i
+// (8-byte aligned whatever the row's start, unlike a row's 8-pair chunks).
 //
 // The stage length sets the cost: a stage carries a fixed cost (barrier round
 // trips, the proxy fence, the ring hand-offs) beside its conversion work, so
@@ -43,7 +49,6 @@
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
 //                quadrant, each half of the columns
 #include "tc_ptx.cuh"
-#include "triangle_store.cuh"
 #include "xeng_internal.h"
 
 namespace xeng {
@@ -203,7 +208,7 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                 const PairItem w = pair_item(a, it);
                 const int f = a.f0 + w.fl;
                 const bool diag = w.I2 == w.J2;
-                const int xa = w.I2 * 256 + (int)rank * 128, xb = w.J2 * 256 + (int)rank * 128;
+                const int xa = w.J2 * 256 + (int)rank * 128, xb = w.I2 * 256 + (int)rank * 128;
                 for (int kc = 0; kc < n_k; kc++) {
                     if (!mbar_try_wait(rawe(s), ph ^ 1u) && !mbar_wait(rawe(s), ph ^ 1u, err, kDevTimeoutProducer)) {
                         ok = false;
@@ -258,8 +263,8 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                         const uint64_t k4 = 256u * kk;
                         mma_f8_cg2(d_re, dar + k4, dbr + k4, pair_idesc(false), acc);
                         mma_f8_cg2(d_re, dai + k4, dbi + k4, pair_idesc(false), 1u);
-                        mma_f8_cg2(d_im, dai + k4, dbr + k4, pair_idesc(false), acc);
-                        mma_f8_cg2(d_im, dar + k4, dbi + k4, pair_idesc(true), 1u);
+                        mma_f8_cg2(d_im, dar + k4, dbi + k4, pair_idesc(false), acc);
+                        mma_f8_cg2(d_im, dai + k4, dbr + k4, pair_idesc(true), 1u);
                     }
                     mma_commit_cg2(empty(s), kBoth);
                     if (++s == kPPlanes) {
@@ -450,39 +455,52 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
             if (bar_any(2, kPEpiWarps * 32, !ok)) break;
             ++uses;
             fence_after();
-            const int i_warp = w.I2 * 256 + (int)rank * 128 + q * 32;  // first row of the warp
-            const int i = i_warp + lane;
-            const bool row_ok = i < N;
-            // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle
-            const int row_base = i * N - i * (i - 1) / 2 - i;
+            const int j_warp = w.J2 * 256 + (int)rank * 128 + q * 32;  // the warp's first input j
+            const int j = j_warp + lane;
+            const bool lane_ok = j < N;
             int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)w.fl * ((int64_t)N * (N + 1) / 2);
             const int2 *sp = sums + par * 384;
-            const int2 pq = sp[row];
-            const int si = pq.x + pq.y, di = pq.x - pq.y;
-            const int2 *cs = sp + 128;
-            const int jbase = w.J2 * 256;
-            if (i_warp < N) {
+            const int2 pq = sp[row];  // this lane's input j (A rows of this CTA)
+            const int sj = pq.x + pq.y, dj = pq.x - pq.y;
+            const int2 *cs = sp + 128;  // inputs i of the 256 columns
+            const int ibase = w.I2 * 256;
+            if (j_warp < N) {
                 for (int c = cbeg; c < cbeg + 128; c += 8) {
-                    const int j0 = jbase + c;
-                    // warp-uniform skips: chunks past the last input or below every row's diagonal
-                    if (j0 >= N) break;
-                    if (j0 + 7 < i_warp) continue;
+                    const int i0 = ibase + c;
+                    // warp-uniform: columns past the last input or past every lane's diagonal
+                    if (i0 >= N || i0 > j_warp + 31) break;
                     uint32_t vre[8], vim[8];
                     tmem_ld8(taddr + c, vre);
                     tmem_ld8(taddr + 256 + c, vim);
                     tmem_ld_wait();
-                    if (!row_ok) continue;
+                    int2 *pe[8];
+                    bool oke[8];
                     #pragma unroll
                     for (int e = 0; e < 8; e++) {  // corrected values in place of the accumulator words
-                        const int2 pj = cs[c + e];  // the same for every lane: a broadcast
+                        const int i = i0 + e;
+                        const int2 pi = cs[c + e];  // the same for every lane: a broadcast
                         // accumulators hold integer sums / 2^18: x 2^18 is exact
                         vre[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vre[e])) -
-                                            8 * (si + pj.x + pj.y) + n128);
+                                            8 * (sj + pi.x + pi.y) + n128);
                         vim[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vim[e])) +
-                                            8 * (di - (pj.x - pj.y)));
+                                            8 * ((pi.x - pi.y) - dj));
+                        // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle
+                        pe[e] = out + (i * N - i * (i - 1) / 2 - i) + j;
+                        oke[e] = lane_ok && i <= j && i < N;
                     }
-                    if (a.accumulate) put8<true>(out + row_base + j0, i - j0, N - j0, vre, vim);
-                    else put8<false>(out + row_base + j0, i - j0, N - j0, vre, vim);
+                    if (a.accumulate) {
+                        int2 o[8];
+                        #pragma unroll
+                        for (int e = 0; e < 8; e++)
+                            if (oke[e]) o[e] = __ldcs(pe[e]);
+                        #pragma unroll
+                        for (int e = 0; e < 8; e++)
+                            if (oke[e]) __stcs(pe[e], make_int2(o[e].x + (int)vre[e], o[e].y + (int)vim[e]));
+                    } else {
+                        #pragma unroll
+                        for (int e = 0; e < 8; e++)
+                            if (oke[e]) __stcs(pe[e], make_int2((int)vre[e], (int)vim[e]));
+                    }
                 }
             }
             fence_before();
