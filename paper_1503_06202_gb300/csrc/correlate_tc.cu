@@ -3,9 +3,11 @@
 // Computes, for every channel of a group and every upper-triangle tile pair
 // (I <= J) of 128 x 128 inputs, the visibility block (paper Sec. IV-C-1, Eq. 1)
 //     V_ij = sum_t x_i(t) conj(x_j(t)),   i in tile I, j in tile J,
-// as a real GEMM on decoded planes a = Re x, b = Im x (K = samples):
+// as a real GEMM on decoded planes a = Re x, b = Im x (K = samples), with the
+// A operand from tile J (TMEM lanes are inputs j) and B from tile I (columns
+// are inputs i):
 //     D[:, 0:128]   = A_a B_a^T + A_b B_b^T          = Re V
-//     D[:, 128:256] = A_a B_b^T - A_b B_a^T          = -Im V
+//     D[:, 128:256] = A_a B_b^T - A_b B_a^T          = Im V
 // issued per 32-sample K step as three tcgen05.mma (kind::f8f6f4, E4M3 x E4M3
 // -> f32 in TMEM):
 //     D[:, 0:256]  += A_a x [B_a ; B_b]^T      (N = 256, B_b follows B_a in smem)
@@ -21,7 +23,10 @@
 // channel-major so one channel's operands stay in L2 while its tiles run.
 //   warp 0      TMA producer: 128x128-byte SWIZZLE_128B boxes of the planes
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2..5  epilogue: tcgen05.ld -> int32 -> packed triangle in HBM
+//   warps 2..5  epilogue: tcgen05.ld -> int32 -> packed triangle in HBM; per
+//               column i a warp's 32 lanes write 32 consecutive pairs of the
+//               triangle's row i (one 256-byte run, 8-byte aligned whatever
+//               the row's start)
 // Smem ring of 3 stages x 64 KB (A_a, A_b, B_a, B_b of a 128-sample chunk;
 // diagonal tiles load only A and reuse it as B).  Two 256-column TMEM
 // accumulators let the epilogue of one tile overlap the MMAs of the next.
@@ -224,8 +229,8 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             for (int it = it_begin; ok && it < it_end; it += it_step) {
                 const Work w = fetch_work<kListed>(it, &tmap, a, sc, n_k, L);
                 const bool diag = (w.I == w.J);
-                const int rowA = w.fl * 2 * w.n_pad + w.I * kTile;
-                const int rowB = w.fl * 2 * w.n_pad + w.J * kTile;
+                const int rowA = w.fl * 2 * w.n_pad + w.J * kTile;  // A: tile J (TMEM lanes = inputs j)
+                const int rowB = w.fl * 2 * w.n_pad + w.I * kTile;  // B: tile I (columns = inputs i)
                 for (int kc = w.kc0; kc < w.kc1; kc++) {
                     if (!mbar_try_wait(empty_bar(stage), phase ^ 1u) &&
                         !mbar_wait(empty_bar(stage), phase ^ 1u, err, kDevTimeoutProducer)) {
@@ -321,162 +326,78 @@ correlate_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a, co
             if (!__all_sync(0xffffffffu, ok)) break;  // keep the warp converged for tcgen05.ld
             ++uses[ab];
             fence_after();
-            const int64_t N = w.N;
-            const int64_t i = (int64_t)w.I * kTile + row;
-            const bool row_ok = i < N;
-            // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle
-            const int64_t row_base = i * N - i * (i - 1) / 2 - i;
+            const int N = w.N;  // <= 4096: offsets within a channel's triangle fit in int
+            const int j_warp = w.J * kTile + q * 32;  // the warp's first input j
+            const int j = j_warp + lane;
+            const bool lane_ok = j < N;
             int2 *out = reinterpret_cast<int2 *>(w.out + (int64_t)w.fl * N * (N + 1));
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)ab * 256u;
-            const int64_t jbase = (int64_t)w.J * kTile;
+            const int ibase = w.I * kTile;
             const bool raw = kRaw || (kListed && w.sums != nullptr);  // uniform over the item
             const int2 *sums = w.sums;                                // (S, D) per input row
-            int2 si = make_int2(0, 0);
-            if (raw && w.offset) si = sums[i];  // i < n_pad
+            int2 sj = make_int2(0, 0);
+            if (raw && w.offset) sj = sums[j];  // j < n_pad
             const int n128 = raw && w.offset ? w.n128 : 0;
             // the triangle is written once and not read again here: streaming
             // stores keep it from evicting the operand planes other tiles
             // still read from L2
+            #pragma unroll 1
             for (int c = 0; c < kTile; c += 16) {
-                uint32_t re[16], nim[16];
+                const int i0 = ibase + c;
+                // warp-uniform: columns past the last input or past every lane's diagonal
+                if (i0 >= N || i0 > j_warp + 31) break;
+                uint32_t re[16], im[16];
                 tmem_ld16(taddr + c, re);
-                tmem_ld16(taddr + 128 + c, nim);
+                tmem_ld16(taddr + 128 + c, im);
                 tmem_ld_wait();
-                if (raw) {
-                    #pragma unroll
-                    for (int e = 0; e < 16; e++) {
-                        // the same for every lane: a broadcast
-                        const int2 sj = w.offset ? sums[jbase + c + e] : make_int2(0, 0);
-                        const int vr = __float2int_rn(262144.0f * __uint_as_float(re[e])) - 8 * (si.x + sj.x) + n128;
-                        const int vi = __float2int_rn(262144.0f * __uint_as_float(nim[e])) - 8 * (si.y - sj.y);
-                        re[e] = __float_as_uint((float)vr);
-                        nim[e] = __float_as_uint((float)vi);
+                int vr[16], vi[16];
+                #pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    if (raw) {
+                        // accumulators hold integer sums / 2^18: x 2^18 is exact
+                        const int2 si = w.offset ? sums[i0 + e] : make_int2(0, 0);  // a broadcast; i < n_pad
+                        vr[e] = __float2int_rn(262144.0f * __uint_as_float(re[e])) - 8 * (si.x + sj.x) + n128;
+                        vi[e] = __float2int_rn(262144.0f * __uint_as_float(im[e])) + 8 * (si.y - sj.y);
+                    } else {
+                        vr[e] = __float2int_rn(__uint_as_float(re[e]));
+                        vi[e] = __float2int_rn(__uint_as_float(im[e]));
                     }
                 }
-                if (row_ok) {
-                    int2 *p = out + row_base + jbase + c;  // pairs j = jbase + c + e, e = 0..15
-                    const int64_t e_lo = i - (jbase + c);  // first e on or above the diagonal
-                    const int64_t e_hi = N - (jbase + c);  // first e past the last input
-                    if (w.mode == kAdd && e_lo <= 0 && e_hi >= 16) {
-                        // interior chunk: the 16 pairs read and written in 32-byte pieces of four
-                        // pairs, 8- and 16-byte pieces at the ends by the row start's offset in a
-                        // 32-byte sector; all loads issued before any store
-                        int v[32], o[32];
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++) {
-                            v[2 * e] = __float2int_rn(__uint_as_float(re[e]));
-                            v[2 * e + 1] = -__float2int_rn(__uint_as_float(nim[e]));
+                // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle;
+                // row i + 1 starts N - i - 1 pairs after row i
+                const int off0 = i0 * N - i0 * (i0 - 1) / 2 - i0 + j;
+                if (w.mode == kStore) {
+                    int off = off0;
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        if (lane_ok && i0 + e <= j && i0 + e < N) __stcs(out + off, make_int2(vr[e], vi[e]));
+                        off += N - (i0 + e) - 1;
+                    }
+                } else if (w.mode == kAdd) {
+                    // all 16 loads issued before any store, so they overlap in flight
+                    int2 old[16];
+                    int off = off0;
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        if (lane_ok && i0 + e <= j && i0 + e < N) old[e] = __ldcs(out + off);
+                        off += N - (i0 + e) - 1;
+                    }
+                    off = off0;
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        if (lane_ok && i0 + e <= j && i0 + e < N)
+                            __stcs(out + off, make_int2(old[e].x + vr[e], old[e].y + vi[e]));
+                        off += N - (i0 + e) - 1;
+                    }
+                } else {
+                    int off = off0;
+                    #pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        if (lane_ok && i0 + e <= j && i0 + e < N) {
+                            atomicAdd(&out[off].x, vr[e]);
+                            atomicAdd(&out[off].y, vi[e]);
                         }
-                        auto ld8 = [&](int e) {
-                            const int2 x = __ldcs(p + e);
-                            o[2 * e] = x.x;
-                            o[2 * e + 1] = x.y;
-                        };
-                        auto ld16 = [&](int e) {
-                            const int4 x = __ldcs(reinterpret_cast<const int4 *>(p + e));
-                            o[2 * e] = x.x;
-                            o[2 * e + 1] = x.y;
-                            o[2 * e + 2] = x.z;
-                            o[2 * e + 3] = x.w;
-                        };
-                        auto ld32 = [&](int e) {
-                            asm volatile("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                                         : "=r"(o[2 * e]), "=r"(o[2 * e + 1]), "=r"(o[2 * e + 2]), "=r"(o[2 * e + 3]),
-                                           "=r"(o[2 * e + 4]), "=r"(o[2 * e + 5]), "=r"(o[2 * e + 6]), "=r"(o[2 * e + 7])
-                                         : "l"(p + e));
-                        };
-                        auto st8 = [&](int e) { __stcs(p + e, make_int2(o[2 * e] + v[2 * e], o[2 * e + 1] + v[2 * e + 1])); };
-                        auto st16 = [&](int e) {
-                            __stcs(reinterpret_cast<int4 *>(p + e),
-                                   make_int4(o[2 * e] + v[2 * e], o[2 * e + 1] + v[2 * e + 1], o[2 * e + 2] + v[2 * e + 2],
-                                             o[2 * e + 3] + v[2 * e + 3]));
-                        };
-                        auto st32 = [&](int e) {
-                            asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                                         ::"l"(p + e), "r"(o[2 * e] + v[2 * e]), "r"(o[2 * e + 1] + v[2 * e + 1]),
-                                         "r"(o[2 * e + 2] + v[2 * e + 2]), "r"(o[2 * e + 3] + v[2 * e + 3]),
-                                         "r"(o[2 * e + 4] + v[2 * e + 4]), "r"(o[2 * e + 5] + v[2 * e + 5]),
-                                         "r"(o[2 * e + 6] + v[2 * e + 6]), "r"(o[2 * e + 7] + v[2 * e + 7])
-                                         : "memory");
-                        };
-                        switch ((reinterpret_cast<uintptr_t>(p) >> 3) & 3) {
-                            case 0:
-                                ld32(0); ld32(4); ld32(8); ld32(12);
-                                st32(0); st32(4); st32(8); st32(12);
-                                break;
-                            case 1:
-                                ld8(0); ld16(1); ld32(3); ld32(7); ld32(11); ld8(15);
-                                st8(0); st16(1); st32(3); st32(7); st32(11); st8(15);
-                                break;
-                            case 2:
-                                ld16(0); ld32(2); ld32(6); ld32(10); ld16(14);
-                                st16(0); st32(2); st32(6); st32(10); st16(14);
-                                break;
-                            default:
-                                ld8(0); ld32(1); ld32(5); ld32(9); ld16(13); ld8(15);
-                                st8(0); st32(1); st32(5); st32(9); st16(13); st8(15);
-                                break;
-                        }
-                    } else if (w.mode == kAdd) {
-                        // all 16 loads issued before any store, so they overlap in flight
-                        int2 old[16];
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi) old[e] = __ldcs(p + e);
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi)
-                                __stcs(p + e, make_int2(old[e].x + __float2int_rn(__uint_as_float(re[e])),
-                                                        old[e].y - __float2int_rn(__uint_as_float(nim[e]))));
-                    } else if (w.mode == kStore && e_lo <= 0 && e_hi >= 16) {
-                        // interior chunk: 16-byte stores of two pairs where the row allows
-                        int v[32];
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++) {
-                            v[2 * e] = __float2int_rn(__uint_as_float(re[e]));
-                            v[2 * e + 1] = -__float2int_rn(__uint_as_float(nim[e]));
-                        }
-                        // 32-byte stores of four pairs, with 8- and 16-byte pieces at the ends by the
-                        // row start's offset in a 32-byte sector
-                        auto st8 = [&](int e) { __stcs(p + e, make_int2(v[2 * e], v[2 * e + 1])); };
-                        auto st16 = [&](int e) {
-                            __stcs(reinterpret_cast<int4 *>(p + e), make_int4(v[2 * e], v[2 * e + 1], v[2 * e + 2],
-                                                                             v[2 * e + 3]));
-                        };
-                        auto st32 = [&](int e) {
-                            asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                                         ::"l"(p + e), "r"(v[2 * e]), "r"(v[2 * e + 1]), "r"(v[2 * e + 2]),
-                                         "r"(v[2 * e + 3]), "r"(v[2 * e + 4]), "r"(v[2 * e + 5]), "r"(v[2 * e + 6]),
-                                         "r"(v[2 * e + 7])
-                                         : "memory");
-                        };
-                        switch ((reinterpret_cast<uintptr_t>(p) >> 3) & 3) {
-                            case 0:
-                                st32(0); st32(4); st32(8); st32(12);
-                                break;
-                            case 1:
-                                st8(0); st16(1); st32(3); st32(7); st32(11); st8(15);
-                                break;
-                            case 2:
-                                st16(0); st32(2); st32(6); st32(10); st16(14);
-                                break;
-                            default:
-                                st8(0); st32(1); st32(5); st32(9); st16(13); st8(15);
-                                break;
-                        }
-                    } else if (w.mode == kStore) {
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi)
-                                __stcs(p + e, make_int2(__float2int_rn(__uint_as_float(re[e])),
-                                                        -__float2int_rn(__uint_as_float(nim[e]))));
-                    } else {
-                        #pragma unroll
-                        for (int e = 0; e < 16; e++)
-                            if (e >= e_lo && e < e_hi) {
-                                atomicAdd(&p[e].x, __float2int_rn(__uint_as_float(re[e])));
-                                atomicAdd(&p[e].y, -__float2int_rn(__uint_as_float(nim[e])));
-                            }
+                        off += N - (i0 + e) - 1;
                     }
                 }
             }

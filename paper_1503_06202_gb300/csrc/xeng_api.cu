@@ -758,21 +758,32 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
             bf = nf;
             bf0 = 0;
         }
+        // Correlation launches per group when the result goes to host memory: each
+        // channel sub-range is downloaded as soon as it is done, so the downloads,
+        // the bottleneck of a host-to-host step, start a fraction of a group's
+        // correlation earlier and end as much sooner after the last one.
+        const int32_t subs = host_out ? std::min<int32_t>(XENG_PIPE_SUBGROUPS, nf) : 1;
+        const int32_t per = (nf + subs - 1) / subs;
         if (fused_ok(h, blk)) {
-            for (int64_t t0 = 0; t0 < n && e == cudaSuccess; t0 += kFusedMaxSamples) {
-                const int64_t nt = (n - t0) < kFusedMaxSamples ? (n - t0) : kFusedMaxSamples;
-                e = timed_launch(h, 1, s, [&] {
-                    return launch_fused(h, blk, n, t0, nt, bf, bf0, nf, target + f0 * nb2, (fresh && t0 == 0) ? 0 : 1,
-                                        s);
-                });
+            for (int32_t c0 = 0; c0 < nf && e == cudaSuccess; c0 += per) {
+                const int32_t nc = std::min<int32_t>(per, nf - c0);
+                for (int64_t t0 = 0; t0 < n && e == cudaSuccess; t0 += kFusedMaxSamples) {
+                    const int64_t nt = (n - t0) < kFusedMaxSamples ? (n - t0) : kFusedMaxSamples;
+                    e = timed_launch(h, 1, s, [&] {
+                        return launch_fused(h, blk, n, t0, nt, bf, bf0 + c0, nc, target + (f0 + c0) * nb2,
+                                            (fresh && t0 == 0) ? 0 : 1, s);
+                    });
+                }
+                if (e == cudaSuccess && host_out) {
+                    e = cudaEventRecord(h->ev_sub, s);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h, h->ev_sub, 0);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(host_out + (f0 + c0) * nb2, target + (f0 + c0) * nb2,
+                                            (size_t)(nc * nb2 * 4), cudaMemcpyDeviceToHost, h->d2h);
+                }
             }
+            // the last launch was the staging buffer's last reader
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
-            if (e == cudaSuccess && host_out) {
-                e = cudaStreamWaitEvent(h->d2h, h->ev_cmp[buf], 0);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(host_out + f0 * nb2, target + f0 * nb2, (size_t)(nf * nb2 * 4),
-                                        cudaMemcpyDeviceToHost, h->d2h);
-            }
             continue;
         }
         e = ensure_planes(h);
@@ -783,12 +794,7 @@ int integrate_pipelined(xeng_s *h, const uint8_t *src, bool host_in, int64_t n, 
         // the decode was the staging buffer's last reader
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_cmp[buf], s);
         if (e != cudaSuccess) break;
-        // Correlate the group in channel sub-ranges, each downloaded as soon as
-        // it is done: the downloads, the bottleneck of a host-to-host step,
-        // start a fraction of a group's correlation earlier and end as much
-        // sooner after the last one.
-        const int32_t subs = host_out ? std::min<int32_t>(XENG_PIPE_SUBGROUPS, nf) : 1;
-        const int32_t per = (nf + subs - 1) / subs;
+        // the correlation in the same channel sub-ranges, each downloaded as soon as it is done
         for (int32_t c0 = 0; c0 < nf && e == cudaSuccess; c0 += per) {
             const int32_t nc = std::min<int32_t>(per, nf - c0);
             TcArgs a;
