@@ -203,3 +203,28 @@ def test_fused_raw_int32_beyond_f32_range(fused_kernel):
     T, F, N = 70000, 1, 272
     out = correlate(np.zeros((T, F, N), np.uint8), engine=FUSED)
     assert (out[..., 0] == 128 * T).all() and (out[..., 1] == 0).all()
+
+
+@pytest.mark.parametrize("N", [272, 512])
+def test_single_pass_host_pipeline_channel_groups(N):
+    # host in, host out through the channel-group pipeline (at least two groups of
+    # about 400 KB rows, each correlated and downloaded in four channel sub-ranges)
+    # with the single-pass kernels (one pass over 128-input block pairs at 272 inputs,
+    # 256-input block pairs at 512): the same bits as device buffers, sampled channels
+    # as the oracle
+    rng = np.random.default_rng(N + 5)
+    T, F = 160, 2 * 409600 // N + 3
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    pinned = torch.from_numpy(blk).pin_memory()
+    hout = torch.zeros((F, N * (N + 1) // 2, 2), dtype=torch.int32).pin_memory()
+    eng = xe.XEngine(N, F, T)
+    for _ in range(2):  # the second call reuses the staging buffers
+        eng.correlate(pinned, hout)
+    dout = torch.empty((F, N * (N + 1) // 2, 2), dtype=torch.int32, device="cuda")
+    eng.correlate(torch.from_numpy(blk).cuda(), dout)
+    torch.cuda.synchronize()
+    eng.close()
+    got = hout.numpy().astype(np.int64)
+    assert np.array_equal(got, dout.cpu().numpy().astype(np.int64))
+    pick = [0, F // 2, F - 1]
+    assert np.array_equal(got[pick], oracle.correlate(np.ascontiguousarray(blk[:, pick])))
