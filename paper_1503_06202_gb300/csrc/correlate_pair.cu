@@ -47,7 +47,8 @@
 //   warp 1       TMEM allocation (collective for the pair); MMA issuer (leader)
 //   warps 2..9   converters: raw slot -> Im and Re planes of a plane stage, nibble sums
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
-//                quadrant, each half of the columns
+//                quadrant taking alternate 8-column chunks (so both have work on
+//                diagonal pairs, where only the columns up to a lane's input count)
 #include "tc_ptx.cuh"
 #include "xeng_internal.h"
 
@@ -71,7 +72,16 @@ constexpr int kPPlaneBytes = 4 * kPBox;     // plane stage: A_im, A_re, B_im, B_
 #endif
 constexpr int kPPlanes = XENG_PAIR_PLANE_STAGES, kPRaws = XENG_PAIR_RAW_SLOTS;
 constexpr int kPConvWarp0 = 2, kPConvWarps = 8;
-constexpr int kPEpiWarp0 = kPConvWarp0 + kPConvWarps, kPEpiWarps = 8;
+// Epilogue warps: a multiple of four (each TMEM lane quadrant gets the same
+// number, which split its 256 columns in interleaved 8-column chunks).  Measured
+// on GB300, full CHIME: 8 warps 41.7 ms; 12 or 16 (fewer registers a thread,
+// some spilled) 44.5.  Each quadrant's columns as two halves instead: 42.8.
+#ifndef XENG_PAIR_EPI_WARPS
+#define XENG_PAIR_EPI_WARPS 8
+#endif
+constexpr int kPEpiWarp0 = kPConvWarp0 + kPConvWarps, kPEpiWarps = XENG_PAIR_EPI_WARPS;
+static_assert(kPEpiWarps % 4 == 0 && kPEpiWarps >= 4, "epilogue warps: a multiple of four");
+constexpr int kPEpiPerQuad = kPEpiWarps / 4;
 constexpr int kPThreads = 32 * (kPEpiWarp0 + kPEpiWarps);
 constexpr uint32_t kPTmemCols = 512;
 constexpr int kPSums = 2 * 384 * 8;     // per item parity: (P, Q) of the CTA's A rows, then all 256 B columns
@@ -438,7 +448,7 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
     } else {
         // ---------------- epilogue (both CTAs) ----------------
         const int q = warp & 3;                          // TMEM lane quadrant this warp may access
-        const int cbeg = ((warp - kPEpiWarp0) >> 2) * 128;  // this warp's columns
+        const int cbeg = 8 * ((warp - kPEpiWarp0) >> 2);  // this warp's first column; then every 8 * kPEpiPerQuad
         const int row = q * 32 + lane;
         const uint32_t acce_leader = mapa_rank(acce, 0);
         uint32_t uses = 0;
@@ -465,7 +475,7 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
             const int2 *cs = sp + 128;  // inputs i of the 256 columns
             const int ibase = w.I2 * 256;
             if (j_warp < N) {
-                for (int c = cbeg; c < cbeg + 128; c += 8) {
+                for (int c = cbeg; c < 256; c += 8 * kPEpiPerQuad) {
                     const int i0 = ibase + c;
                     // warp-uniform: columns past the last input or past every lane's diagonal
                     if (i0 >= N || i0 > j_warp + 31) break;
