@@ -20,6 +20,14 @@
 // to be free first (ORDERED: the CTAs move through the list together and share
 // each channel's operands in L2); each CTA runs its items in job/channel order,
 // a channel's tiles row by row, by diagonal or in Z (Morton) order.
+//
+// Jobs a single-pass kernel takes (N a multiple of 16 up to the build's bound,
+// block 16-byte aligned: the kernel a handle would run for that N) skip the
+// planes: they run after the planned launches, one single-pass launch per
+// 32,768 samples of each, in the same graph -- no decode traffic, and no host
+// call, checks or launch gap between jobs.  The environment variable
+// XENG_FUSED_KERNEL (read at creation) forces a kernel for them as for a
+// handle; "none" sends every job through the planes.
 #include <algorithm>
 #include <cinttypes>
 #include <cstdio>
@@ -56,12 +64,16 @@ struct xeng_batch_s {
     SumJob *d_sjobs = nullptr;
     int n_sjobs = 0;
     int64_t sum_entries = 0;
+    std::vector<std::pair<int, int>> single;  // (job, single-pass kernel) in job order
+    SmallScratch small;                         // the N <= 256 kernel's scratch, if a job takes it
     int grid = 0;
     int64_t n_items = 0;
     double max_load = 0, mean_load = 0;
     std::vector<std::pair<int32_t *, size_t>> zero_outs;  // outputs of split jobs, cleared each run
     int *d_err = nullptr, *h_err = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;     // second branch of a run: the N <= 256 kernel's jobs
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int sticky = XENG_OK;
@@ -100,6 +112,9 @@ void free_batch(xeng_batch_s *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     cudaFree(b->planes);
     cudaFree(b->d_maps);
     cudaFree(b->d_jobs);
@@ -111,6 +126,7 @@ void free_batch(xeng_batch_s *b)
     cudaFree(b->partials);
     cudaFree(b->sums);
     cudaFree(b->d_sjobs);
+    small_scratch_free(&b->small);
     cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     cudaGetLastError();
@@ -120,15 +136,37 @@ void free_batch(xeng_batch_s *b)
 // Enqueue one run: clear split outputs, decode all jobs, correlate all items.
 cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
+    // The single-pass jobs of one kernel, in job order, on stream st.
+    cudaError_t e = cudaSuccess;
+    auto run_single = [&](bool small, cudaStream_t st) {
+        for (const auto &jk : b->single) {
+            if ((jk.second == kSingleSmall) != small) continue;
+            const xeng_job_t &jb = b->jobs[jk.first];
+            for (int64_t t0 = 0; t0 < jb.n_samples && e == cudaSuccess; t0 += kFusedMaxSamples) {
+                const int64_t nt = std::min<int64_t>(kFusedMaxSamples, jb.n_samples - t0);
+                e = launch_single_pass(jk.second, jb.block, jb.n_samples, t0, nt, jb.n_freq, jb.n_inputs, 0,
+                                       jb.n_freq, jb.out, t0 > 0 ? 1 : 0, &b->small, b->d_err, b->num_sms, st);
+            }
+        }
+    };
+    e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
+    // Two branches: the N <= 256 kernel's jobs (cooperative launches sharing one
+    // scratch, so one after another) on a side stream, the rest here; a small
+    // job's few CTAs then run beside a large job's tail.
+    if (e == cudaSuccess && b->side) {
+        e = cudaEventRecord(b->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+        run_single(true, b->side);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
+    }
     for (auto &z : b->zero_outs)
         if (e == cudaSuccess) e = cudaMemsetAsync(z.first, 0, z.second, s);
-    if (e == cudaSuccess) e = launch_decode_tma_batch(b->d_dmaps, b->d_djobs, b->n_djobs, b->dtiles, b->d_err,
-                                                      b->num_sms, s);
+    if (e == cudaSuccess && b->n_djobs > 0)
+        e = launch_decode_tma_batch(b->d_dmaps, b->d_djobs, b->n_djobs, b->dtiles, b->d_err, b->num_sms, s);
     if (e == cudaSuccess && b->n_dec > 0) e = launch_decode_batch(b->d_dec, b->n_dec, b->dec_ctas, s);
     if (e == cudaSuccess && b->n_sjobs > 0)
         e = launch_plane_sums_batch(b->d_sjobs, b->n_sjobs, b->sum_entries, b->num_sms, s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && b->grid > 0) {
         ListArgs L;
         L.maps = b->d_maps;
         L.jobs = b->d_jobs;
@@ -137,6 +175,12 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
         L.err = b->d_err;
         L.n_items = b->n_items;
         e = launch_correlate_tc_listed(L, b->grid, s);
+    }
+    run_single(false, s);
+    if (b->side) {
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join, 0);
+    } else {
+        run_single(true, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     return e;
@@ -168,8 +212,18 @@ int plan(xeng_batch_s *b)
 {
     const int n = (int)b->jobs.size();
     std::vector<int64_t> off(n), n_pad(n), t_pad(n), poff(n, -1), soff(n, -1);
+    std::vector<char> single(n, 0);
+    const int force = single_pass_force_from_env();
+    for (int j = 0; j < n; j++) {
+        const int k = single_pass_kernel(b->jobs[j].block, b->jobs[j].n_inputs, force, true);
+        if (k) {
+            single[j] = 1;
+            b->single.push_back({j, k});
+        }
+    }
     int64_t total = 0, ptotal = 0, stotal = 0;
     for (int j = 0; j < n; j++) {
+        if (single[j]) continue;
         const xeng_job_t &jb = b->jobs[j];
         n_pad[j] = round_up(jb.n_inputs, kTile);
         t_pad[j] = round_up(jb.n_samples, kTile);
@@ -200,6 +254,7 @@ int plan(xeng_batch_s *b)
     std::vector<Cand> cand;
     int64_t cta0 = 0;
     for (int j = 0; j < n; j++) {
+        if (single[j]) continue;
         const xeng_job_t &jb = b->jobs[j];
         uint8_t *pl = b->planes + off[j];
         e = encode_planes_map(&maps[j], pl, t_pad[j], (int64_t)jb.n_freq * 2 * n_pad[j]);
@@ -428,6 +483,17 @@ int xeng_batch_create(const xeng_job_t *jobs, int32_t n_jobs, const xeng_batch_o
     if (st == XENG_OK && e == cudaSuccess) e = prepare_correlate_tc_listed();
     if (st == XENG_OK && e == cudaSuccess) e = prepare_decode_tma_batch();
     if (st == XENG_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    bool small = false, other = false;
+    for (const auto &jk : b->single) (jk.second == kSingleSmall ? small : other) = true;
+    if (st == XENG_OK && e == cudaSuccess && small) {  // allocated (flags zeroed) before any capture
+        e = small_scratch_alloc(&b->small, b->num_sms, b->cap);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+    }
+    if (st == XENG_OK && e == cudaSuccess && small && (other || b->grid > 0)) {
+        e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    }
     if (st == XENG_OK && e == cudaSuccess && o.use_graph) {
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {

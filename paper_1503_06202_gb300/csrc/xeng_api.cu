@@ -32,8 +32,8 @@ struct xeng_s {
     int64_t planes_bytes = 0;
     int2 *partials = nullptr;      // raw-nibble planes: per-tile nibble sums [group_f][n_tb][n_pad]
     int2 *sums = nullptr;          // raw-nibble planes: (S, D) per input [group_f][n_pad]
-    int2 *small_ws = nullptr;      // single-pass kernel up to 256 inputs: partial blocks of split items
-    int *small_flags = nullptr;    // and the flags that publish them, with the launch count
+    SmallScratch small;            // single-pass kernel up to 256 inputs: partial blocks of split items,
+                                   // the flags that publish them and the launch count
     bool planes_raw = false;       // the last decode wrote raw-nibble planes
     int32_t group_f = 0;           // channels per decode + correlate round
     int64_t chunk_t = 0;           // samples per round
@@ -62,7 +62,7 @@ struct xeng_s {
     int64_t hist_H = 0;
     int32_t hist_S = 0;
     bool decode_tma = false;       // decode through the TMA pipeline where the block allows it
-    int fused_force = 0;           // single-pass kernel forced for every N: 0 none, else a FusedKernel
+    int fused_force = 0;           // single_pass_kernel's force: XENG_FUSED_KERNEL at handle creation
     // gate accumulator sets (xeng_set_gates): acc holds n_gates sets of [F][B][2];
     // set 0's "nothing integrated yet" flag is `fresh`, the others' gate_fresh[g]
     int32_t n_gates = 1;
@@ -181,55 +181,6 @@ cudaEvent_t take_event(xeng_s *h)
 #ifndef XENG_TC_2CTA
 #define XENG_TC_2CTA 0
 #endif
-// Up to 256 inputs: decode fused into the correlation (no planes in HBM).
-#ifndef XENG_FUSED_SMALL
-#define XENG_FUSED_SMALL 1
-#endif
-// Above 256 inputs the single pass runs either the 2-CTA pair kernel over
-// 256-input block pairs (correlate_pair.cu) or single CTAs over 128-input block
-// pairs (correlate_onepass.cu), whichever costs less by the measured time of
-// one block pair (GB300, 1024 channels x 8192 samples: 1.09-1.18 ms per 256 x
-// 256 pair, 0.36-0.39 ms per 128 x 128 pair, in units of 10 us).  The pair
-// kernel does a quarter of the MMAs per block in a quarter of the items, but
-// pads N to 256: it wins unless ceil(N / 128) is odd (one pass / pair, ms: N =
-// 384 2.35 / 3.22; 512 3.66 / 3.26; 640 5.41 / 6.75; 768 7.50 / 6.75; 896
-// 10.59 / 11.05; 1024 13.06 / 11.09; 1152 16.39 / 16.68; 1408 23.98 / 23.58;
-// 1664 33.37 / 32.98: the ratio of the two costs must lie between 3.0 and
-// 3.14).  A cost of 0 forces that kernel.
-#ifndef XENG_PAIR_COST
-#define XENG_PAIR_COST 112
-#endif
-#ifndef XENG_ONEPASS_COST
-#define XENG_ONEPASS_COST 36
-#endif
-// Above this many inputs the default engine decodes to planes first (two
-// passes) instead of the single pass: the decode pass grows with N, the
-// correlation with N^2, and the plane GEMM does a block pair about 15% faster
-// than the pair kernel's converters feed it (GB300, 8192 samples, ms single /
-// two passes: N = 2048 x 1024 channels 43.5 / 45.1, N = 3072 x 512 46.8 / 47.7,
-// N = 4096 x 256 40.8 / 40.0; a fit of both puts the crossover near 3600).
-#ifndef XENG_FUSED_MAX_N
-#define XENG_FUSED_MAX_N 3584
-#endif
-
-bool use_pair_kernel(int32_t N)
-{
-    const int64_t b2 = (N + 255) / 256, b1 = (N + 127) / 128;
-    return (int64_t)XENG_PAIR_COST * (b2 * (b2 + 1) / 2) < (int64_t)XENG_ONEPASS_COST * (b1 * (b1 + 1) / 2);
-}
-
-// The single-pass kernel of a handle: by N, unless the environment variable
-// XENG_FUSED_KERNEL (read at handle creation) is "pair" or "onepass", which
-// takes that kernel for every N it covers (all three give the same bits).
-enum FusedKernel { kFusedSmall = 1, kFusedOnepass = 2, kFusedPair = 3 };
-
-int fused_kernel(const xeng_s *h)
-{
-    if (h->fused_force) return h->fused_force;
-    if (h->N <= 256) return kFusedSmall;
-    return use_pair_kernel(h->N) ? kFusedPair : kFusedOnepass;
-}
-
 // Channel groups of the host-buffer pipeline.  More groups shorten the ramp at
 // either end (the first group's upload and the last group's download overlap
 // nothing), but each group's pitched upload copies T rows of (channels x N)
@@ -289,45 +240,23 @@ cudaError_t run_decode(xeng_s *h, const uint8_t *src, int64_t nt, int32_t F, int
 
 // The tensor engines' single-pass kernels (decode fused into the correlation)
 // apply to this block: launches of at most kFusedMaxSamples samples over all
-// channels, no planes in HBM.  The default engine takes them up to
+// channels, no planes in HBM.  The default engine takes them up to the build's
 // XENG_FUSED_MAX_N inputs, XENG_ENGINE_TENSOR_FUSED for every N they cover.
-bool fused_ok(const xeng_s *h, const uint8_t *block)
+int fused_kernel(const xeng_s *h, const uint8_t *block)
 {
-    if (h->engine != XENG_ENGINE_TENSOR && h->engine != XENG_ENGINE_TENSOR_FUSED) return false;
-    if (h->engine == XENG_ENGINE_TENSOR && h->N > XENG_FUSED_MAX_N) return false;
-    switch (fused_kernel(h)) {
-    case kFusedSmall: return XENG_FUSED_SMALL && small_ok(block, h->N);
-    case kFusedPair: return pair_ok(block, h->N);
-    default: return onepass_ok(block, h->N);
-    }
+    if (h->engine == XENG_ENGINE_TENSOR) return single_pass_kernel(block, h->N, h->fused_force, true);
+    if (h->engine == XENG_ENGINE_TENSOR_FUSED)
+        return single_pass_kernel(block, h->N, h->fused_force == kSingleNone ? 0 : h->fused_force, false);
+    return 0;
 }
+
+bool fused_ok(const xeng_s *h, const uint8_t *block) { return fused_kernel(h, block) != 0; }
 
 cudaError_t launch_fused(xeng_s *h, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                          int32_t f0, int32_t nf, int32_t *acc, int accumulate, cudaStream_t s)
 {
-    const int kernel = fused_kernel(h);
-    if (kernel == kFusedSmall) {
-        if (!h->small_ws) {
-            cudaError_t e = cudaMalloc(&h->small_ws, small_ws_bytes(h->num_sms));
-            if (e == cudaSuccess) e = cudaMalloc(&h->small_flags, small_flags_bytes(h->num_sms));
-            if (e == cudaSuccess) e = cudaMemsetAsync(h->small_flags, 0, small_flags_bytes(h->num_sms), s);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                cudaFree(h->small_ws);
-                cudaFree(h->small_flags);
-                h->small_ws = nullptr;
-                h->small_flags = nullptr;
-                return e;
-            }
-        }
-        return launch_correlate_small(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->small_ws,
-                                      h->small_flags, h->d_err, h->num_sms, s);
-    }
-    if (kernel == kFusedPair)
-        return launch_correlate_pair(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
-                                     s);
-    return launch_correlate_onepass(block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate, h->d_err, h->num_sms,
-                                    s);
+    return launch_single_pass(fused_kernel(h, block), block, T_block, t0, nt, F, h->N, f0, nf, acc, accumulate,
+                              &h->small, h->d_err, h->num_sms, s);
 }
 
 // Run one kernel launch, bracketed by events when profiling.
@@ -399,8 +328,7 @@ int xeng_create(int32_t n_inputs, int32_t n_freq, int64_t t_integ, xeng_t *out_h
     {
         const char *env = getenv("XENG_DECODE_THREADS");
         h->decode_tma = XENG_DECODE_TMA && !(env && env[0] == '1');
-        env = getenv("XENG_FUSED_KERNEL");
-        h->fused_force = !env ? 0 : !strcmp(env, "pair") ? kFusedPair : !strcmp(env, "onepass") ? kFusedOnepass : 0;
+        h->fused_force = single_pass_force_from_env();
     }
 
     // Decode buffer: rounds of (group_f channels x chunk_t samples); the
@@ -444,8 +372,7 @@ void xeng_destroy(xeng_t h)
     cudaFree(h->planes);
     cudaFree(h->partials);
     cudaFree(h->sums);
-    cudaFree(h->small_ws);
-    cudaFree(h->small_flags);
+    small_scratch_free(&h->small);
     cudaFree(h->staging);
     cudaFree(h->gidx);
     cudaFree(h->counts);

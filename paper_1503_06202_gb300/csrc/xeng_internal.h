@@ -167,6 +167,31 @@ cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t
                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
                                   cudaStream_t s);
 
+// The single-pass kernel (single_pass.cu) that takes a block of N inputs:
+// kSingleSmall (N <= 256), kSingleOnepass or kSinglePair (above, by the
+// measured cost of their block pairs), or 0 where none applies (N not a
+// multiple of 16, block not 16-byte aligned, a kernel switched off, or
+// `bounded` and N above the build's XENG_FUSED_MAX_N, where two passes are
+// faster).  `force`: 0, a kernel to take for every N it covers, or kSingleNone.
+enum SinglePass { kSingleNone = -1, kSingleSmall = 1, kSingleOnepass = 2, kSinglePair = 3 };
+// The environment variable XENG_FUSED_KERNEL: "pair", "onepass" (force that
+// kernel), "none" (no single pass for the default engine and batches), else 0.
+int single_pass_force_from_env();
+int single_pass_kernel(const uint8_t *block, int32_t N, int force, bool bounded);
+// Scratch of the N <= 256 kernel, allocated at its first launch (flags zeroed
+// on the stream) and owned by the caller.
+struct SmallScratch {
+    int2 *ws = nullptr;
+    int *flags = nullptr;
+};
+cudaError_t small_scratch_alloc(SmallScratch *sc, int num_sms, cudaStream_t s);
+void small_scratch_free(SmallScratch *sc);
+// One launch of single-pass kernel `kernel` over samples t0 .. t0 + nt - 1
+// (nt <= kFusedMaxSamples) and channels f0 .. f0 + nf - 1 of the block.
+cudaError_t launch_single_pass(int kernel, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
+                               int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, SmallScratch *sc,
+                               int *err, int num_sms, cudaStream_t s);
+
 // Beamforming (Sec. IV-C-3).  The host fills T, F, N, B, out and err; the
 // launcher fills the rest.
 struct BfArgs {

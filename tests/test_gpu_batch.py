@@ -1,7 +1,9 @@
 """Batches of uneven jobs (xeng_batch_*) against the oracle and against each
 job correlated alone: bit-exact, whatever the plan (split-K with atomics,
 LPT, round-robin or ordered assignment, row-major, diagonal or Morton tile
-order, graph or direct launches)."""
+order, graph or direct launches).  Jobs with N a multiple of 16 run through
+the single-pass kernels; with XENG_FUSED_KERNEL=none (read at creation) every
+job goes through the planes and the planned launch, and both are tested."""
 import json
 import os
 import tempfile
@@ -20,6 +22,13 @@ import paper_1503_06202_gb300 as xe  # noqa: E402
 # (T, F, N): tiny, ragged, multi-tile and a long integration that must be split
 SMALL_MIX = [(1, 1, 1), (300, 2, 5), (1000, 3, 200), (129, 1, 129), (4096, 2, 256), (64, 1, 300),
              (700, 1, 513), (70000, 1, 64)]
+
+
+@pytest.fixture(params=["single", "none"])
+def batch_path(request, monkeypatch):
+    if request.param == "none":
+        monkeypatch.setenv("XENG_FUSED_KERNEL", "none")
+    return request.param
 
 
 def make_jobs(shapes, seed=40):
@@ -43,7 +52,7 @@ def alone(block):
     return out
 
 
-def test_batch_matches_oracle_and_alone():
+def test_batch_matches_oracle_and_alone(batch_path):
     host, jobs = make_jobs(SMALL_MIX)
     b = xe.XBatch(jobs)
     b.run()
@@ -64,7 +73,7 @@ def test_batch_matches_oracle_and_alone():
                                                       (2, xe.XENG_SCHED_ORDERED, True),
                                                       (512, xe.XENG_SCHED_ORDERED, True)])
 @pytest.mark.parametrize("tile_order", [xe.XENG_TILES_ROW_MAJOR, xe.XENG_TILES_DIAGONAL, xe.XENG_TILES_MORTON])
-def test_batch_plans_agree(max_chunks, policy, graph, tile_order):
+def test_batch_plans_agree(max_chunks, policy, graph, tile_order, batch_path):
     host, jobs = make_jobs(SMALL_MIX[:7], seed=41)
     b = xe.XBatch(jobs, xe.xeng._opts(max_chunks, policy, graph, tile_order))
     assert b.info()["tile_order"] == tile_order
@@ -112,7 +121,7 @@ def test_autotune_and_cache():
     b.close()
 
 
-def test_batched_workload_64_jobs():
+def test_batched_workload_64_jobs(batch_path):
     """The 64-job workload of uneven N, F, T: every job identical alone and in the batch,
     and sampled outputs of every job equal to the oracle's."""
     recipes = synth.batched_jobs()
