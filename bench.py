@@ -494,7 +494,8 @@ def main():
     ap.add_argument("--no-dp4a", action="store_true", help="skip the plain dp4a comparison")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1.0, 1.25, 1.5])
     ap.add_argument("--serve-seconds", type=float, default=1.5)
-    ap.add_argument("--serve-max-blocks", type=int, default=32)
+    ap.add_argument("--serve-max-blocks", type=int, default=128,
+                    help="blocks a stream may contribute to one round (128 x 256 samples: one single-pass launch)")
     ap.add_argument("--serve-compute-budget", type=float, default=0.0, help="TOPS; > 0 admits streams by compute too")
     ap.add_argument("--batch-max-chunks", type=int, default=0, help="fixed batch plan instead of autotuning")
     ap.add_argument("--batch-policy", type=int, default=1)

@@ -437,7 +437,8 @@ typedef struct {
     double  busy_s;              /* first arrival -> last completed round                         */
     double  block_p50_s, block_p99_s;  /* block arrival -> its round complete                     */
     double  dump_p50_s, dump_p99_s;    /* last block of an integration -> dump available          */
-    double  gpu_decode_ms, gpu_correlate_ms;  /* summed device time of the rounds' two launches   */
+    double  gpu_decode_ms, gpu_correlate_ms;  /* summed device time of the rounds' decode and of
+                                                 their correlation (the single-pass launches too) */
     double  host_plan_ms;                     /* summed host time spent building rounds           */
     int64_t late_blocks;                      /* blocks refused with XENG_ERR_LATE                */
     int64_t short_dumps;                      /* dumps of integrations closed with blocks missing */
@@ -457,7 +458,12 @@ XENG_API int xserve_create(const xserve_opts_t *opts, xserve_t *out);
  *   max_blocks must be <= 65536).  rate_blocks_per_s is the declared arrival
  *   rate, used only by the compute budget.  Returns XENG_ERR_NOMEM when the
  *   budget (or a slot) is not available now -- retry after another stream
- *   closes -- and sets *stream_id on success.
+ *   closes -- and sets *stream_id on success.  A stream whose rounds the
+ *   single-pass kernels take (N a multiple of 16 up to 3584, block_samples a
+ *   multiple of 128 and <= 32768; unless the environment variable
+ *   XENG_FUSED_KERNEL was "none" when the server was created) reads its blocks
+ *   in place: it holds no decode planes (its HBM charge is its accumulators and
+ *   two dump buffers) and its blocks must be 16-byte aligned.
  */
 XENG_API int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t block_samples,
                                 int64_t dump_samples, double rate_blocks_per_s, int32_t *stream_id);
@@ -467,7 +473,9 @@ XENG_API int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, i
  *   memory) that arrived at arrival_s (xserve_now clock; <= 0 = now), as the
  *   block after the highest-numbered one submitted so far.  Never waits for
  *   the GPU.  The caller keeps the block unchanged until xserve_consumed
- *   reports it (blocks of a stream are consumed in queue order).
+ *   reports it (blocks of a stream are consumed in queue order).  XENG_ERR_ARG
+ *   for a block of a single-pass stream (see xserve_open_stream) that is not
+ *   16-byte aligned.
  */
 XENG_API int xserve_submit(xserve_t sv, int32_t stream_id, const uint8_t *block, double arrival_s);
 

@@ -39,6 +39,8 @@
 //   warps 2..9   converters: raw slot -> Im and Re planes of a plane stage, nibble sums
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
 //                quadrant, each half of the columns
+#include <cstring>
+
 #include "tc_ptx.cuh"
 #include "triangle_store.cuh"
 #include "xeng_internal.h"
@@ -55,7 +57,7 @@ namespace {
 #endif
 constexpr int kOKc = XENG_ONEPASS_KC;       // samples per stage
 static_assert(kOKc == 32 || kOKc == 64 || kOKc == 128, "32, 64 or 128 samples per stage");
-constexpr int kOBox = kOKc * 128;           // one raw tile or plane tile: 64 samples x 128 inputs
+constexpr int kOBox = kOKc * 128;           // one raw tile or plane tile: kOKc samples x 128 inputs
 constexpr int kORawBytes = 2 * kOBox;       // raw slot: blocks I and J
 constexpr int kOPlaneBytes = 4 * kOBox;     // plane stage: A_im, A_re, B_im, B_re
 // Ring depths (build parameters; 4 x 32 KB + 5 x 16 KB fill the shared memory).
@@ -119,6 +121,8 @@ struct OnepassArgs {
     int32_t *acc;          // [nf][N(N+1)/2][2], channel f0 + fl at fl
     int accumulate;        // 0: store, 1: add
     int *err;
+    const CUtensorMap *maps;  // null: raw_map over one block; else a map per block of spb stages,
+    int32_t spb;              // the launch's samples running through the blocks in order
 };
 
 struct OnepassItem {
@@ -218,10 +222,15 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                         ok = false;
                         break;
                     }
-                    const int z = (int)(a.t0 + (int64_t)kc * kOKc);
+                    const CUtensorMap *mp = &raw_map;
+                    int z = (int)(a.t0 + (int64_t)kc * kOKc);
+                    if (a.maps) {  // blocks of spb stages, each with its own map
+                        mp = a.maps + kc / a.spb;
+                        z = (kc % a.spb) * kOKc;
+                    }
                     mbar_expect_tx(rawf(s), diag ? kOBox : kORawBytes);
-                    tma_load_3d(slot(s), &raw_map, w.I * 128, f, z, rawf(s));
-                    if (!diag) tma_load_3d(slot(s) + kOBox, &raw_map, w.J * 128, f, z, rawf(s));
+                    tma_load_3d(slot(s), mp, w.I * 128, f, z, rawf(s));
+                    if (!diag) tma_load_3d(slot(s) + kOBox, mp, w.J * 128, f, z, rawf(s));
                     ++issued;
                     if (++s == kORaws) {
                         s = 0;
@@ -500,32 +509,47 @@ bool onepass_ok(const uint8_t *block, int32_t N)
     return N >= 16 && N <= 4096 && N % 16 == 0 && (reinterpret_cast<uintptr_t>(block) & 15) == 0;
 }
 
+cudaError_t encode_onepass_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x kOKc
+    // samples with a 128-byte swizzle (the MN-major operand layout); inputs past N and
+    // samples past the block read as zero bytes, nibbles 0 that add nothing (the
+    // converters zero the samples past the launch; rows and columns past N are never
+    // written)
+    cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T_block};
+    cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};
+    cuuint32_t box[3] = {128, 1, (cuuint32_t)kOKc}, estr[3] = {1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+int onepass_stage_samples() { return kOKc; }
+
 cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                                      int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
-                                     int num_sms, cudaStream_t s)
+                                     int num_sms, cudaStream_t s,
+                                     const CUtensorMap *maps, int32_t spb)
 {
     if (nf <= 0 || nt <= 0) return cudaSuccess;
-    if (!onepass_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
+    if (!onepass_ok(maps ? nullptr : block, N) || (maps && (spb < 1 || t0 != 0)) || nt > kFusedMaxSamples ||
+        t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
         f0 < 0 || f0 + nf > F || num_sms < 1 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0)
         return cudaErrorInvalidValue;
     const int32_t nb = (N + 127) / 128;
     const int64_t n_items = (int64_t)nf * (nb * (nb + 1) / 2);
     if (n_items > 2147483647LL) return cudaErrorInvalidValue;
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc) return cudaErrorNotSupported;
-    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x 64
-    // samples with a 128-byte swizzle (the MN-major operand layout); inputs past N and
-    // samples past the block read as zero bytes, nibbles 0 that add nothing (the
-    // converters zero the samples past the launch; rows and columns past N are never
-    // written)
     CUtensorMap map;
-    cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T_block};
-    cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};
-    cuuint32_t box[3] = {128, 1, (cuuint32_t)kOKc}, estr[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    if (maps) {
+        memset(&map, 0, sizeof map);  // not read: the stages take the blocks' maps
+    } else {
+        cudaError_t e0 = encode_onepass_map(&map, block, T_block, F, N);
+        if (e0 != cudaSuccess) return e0;
+    }
     cudaError_t e =
         cudaFuncSetAttribute(correlate_onepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOSmem);
     if (e != cudaSuccess) return e;
@@ -542,6 +566,8 @@ cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int6
     a.acc = acc;
     a.accumulate = accumulate;
     a.err = err;
+    a.maps = maps;
+    a.spb = spb;
     const int grid = n_items < num_sms ? (int)n_items : num_sms;
     correlate_onepass_kernel<<<grid, kOThreads, kOSmem, s>>>(map, a);
     return cudaGetLastError();

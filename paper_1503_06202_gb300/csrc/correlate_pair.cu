@@ -49,6 +49,8 @@
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
 //                quadrant taking alternate 8-column chunks (so both have work on
 //                diagonal pairs, where only the columns up to a lane's input count)
+#include <cstring>
+
 #include "tc_ptx.cuh"
 #include "xeng_internal.h"
 
@@ -121,6 +123,8 @@ struct PairArgs {
     int32_t *acc;            // [nf][N(N+1)/2][2], channel f0 + fl at fl
     int accumulate;          // 0: store, 1: add
     int *err;
+    const CUtensorMap *maps;  // null: raw_map over one block; else a map per block of spb stages,
+    int32_t spb;              // the launch's samples running through the blocks in order
 };
 
 struct PairItem {
@@ -224,10 +228,15 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                         ok = false;
                         break;
                     }
-                    const int z = (int)(a.t0 + (int64_t)kc * kPKc);
+                    const CUtensorMap *mp = &raw_map;
+                    int z = (int)(a.t0 + (int64_t)kc * kPKc);
+                    if (a.maps) {  // blocks of spb stages, each with its own map
+                        mp = a.maps + kc / a.spb;
+                        z = (kc % a.spb) * kPKc;
+                    }
                     mbar_expect_tx(rawf(s), diag ? kPBox : kPRawBytes);
-                    tma_load_3d(slot(s), &raw_map, xa, f, z, rawf(s));
-                    if (!diag) tma_load_3d(slot(s) + kPBox, &raw_map, xb, f, z, rawf(s));
+                    tma_load_3d(slot(s), mp, xa, f, z, rawf(s));
+                    if (!diag) tma_load_3d(slot(s) + kPBox, mp, xb, f, z, rawf(s));
                     ++issued;
                     if (++s == kPRaws) {
                         s = 0;
@@ -541,17 +550,8 @@ bool pair_ok(const uint8_t *block, int32_t N)
     return N >= 16 && N <= 4096 && N % 16 == 0 && (reinterpret_cast<uintptr_t>(block) & 15) == 0;
 }
 
-cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
-                                  int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
-                                  cudaStream_t s)
+cudaError_t encode_pair_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N)
 {
-    if (nf <= 0 || nt <= 0) return cudaSuccess;
-    if (!pair_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
-        f0 < 0 || f0 + nf > F || num_sms < 2 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0)
-        return cudaErrorInvalidValue;
-    const int32_t nt2 = (N + 255) / 256;
-    const int64_t n_items = (int64_t)nf * (nt2 * (nt2 + 1) / 2);
-    if (n_items > 2147483647LL) return cudaErrorInvalidValue;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x kPKc
@@ -559,14 +559,38 @@ cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t
     // samples past the block read as zero bytes, nibbles 0 that add nothing (the
     // converters zero the samples past the launch; rows and columns past N are never
     // written)
-    CUtensorMap map;
     cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T_block};
     cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};
     cuuint32_t box[3] = {128, 1, (cuuint32_t)kPKc}, estr[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+int pair_stage_samples() { return kPKc; }
+
+cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
+                                  int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
+                                  cudaStream_t s,
+                                  const CUtensorMap *maps, int32_t spb)
+{
+    if (nf <= 0 || nt <= 0) return cudaSuccess;
+    if (!pair_ok(maps ? nullptr : block, N) || (maps && (spb < 1 || t0 != 0)) || nt > kFusedMaxSamples ||
+        t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
+        f0 < 0 || f0 + nf > F || num_sms < 2 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0)
+        return cudaErrorInvalidValue;
+    const int32_t nt2 = (N + 255) / 256;
+    const int64_t n_items = (int64_t)nf * (nt2 * (nt2 + 1) / 2);
+    if (n_items > 2147483647LL) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    if (maps) {
+        memset(&map, 0, sizeof map);  // not read: the stages take the blocks' maps
+    } else {
+        cudaError_t e0 = encode_pair_map(&map, block, T_block, F, N);
+        if (e0 != cudaSuccess) return e0;
+    }
     cudaError_t e = cudaFuncSetAttribute(correlate_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
     if (e != cudaSuccess) return e;
     PairArgs a;
@@ -582,6 +606,8 @@ cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t
     a.acc = acc;
     a.accumulate = accumulate;
     a.err = err;
+    a.maps = maps;
+    a.spb = spb;
     const int64_t clusters = n_items < num_sms / 2 ? n_items : num_sms / 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);

@@ -60,6 +60,8 @@
 //   warps 2..9   converters: raw slot -> Re and Im planes of a plane stage, nibble sums
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, one warp per TMEM lane
 //                quadrant and block of the item
+#include <cstring>
+
 #include "tc_ptx.cuh"
 #include "triangle_store.cuh"
 #include "xeng_internal.h"
@@ -135,6 +137,8 @@ struct SmallArgs {
     int *epoch;            // [0]: launches so far on these flags (this launch's epoch is [0] + 1);
                            // [1]: CTAs of this launch finished
     int *err;
+    const CUtensorMap *maps;  // null: raw_map over one block; else a map per block of spb stages,
+    int32_t spb;              // the launch's samples running through the blocks in order
 };
 
 // A CTA's work: the stages [lo, hi) of the launch's sequence (item-major),
@@ -281,10 +285,15 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                         ok = false;
                         break;
                     }
-                    const int z = (int)(a.t0 + (int64_t)kc * kSKc);
+                    const CUtensorMap *mp = &raw_map;
+                    int z = (int)(a.t0 + (int64_t)kc * kSKc);
+                    if (a.maps) {  // blocks of spb stages, each with its own map
+                        mp = a.maps + kc / a.spb;
+                        z = (kc % a.spb) * kSKc;
+                    }
                     mbar_expect_tx(rawf(s), kSRawBytes);
-                    tma_load_3d(slot(s), &raw_map, xX, fX, z, rawf(s));
-                    tma_load_3d(slot(s) + kSBox, &raw_map, xY, fY, z, rawf(s));
+                    tma_load_3d(slot(s), mp, xX, fX, z, rawf(s));
+                    tma_load_3d(slot(s) + kSBox, mp, xY, fY, z, rawf(s));
                     ++issued;
                     if (++s == kSRaws) {
                         s = 0;
@@ -643,31 +652,46 @@ bool small_ok(const uint8_t *block, int32_t N)
 size_t small_ws_bytes(int num_sms) { return (size_t)num_sms * 2 * 16 * 128 * 8 * sizeof(int2); }
 size_t small_flags_bytes(int num_sms) { return (size_t)(num_sms + 2) * sizeof(int); }
 
-cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
-                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
-                                   int *err, int num_sms, cudaStream_t s)
+cudaError_t encode_small_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N)
 {
-    if (nf <= 0 || nt <= 0) return cudaSuccess;
-    if (!small_ok(block, N) || nt > kFusedMaxSamples || t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
-        f0 < 0 || f0 + nf > F || num_sms < 1 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0 || !ws || !flags)
-        return cudaErrorInvalidValue;
-    const int64_t n_items = N > 128 ? (int64_t)nf + (nf + 1) / 2 : (int64_t)(nf + 1) / 2;
-    const int n_k = (int)((nt + kSKc - 1) / kSKc);
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
-    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x 64
+    // raw block: dims (input, channel, sample), boxes of 128 inputs x 1 channel x kSKc
     // samples with a 128-byte swizzle (the MN-major operand layout); inputs past N and
     // samples past the block read as zero bytes, nibbles 0 that add nothing (the
     // converters zero the samples past the launch; rows and columns past N are never
     // written)
-    CUtensorMap map;
     cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)F, (cuuint64_t)T_block};
     cuuint64_t strides[2] = {(cuuint64_t)N, (cuuint64_t)N * F};
     cuuint32_t box[3] = {128, 1, (cuuint32_t)kSKc}, estr[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void *)block, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+int small_stage_samples() { return kSKc; }
+
+cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
+                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
+                                   int *err, int num_sms, cudaStream_t s,
+                                   const CUtensorMap *maps, int32_t spb)
+{
+    if (nf <= 0 || nt <= 0) return cudaSuccess;
+    if (!small_ok(maps ? nullptr : block, N) || (maps && (spb < 1 || t0 != 0)) || nt > kFusedMaxSamples ||
+        t0 < 0 || t0 + nt > T_block || T_block > 2147483647LL ||
+        f0 < 0 || f0 + nf > F || num_sms < 1 || (reinterpret_cast<uintptr_t>(acc) & 7) != 0 || !ws || !flags)
+        return cudaErrorInvalidValue;
+    const int64_t n_items = N > 128 ? (int64_t)nf + (nf + 1) / 2 : (int64_t)(nf + 1) / 2;
+    const int n_k = (int)((nt + kSKc - 1) / kSKc);
+    CUtensorMap map;
+    if (maps) {
+        memset(&map, 0, sizeof map);  // not read: the stages take the blocks' maps
+    } else {
+        cudaError_t e0 = encode_small_map(&map, block, T_block, F, N);
+        if (e0 != cudaSuccess) return e0;
+    }
     auto kern = accumulate ? correlate_small_kernel<true> : correlate_small_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSSmem);
     if (e != cudaSuccess) return e;
@@ -687,6 +711,8 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
     a.flags = flags;
     a.epoch = flags + num_sms;
     a.err = err;
+    a.maps = maps;
+    a.spb = spb;
     // every CTA gets at least kSMinPiece stages (a piece's epilogue and partial
     // cost about as much as a few stages of MMAs), at most one CTA per SM
     int64_t grid = a.total / kSMinPiece;

@@ -10,13 +10,18 @@
 //
 // A worker thread runs the loop.  Each round it takes, from every stream with
 // queued blocks, up to `max_blocks` of them (never across a dump boundary) --
-// blocks that arrived while earlier rounds were on the GPU join the next round
-// -- decodes them with one persistent TMA launch (per-block tensor maps; a
-// thread-per-row launch only for blocks TMA cannot address) into the streams'
-// plane slices and
-// correlates all streams' tiles with one persistent tensor-core launch that
-// adds into each stream's accumulators (or stores, for the first round of an
-// integration).  A stream whose integration reaches `dump_samples` gets a
+// blocks that arrived while earlier rounds were on the GPU join the next round.
+// A stream whose blocks a single-pass kernel takes (N a multiple of 16 up to the
+// build's bound, every block 16-byte aligned, blocks a whole number of the
+// kernel's stages and at most 32,768 samples) gets single-pass launches that
+// read its blocks where they are, one tensor map per block, and add into its
+// accumulators (or store, for the first round of an integration): no planes.
+// The other streams' blocks are decoded with one persistent TMA launch
+// (per-block tensor maps; a thread-per-row launch only for blocks TMA cannot
+// address) into their plane slices and correlated with one persistent
+// tensor-core launch over all of their tiles.  The environment variable
+// XENG_FUSED_KERNEL (read at creation) forces a single-pass kernel as for a
+// handle; "none" sends every stream through the planes.  A stream whose integration reaches `dump_samples` gets a
 // device copy of its accumulators queued into a free dump buffer right after
 // the round, and starts a fresh integration.  Two rounds may be in flight; the
 // worker polls their events, marks blocks consumed, publishes dumps and
@@ -75,6 +80,7 @@ struct SStream {
     int id = -1;
     int32_t N = 0, F = 0;
     int64_t dump_samples = 0, block_samples = 0, bs_pad = 0;
+    int single = 0;                  // single-pass kernel of the stream's rounds (no planes), else 0
     int64_t n_pad = 0;
     double demand_tops = 0;
     int64_t bytes = 0;               // charged to the HBM budget
@@ -102,6 +108,10 @@ struct Round {
     cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;  // timing: round start, decode done, correlate done
     int slot = 0;
     struct Part { int stream; int nblocks; std::vector<double> arrivals; int dump_slot; };
+    // streams of the round on the single-pass kernels: kernel, first map in the
+    // slot's table, blocks, and whether the round stores (first of an integration)
+    struct Single { int stream; int kernel; int64_t map0; int nblocks; bool store; };
+    std::vector<Single> singles;
     std::vector<Part> parts;
     double useful_ops = 0;
 };
@@ -127,6 +137,9 @@ struct xserve_s {
     JobDesc *d_jobs[2] = {nullptr, nullptr}, *h_jobs[2] = {nullptr, nullptr};
     DecodeJob *d_dec[2] = {nullptr, nullptr}, *h_dec[2] = {nullptr, nullptr};  // blocks TMA cannot address
     CUtensorMap *d_dmaps[2] = {nullptr, nullptr}, *h_dmaps[2] = {nullptr, nullptr};  // TMA decode: 2 maps per block
+    CUtensorMap *d_smaps[2] = {nullptr, nullptr}, *h_smaps[2] = {nullptr, nullptr};  // single pass: a map per block
+    SmallScratch small;     // the N <= 256 single-pass kernel's scratch
+    int single_force = 0;   // XENG_FUSED_KERNEL at creation
     DecTmaJob *d_djobs[2] = {nullptr, nullptr}, *h_djobs[2] = {nullptr, nullptr};
     SumJob *d_sjobs[2] = {nullptr, nullptr}, *h_sjobs[2] = {nullptr, nullptr};  // raw-nibble streams of a round
     int *d_err = nullptr, *h_err = nullptr;
@@ -147,6 +160,7 @@ namespace {
 int64_t stream_bytes(const SStream &st, int max_blocks)
 {
     const int64_t acc = (int64_t)st.F * n_baselines(st.N) * 8;
+    if (st.single) return 3 * acc;  // accumulators and two dump buffers: its rounds read the blocks in place
     const int64_t planes = (int64_t)st.F * 2 * st.n_pad * (st.bs_pad * max_blocks);
     const int64_t part = (int64_t)st.F * (st.bs_pad * max_blocks / kTile) * st.n_pad * 8;
     const int64_t sums = (int64_t)st.F * st.n_pad * 8;
@@ -294,7 +308,7 @@ bool launch_round(xserve_s *sv)
 
     Round r;
     r.slot = slot;
-    int64_t n_items = 0, n_dec = 0, dec_ctas = 0, n_djobs = 0, dtiles = 0, n_sjobs = 0, sum_entries = 0;
+    int64_t n_items = 0, n_dec = 0, dec_ctas = 0, n_djobs = 0, dtiles = 0, n_sjobs = 0, sum_entries = 0, n_smaps = 0;
     int jobi = 0;
     for (auto &pk : picks) {
         SStream &st = sv->streams[pk.stream];
@@ -319,6 +333,52 @@ bool launch_round(xserve_s *sv)
             st.integrated = 0;
             st.fresh = true;
             st.last_arrival = 0;
+            r.parts.push_back(std::move(part));
+            continue;
+        }
+        // a stream of the single-pass kernels: its blocks read where they are
+        const int sk = st.single;
+        if (sk) {
+            Round::Part part;
+            part.stream = pk.stream;
+            part.nblocks = pk.nblocks;
+            part.dump_slot = -1;
+            Round::Single sg;
+            sg.stream = pk.stream;
+            sg.kernel = sk;
+            sg.map0 = n_smaps;
+            sg.nblocks = pk.nblocks;
+            sg.store = st.fresh;
+            for (int b = 0; b < pk.nblocks; b++) {
+                QBlock qb = st.queue.front();
+                st.queue.pop_front();
+                part.arrivals.push_back(qb.arrival);
+                st.last_arrival = std::max(st.last_arrival, qb.arrival);
+                if (encode_single_pass_map(sk, sv->h_smaps[slot] + n_smaps++, qb.ptr, st.block_samples, st.F, st.N) !=
+                    cudaSuccess) {
+                    sv->sticky = XENG_ERR_CUDA;  // never launch with a descriptor that failed to encode
+                    return false;
+                }
+            }
+            r.singles.push_back(sg);
+            r.useful_ops += 8.0 * (double)(pk.nblocks * st.block_samples) * st.F * (double)n_baselines(st.N);
+            st.fresh = false;
+            st.integrated += pk.nblocks * st.block_samples;
+            st.inflight += pk.nblocks;
+            if (st.integrated == st.dump_samples) {
+                const int ds = st.dump[0].busy ? 1 : 0;
+                DumpSlot &d = st.dump[ds];
+                d.busy = true;
+                d.ready = false;
+                d.samples = st.integrated;
+                d.blocks = st.integrated / st.block_samples;
+                d.last_arrival = st.last_arrival;
+                d.seq = st.cur_integ++;
+                part.dump_slot = ds;
+                st.integrated = 0;
+                st.fresh = true;
+                st.last_arrival = 0;
+            }
             r.parts.push_back(std::move(part));
             continue;
         }
@@ -452,6 +512,9 @@ bool launch_round(xserve_s *sv)
         e = cudaMemcpyAsync(sv->d_jobs[slot], sv->h_jobs[slot], jobi * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_items > 0)
         e = cudaMemcpyAsync(sv->d_items[slot], sv->h_items[slot], n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_smaps > 0)
+        e = cudaMemcpyAsync(sv->d_smaps[slot], sv->h_smaps[slot], n_smaps * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                            s);
     if (e == cudaSuccess && r.t0) e = cudaEventRecord(r.t0, s);
     if (e == cudaSuccess)
         e = launch_decode_tma_batch(sv->d_dmaps[slot], sv->d_djobs[slot], (int)n_djobs, dtiles, sv->d_err, sv->num_sms, s);
@@ -468,6 +531,20 @@ bool launch_round(xserve_s *sv)
         L.err = sv->d_err;
         L.n_items = n_items;
         e = launch_correlate_tc_listed(L, (int)std::min<int64_t>(sv->num_sms, n_items), s);
+    }
+    for (const auto &sg : r.singles) {
+        // launches of at most kFusedMaxSamples samples (whole blocks), the first
+        // storing when the round opens an integration
+        const SStream &st = sv->streams[sg.stream];
+        const int per = (int)(kFusedMaxSamples / st.block_samples);
+        const int spb = (int)(st.block_samples / single_pass_stage(sg.kernel));
+        for (int b0 = 0; b0 < sg.nblocks && e == cudaSuccess; b0 += per) {
+            const int nb = std::min(per, sg.nblocks - b0);
+            const int64_t nt = (int64_t)nb * st.block_samples;
+            e = launch_single_pass(sg.kernel, nullptr, nt, 0, nt, st.F, st.N, 0, st.F, st.acc,
+                                   (sg.store && b0 == 0) ? 0 : 1, &sv->small, sv->d_err, sv->num_sms, s,
+                                   sv->d_smaps[slot] + sg.map0 + b0, spb);
+        }
     }
     if (e == cudaSuccess && r.t2) e = cudaEventRecord(r.t2, s);
     for (auto &p : r.parts) {
@@ -583,7 +660,11 @@ int xserve_create(const xserve_opts_t *opts, xserve_t *out)
             e = cudaMallocHost(&sv->h_djobs[k], (size_t)o.max_streams * o.max_blocks * sizeof(DecTmaJob));
         if (e == cudaSuccess) e = cudaMalloc(&sv->d_sjobs[k], (size_t)o.max_streams * sizeof(SumJob));
         if (e == cudaSuccess) e = cudaMallocHost(&sv->h_sjobs[k], (size_t)o.max_streams * sizeof(SumJob));
+        if (e == cudaSuccess) e = cudaMalloc(&sv->d_smaps[k], (size_t)o.max_streams * o.max_blocks * sizeof(CUtensorMap));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sv->h_smaps[k], (size_t)o.max_streams * o.max_blocks * sizeof(CUtensorMap));
     }
+    sv->single_force = single_pass_force_from_env();
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(sv->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&sv->h_err, sizeof(int));
@@ -625,6 +706,12 @@ int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t bl
     probe.F = n_freq;
     probe.n_pad = n_pad;
     probe.bs_pad = bs_pad;
+    // a shape a single-pass kernel takes (blocks a whole number of its stages, at
+    // most a launch's samples; 16-byte aligned blocks are then required)
+    if (block_samples <= kFusedMaxSamples) {
+        const int k = single_pass_kernel(nullptr, n_inputs, sv->single_force, true);
+        if (k && block_samples % single_pass_stage(k) == 0) probe.single = k;
+    }
     const int64_t bytes = stream_bytes(probe, sv->opts.max_blocks);
     const double demand = rate_blocks_per_s * 8.0 * block_samples * n_freq * (double)n_baselines(n_inputs) / 1e12;
     if (sv->used_bytes + bytes > sv->opts.hbm_budget_bytes ||
@@ -641,6 +728,7 @@ int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t bl
     st.bs_pad = bs_pad;
     st.dump_samples = dump_samples;
     st.n_pad = n_pad;
+    st.single = probe.single;
     st.demand_tops = demand;
     st.bytes = bytes;
     st.seen.assign((size_t)(dump_samples / block_samples), 0);
@@ -649,11 +737,11 @@ int xserve_open_stream(xserve_t sv, int32_t n_inputs, int32_t n_freq, int64_t bl
     cudaError_t e = cudaMalloc(&st.acc, acc);
     if (e == cudaSuccess) e = cudaMalloc(&st.dump[0].buf, acc);
     if (e == cudaSuccess) e = cudaMalloc(&st.dump[1].buf, acc);
-    if (e == cudaSuccess) e = cudaMalloc(&st.planes[0], planes);
-    if (e == cudaSuccess) e = cudaMalloc(&st.planes[1], planes);
+    if (e == cudaSuccess && !st.single) e = cudaMalloc(&st.planes[0], planes);
+    if (e == cudaSuccess && !st.single) e = cudaMalloc(&st.planes[1], planes);
     const size_t part = (size_t)n_freq * (bs_pad * sv->opts.max_blocks / kTile) * n_pad * sizeof(int2);
     const size_t sums = (size_t)n_freq * n_pad * sizeof(int2);
-    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    for (int k = 0; k < 2 && e == cudaSuccess && !st.single; k++) {
         e = cudaMalloc(&st.partials[k], part);
         if (e == cudaSuccess) e = cudaMalloc(&st.sums[k], sums);
     }
@@ -675,6 +763,7 @@ namespace {
 // Queue block number `seq` of the stream (caller holds the lock).
 int submit_locked(xserve_s *sv, SStream &st, const uint8_t *block, int64_t seq, double t)
 {
+    if (st.single && (reinterpret_cast<uintptr_t>(block) & 15) != 0) return XENG_ERR_ARG;  // read by TMA in place
     const int64_t bpd = st.blocks_per_dump();
     const int64_t integ = seq / bpd;
     if (integ < st.top_integ) {  // a later integration's block has closed this one
@@ -876,7 +965,10 @@ void xserve_destroy(xserve_t sv)
         cudaFreeHost(sv->h_djobs[k]);
         cudaFree(sv->d_sjobs[k]);
         cudaFreeHost(sv->h_sjobs[k]);
+        cudaFree(sv->d_smaps[k]);
+        cudaFreeHost(sv->h_smaps[k]);
     }
+    small_scratch_free(&sv->small);
     cudaFree(sv->d_err);
     if (sv->h_err) cudaFreeHost(sv->h_err);
     for (auto e : sv->free_events) cudaEventDestroy(e);

@@ -94,19 +94,38 @@ void small_scratch_free(SmallScratch *sc)
 
 cudaError_t launch_single_pass(int kernel, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                                int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, SmallScratch *sc,
-                               int *err, int num_sms, cudaStream_t s)
+                               int *err, int num_sms, cudaStream_t s, const CUtensorMap *maps, int32_t spb)
 {
     if (kernel == kSingleSmall) {
         cudaError_t e = small_scratch_alloc(sc, num_sms, s);
         if (e != cudaSuccess) return e;
         return launch_correlate_small(block, T_block, t0, nt, F, N, f0, nf, acc, accumulate, sc->ws, sc->flags, err,
-                                      num_sms, s);
+                                      num_sms, s, maps, spb);
     }
     if (kernel == kSinglePair)
-        return launch_correlate_pair(block, T_block, t0, nt, F, N, f0, nf, acc, accumulate, err, num_sms, s);
+        return launch_correlate_pair(block, T_block, t0, nt, F, N, f0, nf, acc, accumulate, err, num_sms, s, maps,
+                                     spb);
     if (kernel == kSingleOnepass)
-        return launch_correlate_onepass(block, T_block, t0, nt, F, N, f0, nf, acc, accumulate, err, num_sms, s);
+        return launch_correlate_onepass(block, T_block, t0, nt, F, N, f0, nf, acc, accumulate, err, num_sms, s, maps,
+                                        spb);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t encode_single_pass_map(int kernel, CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F,
+                                   int32_t N)
+{
+    if (kernel == kSingleSmall) return encode_small_map(map, block, T_block, F, N);
+    if (kernel == kSinglePair) return encode_pair_map(map, block, T_block, F, N);
+    if (kernel == kSingleOnepass) return encode_onepass_map(map, block, T_block, F, N);
+    return cudaErrorInvalidValue;
+}
+
+int single_pass_stage(int kernel)
+{
+    if (kernel == kSingleSmall) return small_stage_samples();
+    if (kernel == kSinglePair) return pair_stage_samples();
+    if (kernel == kSingleOnepass) return onepass_stage_samples();
+    return 0;
 }
 
 }  // namespace xeng

@@ -147,7 +147,12 @@ size_t small_ws_bytes(int num_sms);
 size_t small_flags_bytes(int num_sms);
 cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
                                    int32_t f0, int32_t nf, int32_t *acc, int accumulate, int2 *ws, int *flags,
-                                   int *err, int num_sms, cudaStream_t s);
+                                   int *err, int num_sms, cudaStream_t s,
+                                   const CUtensorMap *maps = nullptr, int32_t spb = 0);
+// The raw-block tensor map launch_correlate_small uses (3D: input, channel, sample;
+// its stage's box, 128-byte swizzle), and its stage in samples.
+cudaError_t encode_small_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N);
+int small_stage_samples();
 
 // One pass over the raw bytes for N a multiple of 16 up to 4096 (block 16-byte
 // aligned; used above 256 inputs): single CTAs over every channel's
@@ -156,7 +161,12 @@ cudaError_t launch_correlate_small(const uint8_t *block, int64_t T_block, int64_
 bool onepass_ok(const uint8_t *block, int32_t N);
 cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                                      int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err,
-                                     int num_sms, cudaStream_t s);
+                                     int num_sms, cudaStream_t s,
+                                     const CUtensorMap *maps = nullptr, int32_t spb = 0);
+// The raw-block tensor map launch_correlate_onepass uses (3D: input, channel, sample;
+// its stage's box, 128-byte swizzle), and its stage in samples.
+cudaError_t encode_onepass_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N);
+int onepass_stage_samples();
 
 // Decode fused into the correlation for 16 <= N <= 4096 (N % 16 == 0, block
 // 16-byte aligned), as launch_correlate_small: 2-CTA clusters over every
@@ -165,7 +175,12 @@ cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int6
 bool pair_ok(const uint8_t *block, int32_t N);
 cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F, int32_t N,
                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
-                                  cudaStream_t s);
+                                  cudaStream_t s,
+                                  const CUtensorMap *maps = nullptr, int32_t spb = 0);
+// The raw-block tensor map launch_correlate_pair uses (3D: input, channel, sample;
+// its stage's box, 128-byte swizzle), and its stage in samples.
+cudaError_t encode_pair_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N);
+int pair_stage_samples();
 
 // The single-pass kernel (single_pass.cu) that takes a block of N inputs:
 // kSingleSmall (N <= 256), kSingleOnepass or kSinglePair (above, by the
@@ -187,10 +202,18 @@ struct SmallScratch {
 cudaError_t small_scratch_alloc(SmallScratch *sc, int num_sms, cudaStream_t s);
 void small_scratch_free(SmallScratch *sc);
 // One launch of single-pass kernel `kernel` over samples t0 .. t0 + nt - 1
-// (nt <= kFusedMaxSamples) and channels f0 .. f0 + nf - 1 of the block.
+// (nt <= kFusedMaxSamples) and channels f0 .. f0 + nf - 1 of the block.  With
+// `maps` (device memory, 64-byte aligned), the samples come instead from
+// consecutive blocks of spb stages each, block k through maps[k] (made by
+// encode_single_pass_map); block is then unused and t0 must be 0.
 cudaError_t launch_single_pass(int kernel, const uint8_t *block, int64_t T_block, int64_t t0, int64_t nt, int32_t F,
                                int32_t N, int32_t f0, int32_t nf, int32_t *acc, int accumulate, SmallScratch *sc,
-                               int *err, int num_sms, cudaStream_t s);
+                               int *err, int num_sms, cudaStream_t s, const CUtensorMap *maps = nullptr,
+                               int32_t spb = 0);
+// A block's tensor map for `kernel`'s stage tables, and the kernel's stage.
+cudaError_t encode_single_pass_map(int kernel, CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F,
+                                   int32_t N);
+int single_pass_stage(int kernel);
 
 // Beamforming (Sec. IV-C-3).  The host fills T, F, N, B, out and err; the
 // launcher fills the rest.

@@ -1,6 +1,9 @@
 """The streaming service (xserve_*): every stream's dumps bit-identical alone
 and in the mix and equal to the oracle; admission by HBM budget with later
-re-admission; dump back-pressure; argument checks."""
+re-admission; dump back-pressure; argument checks.  Streams with N a multiple
+of 16 run on the single-pass kernels (read their blocks where they are); with
+XENG_FUSED_KERNEL=none (read at creation) every stream goes through the planes,
+and the mix tests run both ways."""
 import random
 import time
 
@@ -16,7 +19,14 @@ import paper_1503_06202_gb300 as xe  # noqa: E402
 
 BS = 256             # samples per block
 PER_DUMP = 6         # blocks per integration
-STREAMS = [(64, 2), (130, 1), (256, 3)]  # (N, F)
+STREAMS = [(64, 2), (130, 1), (256, 3), (512, 1)]  # (N, F)
+
+
+@pytest.fixture(params=["single", "none"])
+def serve_path(request, monkeypatch):
+    if request.param == "none":
+        monkeypatch.setenv("XENG_FUSED_KERNEL", "none")
+    return request.param
 
 
 def make_blocks(N, F, n, seed):
@@ -64,7 +74,7 @@ def run_server(streams, schedule, max_blocks=4, jitter=True):
     return [[d for _, d in sorted(ds, key=lambda x: x[0])] for ds in dumps]
 
 
-def test_serve_alone_and_in_the_mix_match_the_oracle():
+def test_serve_alone_and_in_the_mix_match_the_oracle(serve_path):
     n_int = 2
     data = []
     for k, (N, F) in enumerate(STREAMS):
@@ -88,8 +98,9 @@ def test_serve_alone_and_in_the_mix_match_the_oracle():
             assert np.array_equal(mixed[k][i].astype(np.int64), want[k][i]), ("mix", k, i)
 
 
-def test_serve_single_block_rounds_and_partial_last_round():
-    N, F = 100, 2
+@pytest.mark.parametrize("N", [100, 96])
+def test_serve_single_block_rounds_and_partial_last_round(N):
+    F = 2
     host, dev = make_blocks(N, F, PER_DUMP, seed=9)
     got = run_server([(N, F, dev)], [0] * PER_DUMP, max_blocks=1, jitter=False)[0]
     assert np.array_equal(got[0].astype(np.int64), oracle.correlate(np.concatenate(host, axis=0)))
@@ -97,11 +108,13 @@ def test_serve_single_block_rounds_and_partial_last_round():
     assert np.array_equal(got[0].astype(np.int64), oracle.correlate(np.concatenate(host, axis=0)))
 
 
-def test_serve_admission_by_hbm_budget():
+def test_serve_admission_by_hbm_budget(serve_path):
+    # the HBM charge of a stream: accumulators and two dump buffers, plus two
+    # decode-plane slices on the planes path
     N, F = 256, 4
     acc = F * N * (N + 1) // 2 * 8
     planes = F * 2 * 256 * BS * 4
-    per_stream = 3 * acc + 2 * planes
+    per_stream = 3 * acc + (2 * planes if serve_path == "none" else 0)
     rc, sv = xe.xserve_create(hbm_budget_bytes=2 * per_stream + per_stream // 2, max_blocks=4, max_streams=8)
     assert rc == xe.XENG_OK
     rc, a = xe.xserve_open_stream(sv, N, F, BS, BS * 4)
@@ -225,7 +238,7 @@ def interleave(per_stream, seed):
     return out
 
 
-def test_serve_lost_and_late_blocks_in_a_mix():
+def test_serve_lost_and_late_blocks_in_a_mix(serve_path):
     # Sec. IV-A: lost data must not stop the integration of the rest.  Stream A
     # loses blocks 2 and 11 (one in each integration; the last integration is
     # closed by a flush); stream B's block 5 arrives after block 6 has opened its
@@ -233,7 +246,7 @@ def test_serve_lost_and_late_blocks_in_a_mix():
     # exactly its alone result.
     n = 2 * PER_DUMP
     data = []
-    for k, (N, F) in enumerate(STREAMS):
+    for k, (N, F) in enumerate(STREAMS[:3]):
         host, dev = make_blocks(N, F, n, seed=300 + k)
         data.append((N, F, host, dev))
     ev_a = [(0, "seq", b) for b in range(n) if b not in (2, 11)] + [(0, "flush", None)]
