@@ -1,27 +1,32 @@
 // correlate_onepass.cu -- the X-engine step in one pass over the raw bytes
-// (used for 257..768 inputs): the nibble split (paper Sec. II-A) fused into
-// the Hermitian correlation (Sec. IV-C-1, Eq. 1), with no decoded planes in
-// HBM.
+// with single CTAs over 128-input block pairs: the nibble split (paper Sec.
+// II-A) fused into the Hermitian correlation (Sec. IV-C-1, Eq. 1), with no
+// decoded planes in HBM.
 //
 // A separate decode writes two plane bytes per input byte to HBM and the
 // correlation reads them back.  Converting in shared memory instead takes the
 // converter warps' time: each 128 x 128 block pair converts two raw tiles per
-// 512 MMA cycles, about what eight converter warps manage, so this kernel runs
-// at about half the MMA rate -- ahead of the two passes while the decode is a
-// large share of the step (up to 768 inputs), behind them above.  Here each CTA (one per SM, cta_group::1)
-// takes upper-triangle tile pairs (I <= J) of 128-input blocks of a channel,
-// channel-major and round-robin over the CTAs, so the CTAs at work at any time
-// share one or two channels' raw bytes in L2.  Per stage of 64 samples the
-// producer TMA-loads the raw bytes of blocks I and J (only I on the diagonal)
-// with a 128-byte swizzle -- the canonical MN-major layout of an 8-bit tcgen05
-// operand -- into a raw ring; converter warps split each byte at its own
-// offset into the Im and Re planes of a plane stage and sum each input's
-// nibbles.  Per 32-sample K step the MMA thread issues
-//     D[:, 0:256]   = A_im x [B_im | B_re]^T   (N = 256; B_re 8 KB after B_im)
+// 1024 MMA cycles (per 128-sample stage), so this kernel runs
+// at about 60% of the MMA rate -- ahead of the two passes while the decode is a
+// large share of the step; the library runs it for N > 256 where ceil(N / 128)
+// is odd (there the 2-CTA kernel over 256-input block pairs pads N the most).
+// Each CTA (one per SM, cta_group::1) takes upper-triangle tile pairs (I <= J)
+// of 128-input blocks of a channel, channel-major and round-robin over the
+// CTAs, so the CTAs at work at any time share one or two channels' raw bytes in
+// L2.  Per stage of kOKc samples the producer TMA-loads the raw bytes of block
+// J (the A operand: TMEM lanes are inputs j) and block I (B: columns are inputs
+// i; only one tile on the diagonal) with a 128-byte swizzle -- the canonical
+// MN-major layout of an 8-bit tcgen05 operand -- into a raw ring; converter
+// warps split each byte at its own offset into the Im and Re planes of a plane
+// stage and sum each input's nibbles.  Per 32-sample K step the MMA thread
+// issues
+//     D[:, 0:256]   = A_im x [B_im | B_re]^T   (N = 256; B_re after B_im)
 //     D[:, 0:128]  += A_re x B_re^T            (N = 128)  -> sum(p_i p_j + q_i q_j)
-//     D[:, 128:256]+= (-A_re) x B_im^T         (N = 128)  -> sum(q_i p_j - p_i q_j)
+//     D[:, 128:256]+= (-A_re) x B_im^T         (N = 128)  -> sum(q_j p_i - p_j q_i)
 // into one of two 256-column TMEM accumulators, so the epilogue of a tile pair
-// overlaps the MMAs of the next.
+// overlaps the MMAs of the next; the epilogue negates the Im half (with A = x_j
+// it is minus Im of x_i conj(x_j)), and per column i a warp's 32 lanes write
+// 32 consecutive pairs of the triangle's row i (one 256-byte run).
 //
 // The planes hold raw nibbles: a byte whose low four bits are u (0..15) and
 // whose high four bits are clear is the FP8 E4M3 code of u / 512.  With p, q
@@ -38,11 +43,10 @@
 //   warp 1       TMEM allocation; MMA issuer
 //   warps 2..9   converters: raw slot -> Im and Re planes of a plane stage, nibble sums
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
-//                quadrant, each half of the columns
+//                quadrant taking alternate 8-column chunks
 #include <cstring>
 
 #include "tc_ptx.cuh"
-#include "triangle_store.cuh"
 #include "xeng_internal.h"
 
 namespace xeng {
@@ -229,8 +233,9 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                         z = (kc % a.spb) * kOKc;
                     }
                     mbar_expect_tx(rawf(s), diag ? kOBox : kORawBytes);
-                    tma_load_3d(slot(s), mp, w.I * 128, f, z, rawf(s));
-                    if (!diag) tma_load_3d(slot(s) + kOBox, mp, w.J * 128, f, z, rawf(s));
+                    // A: block J (TMEM lanes = inputs j), B: block I (columns = inputs i)
+                    tma_load_3d(slot(s), mp, w.J * 128, f, z, rawf(s));
+                    if (!diag) tma_load_3d(slot(s) + kOBox, mp, w.I * 128, f, z, rawf(s));
                     ++issued;
                     if (++s == kORaws) {
                         s = 0;
@@ -429,8 +434,8 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
     } else {
         // ---------------- epilogue ----------------
         const int q = warp & 3;                          // TMEM lane quadrant this warp may access
-        constexpr int kCols = 128 / (kOEpiWarps / 4);     // columns per epilogue warp
-        const int half = (warp - kOEpiWarp0) >> 2;       // columns kCols half .. of the tile
+        constexpr int kPerQuad = kOEpiWarps / 4;         // warps of a quadrant: alternate 8-column chunks
+        const int half = (warp - kOEpiWarp0) >> 2;       // this warp's first chunk
         const int et = (warp - kOEpiWarp0) * 32 + lane;
         const int row = q * 32 + lane;                   // TMEM lane: row within the tile
         const int N = a.N;                               // <= 4096: triangle offsets within a channel fit in int
@@ -447,37 +452,62 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
             if (bar_any(2, kOEpiWarps * 32, !ok)) break;
             fence_after();
             const bool diag = w.I == w.J;
-            const int i_warp = w.I * 128 + q * 32;  // first row of the warp
-            const int i = i_warp + lane;
-            const int2 *scol = sums + par * 256 + (diag ? 0 : 128);
-            if (i_warp < N) {
-                const bool row_ok = i < N;
+            const int j_warp = w.J * 128 + q * 32;  // the warp's first input j (TMEM lanes: block J)
+            const int j = j_warp + lane;
+            const int2 *scol = sums + par * 256 + (diag ? 0 : 128);  // inputs i of the columns (block I)
+            if (j_warp < N) {
+                const bool lane_ok = j < N;
                 const int2 pq = sums[par * 256 + row];
-                const int si = pq.x + pq.y, di = pq.x - pq.y;
-                const int row_base = i * N - i * (i - 1) / 2 - i;  // pair (i, j) at row_base + j
+                const int sj = pq.x + pq.y, dj = pq.x - pq.y;
                 int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)w.fl * nb2;
                 const uint32_t tb = taddr + 256u * ab;
-                for (int c = kCols * half; c < kCols * half + kCols; c += 8) {
-                    const int j0 = w.J * 128 + c;
-                    // warp-uniform skips: chunks past the last input or below every row's diagonal
-                    if (j0 >= N) break;
-                    if (j0 + 7 < i_warp) continue;
+                const int ibase = w.I * 128;
+                for (int c = 8 * half; c < 128; c += 8 * kPerQuad) {
+                    const int i0 = ibase + c;
+                    // warp-uniform: columns past the last input or past every lane's diagonal
+                    if (i0 >= N || i0 > j_warp + 31) break;
                     uint32_t vre[8], vim[8];
                     tmem_ld8(tb + c, vre);
                     tmem_ld8(tb + 128u + c, vim);
                     tmem_ld_wait();
-                    if (!row_ok) continue;
                     #pragma unroll
                     for (int e = 0; e < 8; e++) {  // corrected values in place of the accumulator words
-                        const int2 pj = scol[c + e];  // the same for every lane: a broadcast
-                        // accumulators hold integer sums / 2^18: x 2^18 is exact
+                        const int2 pi = scol[c + e];  // the same for every lane: a broadcast
+                        // accumulators hold integer sums / 2^18 (x 2^18 is exact); with A = x_j
+                        // the Im half holds minus Im of x_i conj(x_j)
                         vre[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vre[e])) -
-                                            8 * (si + pj.x + pj.y) + n128);
-                        vim[e] = (uint32_t)(__float2int_rn(262144.0f * __uint_as_float(vim[e])) +
-                                            8 * (di - (pj.x - pj.y)));
+                                            8 * (sj + pi.x + pi.y) + n128);
+                        vim[e] = (uint32_t)(8 * ((pi.x - pi.y) - dj) -
+                                            __float2int_rn(262144.0f * __uint_as_float(vim[e])));
                     }
-                    if (a.accumulate) put8<true>(out + row_base + j0, i - j0, N - j0, vre, vim);
-                    else put8<false>(out + row_base + j0, i - j0, N - j0, vre, vim);
+                    // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle;
+                    // row i + 1 starts N - i - 1 pairs after row i: per column, one 256-byte
+                    // run of the warp's 32 consecutive inputs j
+                    const int off0 = i0 * N - i0 * (i0 - 1) / 2 - i0 + j;
+                    if (a.accumulate) {
+                        int2 o[8];
+                        int off = off0;
+                        #pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            if (lane_ok && i0 + e <= j && i0 + e < N) o[e] = __ldcs(out + off);
+                            off += N - (i0 + e) - 1;
+                        }
+                        off = off0;
+                        #pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            if (lane_ok && i0 + e <= j && i0 + e < N)
+                                __stcs(out + off, make_int2(o[e].x + (int)vre[e], o[e].y + (int)vim[e]));
+                            off += N - (i0 + e) - 1;
+                        }
+                    } else {
+                        int off = off0;
+                        #pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            if (lane_ok && i0 + e <= j && i0 + e < N)
+                                __stcs(out + off, make_int2((int)vre[e], (int)vim[e]));
+                            off += N - (i0 + e) - 1;
+                        }
+                    }
                 }
             }
             // the accumulator is read: hand it back; every epilogue thread is done
