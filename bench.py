@@ -56,7 +56,7 @@ DRAM_BYTES_PER_CHANNEL = {
 # The library's choice between its two single-pass kernels above 256 inputs, at
 # its default build parameters: measured cost of one block pair (tens of us per
 # 1024 channels x 8192 samples) times the upper-triangle block pairs.
-PAIR_COST, ONEPASS_COST, FUSED_MAX_N = 112, 36, 3584
+PAIR_COST, ONEPASS_COST, FUSED_MAX_N = 118, 36, 3584
 
 
 def use_pair_kernel(N):

@@ -16,16 +16,17 @@ namespace xeng {
 // Above 256 inputs the single pass runs either the 2-CTA pair kernel over
 // 256-input block pairs (correlate_pair.cu) or single CTAs over 128-input block
 // pairs (correlate_onepass.cu), whichever costs less by the measured time of
-// one block pair (GB300, 1024 channels x 8192 samples: 1.09-1.18 ms per 256 x
-// 256 pair, 0.36-0.39 ms per 128 x 128 pair, in units of 10 us).  The pair
+// one block pair (GB300, 1024 channels x 8192 samples: 1.09-1.20 ms per 256 x
+// 256 pair, 0.35-0.44 ms per 128 x 128 pair, in units of 10 us).  The pair
 // kernel does a quarter of the MMAs per block in a quarter of the items, but
-// pads N to 256: it wins unless ceil(N / 128) is odd (one pass / pair, ms: N =
-// 384 2.35 / 3.22; 512 3.66 / 3.26; 640 5.41 / 6.75; 768 7.50 / 6.75; 896
-// 10.59 / 11.05; 1024 13.06 / 11.09; 1152 16.39 / 16.68; 1408 23.98 / 23.58;
-// 1664 33.37 / 32.98: the ratio of the two costs must lie between 3.0 and
-// 3.14).  A cost of 0 forces that kernel.
+// pads N to 256: it wins unless ceil(N / 128) is odd, and the one pass's cost
+// per pair grows above about 1900 inputs (one pass / pair, ms: N = 384 2.35 /
+// 3.22; 512 3.66 / 3.26; 640 5.26 / 6.75; 768 7.50 / 6.75; 896 9.79 / 11.05;
+// 1024 13.06 / 11.09; 1152 15.98 / 16.96; 1408 23.15 / 23.90; 1664 32.13 /
+// 33.70; 1920 51.88 / 42.12; 2176 67.87 / 53.46: the ratio of the two costs
+// must lie between 3.25 and 3.33).  A cost of 0 forces that kernel.
 #ifndef XENG_PAIR_COST
-#define XENG_PAIR_COST 112
+#define XENG_PAIR_COST 118
 #endif
 #ifndef XENG_ONEPASS_COST
 #define XENG_ONEPASS_COST 36
