@@ -230,13 +230,15 @@ def run_reference(args, rank, world):
 
 def batch_launches(recipes):
     """Kernel launches of one batched run, as the library plans them: one
-    single-pass launch per 32,768 samples of each job a single-pass kernel
-    takes, and for the rest the TMA decode (N % 16 == 0 above FUSED_MAX_N),
-    the thread-per-row decode (other N), the nibble-sums pass (with the TMA
-    decode) and one listed tensor-core launch."""
+    persistent launch over every block pair of the jobs the 2-CTA pair kernel
+    takes (up to 32,768 samples), one single-pass launch per 32,768 samples of
+    each other job a single-pass kernel takes, and for the rest the TMA decode
+    (N % 16 == 0 above FUSED_MAX_N), the thread-per-row decode (other N), the
+    nibble-sums pass (with the TMA decode) and one listed tensor-core launch."""
     single = [r for r in recipes if r.N % 16 == 0 and r.N <= FUSED_MAX_N]
+    listed = [r for r in single if r.N > 256 and use_pair_kernel(r.N) and r.T <= 32768]
     rest = [r for r in recipes if r not in single]
-    n = sum(-(-r.T // 32768) for r in single)
+    n = (1 if listed else 0) + sum(-(-r.T // 32768) for r in single if r not in listed)
     tma = any(r.N % 16 == 0 for r in rest)
     if rest:
         n += (2 if tma else 0) + (1 if any(r.N % 16 for r in rest) else 0) + 1
@@ -311,9 +313,10 @@ def batched_record(args, steps, warmup, local_rank):
             "config": {"workload": "batched", "description": WORKLOADS["batched"][1], "n_jobs": len(recipes),
                        "input_gb": sum(r.nbytes for r in recipes) / 1e9, "useful_ops": ops,
                        "l2": "inputs (%.1f GB) larger than L2; no flush" % (sum(r.nbytes for r in recipes) / 1e9)},
-            "step_call": "xeng_batch_run (CUDA graph: each job a single-pass kernel takes (N % 16 == 0) in "
-                         "single-pass launches of up to 32,768 samples; the other jobs decoded to planes, then one "
-                         "persistent listed tensor-core launch)",
+            "step_call": "xeng_batch_run (CUDA graph: one persistent 2-CTA pair-kernel launch over the block pairs "
+                         "of every job it takes; single-pass launches for the other jobs with N % 16 == 0 (N <= 256: "
+                         "on a side branch); the rest decoded to planes, then one persistent listed tensor-core "
+                         "launch)",
             "gpu_launches": batch_launches(recipes) * steps,
             "autotune": {"opts": opts.as_dict(), "tuned_ms": tuned_ms, "from_cache": rc == 1, "fixed": rc == 2,
                          "tune_s": tune_s},

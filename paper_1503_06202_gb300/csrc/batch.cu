@@ -23,9 +23,12 @@
 //
 // Jobs a single-pass kernel takes (N a multiple of 16 up to the build's bound,
 // block 16-byte aligned: the kernel a handle would run for that N) skip the
-// planes: they run after the planned launches, one single-pass launch per
-// 32,768 samples of each, in the same graph -- no decode traffic, and no host
-// call, checks or launch gap between jobs.  The environment variable
+// planes and run in the same graph -- no decode traffic, and no host call,
+// checks or launch gap between jobs.  Those of the 2-CTA pair kernel with at
+// most 32,768 samples share one persistent launch over all their block pairs
+// (jobs longest first, so the round-robin over the clusters stays balanced and
+// no job leaves the GPU half idle at its end); the others get single-pass
+// launches of up to 32,768 samples each.  The environment variable
 // XENG_FUSED_KERNEL (read at creation) forces a kernel for them as for a
 // handle; "none" sends every job through the planes.
 #include <algorithm>
@@ -65,6 +68,11 @@ struct xeng_batch_s {
     int n_sjobs = 0;
     int64_t sum_entries = 0;
     std::vector<std::pair<int, int>> single;  // (job, single-pass kernel) in job order
+    std::vector<char> listed;                   // per job: in the pair kernel's listed launch
+    PairJob *d_pjobs = nullptr;                 // that launch's jobs and their maps
+    CUtensorMap *d_pmaps = nullptr;
+    int n_pjobs = 0;
+    int64_t p_items = 0;
     SmallScratch small;                         // the N <= 256 kernel's scratch, if a job takes it
     int grid = 0;
     int64_t n_items = 0;
@@ -127,6 +135,8 @@ void free_batch(xeng_batch_s *b)
     cudaFree(b->sums);
     cudaFree(b->d_sjobs);
     small_scratch_free(&b->small);
+    cudaFree(b->d_pjobs);
+    cudaFree(b->d_pmaps);
     cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     cudaGetLastError();
@@ -140,7 +150,7 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     auto run_single = [&](bool small, cudaStream_t st) {
         for (const auto &jk : b->single) {
-            if ((jk.second == kSingleSmall) != small) continue;
+            if ((jk.second == kSingleSmall) != small || b->listed[jk.first]) continue;
             const xeng_job_t &jb = b->jobs[jk.first];
             for (int64_t t0 = 0; t0 < jb.n_samples && e == cudaSuccess; t0 += kFusedMaxSamples) {
                 const int64_t nt = std::min<int64_t>(kFusedMaxSamples, jb.n_samples - t0);
@@ -159,6 +169,10 @@ cudaError_t enqueue_run(xeng_batch_s *b, cudaStream_t s)
         run_single(true, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
     }
+    // the longest work first: the pair kernel's persistent launch, whose tail the
+    // planes jobs and the side branch fill
+    if (e == cudaSuccess && b->n_pjobs > 0)
+        e = launch_correlate_pair_listed(b->d_pjobs, b->n_pjobs, b->p_items, b->d_err, b->num_sms, s);
     for (auto &z : b->zero_outs)
         if (e == cudaSuccess) e = cudaMemsetAsync(z.first, 0, z.second, s);
     if (e == cudaSuccess && b->n_djobs > 0)
@@ -214,12 +228,49 @@ int plan(xeng_batch_s *b)
     std::vector<int64_t> off(n), n_pad(n), t_pad(n), poff(n, -1), soff(n, -1);
     std::vector<char> single(n, 0);
     const int force = single_pass_force_from_env();
+    b->listed.assign(n, 0);
+    std::vector<int> pj;  // the pair kernel's listed jobs
     for (int j = 0; j < n; j++) {
         const int k = single_pass_kernel(b->jobs[j].block, b->jobs[j].n_inputs, force, true);
         if (k) {
             single[j] = 1;
             b->single.push_back({j, k});
+            if (k == kSinglePair && b->jobs[j].n_samples <= kFusedMaxSamples) {
+                b->listed[j] = 1;
+                pj.push_back(j);
+            }
         }
+    }
+    if (!pj.empty()) {
+        // longest jobs (most stages) first; each job's items after the previous job's
+        std::stable_sort(pj.begin(), pj.end(), [&](int x, int y) { return b->jobs[x].n_samples > b->jobs[y].n_samples; });
+        std::vector<CUtensorMap> pmaps(pj.size());
+        std::vector<PairJob> pjobs(pj.size());
+        const int stage = single_pass_stage(kSinglePair);
+        int64_t item0 = 0;
+        for (size_t k = 0; k < pj.size(); k++) {
+            const xeng_job_t &jb = b->jobs[pj[k]];
+            if (encode_pair_map(&pmaps[k], jb.block, jb.n_samples, jb.n_freq, jb.n_inputs) != cudaSuccess)
+                return XENG_ERR_CUDA;
+            const int32_t nt2 = (jb.n_inputs + 255) / 256;
+            PairJob &p = pjobs[k];
+            p.map = nullptr;  // set once the maps are in device memory
+            p.acc = jb.out;
+            p.N = jb.n_inputs;
+            p.nt = (int32_t)jb.n_samples;
+            p.n_k = (int32_t)((jb.n_samples + stage - 1) / stage);
+            p.nt2 = nt2;
+            p.pairs_per_ch = nt2 * (nt2 + 1) / 2;
+            p.item0 = (int32_t)item0;
+            item0 += (int64_t)jb.n_freq * p.pairs_per_ch;
+            if (item0 > 2147483647LL) return XENG_ERR_RANGE;
+        }
+        cudaError_t e0 = upload(&b->d_pmaps, pmaps);
+        for (size_t k = 0; k < pj.size(); k++) pjobs[k].map = b->d_pmaps + k;
+        if (e0 == cudaSuccess) e0 = upload(&b->d_pjobs, pjobs);
+        if (e0 != cudaSuccess) return status_of(e0);
+        b->n_pjobs = (int)pj.size();
+        b->p_items = item0;
     }
     int64_t total = 0, ptotal = 0, stotal = 0;
     for (int j = 0; j < n; j++) {

@@ -125,20 +125,39 @@ struct PairArgs {
     int *err;
     const CUtensorMap *maps;  // null: raw_map over one block; else a map per block of spb stages,
     int32_t spb;              // the launch's samples running through the blocks in order
+    const PairJob *jobs;      // listed launches: the jobs (items job after job), else unused
+    int32_t n_jobs;
 };
 
 struct PairItem {
     int fl, I2, J2;
+    int job;  // listed launches
 };
 
-// Item `it`: channel-major, the channel's block pairs I2 <= J2 row by row.
+// Item `it`: channel-major, the channel's block pairs I2 <= J2 row by row; in a
+// listed launch first the job whose items hold `it` (the last with item0 <= it).
+template <bool kListed>
 __device__ __forceinline__ PairItem pair_item(const PairArgs &a, int it)
 {
     PairItem w;
-    w.fl = it / a.pairs_per_ch;
-    int r = it - w.fl * a.pairs_per_ch, i = 0;
-    while (r >= a.nt2 - i) {
-        r -= a.nt2 - i;
+    int local = it, ppc = a.pairs_per_ch, nt2 = a.nt2;
+    w.job = 0;
+    if (kListed) {
+        int lo = 0, hi = a.n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.jobs[mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        w.job = lo;
+        local = it - a.jobs[lo].item0;
+        ppc = a.jobs[lo].pairs_per_ch;
+        nt2 = a.jobs[lo].nt2;
+    }
+    w.fl = local / ppc;
+    int r = local - w.fl * ppc, i = 0;
+    while (r >= nt2 - i) {
+        r -= nt2 - i;
         ++i;
     }
     w.I2 = i;
@@ -146,6 +165,7 @@ __device__ __forceinline__ PairItem pair_item(const PairArgs &a, int it)
     return w;
 }
 
+template <bool kListed>
 __global__ void __launch_bounds__(kPThreads, 1)
 correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArgs a)
 {
@@ -219,18 +239,22 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
             uint32_t ph = 0;
             bool ok = true;
             for (int it = it_begin; ok && it < a.n_items; it += it_step) {
-                const PairItem w = pair_item(a, it);
-                const int f = a.f0 + w.fl;
+                const PairItem w = pair_item<kListed>(a, it);
+                const int f = kListed ? w.fl : a.f0 + w.fl;
+                const int nk = kListed ? a.jobs[w.job].n_k : n_k;
                 const bool diag = w.I2 == w.J2;
                 const int xa = w.J2 * 256 + (int)rank * 128, xb = w.I2 * 256 + (int)rank * 128;
-                for (int kc = 0; kc < n_k; kc++) {
+                for (int kc = 0; kc < nk; kc++) {
                     if (!mbar_try_wait(rawe(s), ph ^ 1u) && !mbar_wait(rawe(s), ph ^ 1u, err, kDevTimeoutProducer)) {
                         ok = false;
                         break;
                     }
                     const CUtensorMap *mp = &raw_map;
                     int z = (int)(a.t0 + (int64_t)kc * kPKc);
-                    if (a.maps) {  // blocks of spb stages, each with its own map
+                    if (kListed) {  // the job's own map
+                        mp = a.jobs[w.job].map;
+                        z = kc * kPKc;
+                    } else if (a.maps) {  // blocks of spb stages, each with its own map
                         mp = a.maps + kc / a.spb;
                         z = (kc % a.spb) * kPKc;
                     }
@@ -261,12 +285,13 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
             bool ok = true;
             const uint32_t d_re = tmem, d_im = tmem + 256u;
             for (int it = it_begin; ok && it < a.n_items; it += it_step) {
-                const PairItem w = pair_item(a, it);
+                const PairItem w = pair_item<kListed>(a, it);
                 const bool diag = w.I2 == w.J2;
+                const int nk = kListed ? a.jobs[w.job].n_k : n_k;
                 if (!mbar_wait(acce, (uses & 1u) ^ 1u, err, kDevTimeoutMma)) break;
                 ++uses;
                 fence_after();
-                for (int kc = 0; kc < n_k; kc++) {
+                for (int kc = 0; kc < nk; kc++) {
                     if (!mbar_try_wait(full(s), ph) && !mbar_wait_cluster(full(s), ph, err, kDevTimeoutMma)) {
                         ok = false;
                         break;
@@ -319,9 +344,11 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
         int rs = 0, ps = 0, local = 0;
         uint32_t rph = 0, pph = 0;
         for (int it = it_begin; it < a.n_items; it += it_step, ++local) {
-            const PairItem w = pair_item(a, it);
+            const PairItem w = pair_item<kListed>(a, it);
             const bool diag = w.I2 == w.J2;
             const bool active = g == 0 || !diag;  // the diagonal has the A tile only (B = A)
+            const int nk = kListed ? a.jobs[w.job].n_k : n_k;
+            const int nt_w = kListed ? a.jobs[w.job].nt : nt;  // samples of the item's launch
             bool ok = true;
             uint32_t pb[4] = {0, 0, 0, 0}, qb[4] = {0, 0, 0, 0};
             uint32_t P16[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Q16[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -335,13 +362,13 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                     pb[k] = qb[k] = 0;
                 }
             };
-            for (int kc = 0; kc < n_k; kc++) {
+            for (int kc = 0; kc < nk; kc++) {
                 ok = mbar_wait_backoff(rawf(rs), rph, err, kDevTimeoutProducer, XENG_CONV_SLEEP_NS);
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
                     break;
                 }
-                const int rows_left = nt - kc * kPKc;  // samples of this stage inside the launch (may exceed kPKc)
+                const int rows_left = nt_w - kc * kPKc;  // samples of this stage inside the launch (may exceed kPKc)
                 const uint8_t *src = sgen + (slot(rs) - sbase) + roff;
                 uint4 x[kPChunks];
                 #pragma unroll
@@ -462,11 +489,13 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
         const uint32_t acce_leader = mapa_rank(acce, 0);
         uint32_t uses = 0;
         int local = 0;
-        const int N = a.N;                 // <= 4096: triangle offsets within a channel fit in int
-        const int n128 = 128 * (int)a.nt;  // 64 n from each of the two products
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
         for (int it = it_begin; it < a.n_items; it += it_step, ++local) {
-            const PairItem w = pair_item(a, it);
+            const PairItem w = pair_item<kListed>(a, it);
+            const int N = kListed ? a.jobs[w.job].N : a.N;  // <= 4096: triangle offsets within a channel fit in int
+            const int n128 = 128 * (kListed ? a.jobs[w.job].nt : (int)a.nt);  // 64 n from each of the two products
+            int32_t *const acc = kListed ? a.jobs[w.job].acc : a.acc;
+            const bool accumulate = kListed ? false : a.accumulate != 0;
             const int par = local & 1;
             bool ok = mbar_wait_backoff(accf, uses & 1u, err, kDevTimeoutEpilogue, 128);
             ok = ok && mbar_wait_cluster(sums_full(par), (uint32_t)((local >> 1) & 1), err, kDevTimeoutEpilogue);
@@ -477,7 +506,7 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
             const int j_warp = w.J2 * 256 + (int)rank * 128 + q * 32;  // the warp's first input j
             const int j = j_warp + lane;
             const bool lane_ok = j < N;
-            int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)w.fl * ((int64_t)N * (N + 1) / 2);
+            int2 *out = reinterpret_cast<int2 *>(acc) + (int64_t)w.fl * ((int64_t)N * (N + 1) / 2);
             const int2 *sp = sums + par * 384;
             const int2 pq = sp[row];  // this lane's input j (A rows of this CTA)
             const int sj = pq.x + pq.y, dj = pq.x - pq.y;
@@ -507,7 +536,7 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                         pe[e] = out + (i * N - i * (i - 1) / 2 - i) + j;
                         oke[e] = lane_ok && i <= j && i < N;
                     }
-                    if (a.accumulate) {
+                    if (accumulate) {
                         int2 o[8];
                         #pragma unroll
                         for (int e = 0; e < 8; e++)
@@ -591,7 +620,8 @@ cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t
         cudaError_t e0 = encode_pair_map(&map, block, T_block, F, N);
         if (e0 != cudaSuccess) return e0;
     }
-    cudaError_t e = cudaFuncSetAttribute(correlate_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(correlate_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
     if (e != cudaSuccess) return e;
     PairArgs a;
     a.t0 = t0;
@@ -621,7 +651,41 @@ cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, correlate_pair_kernel, map, a);
+    a.jobs = nullptr;
+    a.n_jobs = 0;
+    return cudaLaunchKernelEx(&cfg, correlate_pair_kernel<false>, map, a);
+}
+
+cudaError_t launch_correlate_pair_listed(const PairJob *jobs, int32_t n_jobs, int64_t n_items, int *err, int num_sms,
+                                         cudaStream_t s)
+{
+    if (n_jobs <= 0 || n_items <= 0) return cudaSuccess;
+    if (!jobs || num_sms < 2 || n_items > 2147483647LL) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaFuncSetAttribute(correlate_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+    if (e != cudaSuccess) return e;
+    CUtensorMap unused;
+    memset(&unused, 0, sizeof unused);  // not read: every item takes its job's map
+    PairArgs a;
+    memset(&a, 0, sizeof a);
+    a.n_items = (int32_t)n_items;
+    a.err = err;
+    a.jobs = jobs;
+    a.n_jobs = n_jobs;
+    const int64_t clusters = n_items < num_sms / 2 ? n_items : num_sms / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    cfg.blockDim = dim3(kPThreads, 1, 1);
+    cfg.dynamicSmemBytes = kPSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, correlate_pair_kernel<true>, unused, a);
 }
 
 }  // namespace xeng

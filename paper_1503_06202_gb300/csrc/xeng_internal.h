@@ -177,6 +177,19 @@ cudaError_t launch_correlate_pair(const uint8_t *block, int64_t T_block, int64_t
                                   int32_t f0, int32_t nf, int32_t *acc, int accumulate, int *err, int num_sms,
                                   cudaStream_t s,
                                   const CUtensorMap *maps = nullptr, int32_t spb = 0);
+// One job of a listed launch of the pair kernel (a batch's jobs in one
+// persistent launch): its raw block's tensor map (encode_pair_map, in device
+// memory, 64-byte aligned), its output [F][N(N+1)/2][2] (stored) and sizes: nt
+// <= kFusedMaxSamples samples in n_k stages, nt2 256-input blocks and
+// pairs_per_ch upper-triangle block pairs per channel, its items item0 ..
+// item0 + F * pairs_per_ch - 1 of the launch (jobs in increasing item0).
+struct PairJob {
+    const CUtensorMap *map;
+    int32_t *acc;
+    int32_t N, nt, n_k, nt2, pairs_per_ch, item0;
+};
+cudaError_t launch_correlate_pair_listed(const PairJob *jobs, int32_t n_jobs, int64_t n_items, int *err, int num_sms,
+                                         cudaStream_t s);
 // The raw-block tensor map launch_correlate_pair uses (3D: input, channel, sample;
 // its stage's box, 128-byte swizzle), and its stage in samples.
 cudaError_t encode_pair_map(CUtensorMap *map, const uint8_t *block, int64_t T_block, int32_t F, int32_t N);
