@@ -146,3 +146,20 @@ def test_batched_workload_64_jobs(batch_path):
         got = out[f][torch.from_numpy(oracle.triangle_index(i, j, r.N)).cuda()].cpu().numpy().astype(np.int64)
         assert np.array_equal(got, want), (r.N, r.F, r.T, f)
     b.close()
+
+
+def test_batch_listed_pair_launch_and_long_jobs():
+    """Jobs the 2-CTA pair kernel takes share one listed launch (one and several
+    channels, a ragged last 256-input block, sample counts from one stage to
+    many), jobs longer than one launch's 32,768 samples run their own launches
+    beside it: every job as alone and as the oracle."""
+    shapes = [(300, 2, 512), (1000, 1, 1264), (40000, 1, 512), (129, 3, 768), (2049, 2, 1024), (1, 1, 512)]
+    host, jobs = make_jobs(shapes, seed=44)
+    b = xe.XBatch(jobs)
+    for _ in range(2):  # a second run overwrites
+        b.run()
+    torch.cuda.synchronize()
+    for (T, F, N), blk, (d, out) in zip(shapes, host, jobs):
+        assert torch.equal(out, alone(d)), (T, F, N)
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), oracle.correlate(blk)), (T, F, N)
+    b.close()

@@ -141,6 +141,24 @@ def test_serve_admission_by_hbm_budget(serve_path):
     xe.xserve_destroy(sv)
 
 
+def test_serve_single_pass_stream_memory_and_alignment():
+    # a stream the single-pass kernels take holds no decode planes (its HBM charge
+    # is its accumulators and two dump buffers) and reads its blocks in place, so
+    # a block that is not 16-byte aligned is refused at submit (never read)
+    N, F = 256, 2
+    rc, sv = xe.xserve_create(max_blocks=4, max_streams=2)
+    assert rc == xe.XENG_OK
+    rc, s = xe.xserve_open_stream(sv, N, F, BS, BS * 4)
+    assert rc == xe.XENG_OK
+    rc, st = xe.xserve_stats(sv)
+    assert st["used_bytes"] == 3 * F * N * (N + 1) // 2 * 8
+    buf = torch.zeros(BS * F * N + 16, dtype=torch.uint8, device="cuda")
+    assert xe.xserve_submit(sv, s, buf[8:8 + BS * F * N]) == xe.XENG_ERR_ARG
+    rc, st = xe.xserve_stats(sv)
+    assert st["backlog_blocks"] == 0
+    xe.xserve_destroy(sv)
+
+
 def test_serve_compute_budget_and_bad_args():
     rc, sv = xe.xserve_create(compute_budget_tops=10.0, max_blocks=4)
     assert rc == xe.XENG_OK
