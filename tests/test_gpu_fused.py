@@ -228,3 +228,17 @@ def test_single_pass_host_pipeline_channel_groups(N):
     assert np.array_equal(got, dout.cpu().numpy().astype(np.int64))
     pick = [0, F // 2, F - 1]
     assert np.array_equal(got[pick], oracle.correlate(np.ascontiguousarray(blk[:, pick])))
+
+
+@pytest.mark.parametrize("N", [3584, 3600])
+def test_default_engine_at_its_single_pass_bound(N):
+    # the default engine takes the single pass up to 3584 inputs (here the pair
+    # kernel) and decodes to planes above: both exact against the oracle on a
+    # few sampled channels, and the same bits as the single-pass engine at 3600
+    rng = np.random.default_rng(N + 7)
+    T, F = 160, 2
+    blk = rng.integers(0, 256, size=(T, F, N), dtype=np.uint8)
+    got = correlate(blk)
+    assert np.array_equal(got, oracle.correlate(blk))
+    if N > 3584:
+        assert np.array_equal(correlate(blk, engine=FUSED), got)
