@@ -45,7 +45,10 @@
 // Roles per CTA (576 threads):
 //   warp 0       TMA producer: raw tiles into the raw ring
 //   warp 1       TMEM allocation (collective for the pair); MMA issuer (leader)
-//   warps 2..9   converters: raw slot -> Im and Re planes of a plane stage, nibble sums
+//   warps 2..9   converters: raw slot -> Im and Re planes of a plane stage, nibble sums;
+//                four warps a tile, all eight on the one tile of a diagonal pair
+//                (each thread half its chunks: 41.8-42.2 ms for full CHIME
+//                against 42.9 with the B tile's warps idle there)
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
 //                quadrant taking alternate 8-column chunks (so both have work on
 //                diagonal pairs, where only the columns up to a lane's input count)
@@ -347,7 +350,12 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
         for (int it = it_begin; it < a.n_items; it += it_step, ++local) {
             const PairItem w = pair_item<kListed>(a, it);
             const bool diag = w.I2 == w.J2;
-            const bool active = g == 0 || !diag;  // the diagonal has the A tile only (B = A)
+            // The diagonal has the A tile only (B = A): there both tiles' threads
+            // split it, the B tile's threads taking its second half of chunks.
+            const int nch = diag ? kPChunks / 2 : kPChunks;  // chunks of this thread
+            const int kofs = diag ? g * (kPChunks / 2) : 0;  // its first chunk
+            const uint32_t roff_w = diag ? (uint32_t)(v * 16 + 2048 * kofs) : roff;
+            const uint32_t poff_w = diag ? (uint32_t)(v * 16 + 2048 * kofs) : poff;
             const int nk = kListed ? a.jobs[w.job].n_k : n_k;
             const int nt_w = kListed ? a.jobs[w.job].nt : nt;  // samples of the item's launch
             bool ok = true;
@@ -370,12 +378,12 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                     break;
                 }
                 const int rows_left = nt_w - kc * kPKc;  // samples of this stage inside the launch (may exceed kPKc)
-                const uint8_t *src = sgen + (slot(rs) - sbase) + roff;
+                const uint8_t *src = sgen + (slot(rs) - sbase) + roff_w;
                 uint4 x[kPChunks];
                 #pragma unroll
                 for (int k = 0; k < kPChunks; k++) {
-                    x[k] = active ? *reinterpret_cast<const uint4 *>(src + 2048 * k) : make_uint4(0, 0, 0, 0);
-                    if (r0 + 16 * k >= rows_left) x[k] = make_uint4(0, 0, 0, 0);  // past the launch: adds nothing
+                    x[k] = k < nch ? *reinterpret_cast<const uint4 *>(src + 2048 * k) : make_uint4(0, 0, 0, 0);
+                    if (r0 + 16 * (k + kofs) >= rows_left) x[k] = make_uint4(0, 0, 0, 0);  // past the launch: adds nothing
                 }
                 // the raw slot goes back with the plane stage, once the plane stores
                 // (which consume the loaded words) are done
@@ -389,27 +397,26 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                     ok = false;
                     break;
                 }
-                if (active) {
-                    uint8_t *dim = sgen + (plane(ps) - sbase) + poff;  // Im plane of the tile
-                    uint8_t *dre = dim + kPBox;                        // Re plane of the tile
-                    #pragma unroll
-                    for (int k = 0; k < kPChunks; k++) {
-                        uint4 re, im;
-                        re.x = (x[k].x >> 4) & 0x0F0F0F0Fu;
-                        re.y = (x[k].y >> 4) & 0x0F0F0F0Fu;
-                        re.z = (x[k].z >> 4) & 0x0F0F0F0Fu;
-                        re.w = (x[k].w >> 4) & 0x0F0F0F0Fu;
-                        im.x = x[k].x & 0x0F0F0F0Fu;
-                        im.y = x[k].y & 0x0F0F0F0Fu;
-                        im.z = x[k].z & 0x0F0F0F0Fu;
-                        im.w = x[k].w & 0x0F0F0F0Fu;
-                        *reinterpret_cast<uint4 *>(dre + 2048 * k) = re;
-                        *reinterpret_cast<uint4 *>(dim + 2048 * k) = im;
-                        pb[0] += re.x; pb[1] += re.y; pb[2] += re.z; pb[3] += re.w;
-                        qb[0] += im.x; qb[1] += im.y; qb[2] += im.z; qb[3] += im.w;
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the MMAs
+                uint8_t *dim = sgen + (plane(ps) - sbase) + poff_w;  // Im plane of the tile
+                uint8_t *dre = dim + kPBox;                          // Re plane of the tile
+                #pragma unroll
+                for (int k = 0; k < kPChunks; k++) {
+                    if (k >= nch) break;
+                    uint4 re, im;
+                    re.x = (x[k].x >> 4) & 0x0F0F0F0Fu;
+                    re.y = (x[k].y >> 4) & 0x0F0F0F0Fu;
+                    re.z = (x[k].z >> 4) & 0x0F0F0F0Fu;
+                    re.w = (x[k].w >> 4) & 0x0F0F0F0Fu;
+                    im.x = x[k].x & 0x0F0F0F0Fu;
+                    im.y = x[k].y & 0x0F0F0F0Fu;
+                    im.z = x[k].z & 0x0F0F0F0Fu;
+                    im.w = x[k].w & 0x0F0F0F0Fu;
+                    *reinterpret_cast<uint4 *>(dre + 2048 * k) = re;
+                    *reinterpret_cast<uint4 *>(dim + 2048 * k) = im;
+                    pb[0] += re.x; pb[1] += re.y; pb[2] += re.z; pb[3] += re.w;
+                    qb[0] += im.x; qb[1] += im.y; qb[2] += im.z; qb[3] += im.w;
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // planes visible to the MMAs
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive_cluster(full(ps) + full_leader);
@@ -452,13 +459,21 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
                 const int k = v;
                 ok = mbar_wait_cluster(sums_empty(par), (uint32_t)((local >> 1) & 1) ^ 1u, err, kDevTimeoutProducer);
                 if (__all_sync(0xffffffffu, ok)) {
-                    const int tg = active ? g : 0;  // on the diagonal the B sums are the A sums
+                    const int tg = diag ? 0 : g;  // on the diagonal the B sums are the A sums
                     int P = 0, Q = 0;
                     #pragma unroll
                     for (int q4 = 0; q4 < 4; q4++) {
                         const int2 p2 = scratch[(tg * 4 + q4) * 128 + k];
                         P += p2.x;
                         Q += p2.y;
+                    }
+                    if (diag) {  // the A tile's other chunks, summed by the B tile's threads
+                        #pragma unroll
+                        for (int q4 = 0; q4 < 4; q4++) {
+                            const int2 p2 = scratch[(4 + q4) * 128 + k];
+                            P += p2.x;
+                            Q += p2.y;
+                        }
                     }
                     int2 *sp = sums + par * 384;
                     if (g == 0) {
