@@ -46,7 +46,7 @@ METRIC = "Correlation TOPS (8 ops per complex MAC, bit-exact int32 visibilities)
 # channels.  Keyed by (kernel, N, T); re-take (or remove) an entry whenever its
 # kernel changes.
 DRAM_BYTES_PER_CHANNEL = {
-    ("correlate_pair", 2048, 8192): (301.481984e6 + 217.341184e6) / 16,  # 256-input block pairs, 16-channel slice
+    ("correlate_pair", 2048, 8192): (300.792576e6 + 217.08416e6) / 16,  # 256-input block pairs, 16-channel slice
     ("correlate_tc", 2048, 8192): (607.22048e6 + 240.377344e6) / 16,   # planes engine, 16-channel slice
     ("correlate_small", 256, 32768): (821.3591e6 + 19.01209e6) / 64,  # N <= 256 kernel, 64-channel slice
     ("correlate_onepass", 640, 8192): (677.037e6 + 184.3619e6) / 128,  # one pass, 128-channel slice
