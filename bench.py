@@ -49,7 +49,7 @@ DRAM_BYTES_PER_CHANNEL = {
     ("correlate_pair", 2048, 8192): (300.792576e6 + 217.08416e6) / 16,  # 256-input block pairs, 16-channel slice
     ("correlate_tc", 2048, 8192): (607.22048e6 + 240.377344e6) / 16,   # planes engine, 16-channel slice
     ("correlate_small", 256, 32768): (821.3591e6 + 19.01209e6) / 64,  # N <= 256 kernel, 64-channel slice
-    ("correlate_onepass", 640, 8192): (677.037e6 + 184.3619e6) / 128,  # one pass, 128-channel slice
+    ("correlate_onepass", 640, 8192): (676.018944e6 + 184.502016e6) / 128,  # one pass, 128-channel slice
 }
 
 

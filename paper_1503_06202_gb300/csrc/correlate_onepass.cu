@@ -148,6 +148,10 @@ __device__ __forceinline__ OnepassItem onepass_item(const OnepassArgs &a, int it
     return w;
 }
 
+// kAdd: the launch adds to the triangle (a later piece of an integration)
+// instead of storing it; a separate instantiation, so the storing epilogue
+// keeps two chunks' TMEM words in registers without spilling.
+template <bool kAdd>
 __global__ void __launch_bounds__(kOThreads, 1)
 correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const OnepassArgs a)
 {
@@ -462,14 +466,12 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                 int2 *out = reinterpret_cast<int2 *>(a.acc) + (int64_t)w.fl * nb2;
                 const uint32_t tb = taddr + 256u * ab;
                 const int ibase = w.I * 128;
-                for (int c = 8 * half; c < 128; c += 8 * kPerQuad) {
+                // Corrects the chunk of columns c..c+7 held in (vre, vim) in place and stores
+                // or adds it: pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's
+                // triangle and row i + 1 starts N - i - 1 pairs after row i, so per column
+                // the warp's 32 consecutive inputs j are one 256-byte run.
+                auto put_chunk = [&](const int c, uint32_t (&vre)[8], uint32_t (&vim)[8]) {
                     const int i0 = ibase + c;
-                    // warp-uniform: columns past the last input or past every lane's diagonal
-                    if (i0 >= N || i0 > j_warp + 31) break;
-                    uint32_t vre[8], vim[8];
-                    tmem_ld8(tb + c, vre);
-                    tmem_ld8(tb + 128u + c, vim);
-                    tmem_ld_wait();
                     #pragma unroll
                     for (int e = 0; e < 8; e++) {  // corrected values in place of the accumulator words
                         const int2 pi = scol[c + e];  // the same for every lane: a broadcast
@@ -480,33 +482,70 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                         vim[e] = (uint32_t)(8 * ((pi.x - pi.y) - dj) -
                                             __float2int_rn(262144.0f * __uint_as_float(vim[e])));
                     }
-                    // pair (i, j) sits at i*N - i*(i-1)/2 + (j - i) in the channel's triangle;
-                    // row i + 1 starts N - i - 1 pairs after row i: per column, one 256-byte
-                    // run of the warp's 32 consecutive inputs j
                     const int off0 = i0 * N - i0 * (i0 - 1) / 2 - i0 + j;
-                    if (a.accumulate) {
+                    const int last = min(j - i0, N - 1 - i0);  // elements e <= last are pairs of the triangle
+                    if (kAdd) {
                         int2 o[8];
                         int off = off0;
                         #pragma unroll
                         for (int e = 0; e < 8; e++) {
-                            if (lane_ok && i0 + e <= j && i0 + e < N) o[e] = __ldcs(out + off);
+                            if (lane_ok && e <= last) o[e] = __ldcs(out + off);
                             off += N - (i0 + e) - 1;
                         }
                         off = off0;
                         #pragma unroll
                         for (int e = 0; e < 8; e++) {
-                            if (lane_ok && i0 + e <= j && i0 + e < N)
-                                __stcs(out + off, make_int2(o[e].x + (int)vre[e], o[e].y + (int)vim[e]));
+                            if (lane_ok && e <= last) __stcs(out + off, make_int2(o[e].x + (int)vre[e], o[e].y + (int)vim[e]));
                             off += N - (i0 + e) - 1;
                         }
                     } else {
                         int off = off0;
                         #pragma unroll
                         for (int e = 0; e < 8; e++) {
-                            if (lane_ok && i0 + e <= j && i0 + e < N)
-                                __stcs(out + off, make_int2((int)vre[e], (int)vim[e]));
+                            if (lane_ok && e <= last) __stcs(out + off, make_int2((int)vre[e], (int)vim[e]));
                             off += N - (i0 + e) - 1;
                         }
+                    }
+                };
+                // warp-uniform: columns inside the channel and up to some lane's diagonal
+                auto chunk_ok = [&](const int c) { return c < 128 && ibase + c < N && ibase + c <= j_warp + 31; };
+                constexpr int kStep = 8 * kPerQuad;
+                if (kAdd) {  // adding to the triangle: one chunk at a time
+                    for (int c = 8 * half; chunk_ok(c); c += kStep) {
+                        uint32_t vre[8], vim[8];
+                        tmem_ld8(tb + c, vre);
+                        tmem_ld8(tb + 128u + c, vim);
+                        tmem_ld_wait();
+                        put_chunk(c, vre, vim);
+                    }
+                } else {
+                    // two register sets: the next chunk's TMEM loads run under this chunk's stores
+                    uint32_t ra[8], ia[8], rb[8], ib[8];
+                    int c = 8 * half;
+                    if (chunk_ok(c)) {
+                        tmem_ld8(tb + c, ra);
+                        tmem_ld8(tb + 128u + c, ia);
+                    }
+                    tmem_ld_wait();
+                    while (chunk_ok(c)) {
+                        const int c1 = c + kStep;
+                        const bool ok1 = chunk_ok(c1);
+                        if (ok1) {
+                            tmem_ld8(tb + c1, rb);
+                            tmem_ld8(tb + 128u + c1, ib);
+                        }
+                        put_chunk(c, ra, ia);
+                        tmem_ld_wait();
+                        if (!ok1) break;
+                        const int c2 = c1 + kStep;
+                        const bool ok2 = chunk_ok(c2);
+                        if (ok2) {
+                            tmem_ld8(tb + c2, ra);
+                            tmem_ld8(tb + 128u + c2, ia);
+                        }
+                        put_chunk(c1, rb, ib);
+                        tmem_ld_wait();
+                        c = c2;
                     }
                 }
             }
@@ -580,8 +619,8 @@ cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int6
         cudaError_t e0 = encode_onepass_map(&map, block, T_block, F, N);
         if (e0 != cudaSuccess) return e0;
     }
-    cudaError_t e =
-        cudaFuncSetAttribute(correlate_onepass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOSmem);
+    auto kernel = accumulate ? correlate_onepass_kernel<true> : correlate_onepass_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOSmem);
     if (e != cudaSuccess) return e;
     OnepassArgs a;
     a.t0 = t0;
@@ -599,7 +638,7 @@ cudaError_t launch_correlate_onepass(const uint8_t *block, int64_t T_block, int6
     a.maps = maps;
     a.spb = spb;
     const int grid = n_items < num_sms ? (int)n_items : num_sms;
-    correlate_onepass_kernel<<<grid, kOThreads, kOSmem, s>>>(map, a);
+    kernel<<<grid, kOThreads, kOSmem, s>>>(map, a);
     return cudaGetLastError();
 }
 
