@@ -51,7 +51,8 @@
 //                against 42.9 with the B tile's warps idle there)
 //   warps 10..17 epilogue: TMEM -> packed int32 triangle, two warps per TMEM lane
 //                quadrant taking alternate 8-column chunks (so both have work on
-//                diagonal pairs, where only the columns up to a lane's input count)
+//                diagonal pairs, where only the columns up to a lane's input count),
+//                each loading its next chunk from TMEM under the current one's stores
 #include <cstring>
 
 #include "tc_ptx.cuh"
