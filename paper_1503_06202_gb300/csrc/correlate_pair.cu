@@ -81,7 +81,9 @@ constexpr int kPConvWarp0 = 2, kPConvWarps = 8;
 // Epilogue warps: a multiple of four (each TMEM lane quadrant gets the same
 // number, which split its 256 columns in interleaved 8-column chunks).  Measured
 // on GB300, full CHIME: 8 warps 41.7 ms; 12 or 16 (fewer registers a thread,
-// some spilled) 44.5; 4 (116 registers, no spills) 1% slower than 8 on one box.
+// some spilled) 44.5; 4 (116 registers, no spills) 1% slower than 8 on one box;
+// with the chunk-ahead epilogue, 4 (123 registers) 41.58-42.32 against
+// 41.55-41.72 for 8 on one box.
 // Each quadrant's columns as two halves instead: 42.8.
 #ifndef XENG_PAIR_EPI_WARPS
 #define XENG_PAIR_EPI_WARPS 8
