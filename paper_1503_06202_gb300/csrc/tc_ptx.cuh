@@ -202,6 +202,10 @@ __device__ __forceinline__ void mma_f8_cg2(uint32_t d, uint64_t a, uint64_t b, u
         ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Completion of the pair's MMAs issued so far, signalled on the mbarrier at the
+// same offset in each CTA of the pair named by `mask` (bit r: cluster rank r).
+// The multicast here is the commit's arrival to several CTAs' barriers; no data
+// moves (there is no multicast load anywhere in the library).
 __device__ __forceinline__ void mma_commit_cg2(uint32_t bar, uint16_t mask)
 {
     asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
