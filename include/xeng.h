@@ -214,7 +214,7 @@ XENG_API int xeng_set_delays(xeng_t h, const int32_t *delays);
 /*
  * Beamforming (Sec. IV-C-3).  The telescope cannot point physically; a beam is
  * formed digitally by phase-shifting the inputs and summing them, so that
- * signals from one region of the sky add in phase, and is written out at the
+ * signals from a chosen sky direction add in phase, and is written out at the
  * full sample cadence.  For every sample t, channel f and beam b:
  *     y_b(t, f) = sum_i w_{f,b,i} x_i(t, f),   w = w_re + i w_im, int8 parts,
  * exact in int32 (|y| <= 2 * 128 * 8 * N < 2^31).

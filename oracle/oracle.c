@@ -295,7 +295,7 @@ int oracle_correlate_shifted(const uint8_t *in, int64_t T, int32_t F, int32_t N,
 
 /*
  * oracle_beamform: discrete beamforming (Sec. IV-C-3: the data of all inputs
- * are phase-shifted and summed, which points a beam at one region of the sky;
+ * are phase-shifted and summed, which points a beam at a chosen sky direction;
  * the beam is written out at the full sample cadence).  With Gaussian-integer
  * weights w_{f,b,i} = w_re + i w_im, for every sample t, channel f, beam b:
  *

@@ -1,6 +1,6 @@
 // beamform.cu -- discrete beamforming on the tensor cores (paper Sec. IV-C-3:
 // the data of all inputs are phase-shifted and summed, so that signals from
-// one region of the sky add in phase; the beam is written out at the full
+// a chosen sky direction add in phase; the beam is written out at the full
 // sample cadence).
 //
 // For every sample t, channel f and beam b
