@@ -278,7 +278,7 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
                     }
                     fence_after();
                     const uint32_t st = plane(s);
-                    // A: block I (Im plane, Re 8 KB on); B: block J, or I on the diagonal
+                    // A: block J (Im plane, Re kOBox on); B: block I, or J itself on the diagonal
                     const uint64_t da_im = odesc(st), da_re = odesc(st + kOBox);
                     const uint64_t db_im = diag ? da_im : odesc(st + 2 * kOBox);
                     const uint64_t db_re = diag ? da_re : odesc(st + 3 * kOBox);
@@ -316,7 +316,7 @@ correlate_onepass_kernel(const __grid_constant__ CUtensorMap raw_map, const Onep
         const int g = u / kOCT, v = u % kOCT;
         const int r0 = v >> 3, lc = (v & 7) ^ (r0 & 7);
         const uint32_t roff = (uint32_t)(g * kOBox + v * 16);      // in a raw slot (+ 16 kOCT k)
-        const uint32_t poff = (uint32_t)(2 * g * kOBox + v * 16);  // Im plane of the tile (+ 16 kOCT k; Re 8 KB on)
+        const uint32_t poff = (uint32_t)(2 * g * kOBox + v * 16);  // Im plane of the tile (+ 16 kOCT k; Re kOBox on)
         const int nt = (int)a.nt;                                  // <= kFusedMaxSamples
         int rs = 0, ps = 0, local = 0;
         uint32_t rph = 0, pph = 0;

@@ -349,7 +349,7 @@ correlate_pair_kernel(const __grid_constant__ CUtensorMap raw_map, const PairArg
         const int r0 = v >> 3, lc = (v & 7) ^ (r0 & 7);
         const int wt = (u >> 5) & 3;                               // warp within the tile
         const uint32_t roff = (uint32_t)(g * kPBox + v * 16);      // in a raw slot (+ 2048 k)
-        const uint32_t poff = (uint32_t)(2 * g * kPBox + v * 16);  // Im plane of the tile (+ 2048 k; Re 8 KB on)
+        const uint32_t poff = (uint32_t)(2 * g * kPBox + v * 16);  // Im plane of the tile (+ 2048 k; Re kPBox on)
         const uint32_t full_leader = mapa_rank(full(0), 0) - full(0);  // offset into the leader's window
         const int nt = (int)a.nt;                                  // <= kFusedMaxSamples
         int rs = 0, ps = 0, local = 0;
