@@ -108,7 +108,7 @@ __host__ __device__ constexpr uint32_t op_idesc(int n, bool neg_a)
 
 // MN-major operand with a 128-byte swizzle: rows of 128 elements along M/N,
 // 8-row groups along K 1 KB apart (stride byte offset), version 1; the
-// leading byte offset (8 KB) is the step to the second 128-element atom of an
+// leading byte offset (kOBox) is the step to the second 128-element atom of an
 // N = 256 operand: the Re plane after the Im plane of the same block.
 __device__ __forceinline__ uint64_t odesc(uint32_t saddr)
 {

@@ -331,7 +331,7 @@ correlate_small_kernel(const __grid_constant__ CUtensorMap raw_map, const SmallA
                     fence_after();
                     const uint32_t st = plane(s);
                     if (w.row) {
-                        // A = X rows, B = X and Y columns (the Y plane 8 KB after the X
+                        // A = X rows, B = X and Y columns (the Y plane kSBox after the X
                         // plane): Re in columns 0..255, Im in 256..511
                         const uint64_t dre = sdesc(st + 2 * kSBox, kSBox), dim = sdesc(st, kSBox);
                         #pragma unroll
